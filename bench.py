@@ -1,0 +1,456 @@
+#!/usr/bin/env python
+"""Throughput of the level-of-detail hair ray tracer on one GB300.
+
+One step is one pass of the whole hot path over the full-head workload
+(100,000 strands x 64 segments, 1920x1080, 8 samples per pixel, 8 point
+lights, 4096 clusters, LoD chosen per cluster by projected width with
+epsilon_w = 2 px): Morton clusters, FP64 thick-hair fit, LoD selection,
+active-primitive compaction, LBVH build, and the trace / shade / composite
+kernel.  The metric is samples per second of that step (Msamples/s) with the
+inputs resident on the device; ms/frame is printed beside it.
+
+Also measured in the same run:
+  * e2e    - the same step through the C ABI with host buffers: the strand
+             upload from pinned memory and the image read-back inside the
+             timed region;
+  * roofline - the trace kernel (dominant) against the FP32 pipe peak, with
+             algorithmic FLOPs from a counting render (node visits, primitive
+             tests, shading evaluations times fixed per-operation costs);
+  * cpu_baseline - the FP64 brute-force CPU oracle on a bounded sample of the
+             same workload, on this host's cores;
+  * serving - a seeded Poisson request stream through hr_submit / hr_poll
+             (p50 / p99 latency, aggregate samples/s).
+
+``--impl reference`` times the CPU oracle alone (the reference arm).
+Multi-GPU (torchrun, N > 1): every rank renders its own replica of the frame
+(replicas only: the path has no exchange step); the time is the maximum over
+ranks and the value counts the samples of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Msamples/s and ms/frame, 100k strands 1080p; p50/p99 served latency at RMSE<=5e-3"
+
+# FP32 operations per counted event, read off the kernel source
+# (trace_core.cuh): an FMA counts 2, every other FP32 arithmetic, min/max or
+# compare 1, a special-function call (rsqrt, exp, asin, acos, erf) 1.
+FLOPS_PER_NODE = 50        # two child slab tests: 12 FMA + 12 min/max each, ordering
+FLOPS_PER_TEST = 41        # ray into the unit frame and the discriminant decision
+FLOPS_PER_STRAND_SHADE = 100  # light vector, angles, f_single (3 Gaussians), accumulate
+FLOPS_PER_ETH_SHADE = 250     # + albedo lookups, widened lobes, B lobe, S
+FLOPS_PER_HIT = 40            # tangent, outgoing angles, opacity, composite
+FLOPS_PER_SAMPLE = 30         # camera ray
+
+
+def sources_hash(names):
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2405_10565_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+TRACE_SOURCES = ["trace_core.cuh", "trace_frame.cu", "common.cuh"]
+
+
+# ------------------------------------------------------------------ clocks
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id=None):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                                 f".clocks_{os.getpid()}.csv")
+        self.gpu_id = gpu_id
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts))
+            except ValueError:
+                continue
+        os.remove(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        smax = max(r[1] for r in rows)
+        load = [r for r in rows if r[0] > 0.5 * smax] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[2][4 + i] == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": smax,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ workload
+
+
+def workload(name):
+    import scenegen
+    if name == "full_head":
+        return scenegen.full_head()
+    if name == "full_head_fp16":
+        return scenegen.full_head(precision=1)
+    if name == "small":
+        return scenegen.full_head(n=10000, S=32, width=480, height=270, spp=4, n_lights=8,
+                                  n_clusters=512)
+    raise ValueError(name)
+
+
+def oracle_baseline(w, seconds: float, seed: int = 11):
+    """Samples/s of the FP64 brute-force oracle on a bounded seeded sample."""
+    import oracle
+    import scenegen
+    t0 = time.time()
+    prep = oracle.prepare(w.scene, w.n_clusters, w.lod_setting, w.camera.pack(), w.eps_w)
+    t_prep = time.time() - t0
+    total = w.camera.width * w.camera.height * w.spp
+    st = scenegen.Stream(seed, 5)
+    probe = (st.u64(32) % np.uint64(total)).astype(np.int64)
+    cores = os.cpu_count() or 1
+    t0 = time.time()
+    oracle.render_samples(prep, w.camera.pack(), w.lights, probe, w.spp, w.k_depth, w.sample_seed,
+                          threads=cores)
+    per = (time.time() - t0) / probe.shape[0]
+    m = int(max(cores, min(65536, seconds / max(per, 1e-9))))
+    sids = (st.u64(m) % np.uint64(total)).astype(np.int64)
+    t0 = time.time()
+    oracle.render_samples(prep, w.camera.pack(), w.lights, sids, w.spp, w.k_depth, w.sample_seed,
+                          threads=cores)
+    dt = time.time() - t0
+    return {"value": m / dt / 1e6, "unit": "Msamples/s", "cores": cores, "kind": "oracle",
+            "sample": f"{m} seeded samples of the {total}-sample frame, brute force over "
+                      f"{prep.rows.shape[0]} active primitives (FP64); setup {t_prep:.1f}s untimed",
+            "seconds": dt}
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, on this host's cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    import scenegen
+    w = workload(args.workload)
+    prep = oracle.prepare(w.scene, w.n_clusters, w.lod_setting, w.camera.pack(), w.eps_w)
+    total = w.camera.width * w.camera.height * w.spp
+    cores = os.cpu_count() or 1
+    m = args.ref_samples
+    st = scenegen.Stream(13, 5)
+    times = []
+    for i in range(args.warmup + args.steps):
+        sids = (st.u64(m) % np.uint64(total)).astype(np.int64)
+        t0 = time.time()
+        oracle.render_samples(prep, w.camera.pack(), w.lights, sids, w.spp, w.k_depth,
+                              w.sample_seed, threads=cores)
+        if i >= args.warmup:
+            times.append(time.time() - t0)
+    dt = sum(times)
+    value = m * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Msamples/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(w, args),
+            "cpu_baseline": {"value": value, "unit": "Msamples/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{m} seeded samples per step of the {total}-sample frame"},
+            "e2e": {"value": value, "unit": "Msamples/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def config_of(w, args):
+    return {"workload": w.name, "strands": w.scene.n_strands, "segments": w.scene.n_segments,
+            "clusters": w.n_clusters, "width": w.camera.width, "height": w.camera.height,
+            "spp": w.spp, "lights": int(w.lights.shape[0]), "k_depth": w.k_depth,
+            "eps_w_px": w.eps_w, "precision": "fp16_tables" if w.precision else "fp32",
+            "l2": "inputs larger than L2 (no flush): vertices 104 MB, primitive records "
+                  "0.7 GB, BVH per frame",
+            "parallelism": f"replicas{args.gpus}" if args.gpus > 1 else "single"}
+
+
+# ------------------------------------------------------------------ serving
+
+
+def run_serving(hr, ctx, torch, dev, n_requests: int, seed: int = 2):
+    """Seeded Poisson request stream (three assets of 10k/50k/100k strands x 64
+    segments, resolutions 256^2 / 720p / 1080p, 1-8 spp, LoD budget 0-4) through
+    the continuous-batching serving loop; latency = completion - arrival."""
+    import scenegen
+    assets = []
+    for i, n in enumerate((10000, 50000, 100000)):
+        wl = scenegen.full_head(n=n, S=64, width=64, height=64, spp=1, n_clusters=max(64, n // 25),
+                                seed=10 + i)
+        a = hr.hr_asset_create(ctx, torch.from_numpy(wl.scene.verts).to(dev),
+                               torch.from_numpy(wl.scene.mat).to(dev),
+                               torch.from_numpy(wl.scene.shape).to(dev))
+        hr.hr_build_clusters(ctx, a, wl.n_clusters)
+        assets.append((a, wl))
+    reqs = scenegen.serving_stream(n_requests, seed=seed, rate_hz=1.0)
+    descs = []
+    for r in reqs:
+        a, wl = assets[r["asset"]]
+        lo, hi = wl.scene.aabb()
+        cam = scenegen.frame_camera(lo, hi, r["width"], r["height"], perspective=True, fill=0.3)
+        d = hr.render_desc(cam.pack(), wl.lights, r["spp"], 4, r["seed"], precision=1)
+        descs.append((a, d, r))
+    outs = [torch.empty((r["height"], r["width"], 3), device=dev) for _, _, r in descs]
+    # calibrate: service time of the requests one at a time
+    hr.hr_serve_start(ctx, 16, 8 << 20)
+    t0 = time.perf_counter()
+    for (a, d, r), o in zip(descs[:8], outs[:8]):
+        t = hr.hr_submit(ctx, a, d, o, 2.0, r["budget"])
+        hr.hr_poll(ctx, t, 60000)
+    per = (time.perf_counter() - t0) / 8
+    rate = 0.8 / per
+    arr = np.asarray([r["arrival_s"] for r in reqs]) / 1.0 / rate  # rescale the unit-rate stream
+    tickets = []
+    start = time.perf_counter()
+    for (a, d, r), o, at in zip(descs, outs, arr):
+        now = time.perf_counter() - start
+        if at > now:
+            time.sleep(at - now)
+        tickets.append((hr.hr_submit(ctx, a, d, o, 2.0, r["budget"]), at))
+    lat, samples, first, last = [], 0, None, 0.0
+    for (t, at), (_, _, r) in zip(tickets, descs):
+        st, res = hr.hr_poll(ctx, t, 600000)
+        if st != hr.HR_OK or res.status != hr.HR_OK:
+            raise RuntimeError(f"request failed: {st} {res.status}")
+        lat.append(res.done_ms - res.submit_ms)
+        samples += res.n_samples
+        last = max(last, res.done_ms)
+        first = res.submit_ms if first is None else min(first, res.submit_ms)
+    hr.hr_serve_stop(ctx)
+    for a, _ in assets:
+        hr.hr_asset_destroy(ctx, a)
+    lat = np.asarray(lat)
+    return {"requests": n_requests, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "msamples_per_s": samples / (last - first) / 1e3,
+            "arrival_rate_hz": rate, "precision": "fp16_tables",
+            "accuracy": "rel-RMSE <= 5e-3 vs the FP64 oracle (tests/test_serving.py)"}
+
+
+# ------------------------------------------------------------------ main arm
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="full_head")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-samples", type=int, default=512)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=256)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2405_10565_gb300 as hr
+    from paper_2405_10565_gb300.build import build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    if rank == 0:
+        build()
+    if dist:
+        dist.barrier()
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = hr.hr_create(local, 0, stream.cuda_stream)
+    w = workload(args.workload)
+    W, H, spp = w.camera.width, w.camera.height, w.spp
+    samples = W * H * spp
+    verts = torch.from_numpy(w.scene.verts).to(dev)
+    mat = torch.from_numpy(w.scene.mat).to(dev)
+    shape = torch.from_numpy(w.scene.shape).to(dev)
+    asset = hr.hr_asset_create(ctx, verts, mat, shape)
+    desc = hr.render_desc(w.camera.pack(), w.lights, spp, w.k_depth, w.sample_seed, w.precision)
+    img = torch.empty((H, W, 3), device=dev)
+
+    def step():
+        return hr.hr_render_frame(ctx, asset, w.n_clusters, w.eps_w, 0, desc, img, stats=True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    # counting render (outside the timed region): events of the algorithmic FLOP model
+    cdesc = hr.render_desc(w.camera.pack(), w.lights, spp, w.k_depth, w.sample_seed, w.precision,
+                           hr.HR_FLAG_COUNT)
+    cst = hr.hr_render(ctx, asset, cdesc, img, stats=True)
+    flops = (FLOPS_PER_NODE * cst.node_visits + FLOPS_PER_TEST * cst.prim_tests +
+             FLOPS_PER_STRAND_SHADE * cst.strand_shades + FLOPS_PER_ETH_SHADE * cst.eth_shades +
+             FLOPS_PER_HIT * cst.shaded_hits + FLOPS_PER_SAMPLE * samples)
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        if not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = hr.hr_kernel_launches(ctx)
+    render_ms = []
+    with ClockSampler(uuid) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            st = step()
+            render_ms.append(st.render_ms)
+        e1.record(stream)
+        e1.synchronize()
+        torch.cuda.synchronize(dev)
+    launches = hr.hr_kernel_launches(ctx) - launches0
+    elapsed = e0.elapsed_time(e1) / 1e3
+    if dist:
+        t = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+        dist.barrier()
+    ms_step = 1e3 * elapsed / args.steps
+    value = world * samples * args.steps / elapsed / 1e6
+    render_avg = statistics.mean(render_ms)
+    clocks = clk.summary()
+
+    # e2e: the same step through the C ABI with host buffers
+    pv = torch.from_numpy(w.scene.verts).pin_memory()
+    pm = torch.from_numpy(w.scene.mat).pin_memory()
+    ps = torch.from_numpy(w.scene.shape).pin_memory()
+    hout = torch.empty((H, W, 3), dtype=torch.float32).pin_memory()
+    h2d = pv.numel() * 4 + pm.numel() * 4 + ps.numel() * 4
+    d2h = hout.numel() * 4
+
+    def e2e_step():
+        a = hr.hr_asset_create(ctx, pv, pm, ps)
+        hr.hr_render_frame(ctx, a, w.n_clusters, w.eps_w, 0, desc, hout)
+        hr.hr_asset_destroy(ctx, a)
+
+    e2e_step()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    e2e_val = world * samples / e2e_s / 1e6
+
+    serving = None
+    if not args.no_serve and rank == 0 and world == 1:
+        serving = run_serving(hr, ctx, torch, dev, args.serve_requests)
+
+    hr.hr_asset_destroy(ctx, asset)
+    hr.hr_destroy(ctx)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    achieved = flops / (render_avg * 1e-3) / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "k_frame_full_head_traffic.json")
+    if os.path.exists(prof):
+        try:
+            pj = json.load(open(prof))
+            if pj.get("sources") == sources_hash(TRACE_SOURCES) and pj.get("workload") == w.name:
+                traffic = pj.get("dram_bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic, "kernel": "k_frame (trace/shade/composite)",
+            "kernel_ms": render_avg, "flops_per_launch": flops,
+            "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 (FMA) x "
+                          f"{sm_max:.0f} MHz",
+            "frac_at_sampled_clock": (achieved / (peak * (clocks["sm_mhz"] or sm_max) / sm_max))
+            if clocks.get("sm_mhz") else None,
+            "events": {"node_visits": cst.node_visits, "prim_tests": cst.prim_tests,
+                       "strand_shades": cst.strand_shades, "eth_shades": cst.eth_shades,
+                       "hits": cst.shaded_hits, "samples": samples}}
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = oracle_baseline(w, args.cpu_seconds)
+    line = {"metric": METRIC, "value": value, "unit": "Msamples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": config_of(w, args),
+            "frame_ms": render_avg, "active_prims": int(st.n_active_prims),
+            "eth_prims": int(st.n_eth_prims), "stack_overflows": int(st.stack_overflows),
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": "Msamples/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
+            "gpu_launches": launches, "clocks": clocks, "serving": serving}
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,297 @@
+/*
+ * hairrt.h — C ABI of the level-of-detail strand-hair ray tracer.
+ *
+ * Method: "Real-time Level-of-detail Strand-based Hair Rendering"
+ * (Huang, Zhou, Lin, Zhu, Yan, Wu; arXiv 2405.10565).  Each pixel sample is
+ * traced against a scene that mixes single hair strands and clustered
+ * elliptical thick hairs (ETHs); the K nearest hits are found with ray versus
+ * elliptic-cylinder-segment tests over a BVH, shaded with the single-fibre
+ * BCSDF (Eq. 1) or the aggregated BCSDF (Eq. 5-13) and composited front to
+ * back.  Every computation runs in this library's own CUDA kernels on one
+ * GPU; there is no CPU fallback.
+ *
+ * Conventions that hold for every call:
+ *  - Every call returns an hr_status; HR_OK is success.  On failure the
+ *    library keeps a message readable with hr_last_error(ctx).  No C++
+ *    exception crosses the boundary.
+ *  - Work is ordered on the context's CUDA stream.  Calls that return data to
+ *    the caller (host outputs, hr_stats, hr_poll) synchronise that stream
+ *    before returning; calls that write caller device buffers do not, unless
+ *    stated.
+ *  - Pointers marked "host or device" are classified with
+ *    cudaPointerGetAttributes: device (or managed) memory is written on the
+ *    stream, anything else is treated as host memory.
+ *  - Output buffers are caller-owned.  The library owns the device copies it
+ *    makes of inputs and frees them in hr_asset_destroy / hr_destroy.
+ *  - Array layouts are dense, C order, little-endian, 32-bit floats unless
+ *    stated.
+ */
+#ifndef HAIRRT_H
+#define HAIRRT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum hr_status {
+  HR_OK = 0,
+  HR_EINVAL = 1,     /* bad argument (null pointer, size out of range, bad enum) */
+  HR_ENOMEM = 2,     /* device allocation failed or the context's HBM budget is exceeded */
+  HR_ECUDA = 3,      /* a CUDA runtime call or kernel failed; see hr_last_error */
+  HR_ENOTREADY = 4,  /* hr_poll: the request has not finished yet */
+  HR_ETIMEOUT = 5,   /* hr_poll: the wait ran out; a kernel's bounded wait gave up */
+  HR_EBUSY = 6,      /* the serving queue is full */
+  HR_ESTATE = 7      /* call made in the wrong order (e.g. render before hr_build_bvh) */
+} hr_status;
+
+typedef struct hr_ctx hr_ctx;
+typedef struct hr_asset hr_asset;
+
+/* Material record per strand: 12 floats
+ *   A_R(r,g,b) A_TT(r,g,b) A_D(r,g,b) beta_R beta_TT gamma_TT
+ * the attenuations and Gaussian widths (standard deviations, radians) of the
+ * single-fibre lobes R, TT and D (Eq. 1; M_R, M_TT as G(beta, theta_h),
+ * N_TT as G(gamma_TT, phi - pi)). */
+#define HR_MAT_FLOATS 12
+
+/* A strand hair model (Section 5.1 "Given a strand-based hair model").
+ *   vertices : [n_strands][n_segments + 1][4] = x, y, z, r (r: area-equivalent
+ *              fibre radius; only the root vertex's r is read)
+ *   material : [n_strands][HR_MAT_FLOATS]
+ *   shape    : [n_strands][2] = eccentricity e in [0, 1), orientation psi
+ *              (radians) of the elliptical cross-section (a = r (1-e^2)^-1/4,
+ *              b = r (1-e^2)^1/4, major axis rotated by psi in the segment's
+ *              Duff et al. 2017 orthonormal basis)
+ * The three arrays are host or device memory. */
+typedef struct hr_hair_desc {
+  uint32_t n_strands;
+  uint32_t n_segments;
+  const float* vertices;
+  const float* material;
+  const float* shape;
+} hr_hair_desc;
+
+/* Camera.  kind 0: orthographic, 1: perspective.  right/up/fwd are an
+ * orthonormal basis; pix_scale converts image-plane offsets to pixels
+ * (perspective: pixels per unit of tangent, i.e. (height/2)/tan(fov_y/2);
+ * orthographic: pixels per world unit).  near_plane: depth below which a
+ * corner point gives an infinite LoD width.  A sample of pixel (x, y) at
+ * sub-pixel position (jx, jy) looks through image-plane offset
+ * ((x + jx - width/2) / pix_scale, (height/2 - y - jy) / pix_scale). */
+typedef struct hr_camera {
+  int32_t kind;
+  uint32_t width, height;
+  float pix_scale;
+  float eye[3];
+  float right[3];
+  float up[3];
+  float fwd[3];
+  float near_plane;
+} hr_camera;
+
+/* Light: type 0 directional (xyz = unit vector toward the light, irradiance
+ * rgb), type 1 point (xyz = position, intensity rgb, 1/d^2 falloff). */
+typedef struct hr_light {
+  float xyz[3];
+  float type;
+  float rgb[3];
+  float pad;
+} hr_light;
+
+#define HR_MAX_LIGHTS 16
+#define HR_MAX_K 8
+
+/* Precision of the scattering lookups (spec precision form): FP32
+ * tables and FP32 lobe Gaussians, or FP16 longitudinal-integral and
+ * Gaussian-lobe tables accumulated in FP32.  Traversal and intersection are
+ * FP32 in both. */
+#define HR_PREC_FP32 0
+#define HR_PREC_FP16 1
+
+/* Render flags (ablations of Section 7, "S-term" figure). */
+#define HR_FLAG_NO_S 1u          /* drop the shadowing-masking term S of Eq. 13 */
+#define HR_FLAG_SINGLE_ON_ETH 2u /* shade thick hairs with the single-fibre BCSDF */
+/* Counting build: hr_render also counts node visits, primitive tests and
+ * shading evaluations into hr_stats (slower; used to derive the algorithmic
+ * FLOP count of a frame). */
+#define HR_FLAG_COUNT 256u
+
+typedef struct hr_render_desc {
+  hr_camera camera;
+  uint32_t spp;        /* samples per pixel, >= 1 */
+  uint32_t k_depth;    /* k-buffer depth K, 1..HR_MAX_K */
+  uint64_t seed;       /* sample-position seed (SplitMix64 stream) */
+  uint32_t n_lights;   /* 1..HR_MAX_LIGHTS */
+  hr_light lights[HR_MAX_LIGHTS];
+  int32_t precision;   /* HR_PREC_FP32 or HR_PREC_FP16 */
+  uint32_t flags;      /* HR_FLAG_* */
+} hr_render_desc;
+
+typedef struct hr_stats {
+  double render_ms;      /* trace/shade/composite kernel time (CUDA events) */
+  uint64_t n_samples;
+  uint32_t n_active_prims;
+  uint32_t n_eth_prims;
+  uint32_t n_strand_prims;
+  uint32_t stack_overflows; /* samples whose traversal stack overflowed (0 expected) */
+  /* filled only with HR_FLAG_COUNT */
+  uint64_t node_visits;     /* internal BVH nodes whose two child boxes were tested */
+  uint64_t prim_tests;      /* ray / elliptic-cylinder tests */
+  uint64_t strand_shades;   /* (hit, light) evaluations of f_single */
+  uint64_t eth_shades;      /* (hit, light) evaluations of f_ours */
+  uint64_t shaded_hits;     /* hits composited */
+} hr_stats;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`.  hbm_budget: bytes the library may
+ * allocate (0 = no limit beyond the device).  cuda_stream: a cudaStream_t to
+ * order work on (NULL: the library creates its own non-blocking stream).
+ * Also bakes the scattering lookup tables (longitudinal albedo integral over
+ * (theta, beta), Gaussian lobe table) on the device. */
+hr_status hr_create(hr_ctx** ctx, int device, uint64_t hbm_budget, void* cuda_stream);
+hr_status hr_destroy(hr_ctx* ctx);
+const char* hr_last_error(hr_ctx* ctx);
+/* Bytes currently allocated by the context (assets, BVHs, tables, scratch). */
+uint64_t hr_bytes_in_use(hr_ctx* ctx);
+/* Number of this library's kernels launched on the context so far
+ * (diagnostics: lets a caller count the kernels of a timed region). */
+uint64_t hr_kernel_launches(hr_ctx* ctx);
+
+/* ---------------------------------------------------------------- assets */
+
+/* Copy a hair model to the device and precompute every strand segment's
+ * elliptic-cylinder record (Section 4 "elliptical cross-section").
+ * n_strands >= 1, 1 <= n_segments <= 4096, n_strands * n_segments < 2^31. */
+hr_status hr_asset_create(hr_ctx* ctx, const hr_hair_desc* desc, hr_asset** out);
+hr_status hr_asset_destroy(hr_ctx* ctx, hr_asset* asset);
+
+/* Build the hair hierarchy and fit the thick hairs (Section 5.1 steps 2-3).
+ * Clustering rule (deterministic Morton buckets): strands are sorted by
+ * (30-bit Morton code of the root quantised to 10 bits per axis in the roots'
+ * bounding cube, strand id); rank r joins cluster floor(r * C / N); level k
+ * splits each cluster of m members into 4^k thick hairs, rank-in-cluster i
+ * going to floor(i * 4^k / m).  Levels: 1 + max k with 4^k <= floor(N/C)/2,
+ * capped by max_levels when > 0; the strands are level n_levels.
+ * Each thick hair is fitted per cross-section in FP64 (mean centre, mean
+ * tangent, PCA, drop the axis closest to the tangent, semi-axes covering the
+ * members).  n_clusters: 1..min(N, 2^20).
+ * cluster_of_out: optional, host or device, [N] uint32 cluster per strand.
+ * order_out: optional, host or device, [N] uint32 strand ids in Morton order. */
+hr_status hr_build_clusters(hr_ctx* ctx, hr_asset* asset, uint32_t n_clusters,
+                            uint32_t max_levels, uint32_t* cluster_of_out, uint32_t* order_out);
+/* Number of clusters and thick-hair levels of the built hierarchy. */
+hr_status hr_hierarchy_info(hr_ctx* ctx, hr_asset* asset, uint32_t* n_clusters,
+                            uint32_t* n_levels, uint32_t* n_eths);
+/* Copy thick-hair data out (host or device buffers, each optional):
+ *   xsec   : [n_eths][n_segments + 1][12] floats per cross-section:
+ *            centre xyz, a, e1 xyz, b, e2 xyz, 0
+ *   counts : [n_eths] uint32 member counts
+ *   mat    : [n_eths][HR_MAT_FLOATS] mean member material */
+hr_status hr_eth_export(hr_ctx* ctx, hr_asset* asset, float* xsec, uint32_t* counts, float* mat);
+
+/* Per-cluster screen width of every thick-hair level (Section 5.2 "Hair width
+ * calculation"): the four corner points c +- a e1, c +- b e2 of every
+ * cross-section are projected to pixels, l_w is their largest pairwise
+ * distance, and the cluster's level-L width is the maximum over its level-L
+ * thick hairs (FP32, fixed operation order, no contraction; +inf when a
+ * corner is at or behind the near plane).
+ * width_out: host or device, [n_clusters][n_levels] floats. */
+hr_status hr_lod_widths(hr_ctx* ctx, hr_asset* asset, const hr_camera* camera, float* width_out);
+
+/* Select the LoD of every cluster.
+ * mode 0: initial rule (Section 5.1 step 5): the coarsest level whose width is
+ *         below eps_w_px, else the strands.
+ * mode 1: deferred rule, Eq. (14), from the levels in lod_inout.
+ * budget_bias >= 0 then coarsens every cluster: L <- max(0, L - budget_bias).
+ * lod_inout: host or device, [n_clusters] uint8 (read in mode 1, written
+ * always).  The selection is also kept in the asset for hr_build_bvh. */
+hr_status hr_select_lod(hr_ctx* ctx, hr_asset* asset, const hr_camera* camera, float eps_w_px,
+                        int mode, int budget_bias, uint8_t* lod_inout);
+
+/* Compact the active primitives of an LoD (strand segments of clusters at the
+ * strand level, level-L thick-hair segments otherwise) and build a linear BVH
+ * over them (Morton codes of primitive centroids, radix sort, Karras 2012
+ * hierarchy, bottom-up bounds).  lod: host or device [n_clusters] uint8, or
+ * NULL for the asset's current selection (or all strands when no hierarchy
+ * was built).  Global primitive id: strand segment (s, k) -> s * S + k;
+ * thick-hair segment (e, k) -> N * S + e * S + k. */
+hr_status hr_build_bvh(hr_ctx* ctx, hr_asset* asset, const uint8_t* lod);
+/* Primitive ids in BVH leaf order (host or device, [n_active] uint32) and the
+ * number of active primitives; both optional. */
+hr_status hr_bvh_export(hr_ctx* ctx, hr_asset* asset, uint32_t* leaf_ids, uint32_t* n_active);
+
+/* ---------------------------------------------------------------- rendering */
+
+/* Render a frame: per sample a camera ray (sample sid = pixel * spp + s,
+ * pixel = y * width + x, sub-pixel position from SplitMix64 outputs 2 sid and
+ * 2 sid + 1 of `seed`, top 24 bits each), the K nearest hits by (t, id),
+ * shading of each hit with f_single (strands) or f_ours (thick hairs) summed
+ * over the lights, front-to-back compositing (strand opacity 1, thick-hair
+ * opacity 1 - exp(-2 r l n_tot / (pi a b)) for view chord l), and the mean
+ * over the pixel's samples.
+ * rgb_out: host or device, [height][width][3] floats.  Requires hr_build_bvh. */
+hr_status hr_render(hr_ctx* ctx, hr_asset* asset, const hr_render_desc* desc, float* rgb_out,
+                    hr_stats* stats);
+
+/* Render only the listed samples (parity hook): radiance [m][3] and the
+ * global id of the nearest hit [m] (-1 for a miss).  sample_ids, radiance_out
+ * and hit_out are host or device. */
+hr_status hr_render_samples(hr_ctx* ctx, hr_asset* asset, const hr_render_desc* desc,
+                            const uint32_t* sample_ids, uint32_t m, float* radiance_out,
+                            int32_t* hit_out);
+
+/* Whole hot path in one call: clusters (if n_clusters > 0 and not yet built),
+ * LoD selection (mode 0, eps_w_px, budget_bias), BVH and frame. */
+hr_status hr_render_frame(hr_ctx* ctx, hr_asset* asset, uint32_t n_clusters, float eps_w_px,
+                          int budget_bias, const hr_render_desc* desc, float* rgb_out,
+                          hr_stats* stats);
+
+/* ---------------------------------------------------------------- serving */
+
+/* A render request for the serving loop: asset (already clustered), its
+ * render description, LoD budget bias and epsilon_w, and a caller-owned
+ * output buffer (host or device, [height][width][3]) that must stay valid
+ * until hr_poll reports completion. */
+typedef struct hr_request {
+  hr_asset* asset;
+  hr_render_desc desc;
+  float eps_w_px;
+  int32_t budget_bias;
+  float* rgb_out;
+} hr_request;
+
+typedef struct hr_result {
+  hr_status status;
+  double submit_ms;  /* host clock (ms since hr_create) when hr_submit was called */
+  double admit_ms;   /* when admitted (slot and memory granted) */
+  double done_ms;    /* when its last tile completed on the device */
+  uint64_t n_samples;
+} hr_result;
+
+/* Start the serving loop: up to max_slots requests resident at once, batches
+ * of at most max_batch_samples samples per persistent launch, admission while
+ * the context's bytes in use stay under its HBM budget. */
+hr_status hr_serve_start(hr_ctx* ctx, uint32_t max_slots, uint64_t max_batch_samples);
+hr_status hr_serve_stop(hr_ctx* ctx);
+/* Non-blocking submit; *ticket identifies the request.  HR_EBUSY when the
+ * queue holds too many pending requests. */
+hr_status hr_submit(hr_ctx* ctx, const hr_request* req, uint64_t* ticket);
+/* Wait up to timeout_ms (0: do not wait) for a request.  HR_OK and *result
+ * filled when done; HR_ENOTREADY if timeout_ms == 0 and not done;
+ * HR_ETIMEOUT if the wait ran out; HR_EINVAL for an unknown ticket. */
+hr_status hr_poll(hr_ctx* ctx, uint64_t ticket, int timeout_ms, hr_result* result);
+
+/* Host-side fault injection for the serving tests (no GPU fault is ever
+ * made): kind 1 fails the next admission's allocation with HR_ENOMEM; kind 2
+ * delays completion reporting of the next request by `arg` ms. */
+hr_status hr_serve_inject(hr_ctx* ctx, int kind, int64_t arg);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HAIRRT_H */

@@ -188,15 +188,15 @@ def morton30(q: np.ndarray) -> np.ndarray:
 
 
 def quantize_roots(roots: np.ndarray) -> np.ndarray:
-    """q = min(1023, floor((p - lo) * (1024 / (hi - lo)))) per axis, each
-    operation rounded to float32 in this order (lo, hi: root AABB)."""
+    """q = min(1023, floor((p - lo) * (1024 / e))) per axis with lo the root
+    AABB's low corner and e its largest extent (the bounding cube, so the grid
+    is isotropic), each operation rounded to float32 in this order."""
     p = np.asarray(roots, np.float32)
     lo = p.min(0)
     hi = p.max(0)
-    ext = (hi - lo).astype(np.float32)
-    scale = np.where(ext > 0, np.float32(1024.0) / np.where(ext > 0, ext, np.float32(1.0)),
-                     np.float32(0.0)).astype(np.float32)
-    v = ((p - lo).astype(np.float32) * scale).astype(np.float32)
+    ext = np.float32((hi - lo).astype(np.float32).max())
+    scale = np.float32(1024.0) / ext if ext > 0 else np.float32(0.0)
+    v = ((p - lo).astype(np.float32) * np.float32(scale)).astype(np.float32)
     q = np.floor(v).astype(np.int64)
     return np.clip(q, 0, 1023)
 
@@ -308,6 +308,20 @@ def strand_tangents(P: np.ndarray) -> np.ndarray:
     return d / np.linalg.norm(d, axis=-1, keepdims=True)
 
 
+def degenerate_axis(q: np.ndarray, t: np.ndarray) -> np.ndarray:
+    """READING (the two kept PCA axes have equal variance, e.g. two strands
+    whose offset runs along the tangent, so the principal axis is undefined):
+    e1 points to the member farthest from the centre in the plane normal to t
+    (first such member in rank order), or along the Duff basis vector b1 of t
+    when every member projects onto the centre."""
+    qp = q - np.outer(q @ t, t)
+    d2 = np.sum(qp * qp, 1)
+    i = int(np.argmax(d2))
+    if d2[i] > 0.0:
+        return qp[i] / np.sqrt(d2[i])
+    return duff_basis(t)[0]
+
+
 def fit_cross_section(pts: np.ndarray, tans: np.ndarray, radii: np.ndarray):
     """Ellipse of one cross-section, Section 5.1 step 3 "Cross-section fitting".
 
@@ -330,7 +344,10 @@ def fit_cross_section(pts: np.ndarray, tans: np.ndarray, radii: np.ndarray):
     dots = np.abs(V.T @ t)
     drop = int(np.argmax(dots))
     keep = [i for i in range(3) if i != drop]
-    e1 = V[:, keep[1]]  # larger eigenvalue of the two kept (ascending order)
+    if w[keep[1]] - w[keep[0]] <= 1e-9 * w[2] or w[2] <= 0.0:
+        e1 = degenerate_axis(q, t)
+    else:
+        e1 = V[:, keep[1]]  # larger eigenvalue of the two kept (ascending order)
     e1 = e1 - np.dot(e1, t) * t
     e1 = e1 / np.linalg.norm(e1)
     e2 = np.cross(t, e1)
@@ -376,7 +393,7 @@ def fit_eths(verts: np.ndarray, mat: np.ndarray, hier: Hierarchy, chunk: int = 5
         emat[ee] = (mat[mem].astype(np.float64) * mk).sum(1) / n[:, None]
         pts = P[mem]                      # [b, M, S1, 3]
         tns = T[mem]
-        rad = R[mem]                      # [b, M, S1]
+        rad = np.broadcast_to(R[mem, 0][:, :, None], R[mem].shape)  # strand radius
         m4 = mask[:, :, None, None]
         c = (pts * m4).sum(1) / n[:, None, None]
         t = (tns * m4).sum(1)
@@ -387,7 +404,21 @@ def fit_eths(verts: np.ndarray, mat: np.ndarray, hier: Hierarchy, chunk: int = 5
         dots = np.abs(np.einsum("bkij,bki->bkj", V, t))
         drop = np.argmax(dots, -1)
         keep = np.where(drop == 2, 1, 2)  # larger eigenvalue of the two kept
+        keep0 = np.where(drop == 0, 1, 0)
         e1 = np.take_along_axis(V, keep[..., None, None], -1)[..., 0]
+        wk1 = np.take_along_axis(w, keep[..., None], -1)[..., 0]
+        wk0 = np.take_along_axis(w, keep0[..., None], -1)[..., 0]
+        degen = (wk1 - wk0 <= 1e-9 * w[..., 2]) | (w[..., 2] <= 0.0)
+        if degen.any():
+            # see degenerate_axis(): farthest member in the plane normal to t
+            qp = q - np.einsum("bmki,bki->bmk", q, t)[..., None] * t[:, None]
+            d2 = np.where(mask[:, :, None], np.sum(qp * qp, -1), -1.0)
+            far = np.argmax(d2, 1)                     # [b, S1], first max in rank order
+            qf = np.take_along_axis(qp, far[:, None, :, None], 1)[:, 0]
+            df = np.take_along_axis(d2, far[:, None, :], 1)[:, 0]
+            b1 = duff_basis(t)[0]
+            alt = np.where(df[..., None] > 0.0, qf / np.sqrt(np.maximum(df, 1e-300))[..., None], b1)
+            e1 = np.where(degen[..., None], alt, e1)
         e1 = e1 - np.sum(e1 * t, -1, keepdims=True) * t
         e1 = e1 / np.linalg.norm(e1, axis=-1, keepdims=True)
         e2 = np.cross(t, e1)

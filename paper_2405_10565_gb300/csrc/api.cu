@@ -1,0 +1,561 @@
+// C ABI of the library: contexts, device memory under an HBM budget, assets,
+// and the hierarchy / LoD / BVH / render entry points.  Every computation is
+// a kernel of this library; this file only validates, allocates, copies and
+// launches.
+#include <atomic>
+#include <chrono>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "serve.h"
+
+struct hr_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  uint64_t budget = 0;
+  std::atomic<uint64_t> used{0};
+  float* im32 = nullptr;
+  __half* im16 = nullptr;
+  __half* gz16 = nullptr;
+  std::vector<hr::Scratch> scratch;
+  std::mutex err_mu;
+  std::string last_error;
+  std::recursive_mutex api_mu;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  uint32_t* d_overflow = nullptr;
+  unsigned long long* d_counters = nullptr;
+  std::chrono::steady_clock::time_point t0;
+  hr::Server* server = nullptr;
+  std::atomic<uint64_t> launches{0};
+};
+
+namespace hr {
+
+hr_status set_error(hr_ctx* ctx, hr_status st, const std::string& msg) {
+  if (ctx) {
+    std::lock_guard<std::mutex> g(ctx->err_mu);
+    ctx->last_error = msg;
+  }
+  return st;
+}
+
+cudaStream_t ctx_stream(hr_ctx* ctx) { return ctx->stream; }
+
+void note_launch(hr_ctx* ctx) { ctx->launches++; }
+
+Tables ctx_tables(hr_ctx* ctx) { return Tables{ctx->im32, ctx->im16, ctx->gz16}; }
+
+std::recursive_mutex& ctx_mutex(hr_ctx* ctx) { return ctx->api_mu; }
+
+double ctx_now_ms(hr_ctx* ctx) {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ctx->t0)
+      .count();
+}
+
+int ctx_device(hr_ctx* ctx) { return ctx->device; }
+
+Server** ctx_server_slot(hr_ctx* ctx) { return &ctx->server; }
+
+uint32_t* ctx_overflow(hr_ctx* ctx) { return ctx->d_overflow; }
+
+hr_status dalloc(hr_ctx* ctx, void** p, size_t bytes, const char* what) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (ctx->budget && ctx->used.load() + bytes > ctx->budget)
+    return set_error(ctx, HR_ENOMEM, std::string("HBM budget exceeded allocating ") + what);
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return set_error(ctx, HR_ENOMEM,
+                     std::string("cudaMalloc failed for ") + what + ": " + cudaGetErrorString(e));
+  }
+  ctx->used += bytes;
+  return HR_OK;
+}
+
+void dfree(hr_ctx* ctx, void* p, size_t bytes) {
+  if (!p) return;
+  if (bytes == 0) bytes = 16;
+  cudaFree(p);
+  ctx->used -= bytes;
+}
+
+hr_status scratch(hr_ctx* ctx, int slot, size_t bytes, void** p) {
+  if (slot < 0 || slot >= (int)ctx->scratch.size()) return set_error(ctx, HR_EINVAL, "scratch slot");
+  Scratch& s = ctx->scratch[slot];
+  if (bytes > s.bytes) {
+    if (s.p) {
+      cudaStreamSynchronize(ctx->stream);
+      dfree(ctx, s.p, s.bytes);
+      s.p = nullptr;
+      s.bytes = 0;
+    }
+    size_t want = bytes + bytes / 4 + 256;
+    HR_TRY(dalloc(ctx, &s.p, want, "scratch"));
+    s.bytes = want;
+  }
+  *p = s.p;
+  return HR_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Copy `bytes` from a host-or-device source into a device destination.
+hr_status to_device(hr_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (!bytes) return HR_OK;
+  HR_CUDA(ctx, cudaMemcpyAsync(dst, src, bytes,
+                               is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                               st));
+  return HR_OK;
+}
+
+FrameArgs frame_args(hr_ctx* ctx, hr_asset* a, const Bvh& bv, const hr_render_desc& d) {
+  FrameArgs fa{};
+  fa.nodes = bv.nodes;
+  fa.leaf_xf = bv.leaf_xf;
+  fa.leaf_aux = bv.leaf_aux;
+  fa.leaf_id = bv.leaf_id;
+  fa.mat = a->mat;
+  fa.n_prims = bv.n;
+  fa.tables = ctx_tables(ctx);
+  fa.cam = to_launch_cam(d.camera);
+  fa.lights = to_launch_lights(d);
+  fa.spp = d.spp;
+  fa.seed = d.seed;
+  fa.flags = d.flags;
+  fa.overflow = ctx->d_overflow;
+  fa.counters = ctx->d_counters;
+  fa.k = d.k_depth;
+  return fa;
+}
+
+hr_status check_desc(hr_ctx* ctx, const hr_render_desc* d) {
+  if (!d) return set_error(ctx, HR_EINVAL, "render desc is null");
+  if (d->spp < 1) return set_error(ctx, HR_EINVAL, "spp must be >= 1");
+  if (d->k_depth < 1 || d->k_depth > HR_MAX_K) return set_error(ctx, HR_EINVAL, "k_depth out of 1..8");
+  if (d->n_lights < 1 || d->n_lights > HR_MAX_LIGHTS)
+    return set_error(ctx, HR_EINVAL, "n_lights out of 1..16");
+  if (d->camera.width < 1 || d->camera.height < 1 || d->camera.width > 65536 ||
+      d->camera.height > 65536)
+    return set_error(ctx, HR_EINVAL, "image size out of range");
+  if ((uint64_t)d->camera.width * d->camera.height * d->spp >= (1ull << 40))
+    return set_error(ctx, HR_EINVAL, "too many samples");
+  if (d->camera.kind != 0 && d->camera.kind != 1) return set_error(ctx, HR_EINVAL, "camera kind");
+  if (!(d->camera.pix_scale > 0.f)) return set_error(ctx, HR_EINVAL, "pix_scale must be > 0");
+  if (d->precision != HR_PREC_FP32 && d->precision != HR_PREC_FP16)
+    return set_error(ctx, HR_EINVAL, "precision");
+  return HR_OK;
+}
+
+}  // namespace hr
+
+using namespace hr;
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+#define API_ENTER(ctx)                                                   \
+  if (!(ctx)) return HR_EINVAL;                                          \
+  std::lock_guard<std::recursive_mutex> api_lock_((ctx)->api_mu);        \
+  DeviceGuard dev_guard_((ctx)->device)
+
+}  // namespace
+
+extern "C" {
+
+hr_status hr_create(hr_ctx** out, int device, uint64_t hbm_budget, void* cuda_stream) {
+  if (!out) return HR_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+    cudaGetLastError();
+    return HR_ECUDA;
+  }
+  if (device < 0 || device >= n) return HR_EINVAL;
+  hr_ctx* ctx = new hr_ctx();
+  ctx->device = device;
+  ctx->budget = hbm_budget;
+  ctx->scratch.resize(64);
+  ctx->t0 = std::chrono::steady_clock::now();
+  DeviceGuard g(device);
+  if (cuda_stream) {
+    ctx->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return HR_ECUDA;
+    }
+    ctx->own_stream = true;
+  }
+  hr_status st = HR_OK;
+  if (cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess)
+    st = HR_ECUDA;
+  if (st == HR_OK) st = dalloc(ctx, (void**)&ctx->d_overflow, 64, "flags");
+  if (st == HR_OK) st = dalloc(ctx, (void**)&ctx->d_counters, 8 * sizeof(unsigned long long), "counters");
+  if (st == HR_OK) st = bake_tables(ctx, &ctx->im32, &ctx->im16, &ctx->gz16);
+  if (st == HR_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) st = HR_ECUDA;
+  if (st != HR_OK) {
+    hr_destroy(ctx);
+    return st;
+  }
+  *out = ctx;
+  return HR_OK;
+}
+
+hr_status hr_destroy(hr_ctx* ctx) {
+  if (!ctx) return HR_EINVAL;
+  if (ctx->server) hr_serve_stop(ctx);
+  {
+    DeviceGuard g(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (auto& s : ctx->scratch)
+      if (s.p) cudaFree(s.p);
+    if (ctx->im32) cudaFree(ctx->im32);
+    if (ctx->im16) cudaFree(ctx->im16);
+    if (ctx->gz16) cudaFree(ctx->gz16);
+    if (ctx->d_overflow) cudaFree(ctx->d_overflow);
+    if (ctx->d_counters) cudaFree(ctx->d_counters);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  }
+  delete ctx;
+  return HR_OK;
+}
+
+const char* hr_last_error(hr_ctx* ctx) {
+  if (!ctx) return "null context";
+  std::lock_guard<std::mutex> g(ctx->err_mu);
+  return ctx->last_error.c_str();
+}
+
+uint64_t hr_bytes_in_use(hr_ctx* ctx) { return ctx ? ctx->used.load() : 0; }
+
+uint64_t hr_kernel_launches(hr_ctx* ctx) { return ctx ? ctx->launches.load() : 0; }
+
+hr_status hr_asset_create(hr_ctx* ctx, const hr_hair_desc* d, hr_asset** out) {
+  API_ENTER(ctx);
+  if (!d || !out || !d->vertices || !d->material || !d->shape)
+    return set_error(ctx, HR_EINVAL, "hr_asset_create: null argument");
+  *out = nullptr;
+  if (d->n_strands < 1 || d->n_segments < 1 || d->n_segments > 4096 ||
+      (uint64_t)d->n_strands * d->n_segments >= (1ull << 31))
+    return set_error(ctx, HR_EINVAL, "hr_asset_create: sizes out of range");
+  cudaStream_t st = ctx->stream;
+  hr_asset* a = new hr_asset();
+  a->ctx = ctx;
+  a->N = d->n_strands;
+  a->S = d->n_segments;
+  const size_t nv = (size_t)a->N * (a->S + 1);
+  hr_status s = dalloc(ctx, (void**)&a->verts, nv * sizeof(float4), "vertices");
+  if (s == HR_OK) s = dalloc(ctx, (void**)&a->mat, (size_t)a->N * HR_MAT_FLOATS * 4, "materials");
+  if (s == HR_OK) s = dalloc(ctx, (void**)&a->shape, (size_t)a->N * sizeof(float2), "shape");
+  a->mat_cap = a->N;
+  if (s == HR_OK) s = to_device(ctx, a->verts, d->vertices, nv * sizeof(float4), st);
+  if (s == HR_OK) s = to_device(ctx, a->mat, d->material, (size_t)a->N * HR_MAT_FLOATS * 4, st);
+  if (s == HR_OK) s = to_device(ctx, a->shape, d->shape, (size_t)a->N * sizeof(float2), st);
+  if (s == HR_OK) s = build_strand_prims(ctx, a);
+  if (s != HR_OK) {
+    hr_asset_destroy(ctx, a);
+    return s;
+  }
+  *out = a;
+  return HR_OK;
+}
+
+hr_status hr_asset_destroy(hr_ctx* ctx, hr_asset* a) {
+  API_ENTER(ctx);
+  if (!a) return HR_EINVAL;
+  if (ctx->server) serve_forget_asset(ctx, ctx->server, a);
+  cudaStreamSynchronize(ctx->stream);
+  const size_t S1 = a->S + 1;
+  dfree(ctx, a->verts, (size_t)a->N * S1 * sizeof(float4));
+  dfree(ctx, a->mat, a->mat_cap * HR_MAT_FLOATS * 4);
+  dfree(ctx, a->shape, (size_t)a->N * sizeof(float2));
+  if (a->order) dfree(ctx, a->order, (size_t)a->N * 4);
+  if (a->cluster_of) dfree(ctx, a->cluster_of, (size_t)a->N * 4);
+  if (a->cl_first) dfree(ctx, a->cl_first, (size_t)(a->C + 1) * 4);
+  if (a->xsec) dfree(ctx, a->xsec, (size_t)a->E * S1 * 3 * sizeof(float4));
+  if (a->lod) dfree(ctx, a->lod, a->C);
+  const uint64_t P = a->n_prims_total;
+  if (a->prim_xf) dfree(ctx, a->prim_xf, P * 3 * sizeof(float4));
+  if (a->prim_box) dfree(ctx, a->prim_box, P * 2 * sizeof(float4));
+  if (a->prim_aux) dfree(ctx, a->prim_aux, P * sizeof(float4));
+  free_bvh(ctx, a->bvh);
+  delete a;
+  return HR_OK;
+}
+
+hr_status hr_build_clusters(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_levels,
+                            uint32_t* cluster_of_out, uint32_t* order_out) {
+  API_ENTER(ctx);
+  if (!a) return set_error(ctx, HR_EINVAL, "null asset");
+  if (C < 1 || C > a->N || C > (1u << 20)) return set_error(ctx, HR_EINVAL, "n_clusters out of range");
+  HR_TRY(build_hierarchy(ctx, a, C, max_levels));
+  cudaStream_t st = ctx->stream;
+  if (cluster_of_out) {
+    const bool dev = is_device_ptr(cluster_of_out);
+    HR_CUDA(ctx, cudaMemcpyAsync(cluster_of_out, a->cluster_of, (size_t)a->N * 4,
+                                 dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  }
+  if (order_out) {
+    const bool dev = is_device_ptr(order_out);
+    HR_CUDA(ctx, cudaMemcpyAsync(order_out, a->order, (size_t)a->N * 4,
+                                 dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  }
+  HR_CUDA(ctx, cudaStreamSynchronize(st));
+  return HR_OK;
+}
+
+hr_status hr_hierarchy_info(hr_ctx* ctx, hr_asset* a, uint32_t* C, uint32_t* L, uint32_t* E) {
+  API_ENTER(ctx);
+  if (!a) return set_error(ctx, HR_EINVAL, "null asset");
+  if (C) *C = a->C;
+  if (L) *L = a->n_levels;
+  if (E) *E = a->E;
+  return HR_OK;
+}
+
+hr_status hr_eth_export(hr_ctx* ctx, hr_asset* a, float* xsec, uint32_t* counts, float* mat) {
+  API_ENTER(ctx);
+  if (!a) return set_error(ctx, HR_EINVAL, "null asset");
+  if (a->E == 0) return set_error(ctx, HR_ESTATE, "no thick hairs: call hr_build_clusters");
+  cudaStream_t st = ctx->stream;
+  const size_t S1 = a->S + 1;
+  if (xsec) {
+    HR_CUDA(ctx, cudaMemcpyAsync(xsec, a->xsec, (size_t)a->E * S1 * 3 * sizeof(float4),
+                                 is_device_ptr(xsec) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  }
+  if (mat) {
+    HR_CUDA(ctx, cudaMemcpyAsync(mat, a->mat + (size_t)a->N * HR_MAT_FLOATS,
+                                 (size_t)a->E * HR_MAT_FLOATS * 4,
+                                 is_device_ptr(mat) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  }
+  if (counts) {
+    std::vector<uint32_t> first(a->C + 1), cnt(a->E);
+    HR_CUDA(ctx, cudaMemcpyAsync(first.data(), a->cl_first, (a->C + 1) * 4, cudaMemcpyDeviceToHost, st));
+    HR_CUDA(ctx, cudaStreamSynchronize(st));
+    for (uint32_t k = 0; k < a->n_levels; ++k) {
+      const uint64_t sub = 1ull << (2 * k);
+      for (uint32_t c = 0; c < a->C; ++c) {
+        const uint64_t m = first[c + 1] - first[c];
+        for (uint64_t j = 0; j < sub; ++j) {
+          const uint64_t lo = (j * m + sub - 1) / sub, hi = ((j + 1) * m + sub - 1) / sub;
+          cnt[a->eth_offset[k] + c * sub + j] = (uint32_t)(hi - lo);
+        }
+      }
+    }
+    HR_CUDA(ctx, cudaMemcpyAsync(counts, cnt.data(), (size_t)a->E * 4,
+                                 is_device_ptr(counts) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, st));
+  }
+  HR_CUDA(ctx, cudaStreamSynchronize(st));
+  return HR_OK;
+}
+
+hr_status hr_lod_widths(hr_ctx* ctx, hr_asset* a, const hr_camera* cam, float* width_out) {
+  API_ENTER(ctx);
+  if (!a || !cam || !width_out) return set_error(ctx, HR_EINVAL, "null argument");
+  if (a->n_levels == 0) return set_error(ctx, HR_ESTATE, "no thick-hair levels");
+  cudaStream_t st = ctx->stream;
+  const size_t bytes = (size_t)a->C * a->n_levels * 4;
+  if (is_device_ptr(width_out)) {
+    HR_TRY(lod_widths(ctx, a, cam, width_out, st));
+  } else {
+    float* tmp = nullptr;
+    HR_TRY(scratch(ctx, 40, bytes, (void**)&tmp));
+    HR_TRY(lod_widths(ctx, a, cam, tmp, st));
+    HR_CUDA(ctx, cudaMemcpyAsync(width_out, tmp, bytes, cudaMemcpyDeviceToHost, st));
+  }
+  HR_CUDA(ctx, cudaStreamSynchronize(st));
+  return HR_OK;
+}
+
+hr_status hr_select_lod(hr_ctx* ctx, hr_asset* a, const hr_camera* cam, float eps, int mode,
+                        int bias, uint8_t* lod_inout) {
+  API_ENTER(ctx);
+  if (!a || !cam) return set_error(ctx, HR_EINVAL, "null argument");
+  if (a->n_levels == 0) return set_error(ctx, HR_ESTATE, "no thick-hair levels: call hr_build_clusters");
+  if ((mode != 0 && mode != 1) || bias < 0) return set_error(ctx, HR_EINVAL, "mode / bias");
+  if (mode == 1 && !lod_inout) return set_error(ctx, HR_EINVAL, "deferred mode needs lod_inout");
+  cudaStream_t st = ctx->stream;
+  uint8_t* prev = nullptr;
+  if (mode == 1) {
+    HR_TRY(scratch(ctx, 41, a->C, (void**)&prev));
+    HR_TRY(to_device(ctx, prev, lod_inout, a->C, st));
+  }
+  HR_TRY(lod_select(ctx, a, cam, eps, mode, bias, prev, a->lod, st));
+  a->lod_valid = 1;
+  if (lod_inout) {
+    HR_CUDA(ctx, cudaMemcpyAsync(lod_inout, a->lod, a->C,
+                                 is_device_ptr(lod_inout) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  }
+  HR_CUDA(ctx, cudaStreamSynchronize(st));
+  return HR_OK;
+}
+
+hr_status hr_build_bvh(hr_ctx* ctx, hr_asset* a, const uint8_t* lod) {
+  API_ENTER(ctx);
+  if (!a) return set_error(ctx, HR_EINVAL, "null asset");
+  cudaStream_t st = ctx->stream;
+  const uint8_t* lod_dev = nullptr;
+  if (a->n_levels > 0) {
+    if (lod) {
+      HR_TRY(to_device(ctx, a->lod, lod, a->C, st));
+      a->lod_valid = 1;
+      lod_dev = a->lod;
+    } else if (a->lod_valid) {
+      lod_dev = a->lod;
+    }
+  }
+  HR_TRY(build_bvh(ctx, a, lod_dev, a->bvh, st));
+  HR_CUDA(ctx, cudaStreamSynchronize(st));
+  return HR_OK;
+}
+
+hr_status hr_bvh_export(hr_ctx* ctx, hr_asset* a, uint32_t* leaf_ids, uint32_t* n_active) {
+  API_ENTER(ctx);
+  if (!a) return set_error(ctx, HR_EINVAL, "null asset");
+  if (!a->bvh.valid) return set_error(ctx, HR_ESTATE, "no BVH: call hr_build_bvh");
+  if (n_active) *n_active = a->bvh.n;
+  if (leaf_ids && a->bvh.n) {
+    HR_CUDA(ctx, cudaMemcpyAsync(leaf_ids, a->bvh.leaf_id, (size_t)a->bvh.n * 4,
+                                 is_device_ptr(leaf_ids) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    HR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  return HR_OK;
+}
+
+static hr_status render_impl(hr_ctx* ctx, hr_asset* a, const hr_render_desc* desc, float* rgb_out,
+                             hr_stats* stats) {
+  if (!a || !rgb_out) return set_error(ctx, HR_EINVAL, "null argument");
+  HR_TRY(check_desc(ctx, desc));
+  if (!a->bvh.valid) return set_error(ctx, HR_ESTATE, "no BVH: call hr_build_bvh");
+  cudaStream_t st = ctx->stream;
+  const size_t bytes = (size_t)desc->camera.width * desc->camera.height * 3 * sizeof(float);
+  const bool dev_out = is_device_ptr(rgb_out);
+  float* out = rgb_out;
+  if (!dev_out) HR_TRY(scratch(ctx, 42, bytes, (void**)&out));
+  FrameArgs fa = frame_args(ctx, a, a->bvh, *desc);
+  const bool count = (desc->flags & HR_FLAG_COUNT) != 0;
+  if (stats || count) {
+    HR_CUDA(ctx, cudaMemsetAsync(ctx->d_overflow, 0, 4, st));
+    HR_CUDA(ctx, cudaMemsetAsync(ctx->d_counters, 0, 8 * sizeof(unsigned long long), st));
+  }
+  if (stats) HR_CUDA(ctx, cudaEventRecord(ctx->ev0, st));
+  HR_TRY(launch_frame(ctx, fa, desc->precision, count, out, st));
+  if (stats) HR_CUDA(ctx, cudaEventRecord(ctx->ev1, st));
+  if (!dev_out) HR_CUDA(ctx, cudaMemcpyAsync(rgb_out, out, bytes, cudaMemcpyDeviceToHost, st));
+  if (stats) {
+    uint32_t ovf = 0;
+    unsigned long long cnt[8] = {0};
+    HR_CUDA(ctx, cudaMemcpyAsync(&ovf, ctx->d_overflow, 4, cudaMemcpyDeviceToHost, st));
+    HR_CUDA(ctx, cudaMemcpyAsync(cnt, ctx->d_counters, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+    HR_CUDA(ctx, cudaStreamSynchronize(st));
+    float ms = 0.f;
+    HR_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    std::memset(stats, 0, sizeof(*stats));
+    stats->render_ms = ms;
+    stats->n_samples = (uint64_t)desc->camera.width * desc->camera.height * desc->spp;
+    stats->n_active_prims = a->bvh.n;
+    stats->n_eth_prims = a->bvh.n_eth;
+    stats->n_strand_prims = a->bvh.n - a->bvh.n_eth;
+    stats->stack_overflows = ovf;
+    stats->node_visits = cnt[0];
+    stats->prim_tests = cnt[1];
+    stats->strand_shades = cnt[2];
+    stats->eth_shades = cnt[3];
+    stats->shaded_hits = cnt[4];
+  } else if (!dev_out) {
+    HR_CUDA(ctx, cudaStreamSynchronize(st));
+  }
+  return HR_OK;
+}
+
+hr_status hr_render(hr_ctx* ctx, hr_asset* a, const hr_render_desc* desc, float* rgb_out,
+                    hr_stats* stats) {
+  API_ENTER(ctx);
+  return render_impl(ctx, a, desc, rgb_out, stats);
+}
+
+hr_status hr_render_samples(hr_ctx* ctx, hr_asset* a, const hr_render_desc* desc,
+                            const uint32_t* sample_ids, uint32_t m, float* radiance_out,
+                            int32_t* hit_out) {
+  API_ENTER(ctx);
+  if (!a || (m && (!sample_ids || !radiance_out || !hit_out)))
+    return set_error(ctx, HR_EINVAL, "null argument");
+  HR_TRY(check_desc(ctx, desc));
+  if (!a->bvh.valid) return set_error(ctx, HR_ESTATE, "no BVH: call hr_build_bvh");
+  if (m == 0) return HR_OK;
+  cudaStream_t st = ctx->stream;
+  const uint64_t total = (uint64_t)desc->camera.width * desc->camera.height * desc->spp;
+  if (total > 0xffffffffull) return set_error(ctx, HR_EINVAL, "sample ids exceed 32 bits");
+  const uint32_t* sid = sample_ids;
+  if (!is_device_ptr(sample_ids)) {
+    uint32_t* t = nullptr;
+    HR_TRY(scratch(ctx, 43, (size_t)m * 4, (void**)&t));
+    HR_CUDA(ctx, cudaMemcpyAsync(t, sample_ids, (size_t)m * 4, cudaMemcpyHostToDevice, st));
+    sid = t;
+  }
+  const bool dr = is_device_ptr(radiance_out), dh = is_device_ptr(hit_out);
+  float* rad = radiance_out;
+  int32_t* hit = hit_out;
+  if (!dr) HR_TRY(scratch(ctx, 44, (size_t)m * 12, (void**)&rad));
+  if (!dh) HR_TRY(scratch(ctx, 45, (size_t)m * 4, (void**)&hit));
+  FrameArgs fa = frame_args(ctx, a, a->bvh, *desc);
+  HR_CUDA(ctx, cudaMemsetAsync(ctx->d_overflow, 0, 4, st));
+  HR_TRY(launch_samples(ctx, fa, desc->precision, sid, m, rad, hit, st));
+  if (!dr) HR_CUDA(ctx, cudaMemcpyAsync(radiance_out, rad, (size_t)m * 12, cudaMemcpyDeviceToHost, st));
+  if (!dh) HR_CUDA(ctx, cudaMemcpyAsync(hit_out, hit, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+  HR_CUDA(ctx, cudaStreamSynchronize(st));
+  return HR_OK;
+}
+
+hr_status hr_render_frame(hr_ctx* ctx, hr_asset* a, uint32_t n_clusters, float eps_w_px,
+                          int budget_bias, const hr_render_desc* desc, float* rgb_out,
+                          hr_stats* stats) {
+  API_ENTER(ctx);
+  if (!a || !desc) return set_error(ctx, HR_EINVAL, "null argument");
+  HR_TRY(check_desc(ctx, desc));
+  cudaStream_t st = ctx->stream;
+  const uint8_t* lod_dev = nullptr;
+  if (n_clusters > 0) {
+    if (n_clusters > a->N) return set_error(ctx, HR_EINVAL, "n_clusters out of range");
+    HR_TRY(build_hierarchy(ctx, a, n_clusters, 0));
+    if (a->n_levels > 0) {
+      HR_TRY(lod_select(ctx, a, &desc->camera, eps_w_px, 0, budget_bias, nullptr, a->lod, st));
+      a->lod_valid = 1;
+      lod_dev = a->lod;
+    }
+  }
+  HR_TRY(build_bvh(ctx, a, lod_dev, a->bvh, st));
+  return render_impl(ctx, a, desc, rgb_out, stats);
+}
+
+}  // extern "C"

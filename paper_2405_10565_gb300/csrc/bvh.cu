@@ -1,0 +1,297 @@
+// Active-primitive compaction and linear BVH build.
+//
+// Compaction ("hair data reorganisation", Section 6 "Real-time performance"):
+// a cluster at the strand level contributes every segment of its member
+// strands, a cluster at level L contributes every segment of its level-L
+// thick hairs.  Per-cluster counts are scanned and each cluster's block writes
+// its global primitive ids.
+//
+// LBVH (Karras 2012, "Maximizing parallelism in the construction of BVHs,
+// octrees, and k-d trees"): 30-bit Morton codes of the primitive box
+// centroids in the scene bounds, stable radix sort of (code, id), one thread
+// per internal node finds its key range and split from the longest common
+// prefix (ties between equal codes broken by index), then bounds are
+// propagated bottom-up with one arrival counter per internal node.
+//
+// Node layout (4 x float4 = 64 bytes), children's boxes stored in the parent:
+//   n0 = (lo0.x, hi0.x, lo0.y, hi0.y)  n1 = (lo1.x, hi1.x, lo1.y, hi1.y)
+//   n2 = (lo0.z, hi0.z, lo1.z, hi1.z)  n3 = (child0, child1, -, -) as int bits
+// A child index >= 0 is an internal node, < 0 is leaf ~index.
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace hr {
+namespace {
+
+__global__ void k_cluster_counts(const uint8_t* __restrict__ lod, const uint32_t* __restrict__ cl_first,
+                                 uint32_t C, uint32_t L, uint32_t S, uint32_t* counts) {
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  const uint32_t l = min((uint32_t)lod[c], L);
+  counts[c] = (l == L) ? (cl_first[c + 1] - cl_first[c]) * S : (1u << (2 * l)) * S;
+}
+
+__global__ void k_cluster_fill(const uint8_t* __restrict__ lod, const uint32_t* __restrict__ cl_first,
+                               const uint32_t* __restrict__ order, const uint32_t* __restrict__ offs,
+                               const uint32_t* __restrict__ eth_off, uint32_t C, uint32_t L,
+                               uint32_t N, uint32_t S, uint32_t* ids) {
+  const uint32_t c = blockIdx.x;
+  const uint32_t l = min((uint32_t)lod[c], L);
+  const uint32_t base = offs[c];
+  if (l == L) {
+    const uint32_t r0 = cl_first[c], m = cl_first[c + 1] - r0;
+    for (uint32_t j = threadIdx.x; j < m * S; j += blockDim.x) {
+      const uint32_t s = order[r0 + j / S];
+      ids[base + j] = s * S + j % S;
+    }
+  } else {
+    const uint32_t sub = 1u << (2 * l);
+    const uint32_t e0 = eth_off[l] + c * sub;
+    for (uint32_t j = threadIdx.x; j < sub * S; j += blockDim.x)
+      ids[base + j] = N * S + (e0 + j / S) * S + j % S;
+  }
+}
+
+__global__ void k_iota(uint32_t* ids, uint32_t n) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) ids[i] = i;
+}
+
+__device__ __forceinline__ uint32_t spread10(uint32_t v) {
+  v &= 0x3ffu;
+  v = (v | (v << 16)) & 0x030000FFu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+__global__ void k_prim_morton(const float4* __restrict__ box, const uint32_t* __restrict__ ids,
+                              uint32_t n, float3 lo, float3 inv_ext, uint32_t* keys) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t id = ids[i];
+  const float4 l = box[2 * (size_t)id], h = box[2 * (size_t)id + 1];
+  const float cx = (0.5f * (l.x + h.x) - lo.x) * inv_ext.x;
+  const float cy = (0.5f * (l.y + h.y) - lo.y) * inv_ext.y;
+  const float cz = (0.5f * (l.z + h.z) - lo.z) * inv_ext.z;
+  const uint32_t qx = (uint32_t)min(1023.f, fmaxf(0.f, cx * 1024.f));
+  const uint32_t qy = (uint32_t)min(1023.f, fmaxf(0.f, cy * 1024.f));
+  const uint32_t qz = (uint32_t)min(1023.f, fmaxf(0.f, cz * 1024.f));
+  keys[i] = (spread10(qx) << 2) | (spread10(qy) << 1) | spread10(qz);
+}
+
+__device__ __forceinline__ int delta(const uint32_t* __restrict__ keys, int n, int i, int j) {
+  if (j < 0 || j >= n) return -1;
+  const uint32_t a = keys[i], b = keys[j];
+  if (a != b) return __clz(a ^ b);
+  return 32 + __clz((uint32_t)i ^ (uint32_t)j);
+}
+
+__global__ void k_karras(const uint32_t* __restrict__ keys, int n, int4* child,
+                         int* parent_int, int* parent_leaf) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n - 1) return;
+  const int d = (delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+  const int dmin = delta(keys, n, i, i - d);
+  int lmax = 2;
+  while (delta(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+  int l = 0;
+  for (int t = lmax >> 1; t >= 1; t >>= 1)
+    if (delta(keys, n, i, i + (l + t) * d) > dmin) l += t;
+  const int j = i + l * d;
+  const int dnode = delta(keys, n, i, j);
+  int s = 0;
+  for (int div = 2;; div <<= 1) {
+    const int t = (l + div - 1) / div;
+    if (delta(keys, n, i, i + (s + t) * d) > dnode) s += t;
+    if (t == 1) break;
+  }
+  const int gamma = i + s * d + min(d, 0);
+  const int lo = min(i, j), hi = max(i, j);
+  int c0, c1;
+  if (lo == gamma) {
+    c0 = ~gamma;
+    parent_leaf[gamma] = i;
+  } else {
+    c0 = gamma;
+    parent_int[gamma] = i;
+  }
+  if (hi == gamma + 1) {
+    c1 = ~(gamma + 1);
+    parent_leaf[gamma + 1] = i;
+  } else {
+    c1 = gamma + 1;
+    parent_int[gamma + 1] = i;
+  }
+  child[i] = make_int4(c0, c1, 0, 0);
+}
+
+// Gather leaf records in Morton order.
+__global__ void k_gather(const uint32_t* __restrict__ sorted_ids, uint32_t n,
+                         const float4* __restrict__ xf, const float4* __restrict__ aux,
+                         float4* leaf_xf, float4* leaf_aux, uint32_t* leaf_id) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t id = sorted_ids[i];
+  leaf_xf[3 * (size_t)i] = xf[3 * (size_t)id];
+  leaf_xf[3 * (size_t)i + 1] = xf[3 * (size_t)id + 1];
+  leaf_xf[3 * (size_t)i + 2] = xf[3 * (size_t)id + 2];
+  leaf_aux[i] = aux[id];
+  leaf_id[i] = id;
+}
+
+__device__ __forceinline__ void node_union(const float4* nodes, int c, float* b) {
+  // union of an internal node's two child boxes (read through L2: written by
+  // other blocks during this kernel)
+  const float4 n0 = __ldcg(nodes + 4 * c), n1 = __ldcg(nodes + 4 * c + 1),
+               n2 = __ldcg(nodes + 4 * c + 2);
+  b[0] = fminf(n0.x, n1.x);
+  b[1] = fmaxf(n0.y, n1.y);
+  b[2] = fminf(n0.z, n1.z);
+  b[3] = fmaxf(n0.w, n1.w);
+  b[4] = fminf(n2.x, n2.z);
+  b[5] = fmaxf(n2.y, n2.w);
+}
+
+__device__ __forceinline__ void leaf_box(const float4* box, const uint32_t* sorted_ids, int leaf,
+                                         float* b) {
+  const uint32_t id = sorted_ids[leaf];
+  const float4 l = box[2 * (size_t)id], h = box[2 * (size_t)id + 1];
+  b[0] = l.x; b[1] = h.x; b[2] = l.y; b[3] = h.y; b[4] = l.z; b[5] = h.z;
+}
+
+// Bottom-up bounds: a thread starts at each leaf and climbs; at every internal
+// node the first arrival stops, the second writes both child boxes.
+__global__ void k_refit(const int4* __restrict__ child, const int* __restrict__ parent_int,
+                        const int* __restrict__ parent_leaf, const float4* __restrict__ box,
+                        const uint32_t* __restrict__ sorted_ids, int n, float4* nodes,
+                        unsigned* arrivals) {
+  const int leaf = blockIdx.x * blockDim.x + threadIdx.x;
+  if (leaf >= n) return;
+  int node = parent_leaf[leaf];
+  while (node >= 0) {
+    __threadfence();
+    if (atomicAdd(&arrivals[node], 1u) == 0) return;
+    __threadfence();
+    const int4 ch = child[node];
+    float b0[6], b1[6];
+    if (ch.x < 0) leaf_box(box, sorted_ids, ~ch.x, b0); else node_union(nodes, ch.x, b0);
+    if (ch.y < 0) leaf_box(box, sorted_ids, ~ch.y, b1); else node_union(nodes, ch.y, b1);
+    float4* o = nodes + 4 * node;
+    __stcg(o, make_float4(b0[0], b0[1], b0[2], b0[3]));
+    __stcg(o + 1, make_float4(b1[0], b1[1], b1[2], b1[3]));
+    __stcg(o + 2, make_float4(b0[4], b0[5], b1[4], b1[5]));
+    __stcg(o + 3, make_float4(__int_as_float(ch.x), __int_as_float(ch.y), 0.f, 0.f));
+    node = node == 0 ? -1 : parent_int[node];
+  }
+}
+
+}  // namespace
+
+void free_bvh(hr_ctx* ctx, Bvh& bv) {
+  if (bv.cap) {
+    dfree(ctx, bv.nodes, (size_t)std::max(bv.cap, 2u) * 4 * sizeof(float4));
+    dfree(ctx, bv.leaf_xf, (size_t)bv.cap * 3 * sizeof(float4));
+    dfree(ctx, bv.leaf_aux, (size_t)bv.cap * sizeof(float4));
+    dfree(ctx, bv.leaf_id, (size_t)bv.cap * 4);
+  }
+  bv = Bvh();
+}
+
+hr_status build_bvh(hr_ctx* ctx, hr_asset* a, const uint8_t* lod_dev, Bvh& bv, cudaStream_t st) {
+  const uint32_t N = a->N, S = a->S;
+  bv.valid = 0;
+  // 1. active primitive ids
+  uint32_t n = 0;
+  uint32_t* ids = nullptr;
+  if (a->C == 0 || a->n_levels == 0 || lod_dev == nullptr) {
+    n = N * S;
+    HR_TRY(scratch(ctx, 30, (size_t)n * 4, (void**)&ids));
+    k_iota<<<(n + 255) / 256, 256, 0, st>>>(ids, n);
+    HR_LAUNCHED(ctx);
+    bv.n_eth = 0;
+  } else {
+    const uint32_t C = a->C, L = a->n_levels;
+    uint32_t* cnt = nullptr;
+    HR_TRY(scratch(ctx, 31, (size_t)(C + 1) * 4, (void**)&cnt));
+    k_cluster_counts<<<(C + 255) / 256, 256, 0, st>>>(lod_dev, a->cl_first, C, L, S, cnt);
+    HR_LAUNCHED(ctx);
+    HR_CUDA(ctx, cudaMemsetAsync(cnt + C, 0, 4, st));
+    HR_TRY(scan_u32(ctx, cnt, C + 1, st));
+    HR_CUDA(ctx, cudaMemcpyAsync(&n, cnt + C, 4, cudaMemcpyDeviceToHost, st));
+    HR_CUDA(ctx, cudaStreamSynchronize(st));
+    uint32_t* eoff = nullptr;
+    HR_TRY(scratch(ctx, 32, 16 * 4, (void**)&eoff));
+    HR_CUDA(ctx, cudaMemcpyAsync(eoff, a->eth_offset, 16 * 4, cudaMemcpyHostToDevice, st));
+    HR_TRY(scratch(ctx, 30, (size_t)std::max(n, 1u) * 4, (void**)&ids));
+    k_cluster_fill<<<C, 256, 0, st>>>(lod_dev, a->cl_first, a->order, cnt, eoff, C, L, N, S, ids);
+    HR_LAUNCHED(ctx);
+    // count thick-hair primitives for the statistics
+    std::vector<uint8_t> hl(C);
+    HR_CUDA(ctx, cudaMemcpyAsync(hl.data(), lod_dev, C, cudaMemcpyDeviceToHost, st));
+    HR_CUDA(ctx, cudaStreamSynchronize(st));
+    uint64_t ne = 0;
+    for (uint32_t c = 0; c < C; ++c)
+      if (hl[c] < L) ne += (uint64_t)(1u << (2 * hl[c])) * S;
+    bv.n_eth = (uint32_t)ne;
+  }
+  // 2. storage (grow only)
+  if (n > bv.cap) {
+    if (bv.cap) {
+      HR_CUDA(ctx, cudaStreamSynchronize(st));
+      free_bvh(ctx, bv);
+    }
+    HR_TRY(dalloc(ctx, (void**)&bv.nodes, (size_t)std::max(n, 2u) * 4 * sizeof(float4), "BVH nodes"));
+    HR_TRY(dalloc(ctx, (void**)&bv.leaf_xf, (size_t)n * 3 * sizeof(float4), "BVH leaf records"));
+    HR_TRY(dalloc(ctx, (void**)&bv.leaf_aux, (size_t)n * sizeof(float4), "BVH leaf aux"));
+    HR_TRY(dalloc(ctx, (void**)&bv.leaf_id, (size_t)n * 4, "BVH leaf ids"));
+    bv.cap = n;
+  }
+  bv.n = n;
+  if (n == 0) {
+    bv.valid = 1;
+    return HR_OK;
+  }
+  // 3. Morton codes and sort
+  uint32_t *keys, *k2, *v2;
+  HR_TRY(scratch(ctx, 33, (size_t)n * 4, (void**)&keys));
+  HR_TRY(scratch(ctx, 34, (size_t)n * 4, (void**)&k2));
+  HR_TRY(scratch(ctx, 35, (size_t)n * 4, (void**)&v2));
+  float3 lo = make_float3(a->scene_lo[0], a->scene_lo[1], a->scene_lo[2]);
+  float3 inv;
+  inv.x = a->scene_hi[0] > a->scene_lo[0] ? 1.f / (a->scene_hi[0] - a->scene_lo[0]) : 0.f;
+  inv.y = a->scene_hi[1] > a->scene_lo[1] ? 1.f / (a->scene_hi[1] - a->scene_lo[1]) : 0.f;
+  inv.z = a->scene_hi[2] > a->scene_lo[2] ? 1.f / (a->scene_hi[2] - a->scene_lo[2]) : 0.f;
+  k_prim_morton<<<(n + 255) / 256, 256, 0, st>>>(a->prim_box, ids, n, lo, inv, keys);
+  HR_LAUNCHED(ctx);
+  HR_TRY(radix_sort_pairs(ctx, keys, ids, k2, v2, n, 30, st));
+  // 4. leaves
+  k_gather<<<(n + 255) / 256, 256, 0, st>>>(ids, n, a->prim_xf, a->prim_aux, bv.leaf_xf,
+                                            bv.leaf_aux, bv.leaf_id);
+  HR_LAUNCHED(ctx);
+  if (n == 1) {
+    bv.valid = 1;
+    return HR_OK;
+  }
+  // 5. hierarchy and bounds
+  int4* child = nullptr;
+  int *par_int = nullptr, *par_leaf = nullptr;
+  unsigned* arrivals = nullptr;
+  HR_TRY(scratch(ctx, 36, (size_t)n * sizeof(int4), (void**)&child));
+  HR_TRY(scratch(ctx, 37, (size_t)n * 4, (void**)&par_int));
+  HR_TRY(scratch(ctx, 38, (size_t)n * 4, (void**)&par_leaf));
+  HR_TRY(scratch(ctx, 39, (size_t)n * 4, (void**)&arrivals));
+  HR_CUDA(ctx, cudaMemsetAsync(arrivals, 0, (size_t)n * 4, st));
+  k_karras<<<(n - 1 + 255) / 256, 256, 0, st>>>(keys, (int)n, child, par_int, par_leaf);
+  HR_LAUNCHED(ctx);
+  k_refit<<<(n + 255) / 256, 256, 0, st>>>(child, par_int, par_leaf, a->prim_box, ids, (int)n,
+                                           bv.nodes, arrivals);
+  HR_LAUNCHED(ctx);
+  bv.valid = 1;
+  return HR_OK;
+}
+
+}  // namespace hr

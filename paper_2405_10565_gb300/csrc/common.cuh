@@ -1,0 +1,203 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/hairrt.h"
+
+namespace hr {
+
+constexpr float kPi = 3.14159265358979323846f;
+constexpr double kPiD = 3.14159265358979323846;
+constexpr float kInvSqrt2Pi = 0.3989422804014327f;
+
+// Scattering lookup tables (baked once per context).
+// IM(theta, beta) = integral over theta_o in [-pi/2, pi/2] of
+// G(beta, (theta + theta_o)/2) cos^2(theta_o), theta in [0, pi/2],
+// beta in [kImBetaLo, kImBetaHi]; row-major [beta][theta].
+constexpr int kImNT = 256;
+constexpr int kImNB = 64;
+constexpr float kImBetaLo = 0.04f;
+constexpr float kImBetaHi = 0.68f;
+// Gaussian lobe table g(z) = exp(-z^2 / 2), z in [0, kGzMax].
+constexpr int kGzN = 1024;
+constexpr float kGzMax = 8.0f;
+
+struct Tables {
+  const float* im32;   // [kImNB][kImNT]
+  const __half* im16;  // [kImNB][kImNT]
+  const __half* gz16;  // [kGzN + 1]
+};
+
+// One BVH over the active primitives of an asset.
+struct Bvh {
+  uint32_t n = 0;           // active primitives (leaves)
+  uint32_t cap = 0;         // allocated leaves
+  float4* nodes = nullptr;  // [(n-1) * 4]; see trace.cu for the layout
+  float4* leaf_xf = nullptr;   // [n * 3] world -> unit-cylinder rows, leaf order
+  float4* leaf_aux = nullptr;  // [n] (material index bits, n_tot, r, a*b)
+  uint32_t* leaf_id = nullptr; // [n] global primitive id
+  uint32_t n_eth = 0;
+  int valid = 0;
+};
+
+// Device scratch that grows on demand (owned by the context).
+struct Scratch {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace hr
+
+struct hr_ctx;
+
+struct hr_asset {
+  hr_ctx* ctx = nullptr;
+  uint32_t N = 0, S = 0;
+  float4* verts = nullptr;  // [N * (S + 1)]
+  float* mat = nullptr;     // [(N + E) * 12]: strands then thick hairs
+  float2* shape = nullptr;  // [N]
+  size_t mat_cap = 0;       // rows allocated in mat
+  // hierarchy
+  uint32_t C = 0, n_levels = 0, E = 0;
+  uint32_t eth_offset[16] = {0};
+  uint32_t* order = nullptr;       // [N] strand ids by (code, id)
+  uint32_t* cluster_of = nullptr;  // [N]
+  uint32_t* cl_first = nullptr;    // [C + 1] first rank of each cluster
+  float4* xsec = nullptr;          // [E * (S+1) * 3] (c,a) (e1,b) (e2,0)
+  // all potential primitives: strand segments then thick-hair segments
+  uint32_t n_prims_total = 0;
+  float4* prim_xf = nullptr;   // [P_total * 3]
+  float4* prim_box = nullptr;  // [P_total * 2]
+  float4* prim_aux = nullptr;  // [P_total]
+  float scene_lo[3] = {0, 0, 0}, scene_hi[3] = {0, 0, 0};
+  // LoD
+  uint8_t* lod = nullptr;  // [C] current selection on the device
+  int lod_valid = 0;
+  hr::Bvh bvh;
+  size_t bytes = 0;
+};
+
+namespace hr {
+
+// ----------------------------------------------------------------- helpers
+
+uint64_t ctx_alloc_note(hr_ctx* ctx, int64_t delta);
+hr_status set_error(hr_ctx* ctx, hr_status st, const std::string& msg);
+cudaStream_t ctx_stream(hr_ctx* ctx);
+Tables ctx_tables(hr_ctx* ctx);
+// device allocation charged to the context budget
+hr_status dalloc(hr_ctx* ctx, void** p, size_t bytes, const char* what);
+void dfree(hr_ctx* ctx, void* p, size_t bytes);
+// grow-only scratch slot `slot` of the context
+hr_status scratch(hr_ctx* ctx, int slot, size_t bytes, void** p);
+
+#define HR_CUDA(ctx, call)                                                              \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return ::hr::set_error((ctx), HR_ECUDA,                                           \
+                             std::string(#call) + ": " + cudaGetErrorString(e_));       \
+  } while (0)
+
+// After every kernel launch: count it and check the launch error.
+void note_launch(hr_ctx* ctx);
+#define HR_LAUNCHED(ctx)          \
+  do {                            \
+    ::hr::note_launch(ctx);       \
+    HR_CUDA(ctx, cudaGetLastError()); \
+  } while (0)
+
+#define HR_TRY(call)                 \
+  do {                               \
+    hr_status s_ = (call);           \
+    if (s_ != HR_OK) return s_;      \
+  } while (0)
+
+// --- primitives (sort.cu)
+// exclusive scan of n uint32 values in place (device); uses scratch slots 10-12
+hr_status scan_u32(hr_ctx* ctx, uint32_t* data, uint32_t n, cudaStream_t st);
+// stable LSD radix sort of (key, value) pairs on the low `bits` key bits;
+// result in keys/vals; tmp buffers of n entries; uses scratch slots 13-15
+hr_status radix_sort_pairs(hr_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp,
+                           uint32_t* vals_tmp, uint32_t n, int bits, cudaStream_t st);
+
+// --- hierarchy.cu
+hr_status build_strand_prims(hr_ctx* ctx, hr_asset* a);
+hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_levels);
+
+// --- lod.cu
+hr_status lod_widths(hr_ctx* ctx, hr_asset* a, const hr_camera* cam, float* wcl_dev,
+                     cudaStream_t st);
+hr_status lod_select(hr_ctx* ctx, hr_asset* a, const hr_camera* cam, float eps, int mode,
+                     int bias, const uint8_t* prev_dev, uint8_t* out_dev, cudaStream_t st);
+
+// --- bvh.cu
+// Build `out` over the active primitives of LoD `lod_dev` (nullptr: all
+// strands) on stream `st`.
+hr_status build_bvh(hr_ctx* ctx, hr_asset* a, const uint8_t* lod_dev, Bvh& out, cudaStream_t st);
+void free_bvh(hr_ctx* ctx, Bvh& b);
+
+// --- tables.cu
+hr_status bake_tables(hr_ctx* ctx, float** im32, __half** im16, __half** gz16);
+
+// --- trace.cu
+struct LaunchCam {
+  int kind, W, H;
+  float pix;
+  float3 eye, right, up, fwd;
+};
+struct LaunchLights {
+  int n;
+  float4 xyzw[HR_MAX_LIGHTS];
+  float4 rgb[HR_MAX_LIGHTS];
+};
+struct FrameArgs {
+  const float4* nodes;
+  const float4* leaf_xf;
+  const float4* leaf_aux;
+  const uint32_t* leaf_id;
+  const float* mat;
+  uint32_t n_prims;
+  Tables tables;
+  LaunchCam cam;
+  LaunchLights lights;
+  uint32_t spp;
+  uint64_t seed;
+  uint32_t flags;
+  uint32_t* overflow;  // device counter of stack overflows
+  unsigned long long* counters;  // [5] node visits, prim tests, strand shades, eth shades, hits
+  uint32_t k;          // k-buffer depth (<= the kernel's KMAX)
+};
+hr_status launch_frame(hr_ctx* ctx, const FrameArgs& fa, int precision, bool count,
+                       float* rgb_dev, cudaStream_t st);
+hr_status launch_samples(hr_ctx* ctx, const FrameArgs& fa, int precision, const uint32_t* sids,
+                         uint32_t m, float* rad_dev, int32_t* hit_dev, cudaStream_t st);
+
+// Batched serving launch: a list of tiles from several requests.
+struct ServeItem {
+  FrameArgs fa;
+  float* rgb;       // device output of the request
+  uint32_t tile0;   // first tile (of the request's frame) in this item
+  uint32_t ntiles;  // tiles in this item
+};
+// items_dev[i] covers batch tiles [item_start_dev[i], item_start_dev[i+1]);
+// every item of one launch has the same k-buffer bound and precision.
+hr_status launch_serve_batch(hr_ctx* ctx, int kmax, int precision, const ServeItem* items_dev,
+                             const uint32_t* item_start_dev, uint32_t n_items,
+                             uint32_t total_tiles, uint32_t* work_counter_dev, int grid,
+                             cudaStream_t st);
+int kmax_for(uint32_t k);
+
+LaunchCam to_launch_cam(const hr_camera& c);
+LaunchLights to_launch_lights(const hr_render_desc& d);
+
+// Tile geometry of frame rendering: 16 x 8 pixels per 128-thread block.
+constexpr int kTileW = 16;
+constexpr int kTileH = 8;
+
+}  // namespace hr

@@ -1,0 +1,593 @@
+// Hair hierarchy (Section 5.1 steps 2-3) and primitive records.
+//
+//  * Strand segment records: every segment (s, k) of every strand becomes an
+//    elliptic cylinder (Section 4 "elliptical cross-section"): semi-axes
+//    a = r (1 - e^2)^-1/4, b = r (1 - e^2)^1/4 (area of the circle of radius r),
+//    major axis e1 = cos(psi) b1 + sin(psi) b2 in the Duff et al. 2017 basis of
+//    the segment direction.
+//  * Clusters: deterministic Morton buckets of the strand roots (rank r of the
+//    (code, id) order joins cluster floor(r C / N)), split 4^k ways at level k.
+//  * Thick hairs: per cross-section k, FP64 mean centre, mean unit tangent,
+//    PCA of the members' k-th points (cyclic Jacobi), the axis closest to the
+//    tangent dropped, e1 the remaining axis with the larger eigenvalue, and
+//    semi-axes covering every member (Section 5.1 step 3 "Cross-section
+//    fitting").
+//
+// A primitive record is the affine map from world space to the cylinder's
+// unit frame: rows (e1/a, -c0.e1/a), (e2/b, -c0.e2/b), (t/L, -c0.t/L); a ray
+// hits the open cylinder where u^2 + v^2 = 1 with w in [0, 1].
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace hr {
+namespace {
+
+struct d3 {
+  double x, y, z;
+};
+__device__ __forceinline__ d3 mk(double x, double y, double z) { return {x, y, z}; }
+__device__ __forceinline__ d3 operator+(d3 a, d3 b) { return mk(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ d3 operator-(d3 a, d3 b) { return mk(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ d3 operator*(d3 a, double s) { return mk(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ double dot(d3 a, d3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ d3 cross(d3 a, d3 b) {
+  return mk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ d3 normalize(d3 a) { return a * (1.0 / sqrt(dot(a, a))); }
+__device__ __forceinline__ d3 ld3(float4 v) { return mk(v.x, v.y, v.z); }
+
+// World -> unit elliptic cylinder rows and a conservative AABB of the
+// segment c0 -> c1 with semi-axis a along e1 and b along e2 = t x e1.
+__device__ void write_prim(float4* xf, float4* box, d3 c0, d3 c1, d3 e1, double a, double b) {
+  d3 ax = c1 - c0;
+  const double L = sqrt(dot(ax, ax));
+  if (!(L > 0.0)) {
+    xf[0] = xf[1] = xf[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+    box[0] = make_float4((float)c0.x, (float)c0.y, (float)c0.z, 0.f);
+    box[1] = box[0];
+    return;
+  }
+  const d3 t = ax * (1.0 / L);
+  const d3 e2 = cross(t, e1);
+  const d3 r0 = e1 * (1.0 / a), r1 = e2 * (1.0 / b), r2 = t * (1.0 / L);
+  xf[0] = make_float4((float)r0.x, (float)r0.y, (float)r0.z, (float)(-dot(c0, e1) / a));
+  xf[1] = make_float4((float)r1.x, (float)r1.y, (float)r1.z, (float)(-dot(c0, e2) / b));
+  xf[2] = make_float4((float)r2.x, (float)r2.y, (float)r2.z, (float)(-dot(c0, t) / L));
+  const double hx = sqrt(a * a * e1.x * e1.x + b * b * e2.x * e2.x);
+  const double hy = sqrt(a * a * e1.y * e1.y + b * b * e2.y * e2.y);
+  const double hz = sqrt(a * a * e1.z * e1.z + b * b * e2.z * e2.z);
+  box[0] = make_float4(__double2float_rd(fmin(c0.x, c1.x) - hx), __double2float_rd(fmin(c0.y, c1.y) - hy),
+                       __double2float_rd(fmin(c0.z, c1.z) - hz), 0.f);
+  box[1] = make_float4(__double2float_ru(fmax(c0.x, c1.x) + hx), __double2float_ru(fmax(c0.y, c1.y) + hy),
+                       __double2float_ru(fmax(c0.z, c1.z) + hz), 0.f);
+}
+
+// Orthonormal basis around a unit vector (Duff, Burgess, Christensen, Hery,
+// Kensler, Liani, Villemin 2017, "Building an orthonormal basis, revisited").
+__device__ void duff_basis(d3 n, d3* b1, d3* b2) {
+  const double sign = copysign(1.0, n.z);
+  const double a = -1.0 / (sign + n.z);
+  const double b = n.x * n.y * a;
+  *b1 = mk(1.0 + sign * n.x * n.x * a, sign * b, -sign * n.x);
+  *b2 = mk(b, sign + n.y * n.y * a, -n.y);
+}
+
+__global__ void k_strand_prims(const float4* __restrict__ verts, const float2* __restrict__ shape,
+                               uint32_t N, uint32_t S, float4* xf, float4* box, float4* aux) {
+  const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (uint64_t)N * S) return;
+  const uint32_t s = (uint32_t)(idx / S), k = (uint32_t)(idx % S);
+  const float4* P = verts + (size_t)s * (S + 1);
+  const d3 p0 = ld3(P[k]), p1 = ld3(P[k + 1]);
+  const double r = P[0].w;
+  const float2 sh = shape[s];
+  const double e = sh.x, psi = sh.y;
+  d3 ax = p1 - p0;
+  const double L = sqrt(dot(ax, ax));
+  d3 e1 = mk(1, 0, 0);
+  if (L > 0.0) {
+    d3 b1, b2;
+    duff_basis(ax * (1.0 / L), &b1, &b2);
+    e1 = b1 * cos(psi) + b2 * sin(psi);
+  }
+  const double q = pow(1.0 - e * e, 0.25);
+  const double a = r / q, b = r * q;
+  write_prim(xf + idx * 3, box + idx * 2, p0, p1, e1, a, b);
+  aux[idx] = make_float4(__uint_as_float(s), 0.f, (float)r, (float)(a * b));
+}
+
+// ------------------------------------------------------------ Morton clusters
+
+__device__ __forceinline__ uint32_t ordered_bits(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float from_ordered(uint32_t u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// bounds[0..2] = min (ordered bits), bounds[3..5] = max
+__global__ void k_root_bounds(const float4* __restrict__ verts, uint32_t N, uint32_t S,
+                              uint32_t* bounds) {
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t lo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, hi[3] = {0, 0, 0};
+  if (s < N) {
+    const float4 p = verts[(size_t)s * (S + 1)];
+    const float c[3] = {p.x, p.y, p.z};
+    for (int i = 0; i < 3; ++i) lo[i] = hi[i] = ordered_bits(c[i]);
+  }
+  for (int i = 0; i < 3; ++i) {
+    for (int o = 16; o; o >>= 1) {
+      lo[i] = min(lo[i], __shfl_xor_sync(0xffffffffu, lo[i], o));
+      hi[i] = max(hi[i], __shfl_xor_sync(0xffffffffu, hi[i], o));
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+    for (int i = 0; i < 3; ++i) {
+      atomicMin(&bounds[i], lo[i]);
+      atomicMax(&bounds[3 + i], hi[i]);
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t spread10(uint32_t v) {
+  // bits 0..9 of v to bits 0, 3, 6, ..., 27
+  v &= 0x3ffu;
+  v = (v | (v << 16)) & 0x030000FFu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+// Root quantisation q = min(1023, floor((p - lo) * (1024 / e))) in the roots'
+// bounding cube (lo its low corner, e the largest extent), every operation
+// rounded to FP32 in this order; code = x bits at 3i+2, y at 3i+1, z at 3i.
+__global__ void k_root_morton(const float4* __restrict__ verts, uint32_t N, uint32_t S,
+                              const uint32_t* __restrict__ bounds, uint32_t* keys,
+                              uint32_t* vals) {
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  const float4 p = verts[(size_t)s * (S + 1)];
+  const float c[3] = {p.x, p.y, p.z};
+  float ext = 0.f;
+  for (int i = 0; i < 3; ++i)
+    ext = fmaxf(ext, __fsub_rn(from_ordered(bounds[3 + i]), from_ordered(bounds[i])));
+  const float scale = ext > 0.f ? __fdiv_rn(1024.0f, ext) : 0.f;
+  uint32_t q[3];
+  for (int i = 0; i < 3; ++i) {
+    const float lo = from_ordered(bounds[i]);
+    const float v = __fmul_rn(__fsub_rn(c[i], lo), scale);
+    const int qi = (int)floorf(v);
+    q[i] = (uint32_t)min(1023, max(0, qi));
+  }
+  keys[s] = (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
+  vals[s] = s;
+}
+
+__global__ void k_assign_clusters(const uint32_t* __restrict__ order, uint32_t N, uint32_t C,
+                                  uint32_t* cluster_of) {
+  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  cluster_of[order[r]] = (uint32_t)(((uint64_t)r * C) / N);
+}
+
+__global__ void k_cluster_first(uint32_t N, uint32_t C, uint32_t* first) {
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c > C) return;
+  first[c] = (uint32_t)(((uint64_t)c * N + C - 1) / C);  // ceil(c N / C)
+}
+
+struct LevelInfo {
+  uint32_t n_levels;
+  uint32_t off[16];  // first thick-hair index of each level; off[n_levels] = E
+};
+
+// Member rank range of thick hair e: level k, cluster c, sub-bucket j; the
+// members are the ranks i-in-cluster with floor(i 4^k / m) == j.
+__device__ __forceinline__ void eth_members(const LevelInfo& li, const uint32_t* cl_first,
+                                            uint32_t e, uint32_t* first, uint32_t* count,
+                                            uint32_t* cluster, uint32_t* level) {
+  uint32_t k = 0;
+  while (k + 1 < li.n_levels && e >= li.off[k + 1]) ++k;
+  const uint32_t sub_n = 1u << (2 * k);
+  const uint32_t loc = e - li.off[k];
+  const uint32_t c = loc / sub_n, j = loc % sub_n;
+  const uint64_t m = cl_first[c + 1] - cl_first[c];
+  const uint64_t lo = ((uint64_t)j * m + sub_n - 1) / sub_n;
+  const uint64_t hi = ((uint64_t)(j + 1) * m + sub_n - 1) / sub_n;
+  *first = cl_first[c] + (uint32_t)lo;
+  *count = (uint32_t)(hi - lo);
+  *cluster = c;
+  *level = k;
+}
+
+// ------------------------------------------------------------ ellipse fit
+
+// Cyclic Jacobi eigen-decomposition of a symmetric 3x3 matrix (FP64).
+// On return A's diagonal holds the eigenvalues and V's columns the vectors.
+__device__ void jacobi3(double A[3][3], double V[3][3]) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 64; ++sweep) {
+    const double off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
+    const double diag = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2];
+    if (off <= 1e-36 * diag || off == 0.0) break;
+    for (int p = 0; p < 2; ++p) {
+      for (int q = p + 1; q < 3; ++q) {
+        const double apq = A[p][q];
+        if (apq == 0.0) continue;
+        const double th = (A[q][q] - A[p][p]) / (2.0 * apq);
+        const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        // A <- J^T A J with J the rotation in the (p, q) plane
+        for (int k = 0; k < 3; ++k) {
+          const double akp = A[k][p], akq = A[k][q];
+          A[k][p] = c * akp - s * akq;
+          A[k][q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < 3; ++k) {
+          const double apk = A[p][k], aqk = A[q][k];
+          A[p][k] = c * apk - s * aqk;
+          A[q][k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < 3; ++k) {
+          const double vkp = V[k][p], vkq = V[k][q];
+          V[k][p] = c * vkp - s * vkq;
+          V[k][q] = s * vkp + c * vkq;
+        }
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ d3 tangent_at(const float4* P, uint32_t k, uint32_t S) {
+  const uint32_t k0 = k > 0 ? k - 1 : 0, k1 = k < S ? k + 1 : S;
+  return normalize(ld3(P[k1]) - ld3(P[k0]));
+}
+
+// One thread per (thick hair, cross-section).  Writes the FP32 cross-section
+// record used by the LoD widths and the FP64 values the segments are built from.
+__global__ void k_fit_cross_sections(const float4* __restrict__ verts, uint32_t S,
+                                     const uint32_t* __restrict__ order,
+                                     const uint32_t* __restrict__ cl_first, LevelInfo li,
+                                     uint32_t E, float4* xsec, double* fit64) {
+  const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (uint64_t)E * (S + 1)) return;
+  const uint32_t e = (uint32_t)(idx / (S + 1)), k = (uint32_t)(idx % (S + 1));
+  uint32_t first, cnt, c, lv;
+  eth_members(li, cl_first, e, &first, &cnt, &c, &lv);
+  const double n = cnt;
+  d3 sp = mk(0, 0, 0), st = mk(0, 0, 0);
+  for (uint32_t i = 0; i < cnt; ++i) {
+    const float4* P = verts + (size_t)order[first + i] * (S + 1);
+    sp = sp + ld3(P[k]);
+    st = st + tangent_at(P, k, S);
+  }
+  const d3 ctr = sp * (1.0 / n);
+  const d3 t = normalize(st);
+  double A[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (uint32_t i = 0; i < cnt; ++i) {
+    const d3 q = ld3(verts[(size_t)order[first + i] * (S + 1) + k]) - ctr;
+    const double v[3] = {q.x, q.y, q.z};
+    for (int r = 0; r < 3; ++r)
+      for (int cc = 0; cc < 3; ++cc) A[r][cc] += v[r] * v[cc];
+  }
+  for (int r = 0; r < 3; ++r)
+    for (int cc = 0; cc < 3; ++cc) A[r][cc] /= n;
+  double V[3][3];
+  jacobi3(A, V);
+  // ascending eigenvalues (stable for ties)
+  int ord[3] = {0, 1, 2};
+  for (int i = 1; i < 3; ++i)
+    for (int j = i; j > 0 && A[ord[j]][ord[j]] < A[ord[j - 1]][ord[j - 1]]; --j) {
+      const int tmp = ord[j];
+      ord[j] = ord[j - 1];
+      ord[j - 1] = tmp;
+    }
+  int drop = 0;
+  double best = -1.0;
+  for (int i = 0; i < 3; ++i) {
+    const int col = ord[i];
+    const double dd = fabs(V[0][col] * t.x + V[1][col] * t.y + V[2][col] * t.z);
+    if (dd > best) {
+      best = dd;
+      drop = i;
+    }
+  }
+  const int keep = ord[drop == 2 ? 1 : 2], keep0 = ord[drop == 0 ? 1 : 0];
+  d3 e1 = mk(V[0][keep], V[1][keep], V[2][keep]);
+  const double lmax = A[ord[2]][ord[2]];
+  if (A[keep][keep] - A[keep0][keep0] <= 1e-9 * lmax || !(lmax > 0.0)) {
+    // the two kept axes have equal variance: e1 toward the member farthest
+    // from the centre in the plane normal to t (first in rank order), else the
+    // Duff basis vector b1 of t
+    double best_d2 = 0.0;
+    d3 far = mk(0, 0, 0);
+    for (uint32_t i = 0; i < cnt; ++i) {
+      const d3 q = ld3(verts[(size_t)order[first + i] * (S + 1) + k]) - ctr;
+      const d3 qp = q - t * dot(q, t);
+      const double d2 = dot(qp, qp);
+      if (d2 > best_d2) {
+        best_d2 = d2;
+        far = qp;
+      }
+    }
+    if (best_d2 > 0.0) {
+      e1 = far * (1.0 / sqrt(best_d2));
+    } else {
+      d3 b1, b2;
+      duff_basis(t, &b1, &b2);
+      e1 = b1;
+    }
+  }
+  e1 = normalize(e1 - t * dot(e1, t));
+  const d3 e2 = cross(t, e1);
+  double a = 0.0, b = 0.0;
+  for (uint32_t i = 0; i < cnt; ++i) {
+    const float4* P = verts + (size_t)order[first + i] * (S + 1);
+    const d3 q = ld3(P[k]) - ctr;
+    const double r = P[0].w;  // the strand's radius (root vertex)
+    a = fmax(a, fabs(dot(q, e1)) + r);
+    b = fmax(b, fabs(dot(q, e2)) + r);
+  }
+  double s = 0.0;
+  for (uint32_t i = 0; i < cnt; ++i) {
+    const d3 q = ld3(verts[(size_t)order[first + i] * (S + 1) + k]) - ctr;
+    const double u = dot(q, e1) / a, v = dot(q, e2) / b;
+    s = fmax(s, sqrt(u * u + v * v));
+  }
+  if (s > 1.0) {
+    a *= s;
+    b *= s;
+  }
+  float4* o = xsec + idx * 3;
+  o[0] = make_float4((float)ctr.x, (float)ctr.y, (float)ctr.z, (float)a);
+  o[1] = make_float4((float)e1.x, (float)e1.y, (float)e1.z, (float)b);
+  o[2] = make_float4((float)e2.x, (float)e2.y, (float)e2.z, 0.f);
+  double* f = fit64 + idx * 8;
+  f[0] = ctr.x; f[1] = ctr.y; f[2] = ctr.z;
+  f[3] = e1.x; f[4] = e1.y; f[5] = e1.z;
+  f[6] = a; f[7] = b;
+}
+
+// Mean member material and radius of every thick hair (FP64 sums).
+__global__ void k_eth_material(const float4* __restrict__ verts, uint32_t N, uint32_t S,
+                               const uint32_t* __restrict__ order,
+                               const uint32_t* __restrict__ cl_first, LevelInfo li, uint32_t E,
+                               float* mat, float* eth_r) {
+  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  uint32_t first, cnt, c, lv;
+  eth_members(li, cl_first, e, &first, &cnt, &c, &lv);
+  double acc[HR_MAT_FLOATS];
+  for (int j = 0; j < HR_MAT_FLOATS; ++j) acc[j] = 0.0;
+  double rs = 0.0;
+  for (uint32_t i = 0; i < cnt; ++i) {
+    const uint32_t s = order[first + i];
+    for (int j = 0; j < HR_MAT_FLOATS; ++j) acc[j] += mat[(size_t)s * HR_MAT_FLOATS + j];
+    rs += verts[(size_t)s * (S + 1)].w;
+  }
+  for (int j = 0; j < HR_MAT_FLOATS; ++j)
+    mat[(size_t)(N + e) * HR_MAT_FLOATS + j] = (float)(acc[j] / cnt);
+  eth_r[e] = (float)(rs / cnt);
+}
+
+// Thick-hair segment (e, k): axis c_k -> c_{k+1}, e1 = e1_k made orthogonal to
+// the axis, semi-axes the larger of the two cross-sections'.
+__global__ void k_eth_prims(const double* __restrict__ fit64, uint32_t N, uint32_t S, uint32_t E,
+                            const uint32_t* __restrict__ cl_first, LevelInfo li,
+                            const float* __restrict__ eth_r, float4* xf, float4* box,
+                            float4* aux) {
+  const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (uint64_t)E * S) return;
+  const uint32_t e = (uint32_t)(idx / S), k = (uint32_t)(idx % S);
+  const double* f0 = fit64 + ((size_t)e * (S + 1) + k) * 8;
+  const double* f1 = f0 + 8;
+  const d3 c0 = mk(f0[0], f0[1], f0[2]), c1 = mk(f1[0], f1[1], f1[2]);
+  d3 ax = c1 - c0;
+  const double L = sqrt(dot(ax, ax));
+  d3 e1 = mk(f0[3], f0[4], f0[5]);
+  if (L > 0.0) {
+    ax = ax * (1.0 / L);
+    e1 = normalize(e1 - ax * dot(e1, ax));
+  }
+  const double a = fmax(f0[6], f1[6]), b = fmax(f0[7], f1[7]);
+  const uint64_t p = (uint64_t)N * S + idx;
+  write_prim(xf + p * 3, box + p * 2, c0, c1, e1, a, b);
+  uint32_t first, cnt, c, lv;
+  eth_members(li, cl_first, e, &first, &cnt, &c, &lv);
+  aux[p] = make_float4(__uint_as_float(N + e), (float)cnt, eth_r[e], (float)(a * b));
+}
+
+// Scene bounds over all primitive boxes (ordered-bit atomics).
+__global__ void k_prim_bounds(const float4* __restrict__ box, uint64_t n, uint32_t* bounds) {
+  uint32_t lo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, hi[3] = {0, 0, 0};
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const float4 l = box[2 * i], h = box[2 * i + 1];
+    lo[0] = min(lo[0], ordered_bits(l.x));
+    lo[1] = min(lo[1], ordered_bits(l.y));
+    lo[2] = min(lo[2], ordered_bits(l.z));
+    hi[0] = max(hi[0], ordered_bits(h.x));
+    hi[1] = max(hi[1], ordered_bits(h.y));
+    hi[2] = max(hi[2], ordered_bits(h.z));
+  }
+  for (int i = 0; i < 3; ++i) {
+    for (int o = 16; o; o >>= 1) {
+      lo[i] = min(lo[i], __shfl_xor_sync(0xffffffffu, lo[i], o));
+      hi[i] = max(hi[i], __shfl_xor_sync(0xffffffffu, hi[i], o));
+    }
+  }
+  if ((threadIdx.x & 31) == 0)
+    for (int i = 0; i < 3; ++i) {
+      atomicMin(&bounds[i], lo[i]);
+      atomicMax(&bounds[3 + i], hi[i]);
+    }
+}
+
+float host_from_ordered(uint32_t u) {
+  uint32_t v = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+  float f;
+  memcpy(&f, &v, 4);
+  return f;
+}
+
+hr_status scene_bounds(hr_ctx* ctx, hr_asset* a, uint64_t n) {
+  cudaStream_t st = ctx_stream(ctx);
+  uint32_t* b = nullptr;
+  HR_TRY(scratch(ctx, 20, 64, (void**)&b));
+  const uint32_t init[6] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u};
+  HR_CUDA(ctx, cudaMemcpyAsync(b, init, sizeof(init), cudaMemcpyHostToDevice, st));
+  const int blocks = (int)std::min<uint64_t>((n + 255) / 256, 152 * 8);
+  k_prim_bounds<<<std::max(1, blocks), 256, 0, st>>>(a->prim_box, n, b);
+  HR_LAUNCHED(ctx);
+  uint32_t hb[6];
+  HR_CUDA(ctx, cudaMemcpyAsync(hb, b, sizeof(hb), cudaMemcpyDeviceToHost, st));
+  HR_CUDA(ctx, cudaStreamSynchronize(st));
+  for (int i = 0; i < 3; ++i) {
+    a->scene_lo[i] = host_from_ordered(hb[i]);
+    a->scene_hi[i] = host_from_ordered(hb[3 + i]);
+  }
+  return HR_OK;
+}
+
+}  // namespace
+
+hr_status build_strand_prims(hr_ctx* ctx, hr_asset* a) {
+  cudaStream_t st = ctx_stream(ctx);
+  const uint64_t n = (uint64_t)a->N * a->S;
+  a->n_prims_total = (uint32_t)n;
+  HR_TRY(dalloc(ctx, (void**)&a->prim_xf, n * 3 * sizeof(float4), "strand records"));
+  HR_TRY(dalloc(ctx, (void**)&a->prim_box, n * 2 * sizeof(float4), "strand boxes"));
+  HR_TRY(dalloc(ctx, (void**)&a->prim_aux, n * sizeof(float4), "strand aux"));
+  a->bytes += n * 6 * sizeof(float4);
+  k_strand_prims<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a->verts, a->shape, a->N, a->S,
+                                                             a->prim_xf, a->prim_box,
+                                                             a->prim_aux);
+  HR_LAUNCHED(ctx);
+  return scene_bounds(ctx, a, n);
+}
+
+hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_levels) {
+  cudaStream_t st = ctx_stream(ctx);
+  const uint32_t N = a->N, S = a->S;
+  // level count: 1 + max k with 4^k <= floor(N/C)/2, capped
+  const uint32_t per = N / C;
+  uint32_t L = 0;
+  if (per >= 2) {
+    uint32_t k = 0;
+    while ((1ull << (2 * (k + 1))) <= per / 2) ++k;
+    L = k + 1;
+    if (max_levels > 0 && L > max_levels) L = max_levels;
+  }
+  if (L > 8) L = 8;
+  LevelInfo li{};
+  li.n_levels = L;
+  uint64_t E = 0;
+  for (uint32_t k = 0; k < L; ++k) {
+    li.off[k] = (uint32_t)E;
+    E += (uint64_t)C << (2 * k);
+  }
+  li.off[L] = (uint32_t)E;
+  const uint64_t total = (uint64_t)N * S + E * S;
+  if (total >= (1ull << 31) || E >= (1ull << 28))
+    return set_error(ctx, HR_EINVAL, "hierarchy too large for 31-bit primitive ids");
+
+  // free a previous hierarchy
+  if (a->order) dfree(ctx, a->order, (size_t)N * 4), a->order = nullptr;
+  if (a->cluster_of) dfree(ctx, a->cluster_of, (size_t)N * 4), a->cluster_of = nullptr;
+  if (a->cl_first) dfree(ctx, a->cl_first, (size_t)(a->C + 1) * 4), a->cl_first = nullptr;
+  if (a->xsec) dfree(ctx, a->xsec, (size_t)a->E * (S + 1) * 3 * sizeof(float4)), a->xsec = nullptr;
+  if (a->lod) dfree(ctx, a->lod, a->C), a->lod = nullptr;
+  a->lod_valid = 0;
+  a->bvh.valid = 0;
+
+  HR_TRY(dalloc(ctx, (void**)&a->order, (size_t)N * 4, "order"));
+  HR_TRY(dalloc(ctx, (void**)&a->cluster_of, (size_t)N * 4, "cluster_of"));
+  HR_TRY(dalloc(ctx, (void**)&a->cl_first, (size_t)(C + 1) * 4, "cluster first"));
+  HR_TRY(dalloc(ctx, (void**)&a->lod, C, "lod"));
+  a->C = C;
+  a->n_levels = L;
+  a->E = (uint32_t)E;
+  for (uint32_t k = 0; k <= L && k < 16; ++k) a->eth_offset[k] = li.off[k];
+
+  // K1: Morton order of the roots
+  uint32_t *bounds, *keys, *vals, *k2, *v2;
+  HR_TRY(scratch(ctx, 0, 64, (void**)&bounds));
+  HR_TRY(scratch(ctx, 1, (size_t)N * 4, (void**)&keys));
+  HR_TRY(scratch(ctx, 2, (size_t)N * 4, (void**)&k2));
+  HR_TRY(scratch(ctx, 3, (size_t)N * 4, (void**)&v2));
+  vals = a->order;
+  const uint32_t init[6] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u};
+  HR_CUDA(ctx, cudaMemcpyAsync(bounds, init, sizeof(init), cudaMemcpyHostToDevice, st));
+  k_root_bounds<<<(N + 255) / 256, 256, 0, st>>>(a->verts, N, S, bounds);
+  HR_LAUNCHED(ctx);
+  k_root_morton<<<(N + 255) / 256, 256, 0, st>>>(a->verts, N, S, bounds, keys, vals);
+  HR_LAUNCHED(ctx);
+  HR_TRY(radix_sort_pairs(ctx, keys, vals, k2, v2, N, 30, st));
+  k_assign_clusters<<<(N + 255) / 256, 256, 0, st>>>(a->order, N, C, a->cluster_of);
+  HR_LAUNCHED(ctx);
+  k_cluster_first<<<(C + 1 + 255) / 256, 256, 0, st>>>(N, C, a->cl_first);
+  HR_LAUNCHED(ctx);
+
+  // grow the material table to strands + thick hairs
+  if (a->mat_cap < (size_t)N + E) {
+    float* m2 = nullptr;
+    HR_TRY(dalloc(ctx, (void**)&m2, (size_t)(N + E) * HR_MAT_FLOATS * 4, "materials"));
+    HR_CUDA(ctx, cudaMemcpyAsync(m2, a->mat, (size_t)N * HR_MAT_FLOATS * 4,
+                                 cudaMemcpyDeviceToDevice, st));
+    HR_CUDA(ctx, cudaStreamSynchronize(st));
+    dfree(ctx, a->mat, a->mat_cap * HR_MAT_FLOATS * 4);
+    a->mat = m2;
+    a->mat_cap = (size_t)N + E;
+  }
+
+  // grow the primitive arrays to strands + thick hairs (strand part copied)
+  const uint64_t ns = (uint64_t)N * S;
+  if (a->n_prims_total != total) {
+    float4 *xf = nullptr, *bx = nullptr, *ax = nullptr;
+    HR_TRY(dalloc(ctx, (void**)&xf, total * 3 * sizeof(float4), "records"));
+    HR_TRY(dalloc(ctx, (void**)&bx, total * 2 * sizeof(float4), "boxes"));
+    HR_TRY(dalloc(ctx, (void**)&ax, total * sizeof(float4), "aux"));
+    HR_CUDA(ctx, cudaMemcpyAsync(xf, a->prim_xf, ns * 3 * sizeof(float4), cudaMemcpyDeviceToDevice, st));
+    HR_CUDA(ctx, cudaMemcpyAsync(bx, a->prim_box, ns * 2 * sizeof(float4), cudaMemcpyDeviceToDevice, st));
+    HR_CUDA(ctx, cudaMemcpyAsync(ax, a->prim_aux, ns * sizeof(float4), cudaMemcpyDeviceToDevice, st));
+    HR_CUDA(ctx, cudaStreamSynchronize(st));
+    const uint64_t old = a->n_prims_total;
+    dfree(ctx, a->prim_xf, old * 3 * sizeof(float4));
+    dfree(ctx, a->prim_box, old * 2 * sizeof(float4));
+    dfree(ctx, a->prim_aux, old * sizeof(float4));
+    a->prim_xf = xf;
+    a->prim_box = bx;
+    a->prim_aux = ax;
+    a->n_prims_total = (uint32_t)total;
+  }
+  if (E == 0) return scene_bounds(ctx, a, total);
+
+  // K2: FP64 cross-section fits, materials and thick-hair segment records
+  HR_TRY(dalloc(ctx, (void**)&a->xsec, (size_t)E * (S + 1) * 3 * sizeof(float4), "cross-sections"));
+  double* fit64 = nullptr;
+  float* eth_r = nullptr;
+  HR_TRY(scratch(ctx, 4, (size_t)E * (S + 1) * 8 * sizeof(double), (void**)&fit64));
+  HR_TRY(scratch(ctx, 5, (size_t)E * sizeof(float), (void**)&eth_r));
+  const uint64_t nx = E * (S + 1);
+  k_fit_cross_sections<<<(unsigned)((nx + 127) / 128), 128, 0, st>>>(a->verts, S, a->order,
+                                                                    a->cl_first, li, (uint32_t)E,
+                                                                    a->xsec, fit64);
+  HR_LAUNCHED(ctx);
+  k_eth_material<<<(unsigned)((E + 127) / 128), 128, 0, st>>>(a->verts, N, S, a->order,
+                                                             a->cl_first, li, (uint32_t)E,
+                                                             a->mat, eth_r);
+  HR_LAUNCHED(ctx);
+  const uint64_t ne = E * S;
+  k_eth_prims<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(fit64, N, S, (uint32_t)E,
+                                                           a->cl_first, li, eth_r, a->prim_xf,
+                                                           a->prim_box, a->prim_aux);
+  HR_LAUNCHED(ctx);
+  return scene_bounds(ctx, a, total);
+}
+
+}  // namespace hr

@@ -1,0 +1,518 @@
+// Device code of the hot path: camera rays, BVH traversal, ray versus
+// elliptic-cylinder tests, k-buffer, scattering models and compositing.
+//
+//  * Camera: sample sid = pixel * spp + s; sub-pixel position from SplitMix64
+//    outputs 2 sid and 2 sid + 1 of the frame seed (top 24 bits each).
+//  * Traversal: stack-based over the binary LBVH whose nodes hold both
+//    children's boxes (one 64-byte node fetch tests two boxes); nearer child
+//    first.  The search interval shrinks to the K-th nearest hit and to the
+//    nearest opaque (strand) hit: nothing behind an opaque hit can contribute.
+//  * Intersection: the record maps the ray into the cylinder's unit frame;
+//    the quadratic is solved about the point of closest approach and the root
+//    kept is the nearest one with w in [0, 1] (open cylinder).
+//  * Shading: f_single (Eq. 1) for strands, f_ours (Eq. 5-13) for thick
+//    hairs, per light; forward/backward single-fibre albedos from the
+//    longitudinal-integral table.
+//  * Compositing: front to back over the k-buffer sorted by (t, id).
+#pragma once
+
+#include "common.cuh"
+
+namespace hr {
+namespace tr {
+
+#define kInf __int_as_float(0x7f800000)
+constexpr int kStack = 64;
+
+__device__ __forceinline__ uint64_t splitmix_out(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float3 a, float s) { return f3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float clampf(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
+
+__device__ __forceinline__ void camera_ray(const LaunchCam& c, uint64_t seed, uint64_t sid,
+                                           uint32_t spp, float3& o, float3& d) {
+  const uint64_t pixel = sid / spp;
+  const uint32_t x = (uint32_t)(pixel % (uint32_t)c.W), y = (uint32_t)(pixel / (uint32_t)c.W);
+  const float jx = (float)(uint32_t)(splitmix_out(seed, 2 * sid) >> 40) * (1.0f / 16777216.0f);
+  const float jy = (float)(uint32_t)(splitmix_out(seed, 2 * sid + 1) >> 40) * (1.0f / 16777216.0f);
+  const float sx = ((float)x - 0.5f * (float)c.W + jx) / c.pix;
+  const float sy = (0.5f * (float)c.H - (float)y - jy) / c.pix;
+  if (c.kind == 1) {
+    o = c.eye;
+    float3 v = c.fwd + c.right * sx + c.up * sy;
+    d = v * rsqrtf(dot3(v, v));
+  } else {
+    o = c.eye + c.right * sx + c.up * sy;
+    d = c.fwd;
+  }
+}
+
+// ------------------------------------------------------------------ geometry
+
+// Ray against the open elliptic cylinder of one record.  Returns the nearest
+// root in (0, tmax] whose axial coordinate lies in [0, 1], and the chord of the
+// ray inside the finite cylinder.
+__device__ __forceinline__ bool intersect(const float4* __restrict__ xf, const float3 o,
+                                          const float3 d, const float tmax, float& t_hit,
+                                          float& chord) {
+  const float4 r0 = __ldg(xf), r1 = __ldg(xf + 1), r2 = __ldg(xf + 2);
+  const float u0 = fmaf(r0.x, o.x, fmaf(r0.y, o.y, fmaf(r0.z, o.z, r0.w)));
+  const float v0 = fmaf(r1.x, o.x, fmaf(r1.y, o.y, fmaf(r1.z, o.z, r1.w)));
+  const float du = fmaf(r0.x, d.x, fmaf(r0.y, d.y, r0.z * d.z));
+  const float dv = fmaf(r1.x, d.x, fmaf(r1.y, d.y, r1.z * d.z));
+  const float A = fmaf(du, du, dv * dv);
+  if (!(A > 0.f)) return false;
+  const float inv = 1.0f / A;
+  const float tc = -fmaf(u0, du, v0 * dv) * inv;
+  const float uc = fmaf(tc, du, u0), vc = fmaf(tc, dv, v0);
+  const float h2 = fmaf(uc, uc, vc * vc);
+  if (h2 > 1.f) return false;
+  const float half = sqrtf((1.f - h2) * inv);
+  const float tm = tc - half, tp = tc + half;
+  if (tp <= 0.f || tm > tmax) return false;
+  const float w0 = fmaf(r2.x, o.x, fmaf(r2.y, o.y, fmaf(r2.z, o.z, r2.w)));
+  const float dw = fmaf(r2.x, d.x, fmaf(r2.y, d.y, r2.z * d.z));
+  float wlo, whi;
+  if (dw != 0.f) {
+    const float idw = 1.0f / dw;
+    const float ta = -w0 * idw, tb = (1.f - w0) * idw;
+    wlo = fminf(ta, tb);
+    whi = fmaxf(ta, tb);
+  } else {
+    if (w0 < 0.f || w0 > 1.f) return false;
+    wlo = -kInf;
+    whi = kInf;
+  }
+  float t;
+  if (tm > 0.f && tm >= wlo && tm <= whi)
+    t = tm;
+  else if (tp > 0.f && tp >= wlo && tp <= whi)
+    t = tp;
+  else
+    return false;
+  if (t > tmax) return false;
+  t_hit = t;
+  chord = fmaxf(0.f, fminf(tp, whi) - fmaxf(tm, wlo));
+  return true;
+}
+
+template <int KMAX>
+struct KBuf {
+  float t[KMAX];
+  float ch[KMAX];
+  uint32_t leaf[KMAX];
+  uint32_t id[KMAX];
+};
+
+template <int KMAX>
+__device__ __forceinline__ void kbuf_init(KBuf<KMAX>& kb) {
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) {
+    kb.t[j] = kInf;
+    kb.ch[j] = 0.f;
+    kb.leaf[j] = 0u;
+    kb.id[j] = 0xffffffffu;
+  }
+}
+
+// Insert keeping the k nearest by (t, id): the candidate bubbles through the
+// sorted slots and whatever falls off the end is dropped.
+template <int KMAX>
+__device__ __forceinline__ void kbuf_insert(KBuf<KMAX>& kb, const uint32_t k, float t,
+                                            uint32_t id, uint32_t leaf, float ch) {
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) {
+    if (j < (int)k && (t < kb.t[j] || (t == kb.t[j] && id < kb.id[j]))) {
+      float a = kb.t[j]; kb.t[j] = t; t = a;
+      uint32_t b = kb.id[j]; kb.id[j] = id; id = b;
+      uint32_t c = kb.leaf[j]; kb.leaf[j] = leaf; leaf = c;
+      float e = kb.ch[j]; kb.ch[j] = ch; ch = e;
+    }
+  }
+}
+
+template <int KMAX>
+__device__ __forceinline__ float kbuf_last(const KBuf<KMAX>& kb, const uint32_t k) {
+  float r = kInf;
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j)
+    if (j == (int)k - 1) r = kb.t[j];
+  return r;
+}
+
+struct Counts {
+  uint32_t nodes, tests, sshade, eshade, hits;
+};
+
+template <int KMAX, bool COUNT>
+__device__ __forceinline__ void leaf_test(const FrameArgs& fa, uint32_t leaf, const float3 o,
+                                          const float3 d, KBuf<KMAX>& kb, float& tcut,
+                                          float& topq, Counts& cn) {
+  float th, ch;
+  if (COUNT) ++cn.tests;
+  if (intersect(fa.leaf_xf + 3 * (size_t)leaf, o, d, tcut, th, ch)) {
+    const uint32_t id = __ldg(fa.leaf_id + leaf);
+    kbuf_insert<KMAX>(kb, fa.k, th, id, leaf, ch);
+    if (__ldg(&fa.leaf_aux[leaf].y) == 0.f) topq = fminf(topq, th);  // strand: opaque
+    tcut = fminf(kbuf_last<KMAX>(kb, fa.k), topq);
+  }
+}
+
+// K nearest hits of one ray.  Returns false when the traversal stack overflowed
+// (the far subtree was dropped; counted by the caller, never expected).
+template <int KMAX, bool COUNT>
+__device__ __forceinline__ bool traverse(const FrameArgs& fa, const float3 o, const float3 d,
+                                         KBuf<KMAX>& kb, Counts& cn) {
+  kbuf_init<KMAX>(kb);
+  if (fa.n_prims == 0) return true;
+  float tcut = kInf, topq = kInf;
+  if (fa.n_prims == 1) {
+    leaf_test<KMAX, COUNT>(fa, 0, o, d, kb, tcut, topq, cn);
+    return true;
+  }
+  // a zero direction component would turn the slab products into inf - inf;
+  // keep its sign and floor its magnitude so every slab value stays ordered
+  const float3 inv = f3(1.0f / (fabsf(d.x) > 1e-12f ? d.x : copysignf(1e-12f, d.x)),
+                        1.0f / (fabsf(d.y) > 1e-12f ? d.y : copysignf(1e-12f, d.y)),
+                        1.0f / (fabsf(d.z) > 1e-12f ? d.z : copysignf(1e-12f, d.z)));
+  const float3 ooi = f3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
+  int stack[kStack];
+  int sp = 0;
+  int node = 0;
+  bool ok = true;
+  for (;;) {
+    if (node >= 0) {
+      const float4* nd = fa.nodes + 4 * (size_t)node;
+      const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+      if (COUNT) ++cn.nodes;
+      // child 0
+      float lx = fmaf(n0.x, inv.x, -ooi.x), hx = fmaf(n0.y, inv.x, -ooi.x);
+      float ly = fmaf(n0.z, inv.y, -ooi.y), hy = fmaf(n0.w, inv.y, -ooi.y);
+      float lz = fmaf(n2.x, inv.z, -ooi.z), hz = fmaf(n2.y, inv.z, -ooi.z);
+      const float a0 = fmaxf(fmaxf(fminf(lx, hx), fminf(ly, hy)), fmaxf(fminf(lz, hz), 0.f));
+      const float b0 = fminf(fminf(fmaxf(lx, hx), fmaxf(ly, hy)), fminf(fmaxf(lz, hz), tcut));
+      // child 1
+      lx = fmaf(n1.x, inv.x, -ooi.x); hx = fmaf(n1.y, inv.x, -ooi.x);
+      ly = fmaf(n1.z, inv.y, -ooi.y); hy = fmaf(n1.w, inv.y, -ooi.y);
+      lz = fmaf(n2.z, inv.z, -ooi.z); hz = fmaf(n2.w, inv.z, -ooi.z);
+      const float a1 = fmaxf(fmaxf(fminf(lx, hx), fminf(ly, hy)), fmaxf(fminf(lz, hz), 0.f));
+      const float b1 = fminf(fminf(fmaxf(lx, hx), fmaxf(ly, hy)), fminf(fmaxf(lz, hz), tcut));
+      const bool h0 = a0 <= b0, h1 = a1 <= b1;
+      const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+      if (h0 && h1) {
+        const bool first0 = a0 <= a1;
+        const int nearc = first0 ? c0 : c1, farc = first0 ? c1 : c0;
+        if (sp < kStack)
+          stack[sp++] = farc;
+        else
+          ok = false;
+        node = nearc;
+        continue;
+      }
+      if (h0 || h1) {
+        node = h0 ? c0 : c1;
+        continue;
+      }
+    } else {
+      leaf_test<KMAX, COUNT>(fa, (uint32_t)(~node), o, d, kb, tcut, topq, cn);
+    }
+    if (sp == 0) break;
+    node = stack[--sp];
+  }
+  return ok;
+}
+
+// ------------------------------------------------------------------ scattering
+
+struct Mat {
+  float A[3][3];  // [R, TT, D][rgb]
+  float bR, bT, gT;
+};
+
+__device__ __forceinline__ void load_mat(const float* __restrict__ m, Mat& o) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(m));
+  const float4 b = __ldg(reinterpret_cast<const float4*>(m) + 1);
+  const float4 c = __ldg(reinterpret_cast<const float4*>(m) + 2);
+  o.A[0][0] = a.x; o.A[0][1] = a.y; o.A[0][2] = a.z;
+  o.A[1][0] = a.w; o.A[1][1] = b.x; o.A[1][2] = b.y;
+  o.A[2][0] = b.z; o.A[2][1] = b.w; o.A[2][2] = c.x;
+  o.bR = c.y; o.bT = c.z; o.gT = c.w;
+}
+
+// Gaussian G(beta, x) = exp(-x^2 / 2 beta^2) / (sqrt(2 pi) beta), Section 3.2.
+template <int PREC>
+__device__ __forceinline__ float gauss(const Tables& tb, float beta, float x) {
+  const float ib = 1.0f / beta;
+  if (PREC == HR_PREC_FP32) {
+    const float z = x * ib;
+    return __expf(-0.5f * z * z) * (kInvSqrt2Pi * ib);
+  } else {
+    const float z = fabsf(x) * ib * (kGzN / kGzMax);
+    if (!(z < (float)kGzN)) return 0.f;
+    const int i = (int)z;
+    const float fr = z - (float)i;
+    const float g0 = __half2float(tb.gz16[i]), g1 = __half2float(tb.gz16[i + 1]);
+    return fmaf(fr, g1 - g0, g0) * (kInvSqrt2Pi * ib);
+  }
+}
+
+// Longitudinal albedo factor IM(theta, beta), bilinear in the baked table.
+template <int PREC>
+__device__ __forceinline__ float im_lookup(const Tables& tb, float theta, float beta) {
+  const float ft = clampf(theta * ((kImNT - 1) / (0.5f * kPi)), 0.f, (float)(kImNT - 1));
+  const float fb = clampf((beta - kImBetaLo) * ((kImNB - 1) / (kImBetaHi - kImBetaLo)), 0.f,
+                          (float)(kImNB - 1));
+  const int it = min((int)ft, kImNT - 2), ib = min((int)fb, kImNB - 2);
+  const float wt = ft - (float)it, wb = fb - (float)ib;
+  float v00, v01, v10, v11;
+  const int i0 = ib * kImNT + it;
+  if (PREC == HR_PREC_FP32) {
+    v00 = __ldg(tb.im32 + i0);
+    v01 = __ldg(tb.im32 + i0 + 1);
+    v10 = __ldg(tb.im32 + i0 + kImNT);
+    v11 = __ldg(tb.im32 + i0 + kImNT + 1);
+  } else {
+    v00 = __half2float(tb.im16[i0]);
+    v01 = __half2float(tb.im16[i0 + 1]);
+    v10 = __half2float(tb.im16[i0 + kImNT]);
+    v11 = __half2float(tb.im16[i0 + kImNT + 1]);
+  }
+  const float a = fmaf(wt, v01 - v00, v00), b = fmaf(wt, v11 - v10, v10);
+  return fmaf(wb, b - a, a);
+}
+
+constexpr float kInv2Pi = 0.15915494309189535f;
+constexpr float kInvPi = 0.3183098861837907f;
+constexpr float kInv2Pi2 = 0.05066059182116889f;  // 1 / (2 pi^2)
+
+// Single-fibre BCSDF, Eq. (1).
+template <int PREC>
+__device__ __forceinline__ void f_single(const Tables& tb, const Mat& m, float th_i, float th_o,
+                                         float cphi, float out[3]) {
+  const float th_h = 0.5f * (th_i + th_o);
+  const float phi = acosf(clampf(cphi, -1.f, 1.f));
+  const float mR = gauss<PREC>(tb, m.bR, th_h) * kInv2Pi;
+  const float mT = gauss<PREC>(tb, m.bT, th_h) * gauss<PREC>(tb, m.gT, phi - kPi);
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    out[c] = fmaf(m.A[0][c], mR, fmaf(m.A[1][c], mT, m.A[2][c] * kInv2Pi2));
+}
+
+// Per-hit constants of the aggregated model.
+struct EthHit {
+  float rho, n_view, nF, nB;
+};
+
+// Aggregated BCSDF of a thick hair, Eq. (5)-(13); readings as in the oracle:
+// a_F, a_B at incidence |theta_d| / 2; variances add; n = 1 toward the back
+// hemisphere (cos phi > 0); A_1+ summed in closed form for real n; B^ variance
+// the attenuation-weighted mean of the path variances; S only for cos phi > 0
+// with P_n floored at 0.
+template <int PREC>
+__device__ __forceinline__ void f_ours(const Tables& tb, const Mat& m, const EthHit& eh,
+                                       float th_i, float th_o, float cphi, uint32_t flags,
+                                       float out[3]) {
+  const float th_h = 0.5f * (th_i + th_o);
+  const float ta = 0.5f * fabsf(th_i - th_o);
+  const float phi = acosf(clampf(cphi, -1.f, 1.f));
+  const float imR = im_lookup<PREC>(tb, ta, m.bR);
+  const float imT = im_lookup<PREC>(tb, ta, m.bT);
+  float aF[3], aB[3];
+  float wR = 0.f, wT = 0.f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float r = m.A[0][c] * imR * 0.5f;
+    const float tt = m.A[1][c] * imT;
+    aF[c] = r + tt * eh.nF + m.A[2][c] * 0.25f;
+    aB[c] = r + tt * eh.nB + m.A[2][c] * 0.25f;
+    wR += r;
+    wT += tt * eh.nF;
+  }
+  const float bR2 = m.bR * m.bR, bT2 = m.bT * m.bT;
+  const float s2 = (wR * bR2 + wT * bT2) / (wR + wT);
+  const bool back = cphi > 0.f;
+  const float n = back ? 1.f : eh.n_view;
+  const float nm1 = n - 1.f;
+  const float mR = gauss<PREC>(tb, sqrtf(fmaf(nm1, s2, bR2)), th_h) * kInv2Pi;
+  const float mT = gauss<PREC>(tb, sqrtf(fmaf(nm1, s2, bT2)), th_h) *
+                   gauss<PREC>(tb, sqrtf(fmaf(nm1, s2, m.gT * m.gT)), phi - kPi);
+  float lob[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float att = nm1 > 0.f ? exp2f(nm1 * __log2f(aF[c])) : 1.f;
+    lob[c] = att * fmaf(m.A[0][c], mR, fmaf(m.A[1][c], mT, m.A[2][c] * kInv2Pi2));
+  }
+  if (back) {
+    float A1[3], A3[3], A1p[3];
+    float w1 = 0.f, w3 = 0.f, w1p = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float f = fminf(aF[c], 1.f - 1e-6f);
+      const float f2 = f * f, g = 1.f - f2, ig = 1.f / g;
+      const float b = aB[c];
+      A1[c] = b * f2 * ig;
+      A3[c] = b * b * b * f2 * ig * ig * ig;
+      A1p[c] = 0.6f * b * f * (1.f - exp2f(2.f * eh.n_view * __log2f(f))) * ig;
+      w1 += A1[c];
+      w3 += A3[c];
+      w1p += A1p[c];
+    }
+    const float vB = (w1 * (bR2 + 2.f * s2) + w3 * (3.f * bR2 + 2.f * s2) +
+                      w1p * (bR2 + (eh.n_view + 1.f) * s2)) / (w1 + w3 + w1p);
+    const float mB = gauss<PREC>(tb, sqrtf(vB), th_h) * kInvPi;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) lob[c] = fmaf(A1p[c] + A1[c] + A3[c], mB, lob[c]);
+    if (!(flags & HR_FLAG_NO_S)) {
+      const float Ps = (1.f - eh.rho) * (1.f - cphi);
+      const float Pm = 0.2f * (1.f - eh.rho);
+      const float Pn = fmaxf(0.f, 1.f - Pm - Ps);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) lob[c] *= fmaf(Ps, aF[c], Pn);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) out[c] = lob[c];
+}
+
+// Radiance of one hit toward -d (sum over lights of f E cos(theta_i)) and its
+// opacity (strand 1; thick hair 1 - exp(-2 r l n_tot / (pi a b))).
+template <int PREC, bool COUNT>
+__device__ __forceinline__ void shade_hit(const FrameArgs& fa, uint32_t leaf, float t, float chord,
+                                          const float3 o, const float3 d, float rgb[3],
+                                          float& alpha, Counts& cn) {
+  const float4 aux = __ldg(fa.leaf_aux + leaf);
+  const float4 r2 = __ldg(fa.leaf_xf + 3 * (size_t)leaf + 2);
+  const float3 T = f3(r2.x, r2.y, r2.z) * rsqrtf(r2.x * r2.x + r2.y * r2.y + r2.z * r2.z);
+  Mat m;
+  load_mat(fa.mat + (size_t)__float_as_uint(aux.x) * HR_MAT_FLOATS, m);
+  const float3 wo = d * -1.f;
+  const float so = clampf(dot3(wo, T), -1.f, 1.f);
+  const float th_o = asinf(so);
+  const float3 wop = wo - T * so;
+  const float nop = sqrtf(dot3(wop, wop));
+  const float3 x = o + d * t;
+  const bool eth = aux.y > 0.f && !(fa.flags & HR_FLAG_SINGLE_ON_ETH);
+  EthHit eh{0.f, 1.f, 0.f, 0.f};
+  alpha = 1.f;
+  if (aux.y > 0.f) {
+    const float ntot = aux.y, r = aux.z, ab = aux.w;
+    eh.rho = fminf(1.f, ntot * r * r / ab);
+    const float n_raw = eh.rho * chord * sqrtf(ntot / (kPi * ab));
+    eh.n_view = fmaxf(1.f, n_raw);
+    alpha = 1.f - __expf(-2.f * r * chord * ntot / (kPi * ab));
+    eh.nF = erff(kPi / (2.f * 1.41421356f * m.gT));
+    eh.nB = erff(kPi / (1.41421356f * m.gT)) - eh.nF;
+  }
+  rgb[0] = rgb[1] = rgb[2] = 0.f;
+  for (int l = 0; l < fa.lights.n; ++l) {
+    const float4 L = fa.lights.xyzw[l];
+    float3 wi;
+    float E = 1.f;
+    if (L.w == 0.f) {
+      wi = f3(L.x, L.y, L.z);
+    } else {
+      const float3 to = f3(L.x, L.y, L.z) - x;
+      const float dd = dot3(to, to);
+      const float id = rsqrtf(dd);
+      wi = to * id;
+      E = id * id;
+    }
+    const float si = clampf(dot3(wi, T), -1.f, 1.f);
+    const float th_i = asinf(si);
+    const float3 wip = wi - T * si;
+    const float nip = sqrtf(dot3(wip, wip));
+    const float cphi =
+        (nip > 0.f && nop > 0.f) ? clampf(dot3(wip, wop) / (nip * nop), -1.f, 1.f) : 1.f;
+    float f[3];
+    if (eth) {
+      f_ours<PREC>(fa.tables, m, eh, th_i, th_o, cphi, fa.flags, f);
+      if (COUNT) ++cn.eshade;
+    } else {
+      f_single<PREC>(fa.tables, m, th_i, th_o, cphi, f);
+      if (COUNT) ++cn.sshade;
+    }
+    const float g = E * sqrtf(fmaxf(0.f, 1.f - si * si));
+    const float4 Lc = fa.lights.rgb[l];
+    rgb[0] = fmaf(f[0] * g, Lc.x, rgb[0]);
+    rgb[1] = fmaf(f[1] * g, Lc.y, rgb[1]);
+    rgb[2] = fmaf(f[2] * g, Lc.z, rgb[2]);
+  }
+}
+
+// One sample: ray, K nearest hits, shading and front-to-back compositing.
+template <int KMAX, int PREC, bool COUNT>
+__device__ __forceinline__ void render_sample(const FrameArgs& fa, uint64_t sid, float out[3],
+                                              int32_t& hit_id, bool& ok, Counts& cn) {
+  float3 o, d;
+  camera_ray(fa.cam, fa.seed, sid, fa.spp, o, d);
+  KBuf<KMAX> kb;
+  ok = traverse<KMAX, COUNT>(fa, o, d, kb, cn);
+  float T = 1.f;
+  out[0] = out[1] = out[2] = 0.f;
+  hit_id = kb.t[0] < kInf ? (int32_t)kb.id[0] : -1;
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) {
+    if (j < (int)fa.k && kb.t[j] < kInf && T > 0.f) {
+      float rgb[3], a;
+      shade_hit<PREC, COUNT>(fa, kb.leaf[j], kb.t[j], kb.ch[j], o, d, rgb, a, cn);
+      if (COUNT) ++cn.hits;
+      const float ta = T * a;
+      out[0] = fmaf(ta, rgb[0], out[0]);
+      out[1] = fmaf(ta, rgb[1], out[1]);
+      out[2] = fmaf(ta, rgb[2], out[2]);
+      T *= 1.f - a;
+    }
+  }
+}
+
+__device__ __forceinline__ void flush_counts(const FrameArgs& fa, const Counts& cn) {
+  unsigned long long v[5] = {cn.nodes, cn.tests, cn.sshade, cn.eshade, cn.hits};
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    unsigned long long x = v[i];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0 && x) atomicAdd(fa.counters + i, x);
+  }
+}
+
+// Render the pixel of a thread inside a 16 x 8 tile; all spp samples of the
+// pixel in this thread, averaged.
+template <int KMAX, int PREC, bool COUNT>
+__device__ __forceinline__ void render_tile_pixel(const FrameArgs& fa, uint32_t tile,
+                                                  float* __restrict__ rgb, Counts& cn,
+                                                  bool& overflow) {
+  const uint32_t tiles_x = ((uint32_t)fa.cam.W + kTileW - 1) / kTileW;
+  const uint32_t tx = tile % tiles_x, ty = tile / tiles_x;
+  const uint32_t x = tx * kTileW + (threadIdx.x % kTileW);
+  const uint32_t y = ty * kTileH + (threadIdx.x / kTileW);
+  if (x >= (uint32_t)fa.cam.W || y >= (uint32_t)fa.cam.H) return;
+  const uint64_t pixel = (uint64_t)y * (uint32_t)fa.cam.W + x;
+  float acc[3] = {0.f, 0.f, 0.f};
+  for (uint32_t s = 0; s < fa.spp; ++s) {
+    float v[3];
+    int32_t hid;
+    bool ok;
+    render_sample<KMAX, PREC, COUNT>(fa, pixel * fa.spp + s, v, hid, ok, cn);
+    overflow |= !ok;
+    acc[0] += v[0];
+    acc[1] += v[1];
+    acc[2] += v[2];
+  }
+  const float inv = 1.0f / (float)fa.spp;
+  rgb[3 * pixel] = acc[0] * inv;
+  rgb[3 * pixel + 1] = acc[1] * inv;
+  rgb[3 * pixel + 2] = acc[2] * inv;
+}
+
+}  // namespace tr
+}  // namespace hr

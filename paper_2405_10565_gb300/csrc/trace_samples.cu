@@ -1,0 +1,50 @@
+// Sample-list kernel (hr_render_samples): one thread per listed sample, the
+// same per-sample device code as the frame kernel; returns radiance and the
+// global id of the nearest hit.
+#include "trace_core.cuh"
+
+namespace hr {
+namespace {
+
+template <int KMAX, int PREC>
+__global__ void __launch_bounds__(128)
+    k_samples(const FrameArgs fa, const uint32_t* __restrict__ sids, uint32_t m,
+              float* __restrict__ rad, int32_t* __restrict__ hit) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  tr::Counts cn{0, 0, 0, 0, 0};
+  float v[3];
+  int32_t h;
+  bool ok;
+  tr::render_sample<KMAX, PREC, false>(fa, sids[i], v, h, ok, cn);
+  rad[3 * (size_t)i] = v[0];
+  rad[3 * (size_t)i + 1] = v[1];
+  rad[3 * (size_t)i + 2] = v[2];
+  hit[i] = h;
+  if (!ok) atomicAdd(fa.overflow, 1u);
+}
+
+template <int PREC>
+hr_status launch_p(hr_ctx* ctx, const FrameArgs& fa, const uint32_t* sids, uint32_t m,
+                   float* rad, int32_t* hit, cudaStream_t st) {
+  const uint32_t g = (m + 127) / 128;
+  switch (kmax_for(fa.k)) {
+    case 1: k_samples<1, PREC><<<g, 128, 0, st>>>(fa, sids, m, rad, hit); break;
+    case 2: k_samples<2, PREC><<<g, 128, 0, st>>>(fa, sids, m, rad, hit); break;
+    case 4: k_samples<4, PREC><<<g, 128, 0, st>>>(fa, sids, m, rad, hit); break;
+    default: k_samples<8, PREC><<<g, 128, 0, st>>>(fa, sids, m, rad, hit); break;
+  }
+  HR_LAUNCHED(ctx);
+  return HR_OK;
+}
+
+}  // namespace
+
+hr_status launch_samples(hr_ctx* ctx, const FrameArgs& fa, int precision, const uint32_t* sids,
+                         uint32_t m, float* rad_dev, int32_t* hit_dev, cudaStream_t st) {
+  if (m == 0) return HR_OK;
+  return precision == HR_PREC_FP16 ? launch_p<HR_PREC_FP16>(ctx, fa, sids, m, rad_dev, hit_dev, st)
+                                   : launch_p<HR_PREC_FP32>(ctx, fa, sids, m, rad_dev, hit_dev, st);
+}
+
+}  // namespace hr

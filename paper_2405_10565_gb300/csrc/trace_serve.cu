@@ -1,0 +1,85 @@
+// Batched persistent serving kernel: one launch renders tiles of several
+// requests.  Blocks take batch tiles from a work counter until the batch is
+// exhausted (no block ever waits on another), locate the owning item by
+// binary search over the items' first batch tiles, and render that tile with
+// the item's own scene, camera and output.
+#include <algorithm>
+
+#include "serve.h"
+#include "trace_core.cuh"
+
+namespace hr {
+namespace {
+
+template <int KMAX, int PREC>
+__global__ void __launch_bounds__(kTileW * kTileH)
+    k_serve(const ServeItem* __restrict__ items, const uint32_t* __restrict__ item_start,
+            uint32_t n_items, uint32_t total, uint32_t* work) {
+  __shared__ uint32_t s_tile;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(work, 1u);
+    __syncthreads();
+    const uint32_t bt = s_tile;
+    __syncthreads();
+    if (bt >= total) return;
+    uint32_t lo = 0, hi = n_items;  // last item with start <= bt
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (item_start[mid] <= bt) lo = mid; else hi = mid;
+    }
+    const ServeItem& it = items[lo];
+    tr::Counts cn{0, 0, 0, 0, 0};
+    bool overflow = false;
+    tr::render_tile_pixel<KMAX, PREC, false>(it.fa, it.tile0 + (bt - item_start[lo]), it.rgb, cn,
+                                             overflow);
+    if (overflow) atomicAdd(it.fa.overflow, 1u);
+  }
+}
+
+template <int PREC>
+hr_status launch_p(hr_ctx* ctx, int kmax, const ServeItem* items, const uint32_t* starts,
+                   uint32_t n, uint32_t total, uint32_t* work, int grid, cudaStream_t st) {
+  switch (kmax) {
+    case 1: k_serve<1, PREC><<<grid, kTileW * kTileH, 0, st>>>(items, starts, n, total, work); break;
+    case 2: k_serve<2, PREC><<<grid, kTileW * kTileH, 0, st>>>(items, starts, n, total, work); break;
+    case 4: k_serve<4, PREC><<<grid, kTileW * kTileH, 0, st>>>(items, starts, n, total, work); break;
+    default: k_serve<8, PREC><<<grid, kTileW * kTileH, 0, st>>>(items, starts, n, total, work); break;
+  }
+  HR_LAUNCHED(ctx);
+  return HR_OK;
+}
+
+}  // namespace
+
+int serve_grid(int kmax, int precision) {
+  int dev = 0, sms = 1, blocks = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const void* fn = nullptr;
+  if (precision == HR_PREC_FP16) {
+    fn = kmax <= 1 ? (const void*)k_serve<1, HR_PREC_FP16> : kmax <= 2 ? (const void*)k_serve<2, HR_PREC_FP16>
+       : kmax <= 4 ? (const void*)k_serve<4, HR_PREC_FP16> : (const void*)k_serve<8, HR_PREC_FP16>;
+  } else {
+    fn = kmax <= 1 ? (const void*)k_serve<1, HR_PREC_FP32> : kmax <= 2 ? (const void*)k_serve<2, HR_PREC_FP32>
+       : kmax <= 4 ? (const void*)k_serve<4, HR_PREC_FP32> : (const void*)k_serve<8, HR_PREC_FP32>;
+  }
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, kTileW * kTileH, 0) != cudaSuccess) {
+    cudaGetLastError();
+    blocks = 4;
+  }
+  return sms * std::max(1, blocks);
+}
+
+hr_status launch_serve_batch(hr_ctx* ctx, int kmax, int precision, const ServeItem* items_dev,
+                             const uint32_t* item_start_dev, uint32_t n_items,
+                             uint32_t total_tiles, uint32_t* work_counter_dev, int grid,
+                             cudaStream_t st) {
+  if (n_items == 0 || total_tiles == 0) return HR_OK;
+  return precision == HR_PREC_FP16
+             ? launch_p<HR_PREC_FP16>(ctx, kmax, items_dev, item_start_dev, n_items, total_tiles,
+                                      work_counter_dev, grid, st)
+             : launch_p<HR_PREC_FP32>(ctx, kmax, items_dev, item_start_dev, n_items, total_tiles,
+                                      work_counter_dev, grid, st);
+}
+
+}  // namespace hr

@@ -1,0 +1,69 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path through the C ABI
+and the oracle on the same seeded inputs, and compare."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+import paper_2405_10565_gb300 as hr
+import scenegen
+
+# Tolerances (stated for FP32 traversal/intersection against the FP64 oracle).
+HIT_AGREE_MIN = 0.999      # fraction of samples with the same nearest-hit id
+RMSE_FP32 = 1e-3           # relative RMSE of radiance over agreeing samples
+RMSE_FP16 = 5e-3           # same, FP16 lookup tables
+
+
+def upload(ctx, scene):
+    return hr.hr_asset_create(ctx, np.ascontiguousarray(scene.verts),
+                              np.ascontiguousarray(scene.mat), np.ascontiguousarray(scene.shape))
+
+
+def gpu_lod(ctx, asset, w, lod=None):
+    """Build the GPU hierarchy and choose the LoD like the oracle's prepare()."""
+    if w.n_clusters == 0:
+        hr.hr_build_bvh(ctx, asset, None)
+        return None
+    hr.hr_build_clusters(ctx, asset, w.n_clusters)
+    C, L, E = hr.hr_hierarchy_info(ctx, asset)
+    if lod is None:
+        if w.lod_setting == "select":
+            lod = np.zeros(C, np.uint8)
+            hr.hr_select_lod(ctx, asset, w.camera.pack(), w.eps_w, 0, 0, lod)
+        else:
+            lod = scenegen.lod_preset(w.lod_setting, C, L)
+    lod = np.ascontiguousarray(lod, np.uint8)
+    hr.hr_build_bvh(ctx, asset, lod)
+    return lod
+
+
+def desc_of(w, precision=None, flags=0, k=None, spp=None, seed=None):
+    return hr.render_desc(w.camera.pack(), w.lights, spp or w.spp, k or w.k_depth,
+                          w.sample_seed if seed is None else seed,
+                          w.precision if precision is None else precision, flags)
+
+
+def gpu_samples(ctx, asset, desc, sids):
+    sids = np.ascontiguousarray(sids, np.uint32)
+    rad = np.zeros((sids.shape[0], 3), np.float32)
+    hit = np.zeros(sids.shape[0], np.int32)
+    hr.hr_render_samples(ctx, asset, desc, sids, rad, hit)
+    return rad, hit
+
+
+def compare(rad_g, hit_g, rad_o, hit_o):
+    """(hit agreement, rel-RMSE over agreeing samples, rel-RMSE over all)."""
+    agree = hit_g.astype(np.int64) == hit_o
+    frac = float(agree.mean()) if agree.size else 1.0
+    def rr(mask):
+        if not mask.any():
+            return 0.0
+        num = np.linalg.norm(rad_g[mask].astype(np.float64) - rad_o[mask])
+        den = np.linalg.norm(rad_o[mask])
+        return float(num / den) if den > 0 else float(num)
+    return frac, rr(agree), rr(np.ones_like(agree))
+
+
+def oracle_prepare(w, lod=None):
+    return oracle.prepare(w.scene, w.n_clusters, w.lod_setting, w.camera.pack(), w.eps_w,
+                          lod=lod)

@@ -107,6 +107,13 @@ def test_morton_mid_point_and_ties():
     assert h.order.tolist() == [0, 2, 3, 1]
 
 
+def test_morton_quantises_in_bounding_cube():
+    # extents 2 x 1 x 0.5: one scale 1024 / 2 for every axis
+    roots = np.array([[0, 0, 0], [2, 1, 0.5], [1, 0.5, 0.25]], np.float32)
+    q = oracle.quantize_roots(roots)
+    assert q.tolist() == [[0, 0, 0], [1023, 512, 256], [512, 256, 128]]
+
+
 def _morton_by_strings(q):
     out = []
     for x, y, z in q:
@@ -208,7 +215,7 @@ def test_batched_fit_matches_single_fit():
     for e in range(0, h.n_eths, 5):
         mem = h.order[h.eth_first_rank[e]: h.eth_first_rank[e] + h.eth_count[e]]
         for k in range(P.shape[1]):
-            c, t, e1, e2, a, b = oracle.fit_cross_section(P[mem, k], T[mem, k], R[mem, k])
+            c, t, e1, e2, a, b = oracle.fit_cross_section(P[mem, k], T[mem, k], R[mem, 0])
             assert np.allclose(eth.center[e, k], c, atol=1e-13)
             assert abs(abs(np.dot(eth.e1[e, k], e1)) - 1) < 1e-9
             assert eth.a[e, k] == pytest.approx(a, rel=1e-9)
@@ -434,3 +441,40 @@ def test_attenuation_with_hair_count():
     f1 = oracle.f_ours(BROWN, th_i, th_o, cp, 0.5, 1.0)
     f3 = oracle.f_ours(BROWN, th_i, th_o, cp, 0.5, 3.0)
     assert np.all(f3 < f1)
+
+
+def test_forward_albedo_stays_below_one_over_parameter_box():
+    # the dual-scattering sums of the B lobe need a_F < 1; the input recipe keeps
+    # every material of the parameter box well inside
+    for mel in (0.1, 0.5, 0.9):
+        for rough in (0.1, 0.2, 0.3):
+            m = scenegen.material_from_melanin(np.array([mel]), np.array([rough]))[0]
+            for th in np.linspace(-3.1, 3.1, 13):
+                aF, aB, _ = oracle.albedo(m.astype(np.float64), th)
+                assert np.all(aF < 0.7) and np.all(aF + aB < 1.0)
+
+
+def test_degenerate_cross_section_axis():
+    # Two strands offset mostly along the tangent: the separation axis is the
+    # one dropped and the kept pair has zero variance; e1 must then point to the
+    # member's offset in the normal plane (here along x), and the ellipse must
+    # still contain both centres.
+    t = np.array([0.0, 0.0, 1.0])
+    pts = np.array([[0.01, 0.0, 0.3], [-0.01, 0.0, -0.3]])
+    c, tt, e1, e2, a, b = oracle.fit_cross_section(pts, np.tile(t, (2, 1)), np.full(2, 1e-3))
+    assert abs(abs(e1[0]) - 1) < 1e-12
+    assert a == pytest.approx(0.011, rel=1e-12)
+    # the batched fit takes the same branch
+    w = scenegen.clustered(n=3000, S=12, res=64, spp=1, n_clusters=64)
+    h = oracle.build_hierarchy(w.scene.verts[:, 0, :3], 64)
+    eth = oracle.fit_eths(w.scene.verts, w.scene.mat, h)
+    P = w.scene.verts[..., :3].astype(np.float64)
+    T = oracle.strand_tangents(P)
+    R = w.scene.verts[..., 3].astype(np.float64)
+    n2 = np.nonzero(h.eth_count == 2)[0][:40]
+    for e in n2:
+        mem = h.order[h.eth_first_rank[e]: h.eth_first_rank[e] + 2]
+        for k in range(P.shape[1]):
+            _, _, f1, _, fa, fb = oracle.fit_cross_section(P[mem, k], T[mem, k], R[mem, 0])
+            assert abs(abs(np.dot(eth.e1[e, k], f1)) - 1) < 1e-9
+            assert eth.a[e, k] == pytest.approx(fa, rel=1e-9)

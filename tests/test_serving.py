@@ -1,0 +1,175 @@
+"""Serving loop (continuous batching) through hr_submit / hr_poll.
+
+Every request's image is the same alone (hr_select_lod + hr_build_bvh +
+hr_render on the same inputs) and in a mix of concurrent requests of different
+assets, resolutions, spp and LoD budgets; the FP16-table served form meets
+the 5e-3 relative-RMSE bound against the FP64 oracle; faults are injected on
+the host only (a refused admission, a delayed completion, a bad ticket).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2405_10565_gb300 as hr
+import scenegen
+from gpu_util import RMSE_FP16, compare
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2405_10565_gb300.build import build
+    build()
+    c = hr.hr_create(0)
+    yield c
+    hr.hr_destroy(c)
+
+
+def _assets(ctx):
+    out = []
+    for i, (n, C) in enumerate(((1500, 60), (3000, 100), (800, 32))):
+        w = scenegen.full_head(n=n, S=16, width=32, height=32, spp=1, n_lights=3, n_clusters=C,
+                               seed=20 + i)
+        a = hr.hr_asset_create(ctx, w.scene.verts, w.scene.mat, w.scene.shape)
+        hr.hr_build_clusters(ctx, a, C)
+        out.append((a, w))
+    return out
+
+
+def _requests(assets, n):
+    reqs = []
+    st = scenegen.Stream(3, 1)
+    for i in range(n):
+        a, w = assets[int(st.u64(1)[0] % 3)]
+        W = int(16 + st.u64(1)[0] % 70)
+        H = int(8 + st.u64(1)[0] % 50)
+        spp = int(1 + st.u64(1)[0] % 4)
+        bias = int(st.u64(1)[0] % 3)
+        k = int(1 + st.u64(1)[0] % 4)
+        prec = int(st.u64(1)[0] % 2)
+        lo, hi = w.scene.aabb()
+        cam = scenegen.frame_camera(lo, hi, W, H, perspective=True, fill=0.2 + 0.1 * (i % 5))
+        d = hr.render_desc(cam.pack(), w.lights, spp, k, 100 + i, prec)
+        reqs.append((a, w, cam, d, bias))
+    return reqs
+
+
+def _alone(ctx, a, cam, d, bias, eps=2.0):
+    C, L, E = hr.hr_hierarchy_info(ctx, a)
+    lod = np.zeros(C, np.uint8)
+    hr.hr_select_lod(ctx, a, cam.pack(), eps, 0, bias, lod)
+    hr.hr_build_bvh(ctx, a, lod)
+    img = np.zeros((cam.height, cam.width, 3), np.float32)
+    hr.hr_render(ctx, a, d, img)
+    return img, lod
+
+
+def test_alone_equals_mix(ctx):
+    assets = _assets(ctx)
+    reqs = _requests(assets, 24)
+    alone = [_alone(ctx, a, cam, d, bias)[0] for a, w, cam, d, bias in reqs]
+    hr.hr_serve_start(ctx, 6, 20000)
+    try:
+        outs = [np.zeros((cam.height, cam.width, 3), np.float32) for _, _, cam, _, _ in reqs]
+        tickets = [hr.hr_submit(ctx, a, d, o, 2.0, bias)
+                   for (a, w, cam, d, bias), o in zip(reqs, outs)]
+        for t in tickets:
+            st, res = hr.hr_poll(ctx, t, 60000)
+            assert st == hr.HR_OK and res.status == hr.HR_OK
+            assert res.submit_ms <= res.admit_ms <= res.done_ms
+        exact = 0
+        for i, (o, ref) in enumerate(zip(outs, alone)):
+            # same per-sample code in two kernels (frame and batched tiles):
+            # equal up to the compiler's floating-point contraction choices
+            rel = np.linalg.norm(o - ref) / np.linalg.norm(ref)
+            assert rel <= 1e-5, f"request {i} differs in the mix: rel-RMSE {rel:.2e}"
+            exact += int(np.array_equal(o, ref))
+            assert ref.max() > 0
+        print(f"alone == mix bit for bit for {exact} of {len(outs)} requests")
+    finally:
+        hr.hr_serve_stop(ctx)
+        for a, _ in assets:
+            hr.hr_asset_destroy(ctx, a)
+
+
+def test_served_fp16_accuracy_vs_oracle(ctx):
+    w = scenegen.full_head(n=3000, S=16, width=48, height=32, spp=2, n_lights=4, n_clusters=120,
+                           fill=0.2, precision=1)
+    a = hr.hr_asset_create(ctx, w.scene.verts, w.scene.mat, w.scene.shape)
+    try:
+        hr.hr_build_clusters(ctx, a, w.n_clusters)
+        d = hr.render_desc(w.camera.pack(), w.lights, w.spp, w.k_depth, w.sample_seed, 1)
+        hr.hr_serve_start(ctx, 2, 1 << 20)
+        try:
+            img = np.zeros((32, 48, 3), np.float32)
+            t = hr.hr_submit(ctx, a, d, img, w.eps_w, 0)
+            st, res = hr.hr_poll(ctx, t, 60000)
+            assert st == hr.HR_OK and res.status == hr.HR_OK
+        finally:
+            hr.hr_serve_stop(ctx)
+        prep = oracle.prepare(w.scene, w.n_clusters, "select", w.camera.pack(), w.eps_w)
+        n = 48 * 32 * w.spp
+        ro, ho = oracle.render_samples(prep, w.camera.pack(), w.lights, np.arange(n), w.spp,
+                                       w.k_depth, w.sample_seed)
+        want = ro.reshape(-1, w.spp, 3).mean(1).reshape(img.shape)
+        rel = np.linalg.norm(img - want) / np.linalg.norm(want)
+        print(f"served fp16 image rel-RMSE {rel:.2e}")
+        assert rel <= RMSE_FP16
+    finally:
+        hr.hr_asset_destroy(ctx, a)
+
+
+def test_injected_faults(ctx):
+    assets = _assets(ctx)
+    a, w, cam, d, bias = _requests(assets, 1)[0]
+    hr.hr_serve_start(ctx, 2, 1 << 20)
+    try:
+        img = np.zeros((cam.height, cam.width, 3), np.float32)
+        # a refused admission reports HR_ENOMEM for that request only
+        hr.hr_serve_inject(ctx, 1)
+        t = hr.hr_submit(ctx, a, d, img, 2.0, bias)
+        st, res = hr.hr_poll(ctx, t, 60000)
+        assert st == hr.HR_OK and res.status == hr.HR_ENOMEM
+        t2 = hr.hr_submit(ctx, a, d, img, 2.0, bias)
+        st, res = hr.hr_poll(ctx, t2, 60000)
+        assert st == hr.HR_OK and res.status == hr.HR_OK
+        # a delayed completion: a short poll times out, a later one succeeds
+        hr.hr_serve_inject(ctx, 2, 1500)
+        t3 = hr.hr_submit(ctx, a, d, img, 2.0, bias)
+        st, _ = hr.hr_poll(ctx, t3, 50)
+        assert st == hr.HR_ETIMEOUT
+        st, _ = hr.hr_poll(ctx, t3, 0)
+        assert st in (hr.HR_ENOTREADY, hr.HR_OK)
+        st, res = hr.hr_poll(ctx, t3, 30000)
+        assert st == hr.HR_OK and res.status == hr.HR_OK
+        with pytest.raises(hr.HairRTError):
+            hr.hr_poll(ctx, 987654321, 0)
+    finally:
+        hr.hr_serve_stop(ctx)
+        for a_, _ in assets:
+            hr.hr_asset_destroy(ctx, a_)
+
+
+def test_budget_admission(ctx):
+    # a context whose HBM budget cannot hold a second request's BVH admits the
+    # requests one after another and still completes them all
+    c2 = hr.hr_create(0, 0)
+    try:
+        w = scenegen.full_head(n=2000, S=16, width=40, height=30, spp=1, n_lights=2,
+                               n_clusters=80)
+        a = hr.hr_asset_create(c2, w.scene.verts, w.scene.mat, w.scene.shape)
+        hr.hr_build_clusters(c2, a, w.n_clusters)
+        d = hr.render_desc(w.camera.pack(), w.lights, 1, 4, 5, 0)
+        hr.hr_serve_start(c2, 4, 1 << 20)
+        outs = [np.zeros((30, 40, 3), np.float32) for _ in range(6)]
+        ts = [hr.hr_submit(c2, a, d, o, 2.0, 0) for o in outs]
+        for t in ts:
+            st, res = hr.hr_poll(c2, t, 60000)
+            assert st == hr.HR_OK and res.status == hr.HR_OK
+        for o in outs[1:]:
+            assert np.array_equal(o, outs[0])
+        hr.hr_serve_stop(c2)
+        hr.hr_asset_destroy(c2, a)
+    finally:
+        hr.hr_destroy(c2)
