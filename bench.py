@@ -283,7 +283,7 @@ def run_serving(hr, ctx, torch, dev, n_requests: int, seed: int = 2):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="full_head")
@@ -293,6 +293,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -389,14 +390,17 @@ def main():
         hr.hr_render_frame(ctx, a, w.n_clusters, w.eps_w, 0, desc, hout)
         hr.hr_asset_destroy(ctx, a)
 
-    e2e_step()
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
+    e2e = None
+    if not args.no_e2e:
         e2e_step()
-    torch.cuda.synchronize(dev)
-    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-    e2e_val = world * samples / e2e_s / 1e6
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        e2e = {"value": world * samples / e2e_s / 1e6, "unit": "Msamples/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3}
 
     serving = None
     if not args.no_serve and rank == 0 and world == 1:
@@ -443,8 +447,7 @@ def main():
             "frame_ms": render_avg, "active_prims": int(st.n_active_prims),
             "eth_prims": int(st.n_eth_prims), "stack_overflows": int(st.stack_overflows),
             "roofline": roof, "cpu_baseline": cpu,
-            "e2e": {"value": e2e_val, "unit": "Msamples/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
+            "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks, "serving": serving}
     print(json.dumps(line))
     if dist:

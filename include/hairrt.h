@@ -238,8 +238,10 @@ hr_status hr_render(hr_ctx* ctx, hr_asset* asset, const hr_render_desc* desc, fl
                     hr_stats* stats);
 
 /* Render only the listed samples (parity hook): radiance [m][3] and the
- * global id of the nearest hit [m] (-1 for a miss).  sample_ids, radiance_out
- * and hit_out are host or device. */
+ * global ids of the composited hits, [m][k_depth]: the k nearest by (t, id),
+ * nearest first, cut after the first opaque (strand) hit, -1 padded (column 0
+ * is the nearest hit, -1 for a miss).
+ * sample_ids, radiance_out and hit_out are host or device. */
 hr_status hr_render_samples(hr_ctx* ctx, hr_asset* asset, const hr_render_desc* desc,
                             const uint32_t* sample_ids, uint32_t m, float* radiance_out,
                             int32_t* hit_out);

@@ -687,12 +687,14 @@ def prepare(scene, n_clusters: int, lod_setting: str = "select", cam=None, eps_w
 def render_samples(prep: Prepared, cam: np.ndarray, lights: np.ndarray, samples: np.ndarray,
                    spp: int, K: int, seed: int, flags: int = 0, nq: int = 384,
                    threads: Optional[int] = None):
-    """Radiance (f64 [m, 3]) and nearest-hit global id (int64 [m], -1 = miss)
-    of the listed samples, by brute force over every active primitive."""
+    """Radiance (f64 [m, 3]) and the global ids of the composited hits
+    (int64 [m, K]: the K nearest, nearest first, cut after the first opaque
+    strand hit, -1 padded) of the listed samples, by brute force over every
+    active primitive."""
     samples = np.ascontiguousarray(samples, np.int64)
     m = samples.shape[0]
     rad = np.zeros((m, 3))
-    hit = np.full(m, -1, np.int64)
+    hit = np.full((m, K), -1, np.int64)
     x, w = gauss_legendre(nq)
     camd = np.ascontiguousarray(cam, np.float64)
     L = np.ascontiguousarray(lights, np.float64)

@@ -483,7 +483,13 @@ static void* worker(void* arg) {
       T *= 1.0 - a;
     }
     for (int c = 0; c < 3; ++c) jb->rad[3 * i + c] = C[c];
-    jb->hit[i] = cnt ? jb->prims[kp[0]].id : -1;
+    /* the composited hits: nearest first, none after the first opaque one */
+    int past = 0;
+    for (int h = 0; h < jb->K; ++h) {
+      const int live = h < cnt && !past;
+      jb->hit[(int64_t)jb->K * i + h] = live ? jb->prims[kp[h]].id : -1;
+      if (live && jb->prims[kp[h]].kind == 0) past = 1;
+    }
   }
   return 0;
 }

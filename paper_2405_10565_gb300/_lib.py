@@ -286,6 +286,7 @@ def hr_render(ctx: int, asset: int, desc: hr_render_desc, rgb_out, stats: bool =
 
 def hr_render_samples(ctx: int, asset: int, desc: hr_render_desc, sample_ids, radiance_out,
                       hit_out) -> None:
+    """radiance_out [m, 3] float32, hit_out [m, k_depth] int32 (host or device)."""
     m = int(sample_ids.shape[0])
     _check(ctx, load().hr_render_samples(ctx, asset, ctypes.byref(desc), ptr(sample_ids), m,
                                          ptr(radiance_out), ptr(hit_out)), "hr_render_samples")

@@ -60,6 +60,8 @@ int ctx_device(hr_ctx* ctx) { return ctx->device; }
 
 Server** ctx_server_slot(hr_ctx* ctx) { return &ctx->server; }
 
+uint64_t ctx_budget(hr_ctx* ctx) { return ctx->budget; }
+
 uint32_t* ctx_overflow(hr_ctx* ctx) { return ctx->d_overflow; }
 
 hr_status dalloc(hr_ctx* ctx, void** p, size_t bytes, const char* what) {
@@ -527,12 +529,13 @@ hr_status hr_render_samples(hr_ctx* ctx, hr_asset* a, const hr_render_desc* desc
   float* rad = radiance_out;
   int32_t* hit = hit_out;
   if (!dr) HR_TRY(scratch(ctx, 44, (size_t)m * 12, (void**)&rad));
-  if (!dh) HR_TRY(scratch(ctx, 45, (size_t)m * 4, (void**)&hit));
+  const size_t hit_bytes = (size_t)m * desc->k_depth * 4;
+  if (!dh) HR_TRY(scratch(ctx, 45, hit_bytes, (void**)&hit));
   FrameArgs fa = frame_args(ctx, a, a->bvh, *desc);
   HR_CUDA(ctx, cudaMemsetAsync(ctx->d_overflow, 0, 4, st));
   HR_TRY(launch_samples(ctx, fa, desc->precision, sid, m, rad, hit, st));
   if (!dr) HR_CUDA(ctx, cudaMemcpyAsync(radiance_out, rad, (size_t)m * 12, cudaMemcpyDeviceToHost, st));
-  if (!dh) HR_CUDA(ctx, cudaMemcpyAsync(hit_out, hit, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+  if (!dh) HR_CUDA(ctx, cudaMemcpyAsync(hit_out, hit, hit_bytes, cudaMemcpyDeviceToHost, st));
   HR_CUDA(ctx, cudaStreamSynchronize(st));
   return HR_OK;
 }

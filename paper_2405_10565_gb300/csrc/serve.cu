@@ -25,6 +25,7 @@
 namespace hr {
 
 Server** ctx_server_slot(hr_ctx* ctx);
+uint64_t ctx_budget(hr_ctx* ctx);
 
 namespace {
 
@@ -104,12 +105,15 @@ uint32_t request_tiles(const hr_render_desc& d) {
 // Upper bound of the device bytes a request may add: a BVH over every
 // primitive of its asset, its LoD array and a device output when needed.
 uint64_t estimate_bytes(const Request* r, const Slot& sl) {
+  // growth of the slot's grow-only buffers, bounding the active primitives by
+  // every primitive of the asset
   const hr_asset* a = r->req.asset;
   const uint64_t P = a->n_prims_total;
   uint64_t need = 0;
-  if (P > sl.bvh.cap) need += P * (4 * 16 + 3 * 16 + 16 + 4);
+  if (P > sl.bvh.cap) need += (P - sl.bvh.cap) * (4 * 16 + 3 * 16 + 16 + 4);
   const size_t out = (size_t)r->req.desc.camera.width * r->req.desc.camera.height * 12;
-  if (r->host_out && out > sl.out_cap) need += out;
+  if (r->host_out && out > sl.out_cap) need += out - sl.out_cap;
+  if (a->C > sl.lod_cap) need += a->C - sl.lod_cap;
   return need;
 }
 
@@ -178,11 +182,16 @@ void loop(Server* s) {
     // 1. admissions (FIFO, while a slot is free and the budget allows)
     while (!s->pending.empty()) {
       Request* r = s->pending.front();
+      // the free slot whose resident buffers need the least growth
       int slot = -1;
+      uint64_t best = ~0ull;
       for (size_t i = 0; i < s->slots.size(); ++i)
         if (!s->slots[i].busy) {
-          slot = (int)i;
-          break;
+          const uint64_t nd = estimate_bytes(r, s->slots[i]);
+          if (nd < best) {
+            best = nd;
+            slot = (int)i;
+          }
         }
       if (slot < 0) break;
       if (s->inject_nomem) {
@@ -193,21 +202,50 @@ void loop(Server* s) {
         progressed = true;
         continue;
       }
-      const uint64_t need = estimate_bytes(r, s->slots[slot]);
-      const uint64_t budget_left = hr_bytes_in_use(ctx);
-      (void)budget_left;
+      // admission by free HBM: the bytes the slot must grow by have to fit in
+      // the context budget (or, without one, in the device's free memory)
+      uint64_t need = estimate_bytes(r, s->slots[slot]);
+      auto fits = [&]() {
+        if (need == 0) return true;
+        const uint64_t budget = ctx_budget(ctx);
+        if (budget) return hr_bytes_in_use(ctx) + need <= budget;
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+          cudaGetLastError();
+          return false;
+        }
+        return need <= fr;
+      };
+      if (!fits()) {
+        // reclaim the resident buffers of idle slots, then retry
+        std::lock_guard<std::recursive_mutex> g(ctx_mutex(ctx));
+        cudaStreamSynchronize(s->stream);
+        for (size_t i = 0; i < s->slots.size(); ++i) {
+          Slot& sl = s->slots[i];
+          if (sl.busy || (int)i == slot) continue;
+          free_bvh(ctx, sl.bvh);
+          if (sl.lod) dfree(ctx, sl.lod, sl.lod_cap);
+          if (sl.out) dfree(ctx, sl.out, sl.out_cap);
+          sl.lod = nullptr;
+          sl.out = nullptr;
+          sl.lod_cap = 0;
+          sl.out_cap = 0;
+        }
+        need = estimate_bytes(r, s->slots[slot]);
+      }
+      if (!fits()) {
+        if (!s->active.empty()) break;  // wait for running requests to finish
+        s->pending.pop_front();
+        finish(s, r, HR_ENOMEM, ctx_now_ms(ctx));
+        s->cv_done.notify_all();
+        progressed = true;
+        continue;
+      }
       s->pending.pop_front();
       r->slot = slot;
       s->slots[slot].busy = true;
       lk.unlock();
-      hr_status st = HR_OK;
-      if (need) {
-        // admission by free HBM: the context budget check happens inside the
-        // allocations; also require the device to have the bytes free now
-        size_t fr = 0, tot = 0;
-        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && need > fr) st = HR_ENOMEM;
-      }
-      if (st == HR_OK) st = admit(s, r);
+      hr_status st = admit(s, r);
       lk.lock();
       if (st != HR_OK) {
         finish(s, r, st, ctx_now_ms(ctx));
@@ -341,10 +379,11 @@ hr_status hr_serve_start(hr_ctx* ctx, uint32_t max_slots, uint64_t max_batch_sam
   s->max_items = std::min<uint32_t>(kMaxItems, std::max<uint32_t>(max_slots, 1));
   bool ok = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess;
   for (int b = 0; b < 2 && ok; ++b) {
-    ok &= cudaMallocHost((void**)&s->h_items[b], kMaxItems * sizeof(ServeItem)) == cudaSuccess;
-    ok &= cudaMallocHost((void**)&s->h_starts[b], (kMaxItems + 1) * 4) == cudaSuccess;
-    ok &= dalloc(ctx, (void**)&s->d_items[b], kMaxItems * sizeof(ServeItem), "serve items") == HR_OK;
-    ok &= dalloc(ctx, (void**)&s->d_starts[b], (kMaxItems + 1) * 4, "serve starts") == HR_OK;
+    const size_t ni = s->max_items;
+    ok &= cudaMallocHost((void**)&s->h_items[b], ni * sizeof(ServeItem)) == cudaSuccess;
+    ok &= cudaMallocHost((void**)&s->h_starts[b], (ni + 1) * 4) == cudaSuccess;
+    ok &= dalloc(ctx, (void**)&s->d_items[b], ni * sizeof(ServeItem), "serve items") == HR_OK;
+    ok &= dalloc(ctx, (void**)&s->d_starts[b], (ni + 1) * 4, "serve starts") == HR_OK;
     ok &= cudaEventCreateWithFlags(&s->batch_ev[b], cudaEventDisableTiming) == cudaSuccess;
   }
   ok = ok && dalloc(ctx, (void**)&s->d_work, 16, "serve work") == HR_OK;
@@ -390,8 +429,8 @@ hr_status hr_serve_stop(hr_ctx* ctx) {
   for (int b = 0; b < 2; ++b) {
     if (s->h_items[b]) cudaFreeHost(s->h_items[b]);
     if (s->h_starts[b]) cudaFreeHost(s->h_starts[b]);
-    if (s->d_items[b]) dfree(ctx, s->d_items[b], kMaxItems * sizeof(ServeItem));
-    if (s->d_starts[b]) dfree(ctx, s->d_starts[b], (kMaxItems + 1) * 4);
+    if (s->d_items[b]) dfree(ctx, s->d_items[b], s->max_items * sizeof(ServeItem));
+    if (s->d_starts[b]) dfree(ctx, s->d_starts[b], (s->max_items + 1) * 4);
     if (s->batch_ev[b]) cudaEventDestroy(s->batch_ev[b]);
   }
   if (s->d_work) dfree(ctx, s->d_work, 16);

@@ -38,10 +38,9 @@ __device__ __forceinline__ float3 operator*(float3 a, float s) { return f3(a.x *
 __device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 __device__ __forceinline__ float clampf(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
 
-__device__ __forceinline__ void camera_ray(const LaunchCam& c, uint64_t seed, uint64_t sid,
-                                           uint32_t spp, float3& o, float3& d) {
-  const uint64_t pixel = sid / spp;
-  const uint32_t x = (uint32_t)(pixel % (uint32_t)c.W), y = (uint32_t)(pixel / (uint32_t)c.W);
+// Camera ray of sample `sid` of pixel (x, y).
+__device__ __forceinline__ void camera_ray_xy(const LaunchCam& c, uint64_t seed, uint64_t sid,
+                                              uint32_t x, uint32_t y, float3& o, float3& d) {
   const float jx = (float)(uint32_t)(splitmix_out(seed, 2 * sid) >> 40) * (1.0f / 16777216.0f);
   const float jy = (float)(uint32_t)(splitmix_out(seed, 2 * sid + 1) >> 40) * (1.0f / 16777216.0f);
   const float sx = ((float)x - 0.5f * (float)c.W + jx) / c.pix;
@@ -54,6 +53,13 @@ __device__ __forceinline__ void camera_ray(const LaunchCam& c, uint64_t seed, ui
     o = c.eye + c.right * sx + c.up * sy;
     d = c.fwd;
   }
+}
+
+__device__ __forceinline__ void camera_ray(const LaunchCam& c, uint64_t seed, uint64_t sid,
+                                           uint32_t spp, float3& o, float3& d) {
+  const uint64_t pixel = sid / spp;
+  camera_ray_xy(c, seed, sid, (uint32_t)(pixel % (uint32_t)c.W), (uint32_t)(pixel / (uint32_t)c.W),
+                o, d);
 }
 
 // ------------------------------------------------------------------ geometry
@@ -450,15 +456,22 @@ __device__ __forceinline__ void shade_hit(const FrameArgs& fa, uint32_t leaf, fl
 
 // One sample: ray, K nearest hits, shading and front-to-back compositing.
 template <int KMAX, int PREC, bool COUNT>
-__device__ __forceinline__ void render_sample(const FrameArgs& fa, uint64_t sid, float out[3],
-                                              int32_t& hit_id, bool& ok, Counts& cn) {
-  float3 o, d;
-  camera_ray(fa.cam, fa.seed, sid, fa.spp, o, d);
+__device__ __forceinline__ void render_ray(const FrameArgs& fa, const float3 o, const float3 d,
+                                           float out[3], int32_t* ids, bool& ok, Counts& cn) {
   KBuf<KMAX> kb;
   ok = traverse<KMAX, COUNT>(fa, o, d, kb, cn);
   float T = 1.f;
   out[0] = out[1] = out[2] = 0.f;
-  hit_id = kb.t[0] < kInf ? (int32_t)kb.id[0] : -1;
+  if (ids) {  // the composited hits: none after the first opaque (strand) one
+    bool past = false;
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+      if (j < (int)fa.k) {
+        const bool live = kb.t[j] < kInf && !past;
+        ids[j] = live ? (int32_t)kb.id[j] : -1;
+        if (live && __ldg(&fa.leaf_aux[kb.leaf[j]].y) == 0.f) past = true;
+      }
+  }
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) {
     if (j < (int)fa.k && kb.t[j] < kInf && T > 0.f) {
@@ -472,6 +485,14 @@ __device__ __forceinline__ void render_sample(const FrameArgs& fa, uint64_t sid,
       T *= 1.f - a;
     }
   }
+}
+
+template <int KMAX, int PREC, bool COUNT>
+__device__ __forceinline__ void render_sample(const FrameArgs& fa, uint64_t sid, float out[3],
+                                              int32_t* ids, bool& ok, Counts& cn) {
+  float3 o, d;
+  camera_ray(fa.cam, fa.seed, sid, fa.spp, o, d);
+  render_ray<KMAX, PREC, COUNT>(fa, o, d, out, ids, ok, cn);
 }
 
 __device__ __forceinline__ void flush_counts(const FrameArgs& fa, const Counts& cn) {
@@ -500,9 +521,10 @@ __device__ __forceinline__ void render_tile_pixel(const FrameArgs& fa, uint32_t 
   float acc[3] = {0.f, 0.f, 0.f};
   for (uint32_t s = 0; s < fa.spp; ++s) {
     float v[3];
-    int32_t hid;
     bool ok;
-    render_sample<KMAX, PREC, COUNT>(fa, pixel * fa.spp + s, v, hid, ok, cn);
+    float3 o, d;
+    camera_ray_xy(fa.cam, fa.seed, pixel * fa.spp + s, x, y, o, d);
+    render_ray<KMAX, PREC, COUNT>(fa, o, d, v, nullptr, ok, cn);
     overflow |= !ok;
     acc[0] += v[0];
     acc[1] += v[1];

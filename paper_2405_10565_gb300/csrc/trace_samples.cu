@@ -14,13 +14,15 @@ __global__ void __launch_bounds__(128)
   if (i >= m) return;
   tr::Counts cn{0, 0, 0, 0, 0};
   float v[3];
-  int32_t h;
+  int32_t ids[KMAX];
   bool ok;
-  tr::render_sample<KMAX, PREC, false>(fa, sids[i], v, h, ok, cn);
+  tr::render_sample<KMAX, PREC, false>(fa, sids[i], v, ids, ok, cn);
   rad[3 * (size_t)i] = v[0];
   rad[3 * (size_t)i + 1] = v[1];
   rad[3 * (size_t)i + 2] = v[2];
-  hit[i] = h;
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j)
+    if (j < (int)fa.k) hit[(size_t)fa.k * i + j] = ids[j];
   if (!ok) atomicAdd(fa.overflow, 1u);
 }
 

@@ -152,21 +152,42 @@ def test_injected_faults(ctx):
 
 
 def test_budget_admission(ctx):
-    # a context whose HBM budget cannot hold a second request's BVH admits the
-    # requests one after another and still completes them all
-    c2 = hr.hr_create(0, 0)
+    """With an HBM budget that holds one request's BVH at a time, requests are
+    admitted one after another (each after the previous finished) and all
+    complete with the same image."""
+    w = scenegen.full_head(n=2000, S=16, width=40, height=30, spp=1, n_lights=2, n_clusters=80)
+    P = 2000 * 16 + (80 * 5) * 16          # strand + thick-hair segments of the asset
+    probe = hr.hr_create(0, 0)
     try:
-        w = scenegen.full_head(n=2000, S=16, width=40, height=30, spp=1, n_lights=2,
-                               n_clusters=80)
+        # bytes of the asset, its hierarchy and one request's LoD + BVH build
+        a = hr.hr_asset_create(probe, w.scene.verts, w.scene.mat, w.scene.shape)
+        hr.hr_build_clusters(probe, a, w.n_clusters)
+        C, L, E = hr.hr_hierarchy_info(probe, a)
+        lod = np.zeros(C, np.uint8)
+        hr.hr_select_lod(probe, a, w.camera.pack(), 2.0, 0, 0, lod)
+        hr.hr_build_bvh(probe, a, lod)
+        base = hr.hr_bytes_in_use(probe)
+        hr.hr_asset_destroy(probe, a)
+    finally:
+        hr.hr_destroy(probe)
+    # room for that one request plus its admission estimate (a BVH over every
+    # primitive), but not for a second resident request
+    c2 = hr.hr_create(0, base + P * (4 * 16 + 3 * 16 + 16 + 4) + (16 << 10))
+    try:
         a = hr.hr_asset_create(c2, w.scene.verts, w.scene.mat, w.scene.shape)
         hr.hr_build_clusters(c2, a, w.n_clusters)
         d = hr.render_desc(w.camera.pack(), w.lights, 1, 4, 5, 0)
         hr.hr_serve_start(c2, 4, 1 << 20)
         outs = [np.zeros((30, 40, 3), np.float32) for _ in range(6)]
         ts = [hr.hr_submit(c2, a, d, o, 2.0, 0) for o in outs]
+        res = []
         for t in ts:
-            st, res = hr.hr_poll(c2, t, 60000)
-            assert st == hr.HR_OK and res.status == hr.HR_OK
+            st, r = hr.hr_poll(c2, t, 60000)
+            assert st == hr.HR_OK and r.status == hr.HR_OK, hr.hr_last_error(c2)
+            res.append(r)
+        spans = sorted((r.admit_ms, r.done_ms) for r in res)
+        for (a0, d0), (a1, d1) in zip(spans, spans[1:]):
+            assert a1 >= d0 - 1e-3, "two requests were resident at once despite the budget"
         for o in outs[1:]:
             assert np.array_equal(o, outs[0])
         hr.hr_serve_stop(c2)
