@@ -252,6 +252,35 @@ hr_status hr_render_frame(hr_ctx* ctx, hr_asset* asset, uint32_t n_clusters, flo
                           int budget_bias, const hr_render_desc* desc, float* rgb_out,
                           hr_stats* stats);
 
+/* Morton clustering without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not let a library allocate device memory, such as a host application that
+ * owns every allocation under a fixed budget, or a real-time loop in which
+ * cudaMalloc / cudaFree are not allowed because they synchronise the device.
+ * It computes the same strand order and cluster ids as hr_build_clusters
+ * (order_out and cluster_of_out there) with the same kernels, and needs no
+ * context.
+ *   vertices       : device, [n_strands][n_segments + 1][4] floats (as in
+ *                    hr_hair_desc; only the root vertex of each strand is read)
+ *   order_out      : device, [n_strands] uint32, strand ids in Morton order
+ *   cluster_of_out : device, [n_strands] uint32, cluster of each strand
+ *   cuda_stream    : stream the work is ordered on (NULL: legacy default
+ *                    stream); the call returns without synchronising it.
+ * Scratch lives in one fixed device array of the library (about 13 MB, held
+ * on every device that loads the library until the process exits); hence
+ * n_strands <= HR_NOALLOC_MAX_STRANDS, larger inputs are rejected with
+ * HR_EINVAL.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call on a device uses the same array:
+ * calls whose work overlaps on the GPU (different streams, no ordering
+ * between them) race and must not be issued.  Pointers that are not device
+ * memory, or sizes out of range, give HR_EINVAL; a CUDA error gives HR_ECUDA. */
+#define HR_NOALLOC_MAX_STRANDS 1048576u
+hr_status hr_morton_clusters_noalloc(const float* vertices, uint32_t n_strands,
+                                     uint32_t n_segments, uint32_t n_clusters,
+                                     uint32_t* order_out, uint32_t* cluster_of_out,
+                                     void* cuda_stream);
+
 /* ---------------------------------------------------------------- serving */
 
 /* A render request for the serving loop: asset (already clustered), its

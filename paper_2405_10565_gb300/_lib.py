@@ -108,6 +108,7 @@ _SIGS = {
     "hr_submit": (c_int, [P, ctypes.POINTER(hr_request), ctypes.POINTER(c_u64)]),
     "hr_poll": (c_int, [P, c_u64, c_int, ctypes.POINTER(hr_result)]),
     "hr_serve_inject": (c_int, [P, c_int, ctypes.c_int64]),
+    "hr_morton_clusters_noalloc": (c_int, [P, c_u32, c_u32, c_u32, P, P, P]),
 }
 
 _lib = None
@@ -335,6 +336,18 @@ def hr_poll(ctx: int, ticket: int, timeout_ms: int = 0):
 
 def hr_serve_inject(ctx: int, kind: int, arg: int = 0) -> None:
     _check(ctx, load().hr_serve_inject(ctx, kind, arg), "hr_serve_inject")
+
+
+HR_NOALLOC_MAX_STRANDS = 1048576
+
+
+def hr_morton_clusters_noalloc(vertices, n_clusters: int, order_out, cluster_of_out,
+                               stream: Optional[int] = None) -> None:
+    """Allocation-free Morton clustering; every buffer is device memory."""
+    n, s1 = int(vertices.shape[0]), int(vertices.shape[1])
+    _check(None, load().hr_morton_clusters_noalloc(ptr(vertices), n, s1 - 1, n_clusters,
+                                                   ptr(order_out), ptr(cluster_of_out), stream),
+           "hr_morton_clusters_noalloc")
 
 
 def header_functions(header_path: Optional[str] = None) -> Sequence[str]:

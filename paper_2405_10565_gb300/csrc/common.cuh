@@ -126,6 +126,16 @@ hr_status scan_u32(hr_ctx* ctx, uint32_t* data, uint32_t n, cudaStream_t st);
 hr_status radix_sort_pairs(hr_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp,
                            uint32_t* vals_tmp, uint32_t n, int bits, cudaStream_t st);
 
+// no-allocation variants on caller-provided scratch (sort.cu, hierarchy.cu)
+cudaError_t scan_u32_with(uint32_t* data, uint32_t n, uint32_t* sums, cudaStream_t st);
+cudaError_t radix_sort_pairs_with(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp,
+                                  uint32_t* vals_tmp, uint32_t n, int bits, uint32_t* counts,
+                                  uint32_t* sums, cudaStream_t st);
+cudaError_t morton_clusters_with(const float4* verts, uint32_t N, uint32_t S, uint32_t C,
+                                 uint32_t* order, uint32_t* cluster_of, uint32_t* bounds,
+                                 uint32_t* keys, uint32_t* keys_tmp, uint32_t* vals_tmp,
+                                 uint32_t* counts, uint32_t* sums, cudaStream_t st);
+
 // --- hierarchy.cu
 hr_status build_strand_prims(hr_ctx* ctx, hr_asset* a);
 hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_levels);

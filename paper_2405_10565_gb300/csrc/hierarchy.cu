@@ -428,6 +428,11 @@ __global__ void k_prim_bounds(const float4* __restrict__ box, uint64_t n, uint32
     }
 }
 
+__global__ void k_init_bounds(uint32_t* bounds) {
+  if (threadIdx.x < 3) bounds[threadIdx.x] = 0xffffffffu;
+  else if (threadIdx.x < 6) bounds[threadIdx.x] = 0u;
+}
+
 float host_from_ordered(uint32_t u) {
   uint32_t v = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
   float f;
@@ -590,4 +595,23 @@ hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_lev
   return scene_bounds(ctx, a, total);
 }
 
+// Morton clustering of strand roots on caller-provided scratch (no
+// allocation): bounds (6 words), keys / key / value temporaries (n words
+// each), digit counts (ceil(n / 2048) * 256 words), scan sums (<= 1024 words).
+cudaError_t morton_clusters_with(const float4* verts, uint32_t N, uint32_t S, uint32_t C,
+                                 uint32_t* order, uint32_t* cluster_of, uint32_t* bounds,
+                                 uint32_t* keys, uint32_t* keys_tmp, uint32_t* vals_tmp,
+                                 uint32_t* counts, uint32_t* sums, cudaStream_t st) {
+  k_init_bounds<<<1, 32, 0, st>>>(bounds);
+  k_root_bounds<<<(N + 255) / 256, 256, 0, st>>>(verts, N, S, bounds);
+  k_root_morton<<<(N + 255) / 256, 256, 0, st>>>(verts, N, S, bounds, keys, order);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = radix_sort_pairs_with(keys, order, keys_tmp, vals_tmp, N, 30, counts, sums, st);
+  if (e != cudaSuccess) return e;
+  k_assign_clusters<<<(N + 255) / 256, 256, 0, st>>>(order, N, C, cluster_of);
+  return cudaGetLastError();
+}
+
 }  // namespace hr
+

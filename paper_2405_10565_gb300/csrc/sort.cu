@@ -210,3 +210,46 @@ hr_status radix_sort_pairs(hr_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t
 }
 
 }  // namespace hr
+
+namespace hr {
+
+// Scan and radix sort on caller-provided scratch (no allocation).  `sums`
+// holds ceil(n / 1024) words; n <= 1024 * 1024.
+cudaError_t scan_u32_with(uint32_t* data, uint32_t n, uint32_t* sums, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const uint32_t nb = (n + kScanTile - 1) / kScanTile;
+  if (nb > (uint32_t)kScanTile) return cudaErrorInvalidValue;
+  if (nb == 1) {
+    k_scan_tiles<<<1, kScanThreads, 0, st>>>(data, n, nullptr);
+    return cudaGetLastError();
+  }
+  k_scan_tiles<<<nb, kScanThreads, 0, st>>>(data, n, sums);
+  k_scan_tiles<<<1, kScanThreads, 0, st>>>(sums, nb, nullptr);
+  k_scan_add<<<nb, kScanThreads, 0, st>>>(data, n, sums);
+  return cudaGetLastError();
+}
+
+cudaError_t radix_sort_pairs_with(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp,
+                                  uint32_t* vals_tmp, uint32_t n, int bits, uint32_t* counts,
+                                  uint32_t* sums, cudaStream_t st) {
+  if (n <= 1) return cudaSuccess;
+  const uint32_t nb = (n + kSortTile - 1) / kSortTile;
+  uint32_t *ki = keys, *vi = vals, *ko = keys_tmp, *vo = vals_tmp;
+  int passes = 0;
+  for (int shift = 0; shift < bits; shift += 8, ++passes) {
+    k_digit_hist<<<nb, kSortThreads, 0, st>>>(ki, n, shift, counts, nb);
+    cudaError_t e = scan_u32_with(counts, nb * kRadix, sums, st);
+    if (e != cudaSuccess) return e;
+    k_digit_scatter<<<nb, kSortThreads, 0, st>>>(ki, vi, ko, vo, n, shift, counts, nb);
+    uint32_t* t;
+    t = ki; ki = ko; ko = t;
+    t = vi; vi = vo; vo = t;
+  }
+  if (passes & 1) {
+    cudaMemcpyAsync(keys, ki, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(vals, vi, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace hr
