@@ -342,7 +342,7 @@ def main():
     cst = hr.hr_render(ctx, asset, cdesc, img, stats=True)
     flops = (FLOPS_PER_NODE * cst.node_visits + FLOPS_PER_TEST * cst.prim_tests +
              FLOPS_PER_STRAND_SHADE * cst.strand_shades + FLOPS_PER_ETH_SHADE * cst.eth_shades +
-             FLOPS_PER_HIT * cst.shaded_hits + FLOPS_PER_SAMPLE * samples)
+             FLOPS_PER_HIT * cst.shaded_hits + FLOPS_PER_SAMPLE * cst.traced_samples)
     uuid = None
     try:
         uuid = str(torch.cuda.get_device_properties(dev).uuid)
@@ -436,7 +436,8 @@ def main():
             if clocks.get("sm_mhz") else None,
             "events": {"node_visits": cst.node_visits, "prim_tests": cst.prim_tests,
                        "strand_shades": cst.strand_shades, "eth_shades": cst.eth_shades,
-                       "hits": cst.shaded_hits, "samples": samples}}
+                       "hits": cst.shaded_hits, "traced_samples": cst.traced_samples,
+                       "samples": samples}}
     cpu = None
     if not args.no_cpu_baseline:
         cpu = oracle_baseline(w, args.cpu_seconds)

@@ -143,6 +143,8 @@ typedef struct hr_stats {
   uint64_t strand_shades;   /* (hit, light) evaluations of f_single */
   uint64_t eth_shades;      /* (hit, light) evaluations of f_ours */
   uint64_t shaded_hits;     /* hits composited */
+  uint64_t traced_samples;  /* samples traced (pixels outside the scene's
+                               projected bounds are background untraced) */
 } hr_stats;
 
 /* ---------------------------------------------------------------- context */

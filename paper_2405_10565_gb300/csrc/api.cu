@@ -142,6 +142,10 @@ FrameArgs frame_args(hr_ctx* ctx, hr_asset* a, const Bvh& bv, const hr_render_de
   fa.overflow = ctx->d_overflow;
   fa.counters = ctx->d_counters;
   fa.k = d.k_depth;
+  const TileGeom tg = tile_geom(d.spp);
+  fa.grp = tg.grp;
+  fa.tile_w = tg.tile_w;
+  fa.tile_h = tg.tile_h;
   return fa;
 }
 
@@ -494,6 +498,7 @@ static hr_status render_impl(hr_ctx* ctx, hr_asset* a, const hr_render_desc* des
     stats->strand_shades = cnt[2];
     stats->eth_shades = cnt[3];
     stats->shaded_hits = cnt[4];
+    stats->traced_samples = cnt[5];
   } else if (!dev_out) {
     HR_CUDA(ctx, cudaStreamSynchronize(st));
   }

@@ -180,9 +180,30 @@ struct FrameArgs {
   uint64_t seed;
   uint32_t flags;
   uint32_t* overflow;  // device counter of stack overflows
-  unsigned long long* counters;  // [5] node visits, prim tests, strand shades, eth shades, hits
+  unsigned long long* counters;  // [6] node visits, prim tests, strand shades, eth shades,
+                                 // hits, traced samples
   uint32_t k;          // k-buffer depth (<= the kernel's KMAX)
+  uint32_t grp;        // lanes per pixel (power of two <= 32; samples spread over them)
+  uint32_t tile_w, tile_h;  // pixels per 128-thread block: tile_w x tile_h = 128 / grp
 };
+
+// Tile geometry of the frame and serving kernels for a given spp: each pixel
+// owns `grp` adjacent lanes (the smallest power of two >= spp, at most 32),
+// a 128-thread block covers 128 / grp pixels in a tile_w x tile_h rectangle.
+struct TileGeom {
+  uint32_t grp, tile_w, tile_h;
+};
+inline TileGeom tile_geom(uint32_t spp) {
+  uint32_t g = 1, lg = 0;
+  while (g < spp && g < 32) g <<= 1, ++lg;
+  const uint32_t pixels = 128 / g;
+  const uint32_t tw = 16u >> ((lg + 1) / 2);
+  return TileGeom{g, tw, pixels / tw};
+}
+inline uint32_t tiles_for(uint32_t W, uint32_t H, uint32_t spp) {
+  const TileGeom t = tile_geom(spp);
+  return ((W + t.tile_w - 1) / t.tile_w) * ((H + t.tile_h - 1) / t.tile_h);
+}
 hr_status launch_frame(hr_ctx* ctx, const FrameArgs& fa, int precision, bool count,
                        float* rgb_dev, cudaStream_t st);
 hr_status launch_samples(hr_ctx* ctx, const FrameArgs& fa, int precision, const uint32_t* sids,
@@ -206,8 +227,7 @@ int kmax_for(uint32_t k);
 LaunchCam to_launch_cam(const hr_camera& c);
 LaunchLights to_launch_lights(const hr_render_desc& d);
 
-// Tile geometry of frame rendering: 16 x 8 pixels per 128-thread block.
-constexpr int kTileW = 16;
-constexpr int kTileH = 8;
+// Threads per block of the frame and serving kernels.
+constexpr int kBlock = 128;
 
 }  // namespace hr

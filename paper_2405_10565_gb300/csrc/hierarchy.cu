@@ -206,35 +206,36 @@ __device__ __forceinline__ void eth_members(const LevelInfo& li, const uint32_t*
 
 // ------------------------------------------------------------ ellipse fit
 
-// Cyclic Jacobi eigen-decomposition of a symmetric 3x3 matrix (FP64).
-// On return A's diagonal holds the eigenvalues and V's columns the vectors.
-__device__ void jacobi3(double A[3][3], double V[3][3]) {
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
-  for (int sweep = 0; sweep < 64; ++sweep) {
-    const double off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
-    const double diag = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2];
-    if (off <= 1e-36 * diag || off == 0.0) break;
+// Cyclic Jacobi sweeps on a symmetric 3x3 matrix, accumulating the rotations
+// into V (which must hold an orthonormal basis on entry).  On return A's
+// diagonal holds the eigenvalues and V's columns the vectors.  T is float
+// (a cheap first guess) or double (the refinement that sets the accuracy).
+template <typename T>
+__device__ void jacobi_sweeps(T A[3][3], T V[3][3], int max_sweeps, T rel_tol) {
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    const T off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
+    const T diag = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2];
+    if (off <= rel_tol * diag || off == T(0)) break;
     for (int p = 0; p < 2; ++p) {
       for (int q = p + 1; q < 3; ++q) {
-        const double apq = A[p][q];
-        if (apq == 0.0) continue;
-        const double th = (A[q][q] - A[p][p]) / (2.0 * apq);
-        const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        const T apq = A[p][q];
+        if (apq == T(0)) continue;
+        const T th = (A[q][q] - A[p][p]) / (T(2) * apq);
+        const T t = (th >= T(0) ? T(1) : T(-1)) / (fabs(th) + sqrt(th * th + T(1)));
+        const T c = T(1) / sqrt(t * t + T(1)), s = t * c;
         // A <- J^T A J with J the rotation in the (p, q) plane
         for (int k = 0; k < 3; ++k) {
-          const double akp = A[k][p], akq = A[k][q];
+          const T akp = A[k][p], akq = A[k][q];
           A[k][p] = c * akp - s * akq;
           A[k][q] = s * akp + c * akq;
         }
         for (int k = 0; k < 3; ++k) {
-          const double apk = A[p][k], aqk = A[q][k];
+          const T apk = A[p][k], aqk = A[q][k];
           A[p][k] = c * apk - s * aqk;
           A[q][k] = s * apk + c * aqk;
         }
         for (int k = 0; k < 3; ++k) {
-          const double vkp = V[k][p], vkq = V[k][q];
+          const T vkp = V[k][p], vkq = V[k][q];
           V[k][p] = c * vkp - s * vkq;
           V[k][q] = s * vkp + c * vkq;
         }
@@ -243,13 +244,47 @@ __device__ void jacobi3(double A[3][3], double V[3][3]) {
   }
 }
 
-__device__ __forceinline__ d3 tangent_at(const float4* P, uint32_t k, uint32_t S) {
-  const uint32_t k0 = k > 0 ? k - 1 : 0, k1 = k < S ? k + 1 : S;
-  return normalize(ld3(P[k1]) - ld3(P[k0]));
+// Eigen-decomposition of a symmetric 3x3 covariance to FP64 accuracy: an FP32
+// Jacobi solve of the trace-normalised matrix gives a basis that is already
+// diagonalising to ~1e-7, the basis is re-orthonormalised in FP64, the matrix
+// is rotated into it in FP64 and FP64 Jacobi sweeps finish the job (they
+// converge quadratically from there, so one or two sweeps suffice).  The FP64
+// rate of this part is the limit of the fit, hence the FP32 start.
+__device__ void eigen3(const double C[3][3], double A[3][3], double V[3][3]) {
+  const double tr = C[0][0] + C[1][1] + C[2][2];
+  float Af[3][3], Vf[3][3];
+  const double inv = tr > 0.0 ? 1.0 / tr : 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      Af[i][j] = (float)(C[i][j] * inv);
+      Vf[i][j] = (i == j) ? 1.f : 0.f;
+    }
+  if (tr > 0.0) jacobi_sweeps<float>(Af, Vf, 8, 1e-12f);
+  // FP64 Gram-Schmidt of the FP32 basis
+  d3 v0 = normalize(mk(Vf[0][0], Vf[1][0], Vf[2][0]));
+  d3 v1 = mk(Vf[0][1], Vf[1][1], Vf[2][1]);
+  v1 = normalize(v1 - v0 * dot(v1, v0));
+  const d3 v2 = cross(v0, v1);
+  const d3 cols[3] = {v0, v1, v2};
+  for (int j = 0; j < 3; ++j) {
+    V[0][j] = cols[j].x;
+    V[1][j] = cols[j].y;
+    V[2][j] = cols[j].z;
+  }
+  // A = V^T C V
+  double CV[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) CV[i][j] = C[i][0] * V[0][j] + C[i][1] * V[1][j] + C[i][2] * V[2][j];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) A[i][j] = V[0][i] * CV[0][j] + V[1][i] * CV[1][j] + V[2][i] * CV[2][j];
+  jacobi_sweeps<double>(A, V, 16, 1e-36);
 }
 
 // One thread per (thick hair, cross-section).  Writes the FP32 cross-section
 // record used by the LoD widths and the FP64 values the segments are built from.
+// The centring sums, the eigen-decomposition and the semi-axes are FP64; the
+// members' unit tangents (which only pick the dropped axis and orient e1, e2)
+// are summed in FP32.
 __global__ void k_fit_cross_sections(const float4* __restrict__ verts, uint32_t S,
                                      const uint32_t* __restrict__ order,
                                      const uint32_t* __restrict__ cl_first, LevelInfo li,
@@ -259,26 +294,32 @@ __global__ void k_fit_cross_sections(const float4* __restrict__ verts, uint32_t 
   const uint32_t e = (uint32_t)(idx / (S + 1)), k = (uint32_t)(idx % (S + 1));
   uint32_t first, cnt, c, lv;
   eth_members(li, cl_first, e, &first, &cnt, &c, &lv);
-  const double n = cnt;
-  d3 sp = mk(0, 0, 0), st = mk(0, 0, 0);
+  const double n = cnt, inv_n = 1.0 / n;
+  const uint32_t k0 = k > 0 ? k - 1 : 0, k1 = k < S ? k + 1 : S;
+  // pass 1: sums of the offsets from the first member (centring in FP64 with
+  // a shift, so the second moments do not cancel) and of the unit tangents
+  const d3 p0 = ld3(__ldg(verts + (size_t)order[first] * (S + 1) + k));
+  double s1x = 0, s1y = 0, s1z = 0, sxx = 0, sxy = 0, sxz = 0, syy = 0, syz = 0, szz = 0;
+  float tx = 0.f, ty = 0.f, tz = 0.f;
   for (uint32_t i = 0; i < cnt; ++i) {
-    const float4* P = verts + (size_t)order[first + i] * (S + 1);
-    sp = sp + ld3(P[k]);
-    st = st + tangent_at(P, k, S);
+    const float4* P = verts + (size_t)__ldg(order + first + i) * (S + 1);
+    const float4 pk = __ldg(P + k), pa = __ldg(P + k0), pb = __ldg(P + k1);
+    const double dx = (double)pk.x - p0.x, dy = (double)pk.y - p0.y, dz = (double)pk.z - p0.z;
+    s1x += dx; s1y += dy; s1z += dz;
+    sxx = fma(dx, dx, sxx); sxy = fma(dx, dy, sxy); sxz = fma(dx, dz, sxz);
+    syy = fma(dy, dy, syy); syz = fma(dy, dz, syz); szz = fma(dz, dz, szz);
+    const float gx = pb.x - pa.x, gy = pb.y - pa.y, gz = pb.z - pa.z;
+    const float ig = rsqrtf(gx * gx + gy * gy + gz * gz);
+    tx += gx * ig; ty += gy * ig; tz += gz * ig;
   }
-  const d3 ctr = sp * (1.0 / n);
-  const d3 t = normalize(st);
-  double A[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-  for (uint32_t i = 0; i < cnt; ++i) {
-    const d3 q = ld3(verts[(size_t)order[first + i] * (S + 1) + k]) - ctr;
-    const double v[3] = {q.x, q.y, q.z};
-    for (int r = 0; r < 3; ++r)
-      for (int cc = 0; cc < 3; ++cc) A[r][cc] += v[r] * v[cc];
-  }
-  for (int r = 0; r < 3; ++r)
-    for (int cc = 0; cc < 3; ++cc) A[r][cc] /= n;
-  double V[3][3];
-  jacobi3(A, V);
+  const double mx = s1x * inv_n, my = s1y * inv_n, mz = s1z * inv_n;
+  const d3 ctr = mk(p0.x + mx, p0.y + my, p0.z + mz);
+  const d3 t = normalize(mk(tx, ty, tz));
+  const double C[3][3] = {{sxx * inv_n - mx * mx, sxy * inv_n - mx * my, sxz * inv_n - mx * mz},
+                          {sxy * inv_n - mx * my, syy * inv_n - my * my, syz * inv_n - my * mz},
+                          {sxz * inv_n - mx * mz, syz * inv_n - my * mz, szz * inv_n - mz * mz}};
+  double A[3][3], V[3][3];
+  eigen3(C, A, V);
   // ascending eigenvalues (stable for ties)
   int ord[3] = {0, 1, 2};
   for (int i = 1; i < 3; ++i)
@@ -325,21 +366,24 @@ __global__ void k_fit_cross_sections(const float4* __restrict__ verts, uint32_t 
   }
   e1 = normalize(e1 - t * dot(e1, t));
   const d3 e2 = cross(t, e1);
+  // pass 2: semi-axes; pass 3: the coverage scale (one square root)
   double a = 0.0, b = 0.0;
   for (uint32_t i = 0; i < cnt; ++i) {
-    const float4* P = verts + (size_t)order[first + i] * (S + 1);
-    const d3 q = ld3(P[k]) - ctr;
-    const double r = P[0].w;  // the strand's radius (root vertex)
+    const float4* P = verts + (size_t)__ldg(order + first + i) * (S + 1);
+    const d3 q = ld3(__ldg(P + k)) - ctr;
+    const double r = __ldg(&P[0].w);  // the strand's radius (root vertex)
     a = fmax(a, fabs(dot(q, e1)) + r);
     b = fmax(b, fabs(dot(q, e2)) + r);
   }
-  double s = 0.0;
+  const double ia = 1.0 / a, ib = 1.0 / b;
+  double s2 = 0.0;
   for (uint32_t i = 0; i < cnt; ++i) {
-    const d3 q = ld3(verts[(size_t)order[first + i] * (S + 1) + k]) - ctr;
-    const double u = dot(q, e1) / a, v = dot(q, e2) / b;
-    s = fmax(s, sqrt(u * u + v * v));
+    const d3 q = ld3(__ldg(verts + (size_t)__ldg(order + first + i) * (S + 1) + k)) - ctr;
+    const double u = dot(q, e1) * ia, v = dot(q, e2) * ib;
+    s2 = fmax(s2, fma(u, u, v * v));
   }
-  if (s > 1.0) {
+  if (s2 > 1.0) {
+    const double s = sqrt(s2);
     a *= s;
     b *= s;
   }

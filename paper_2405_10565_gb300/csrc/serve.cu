@@ -99,7 +99,7 @@ double event_ms(Server* s, cudaEvent_t ev) {
 }
 
 uint32_t request_tiles(const hr_render_desc& d) {
-  return ((d.camera.width + kTileW - 1) / kTileW) * ((d.camera.height + kTileH - 1) / kTileH);
+  return tiles_for(d.camera.width, d.camera.height, d.spp);
 }
 
 // Upper bound of the device bytes a request may add: a BVH over every
@@ -279,7 +279,8 @@ void loop(Server* s) {
       const uint64_t share = std::max<uint64_t>(1, budget / grp.size());
       for (Request* r : grp) {
         if (n_items >= s->max_items) break;
-        const uint64_t spt = (uint64_t)kTileW * kTileH * r->req.desc.spp;
+        const TileGeom tg = tile_geom(r->req.desc.spp);
+        const uint64_t spt = (uint64_t)tg.tile_w * tg.tile_h * r->req.desc.spp;
         uint32_t take = (uint32_t)std::max<uint64_t>(1, share / spt);
         take = std::min(take, r->tiles_total - r->tiles_issued);
         ServeItem& it = s->h_items[b][n_items];

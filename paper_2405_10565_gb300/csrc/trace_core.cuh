@@ -156,7 +156,7 @@ __device__ __forceinline__ float kbuf_last(const KBuf<KMAX>& kb, const uint32_t 
 }
 
 struct Counts {
-  uint32_t nodes, tests, sshade, eshade, hits;
+  uint32_t nodes, tests, sshade, eshade, hits, rays;
 };
 
 template <int KMAX, bool COUNT>
@@ -496,9 +496,9 @@ __device__ __forceinline__ void render_sample(const FrameArgs& fa, uint64_t sid,
 }
 
 __device__ __forceinline__ void flush_counts(const FrameArgs& fa, const Counts& cn) {
-  unsigned long long v[5] = {cn.nodes, cn.tests, cn.sshade, cn.eshade, cn.hits};
+  unsigned long long v[6] = {cn.nodes, cn.tests, cn.sshade, cn.eshade, cn.hits, cn.rays};
 #pragma unroll
-  for (int i = 0; i < 5; ++i) {
+  for (int i = 0; i < 6; ++i) {
     unsigned long long x = v[i];
 #pragma unroll
     for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -506,34 +506,98 @@ __device__ __forceinline__ void flush_counts(const FrameArgs& fa, const Counts& 
   }
 }
 
-// Render the pixel of a thread inside a 16 x 8 tile; all spp samples of the
-// pixel in this thread, averaged.
+// Pixel-space rectangle (x0, y0, x1, y1) that contains the projection of the
+// BVH root box, grown by one pixel; computed by the first warp of a block and
+// returned to every thread through `rect`.  A pixel whose square lies outside
+// it cannot see any primitive.  The whole screen when the box reaches behind
+// the eye or the BVH has fewer than two leaves.  Call with the whole block.
+__device__ __forceinline__ void scene_rect(const FrameArgs& fa, float4* rect) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    float X0 = kInf, Y0 = kInf, X1 = -kInf, Y1 = -kInf;
+    bool ok = fa.n_prims >= 2;
+    if (ok && lane < 8) {
+      const float4 n0 = __ldg(fa.nodes), n1 = __ldg(fa.nodes + 1), n2 = __ldg(fa.nodes + 2);
+      const float3 p = f3((lane & 1) ? fmaxf(n0.y, n1.y) : fminf(n0.x, n1.x),
+                          (lane & 2) ? fmaxf(n0.w, n1.w) : fminf(n0.z, n1.z),
+                          (lane & 4) ? fmaxf(n2.y, n2.w) : fminf(n2.x, n2.z));
+      const float3 r = p - fa.cam.eye;
+      const float xc = dot3(r, fa.cam.right), yc = dot3(r, fa.cam.up), zc = dot3(r, fa.cam.fwd);
+      float X, Y;
+      if (fa.cam.kind == 1) {
+        ok = zc > 1e-6f;
+        X = xc / zc * fa.cam.pix;
+        Y = -yc / zc * fa.cam.pix;
+      } else {
+        X = xc * fa.cam.pix;
+        Y = -yc * fa.cam.pix;
+      }
+      X += 0.5f * (float)fa.cam.W;
+      Y += 0.5f * (float)fa.cam.H;
+      if (!(X == X) || !(Y == Y)) ok = false;
+      X0 = X1 = X;
+      Y0 = Y1 = Y;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      X0 = fminf(X0, __shfl_xor_sync(0xffffffffu, X0, o));
+      Y0 = fminf(Y0, __shfl_xor_sync(0xffffffffu, Y0, o));
+      X1 = fmaxf(X1, __shfl_xor_sync(0xffffffffu, X1, o));
+      Y1 = fmaxf(Y1, __shfl_xor_sync(0xffffffffu, Y1, o));
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (lane == 0)
+      *rect = ok ? make_float4(X0 - 1.f, Y0 - 1.f, X1 + 1.f, Y1 + 1.f)
+                 : make_float4(-kInf, -kInf, kInf, kInf);
+  }
+  __syncthreads();
+}
+
+// Render one tile: each pixel's samples are spread over `grp` adjacent lanes
+// (sample s on lane s mod grp), every lane traces its samples and the pixel
+// mean is a fixed XOR-shuffle sum over the group divided by spp.  Pixels
+// outside `rect` are background.  All 32 lanes of every warp reach the
+// shuffles (no early return).
 template <int KMAX, int PREC, bool COUNT>
-__device__ __forceinline__ void render_tile_pixel(const FrameArgs& fa, uint32_t tile,
-                                                  float* __restrict__ rgb, Counts& cn,
-                                                  bool& overflow) {
-  const uint32_t tiles_x = ((uint32_t)fa.cam.W + kTileW - 1) / kTileW;
+__device__ __forceinline__ void render_tile(const FrameArgs& fa, uint32_t tile, const float4 rect,
+                                            float* __restrict__ rgb, Counts& cn, bool& overflow) {
+  const uint32_t G = fa.grp;
+  const uint32_t tiles_x = ((uint32_t)fa.cam.W + fa.tile_w - 1) / fa.tile_w;
   const uint32_t tx = tile % tiles_x, ty = tile / tiles_x;
-  const uint32_t x = tx * kTileW + (threadIdx.x % kTileW);
-  const uint32_t y = ty * kTileH + (threadIdx.x / kTileW);
-  if (x >= (uint32_t)fa.cam.W || y >= (uint32_t)fa.cam.H) return;
+  const uint32_t lane_g = threadIdx.x & (G - 1);
+  const uint32_t pib = threadIdx.x / G;  // pixel in block
+  const uint32_t x = tx * fa.tile_w + pib % fa.tile_w;
+  const uint32_t y = ty * fa.tile_h + pib / fa.tile_w;
+  const bool valid = x < (uint32_t)fa.cam.W && y < (uint32_t)fa.cam.H;
+  const bool inside = valid && (float)x + 1.f >= rect.x && (float)x <= rect.z &&
+                      (float)y + 1.f >= rect.y && (float)y <= rect.w;
   const uint64_t pixel = (uint64_t)y * (uint32_t)fa.cam.W + x;
   float acc[3] = {0.f, 0.f, 0.f};
-  for (uint32_t s = 0; s < fa.spp; ++s) {
-    float v[3];
-    bool ok;
-    float3 o, d;
-    camera_ray_xy(fa.cam, fa.seed, pixel * fa.spp + s, x, y, o, d);
-    render_ray<KMAX, PREC, COUNT>(fa, o, d, v, nullptr, ok, cn);
-    overflow |= !ok;
-    acc[0] += v[0];
-    acc[1] += v[1];
-    acc[2] += v[2];
+  if (inside) {
+    for (uint32_t s = lane_g; s < fa.spp; s += G) {
+      float v[3];
+      bool ok;
+      float3 o, d;
+      camera_ray_xy(fa.cam, fa.seed, pixel * fa.spp + s, x, y, o, d);
+      render_ray<KMAX, PREC, COUNT>(fa, o, d, v, nullptr, ok, cn);
+      if (COUNT) ++cn.rays;
+      overflow |= !ok;
+      acc[0] += v[0];
+      acc[1] += v[1];
+      acc[2] += v[2];
+    }
   }
-  const float inv = 1.0f / (float)fa.spp;
-  rgb[3 * pixel] = acc[0] * inv;
-  rgb[3 * pixel + 1] = acc[1] * inv;
-  rgb[3 * pixel + 2] = acc[2] * inv;
+  for (uint32_t o = 1; o < G; o <<= 1) {
+    acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
+    acc[1] += __shfl_xor_sync(0xffffffffu, acc[1], o);
+    acc[2] += __shfl_xor_sync(0xffffffffu, acc[2], o);
+  }
+  if (valid && lane_g == 0) {
+    const float inv = 1.0f / (float)fa.spp;
+    rgb[3 * pixel] = acc[0] * inv;
+    rgb[3 * pixel + 1] = acc[1] * inv;
+    rgb[3 * pixel + 2] = acc[2] * inv;
+  }
 }
 
 }  // namespace tr

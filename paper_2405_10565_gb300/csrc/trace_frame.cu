@@ -6,22 +6,24 @@ namespace hr {
 namespace {
 
 template <int KMAX, int PREC, bool COUNT>
-__global__ void __launch_bounds__(kTileW * kTileH)
+__global__ void __launch_bounds__(kBlock)
     k_frame(const FrameArgs fa, float* __restrict__ rgb) {
-  tr::Counts cn{0, 0, 0, 0, 0};
+  __shared__ float4 s_rect;
+  tr::scene_rect(fa, &s_rect);
+  tr::Counts cn{0, 0, 0, 0, 0, 0};
   bool overflow = false;
-  tr::render_tile_pixel<KMAX, PREC, COUNT>(fa, blockIdx.x, rgb, cn, overflow);
+  tr::render_tile<KMAX, PREC, COUNT>(fa, blockIdx.x, s_rect, rgb, cn, overflow);
   if (COUNT) tr::flush_counts(fa, cn);
   if (overflow) atomicAdd(fa.overflow, 1u);
 }
 
 template <int KMAX, int PREC>
 hr_status launch_k(hr_ctx* ctx, const FrameArgs& fa, bool count, float* rgb, cudaStream_t st) {
-  const uint32_t tiles = ((fa.cam.W + kTileW - 1) / kTileW) * ((fa.cam.H + kTileH - 1) / kTileH);
+  const uint32_t tiles = tiles_for(fa.cam.W, fa.cam.H, fa.spp);
   if (count)
-    k_frame<KMAX, PREC, true><<<tiles, kTileW * kTileH, 0, st>>>(fa, rgb);
+    k_frame<KMAX, PREC, true><<<tiles, kBlock, 0, st>>>(fa, rgb);
   else
-    k_frame<KMAX, PREC, false><<<tiles, kTileW * kTileH, 0, st>>>(fa, rgb);
+    k_frame<KMAX, PREC, false><<<tiles, kBlock, 0, st>>>(fa, rgb);
   HR_LAUNCHED(ctx);
   return HR_OK;
 }

@@ -12,10 +12,11 @@ namespace hr {
 namespace {
 
 template <int KMAX, int PREC>
-__global__ void __launch_bounds__(kTileW * kTileH)
+__global__ void __launch_bounds__(kBlock)
     k_serve(const ServeItem* __restrict__ items, const uint32_t* __restrict__ item_start,
             uint32_t n_items, uint32_t total, uint32_t* work) {
   __shared__ uint32_t s_tile;
+  __shared__ float4 s_rect;
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(work, 1u);
     __syncthreads();
@@ -28,10 +29,11 @@ __global__ void __launch_bounds__(kTileW * kTileH)
       if (item_start[mid] <= bt) lo = mid; else hi = mid;
     }
     const ServeItem& it = items[lo];
-    tr::Counts cn{0, 0, 0, 0, 0};
+    tr::scene_rect(it.fa, &s_rect);
+    tr::Counts cn{0, 0, 0, 0, 0, 0};
     bool overflow = false;
-    tr::render_tile_pixel<KMAX, PREC, false>(it.fa, it.tile0 + (bt - item_start[lo]), it.rgb, cn,
-                                             overflow);
+    tr::render_tile<KMAX, PREC, false>(it.fa, it.tile0 + (bt - item_start[lo]), s_rect, it.rgb,
+                                       cn, overflow);
     if (overflow) atomicAdd(it.fa.overflow, 1u);
   }
 }
@@ -40,10 +42,10 @@ template <int PREC>
 hr_status launch_p(hr_ctx* ctx, int kmax, const ServeItem* items, const uint32_t* starts,
                    uint32_t n, uint32_t total, uint32_t* work, int grid, cudaStream_t st) {
   switch (kmax) {
-    case 1: k_serve<1, PREC><<<grid, kTileW * kTileH, 0, st>>>(items, starts, n, total, work); break;
-    case 2: k_serve<2, PREC><<<grid, kTileW * kTileH, 0, st>>>(items, starts, n, total, work); break;
-    case 4: k_serve<4, PREC><<<grid, kTileW * kTileH, 0, st>>>(items, starts, n, total, work); break;
-    default: k_serve<8, PREC><<<grid, kTileW * kTileH, 0, st>>>(items, starts, n, total, work); break;
+    case 1: k_serve<1, PREC><<<grid, kBlock, 0, st>>>(items, starts, n, total, work); break;
+    case 2: k_serve<2, PREC><<<grid, kBlock, 0, st>>>(items, starts, n, total, work); break;
+    case 4: k_serve<4, PREC><<<grid, kBlock, 0, st>>>(items, starts, n, total, work); break;
+    default: k_serve<8, PREC><<<grid, kBlock, 0, st>>>(items, starts, n, total, work); break;
   }
   HR_LAUNCHED(ctx);
   return HR_OK;
@@ -63,7 +65,7 @@ int serve_grid(int kmax, int precision) {
     fn = kmax <= 1 ? (const void*)k_serve<1, HR_PREC_FP32> : kmax <= 2 ? (const void*)k_serve<2, HR_PREC_FP32>
        : kmax <= 4 ? (const void*)k_serve<4, HR_PREC_FP32> : (const void*)k_serve<8, HR_PREC_FP32>;
   }
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, kTileW * kTileH, 0) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, kBlock, 0) != cudaSuccess) {
     cudaGetLastError();
     blocks = 4;
   }
