@@ -156,21 +156,31 @@ __device__ __forceinline__ void node_union(const float4* nodes, int c, float* b)
   b[5] = fmaxf(n2.y, n2.w);
 }
 
-__device__ __forceinline__ void leaf_box(const float4* box, const uint32_t* sorted_ids, int leaf,
-                                         float* b) {
-  const uint32_t id = sorted_ids[leaf];
-  const float4 l = box[2 * (size_t)id], h = box[2 * (size_t)id + 1];
+__device__ __forceinline__ void lbox_read(const float4* lbox, int leaf, float* b) {
+  const float4 l = __ldcg(lbox + 2 * leaf), h = __ldcg(lbox + 2 * leaf + 1);
   b[0] = l.x; b[1] = h.x; b[2] = l.y; b[3] = h.y; b[4] = l.z; b[5] = h.z;
 }
 
-// Bottom-up bounds: a thread starts at each leaf and climbs; at every internal
-// node the first arrival stops, the second writes both child boxes.
-__global__ void k_refit(const int4* __restrict__ child, const int* __restrict__ parent_int,
-                        const int* __restrict__ parent_leaf, const float4* __restrict__ box,
-                        const uint32_t* __restrict__ sorted_ids, int n, float4* nodes,
-                        unsigned* arrivals) {
+// Leaf gather and bottom-up bounds in one pass: a thread copies its leaf's
+// record into Morton order, publishes the leaf box (leaf order, read by the
+// sibling's thread) and climbs; at every internal node the first arrival
+// stops, the second writes both child boxes.
+__global__ void k_gather_refit(const int4* __restrict__ child, const int* __restrict__ parent_int,
+                               const int* __restrict__ parent_leaf, const float4* __restrict__ box,
+                               const uint32_t* __restrict__ sorted_ids,
+                               const float4* __restrict__ xf, const float4* __restrict__ aux,
+                               int n, float4* nodes, float4* lbox, float4* leaf_xf,
+                               float4* leaf_aux, uint32_t* leaf_id, unsigned* arrivals) {
   const int leaf = blockIdx.x * blockDim.x + threadIdx.x;
   if (leaf >= n) return;
+  const uint32_t id = sorted_ids[leaf];
+  leaf_xf[3 * (size_t)leaf] = xf[3 * (size_t)id];
+  leaf_xf[3 * (size_t)leaf + 1] = xf[3 * (size_t)id + 1];
+  leaf_xf[3 * (size_t)leaf + 2] = xf[3 * (size_t)id + 2];
+  leaf_aux[leaf] = aux[id];
+  leaf_id[leaf] = id;
+  __stcg(lbox + 2 * leaf, box[2 * (size_t)id]);
+  __stcg(lbox + 2 * leaf + 1, box[2 * (size_t)id + 1]);
   int node = parent_leaf[leaf];
   while (node >= 0) {
     __threadfence();
@@ -178,8 +188,8 @@ __global__ void k_refit(const int4* __restrict__ child, const int* __restrict__ 
     __threadfence();
     const int4 ch = child[node];
     float b0[6], b1[6];
-    if (ch.x < 0) leaf_box(box, sorted_ids, ~ch.x, b0); else node_union(nodes, ch.x, b0);
-    if (ch.y < 0) leaf_box(box, sorted_ids, ~ch.y, b1); else node_union(nodes, ch.y, b1);
+    if (ch.x < 0) lbox_read(lbox, ~ch.x, b0); else node_union(nodes, ch.x, b0);
+    if (ch.y < 0) lbox_read(lbox, ~ch.y, b1); else node_union(nodes, ch.y, b1);
     float4* o = nodes + 4 * node;
     __stcg(o, make_float4(b0[0], b0[1], b0[2], b0[3]));
     __stcg(o + 1, make_float4(b1[0], b1[1], b1[2], b1[3]));
@@ -268,27 +278,30 @@ hr_status build_bvh(hr_ctx* ctx, hr_asset* a, const uint8_t* lod_dev, Bvh& bv, c
   k_prim_morton<<<(n + 255) / 256, 256, 0, st>>>(a->prim_box, ids, n, lo, inv, keys);
   HR_LAUNCHED(ctx);
   HR_TRY(radix_sort_pairs(ctx, keys, ids, k2, v2, n, 30, st));
-  // 4. leaves
-  k_gather<<<(n + 255) / 256, 256, 0, st>>>(ids, n, a->prim_xf, a->prim_aux, bv.leaf_xf,
-                                            bv.leaf_aux, bv.leaf_id);
-  HR_LAUNCHED(ctx);
   if (n == 1) {
+    k_gather<<<1, 32, 0, st>>>(ids, n, a->prim_xf, a->prim_aux, bv.leaf_xf, bv.leaf_aux,
+                               bv.leaf_id);
+    HR_LAUNCHED(ctx);
     bv.valid = 1;
     return HR_OK;
   }
-  // 5. hierarchy and bounds
+  // 4. hierarchy, then leaf records and bounds in one bottom-up pass
   int4* child = nullptr;
   int *par_int = nullptr, *par_leaf = nullptr;
   unsigned* arrivals = nullptr;
+  float4* lbox = nullptr;
   HR_TRY(scratch(ctx, 36, (size_t)n * sizeof(int4), (void**)&child));
   HR_TRY(scratch(ctx, 37, (size_t)n * 4, (void**)&par_int));
   HR_TRY(scratch(ctx, 38, (size_t)n * 4, (void**)&par_leaf));
   HR_TRY(scratch(ctx, 39, (size_t)n * 4, (void**)&arrivals));
+  HR_TRY(scratch(ctx, 46, (size_t)n * 2 * sizeof(float4), (void**)&lbox));
   HR_CUDA(ctx, cudaMemsetAsync(arrivals, 0, (size_t)n * 4, st));
   k_karras<<<(n - 1 + 255) / 256, 256, 0, st>>>(keys, (int)n, child, par_int, par_leaf);
   HR_LAUNCHED(ctx);
-  k_refit<<<(n + 255) / 256, 256, 0, st>>>(child, par_int, par_leaf, a->prim_box, ids, (int)n,
-                                           bv.nodes, arrivals);
+  k_gather_refit<<<(n + 255) / 256, 256, 0, st>>>(child, par_int, par_leaf, a->prim_box, ids,
+                                                  a->prim_xf, a->prim_aux, (int)n, bv.nodes,
+                                                  lbox, bv.leaf_xf, bv.leaf_aux, bv.leaf_id,
+                                                  arrivals);
   HR_LAUNCHED(ctx);
   bv.valid = 1;
   return HR_OK;

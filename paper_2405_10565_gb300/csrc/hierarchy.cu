@@ -42,22 +42,26 @@ __device__ __forceinline__ d3 ld3(float4 v) { return mk(v.x, v.y, v.z); }
 // segment c0 -> c1 with semi-axis a along e1 and b along e2 = t x e1.
 __device__ void write_prim(float4* xf, float4* box, d3 c0, d3 c1, d3 e1, double a, double b) {
   d3 ax = c1 - c0;
-  const double L = sqrt(dot(ax, ax));
-  if (!(L > 0.0)) {
+  const double L2 = dot(ax, ax);
+  if (!(L2 > 0.0)) {
     xf[0] = xf[1] = xf[2] = make_float4(0.f, 0.f, 0.f, 0.f);
     box[0] = make_float4((float)c0.x, (float)c0.y, (float)c0.z, 0.f);
     box[1] = box[0];
     return;
   }
-  const d3 t = ax * (1.0 / L);
+  const double iL = rsqrt(L2);
+  const d3 t = ax * iL;
   const d3 e2 = cross(t, e1);
-  const d3 r0 = e1 * (1.0 / a), r1 = e2 * (1.0 / b), r2 = t * (1.0 / L);
-  xf[0] = make_float4((float)r0.x, (float)r0.y, (float)r0.z, (float)(-dot(c0, e1) / a));
-  xf[1] = make_float4((float)r1.x, (float)r1.y, (float)r1.z, (float)(-dot(c0, e2) / b));
-  xf[2] = make_float4((float)r2.x, (float)r2.y, (float)r2.z, (float)(-dot(c0, t) / L));
-  const double hx = sqrt(a * a * e1.x * e1.x + b * b * e2.x * e2.x);
-  const double hy = sqrt(a * a * e1.y * e1.y + b * b * e2.y * e2.y);
-  const double hz = sqrt(a * a * e1.z * e1.z + b * b * e2.z * e2.z);
+  const double ia = 1.0 / a, ib = 1.0 / b;
+  const d3 r0 = e1 * ia, r1 = e2 * ib, r2 = t * iL;
+  xf[0] = make_float4((float)r0.x, (float)r0.y, (float)r0.z, (float)(-dot(c0, e1) * ia));
+  xf[1] = make_float4((float)r1.x, (float)r1.y, (float)r1.z, (float)(-dot(c0, e2) * ib));
+  xf[2] = make_float4((float)r2.x, (float)r2.y, (float)r2.z, (float)(-dot(c0, t) * iL));
+  // half extents of the elliptic disc per axis, grown by 1e-6 relative so the
+  // FP32 square root stays conservative; the corners are rounded outward
+  const float hx = sqrtf((float)(a * a * e1.x * e1.x + b * b * e2.x * e2.x)) * 1.000001f;
+  const float hy = sqrtf((float)(a * a * e1.y * e1.y + b * b * e2.y * e2.y)) * 1.000001f;
+  const float hz = sqrtf((float)(a * a * e1.z * e1.z + b * b * e2.z * e2.z)) * 1.000001f;
   box[0] = make_float4(__double2float_rd(fmin(c0.x, c1.x) - hx), __double2float_rd(fmin(c0.y, c1.y) - hy),
                        __double2float_rd(fmin(c0.z, c1.z) - hz), 0.f);
   box[1] = make_float4(__double2float_ru(fmax(c0.x, c1.x) + hx), __double2float_ru(fmax(c0.y, c1.y) + hy),
@@ -74,7 +78,22 @@ __device__ void duff_basis(d3 n, d3* b1, d3* b2) {
   *b2 = mk(b, sign + n.y * n.y * a, -n.y);
 }
 
-__global__ void k_strand_prims(const float4* __restrict__ verts, const float2* __restrict__ shape,
+// Per strand (FP64): cos(psi), sin(psi) and the semi-axes a, b of its
+// cross-section, so the segment kernel does no transcendental per segment.
+__global__ void k_strand_shape(const float4* __restrict__ verts, const float2* __restrict__ shape,
+                               uint32_t N, uint32_t S, double4_32a* out) {
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  const double r = verts[(size_t)s * (S + 1)].w;
+  const float2 sh = shape[s];
+  const double e = sh.x, psi = sh.y;
+  double sp, cp;
+  sincos(psi, &sp, &cp);
+  const double q = sqrt(sqrt(1.0 - e * e));
+  out[s] = make_double4_32a(cp, sp, r / q, r * q);
+}
+
+__global__ void k_strand_prims(const float4* __restrict__ verts, const double4_32a* __restrict__ sh4,
                                uint32_t N, uint32_t S, float4* xf, float4* box, float4* aux) {
   const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (uint64_t)N * S) return;
@@ -82,18 +101,16 @@ __global__ void k_strand_prims(const float4* __restrict__ verts, const float2* _
   const float4* P = verts + (size_t)s * (S + 1);
   const d3 p0 = ld3(P[k]), p1 = ld3(P[k + 1]);
   const double r = P[0].w;
-  const float2 sh = shape[s];
-  const double e = sh.x, psi = sh.y;
+  const double4_32a sh = sh4[s];
   d3 ax = p1 - p0;
   const double L = sqrt(dot(ax, ax));
   d3 e1 = mk(1, 0, 0);
   if (L > 0.0) {
     d3 b1, b2;
     duff_basis(ax * (1.0 / L), &b1, &b2);
-    e1 = b1 * cos(psi) + b2 * sin(psi);
+    e1 = b1 * sh.x + b2 * sh.y;
   }
-  const double q = pow(1.0 - e * e, 0.25);
-  const double a = r / q, b = r * q;
+  const double a = sh.z, b = sh.w;
   write_prim(xf + idx * 3, box + idx * 2, p0, p1, e1, a, b);
   aux[idx] = make_float4(__uint_as_float(s), 0.f, (float)r, (float)(a * b));
 }
@@ -277,7 +294,30 @@ __device__ void eigen3(const double C[3][3], double A[3][3], double V[3][3]) {
     for (int j = 0; j < 3; ++j) CV[i][j] = C[i][0] * V[0][j] + C[i][1] * V[1][j] + C[i][2] * V[2][j];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) A[i][j] = V[0][i] * CV[0][j] + V[1][i] * CV[1][j] + V[2][i] * CV[2][j];
-  jacobi_sweeps<double>(A, V, 16, 1e-36);
+  // A is diagonal up to ~1e-7 relative.  With well-separated diagonal entries
+  // the first-order correction v_i += sum_j A_ji / (A_ii - A_jj) v_j leaves an
+  // error of (off / gap)^2; otherwise finish with FP64 Jacobi sweeps.
+  const double d0 = A[0][0], d1 = A[1][1], d2 = A[2][2];
+  const double g01 = d0 - d1, g02 = d0 - d2, g12 = d1 - d2;
+  const double scale = fmax(fabs(d0), fmax(fabs(d1), fabs(d2)));
+  const double off = fmax(fabs(A[0][1]), fmax(fabs(A[0][2]), fabs(A[1][2])));
+  const double gap = fmin(fabs(g01), fmin(fabs(g02), fabs(g12)));
+  if (scale > 0.0 && gap > 1e-3 * scale && off < 1e-5 * gap) {
+    const double c01 = A[0][1] / g01, c02 = A[0][2] / g02, c12 = A[1][2] / g12;
+    double W[3][3];
+    for (int r = 0; r < 3; ++r) {
+      W[r][0] = V[r][0] + c01 * V[r][1] + c02 * V[r][2];
+      W[r][1] = V[r][1] - c01 * V[r][0] + c12 * V[r][2];
+      W[r][2] = V[r][2] - c02 * V[r][0] - c12 * V[r][1];
+    }
+    for (int r = 0; r < 3; ++r)
+      for (int j = 0; j < 3; ++j) V[r][j] = W[r][j];
+    A[0][1] = A[1][0] = A[0][2] = A[2][0] = A[1][2] = A[2][1] = 0.0;
+  } else {
+    // stop at an off-diagonal of ~3e-14 relative: the axes are then exact to
+    // far below the FP32 records they end up in
+    jacobi_sweeps<double>(A, V, 16, 1e-27);
+  }
 }
 
 // One thread per (thick hair, cross-section).  Writes the FP32 cross-section
@@ -366,26 +406,38 @@ __global__ void k_fit_cross_sections(const float4* __restrict__ verts, uint32_t 
   }
   e1 = normalize(e1 - t * dot(e1, t));
   const d3 e2 = cross(t, e1);
-  // pass 2: semi-axes; pass 3: the coverage scale (one square root)
-  double a = 0.0, b = 0.0;
+  // pass 2: semi-axes; pass 3: the coverage scale (one square root).  A
+  // member's offset from the centre is (p - p0) - (c - p0): the first
+  // difference of nearby floats is exact in FP32, the second term is the FP64
+  // mean shift rounded once, so the projections can run in FP32 (the results
+  // are stored as FP32 anyway).
+  const float e1x = (float)e1.x, e1y = (float)e1.y, e1z = (float)e1.z;
+  const float e2x = (float)e2.x, e2y = (float)e2.y, e2z = (float)e2.z;
+  const float p0x = (float)p0.x, p0y = (float)p0.y, p0z = (float)p0.z;
+  const float mfx = (float)mx, mfy = (float)my, mfz = (float)mz;
+  float af = 0.f, bf = 0.f;
   for (uint32_t i = 0; i < cnt; ++i) {
     const float4* P = verts + (size_t)__ldg(order + first + i) * (S + 1);
-    const d3 q = ld3(__ldg(P + k)) - ctr;
-    const double r = __ldg(&P[0].w);  // the strand's radius (root vertex)
-    a = fmax(a, fabs(dot(q, e1)) + r);
-    b = fmax(b, fabs(dot(q, e2)) + r);
+    const float4 pk = __ldg(P + k);
+    const float qx = (pk.x - p0x) - mfx, qy = (pk.y - p0y) - mfy, qz = (pk.z - p0z) - mfz;
+    const float r = __ldg(&P[0].w);  // the strand's radius (root vertex)
+    af = fmaxf(af, fabsf(fmaf(qx, e1x, fmaf(qy, e1y, qz * e1z))) + r);
+    bf = fmaxf(bf, fabsf(fmaf(qx, e2x, fmaf(qy, e2y, qz * e2z))) + r);
   }
-  const double ia = 1.0 / a, ib = 1.0 / b;
-  double s2 = 0.0;
+  const float ia = 1.0f / af, ib = 1.0f / bf;
+  float s2 = 0.f;
   for (uint32_t i = 0; i < cnt; ++i) {
-    const d3 q = ld3(__ldg(verts + (size_t)__ldg(order + first + i) * (S + 1) + k)) - ctr;
-    const double u = dot(q, e1) * ia, v = dot(q, e2) * ib;
-    s2 = fmax(s2, fma(u, u, v * v));
+    const float4 pk = __ldg(verts + (size_t)__ldg(order + first + i) * (S + 1) + k);
+    const float qx = (pk.x - p0x) - mfx, qy = (pk.y - p0y) - mfy, qz = (pk.z - p0z) - mfz;
+    const float u = fmaf(qx, e1x, fmaf(qy, e1y, qz * e1z)) * ia;
+    const float v = fmaf(qx, e2x, fmaf(qy, e2y, qz * e2z)) * ib;
+    s2 = fmaxf(s2, fmaf(u, u, v * v));
   }
-  if (s2 > 1.0) {
-    const double s = sqrt(s2);
-    a *= s;
-    b *= s;
+  double a = af, b = bf;
+  if (s2 > 1.f) {
+    const float sc = sqrtf(s2);
+    a = (double)(af * sc);
+    b = (double)(bf * sc);
   }
   float4* o = xsec + idx * 3;
   o[0] = make_float4((float)ctr.x, (float)ctr.y, (float)ctr.z, (float)a);
@@ -432,11 +484,12 @@ __global__ void k_eth_prims(const double* __restrict__ fit64, uint32_t N, uint32
   const double* f1 = f0 + 8;
   const d3 c0 = mk(f0[0], f0[1], f0[2]), c1 = mk(f1[0], f1[1], f1[2]);
   d3 ax = c1 - c0;
-  const double L = sqrt(dot(ax, ax));
+  const double L2 = dot(ax, ax);
   d3 e1 = mk(f0[3], f0[4], f0[5]);
-  if (L > 0.0) {
-    ax = ax * (1.0 / L);
-    e1 = normalize(e1 - ax * dot(e1, ax));
+  if (L2 > 0.0) {
+    ax = ax * rsqrt(L2);
+    e1 = e1 - ax * dot(e1, ax);
+    e1 = e1 * rsqrt(dot(e1, e1));
   }
   const double a = fmax(f0[6], f1[6]), b = fmax(f0[7], f1[7]);
   const uint64_t p = (uint64_t)N * S + idx;
@@ -513,7 +566,11 @@ hr_status build_strand_prims(hr_ctx* ctx, hr_asset* a) {
   HR_TRY(dalloc(ctx, (void**)&a->prim_box, n * 2 * sizeof(float4), "strand boxes"));
   HR_TRY(dalloc(ctx, (void**)&a->prim_aux, n * sizeof(float4), "strand aux"));
   a->bytes += n * 6 * sizeof(float4);
-  k_strand_prims<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a->verts, a->shape, a->N, a->S,
+  double4_32a* sh4 = nullptr;
+  HR_TRY(scratch(ctx, 6, (size_t)a->N * sizeof(double4_32a), (void**)&sh4));
+  k_strand_shape<<<(a->N + 255) / 256, 256, 0, st>>>(a->verts, a->shape, a->N, a->S, sh4);
+  HR_LAUNCHED(ctx);
+  k_strand_prims<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a->verts, sh4, a->N, a->S,
                                                              a->prim_xf, a->prim_box,
                                                              a->prim_aux);
   HR_LAUNCHED(ctx);
