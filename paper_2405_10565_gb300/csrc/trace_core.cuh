@@ -507,13 +507,13 @@ __device__ __forceinline__ void flush_counts(const FrameArgs& fa, const Counts& 
 }
 
 // Pixel-space rectangle (x0, y0, x1, y1) that contains the projection of the
-// BVH root box, grown by one pixel; computed by the first warp of a block and
-// returned to every thread through `rect`.  A pixel whose square lies outside
-// it cannot see any primitive.  The whole screen when the box reaches behind
-// the eye or the BVH has fewer than two leaves.  Call with the whole block.
-__device__ __forceinline__ void scene_rect(const FrameArgs& fa, float4* rect) {
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
+// BVH root box, grown by one pixel; computed by one warp (lanes 0-7 project
+// the box corners) and stored by lane 0.  A pixel whose square lies outside it
+// cannot see any primitive.  The whole screen when the box reaches behind the
+// eye or the BVH has fewer than two leaves.
+__device__ __forceinline__ void scene_rect_warp(const FrameArgs& fa, float4* rect) {
+  {
+    const int lane = threadIdx.x & 31;
     float X0 = kInf, Y0 = kInf, X1 = -kInf, Y1 = -kInf;
     bool ok = fa.n_prims >= 2;
     if (ok && lane < 8) {
@@ -550,6 +550,11 @@ __device__ __forceinline__ void scene_rect(const FrameArgs& fa, float4* rect) {
       *rect = ok ? make_float4(X0 - 1.f, Y0 - 1.f, X1 + 1.f, Y1 + 1.f)
                  : make_float4(-kInf, -kInf, kInf, kInf);
   }
+}
+
+// Block-wide version (the first warp computes, every thread reads `rect`).
+__device__ __forceinline__ void scene_rect(const FrameArgs& fa, float4* rect) {
+  if (threadIdx.x < 32) scene_rect_warp(fa, rect);
   __syncthreads();
 }
 
@@ -559,11 +564,10 @@ __device__ __forceinline__ void scene_rect(const FrameArgs& fa, float4* rect) {
 // outside `rect` are background.  All 32 lanes of every warp reach the
 // shuffles (no early return).
 template <int KMAX, int PREC, bool COUNT>
-__device__ __forceinline__ void render_tile(const FrameArgs& fa, uint32_t tile, const float4 rect,
-                                            float* __restrict__ rgb, Counts& cn, bool& overflow) {
+__device__ __forceinline__ void render_tile_xy(const FrameArgs& fa, uint32_t tx, uint32_t ty,
+                                               const float4 rect, float* __restrict__ rgb,
+                                               Counts& cn, bool& overflow) {
   const uint32_t G = fa.grp;
-  const uint32_t tiles_x = ((uint32_t)fa.cam.W + fa.tile_w - 1) / fa.tile_w;
-  const uint32_t tx = tile % tiles_x, ty = tile / tiles_x;
   const uint32_t lane_g = threadIdx.x & (G - 1);
   const uint32_t pib = threadIdx.x / G;  // pixel in block
   const uint32_t x = tx * fa.tile_w + pib % fa.tile_w;
@@ -598,6 +602,58 @@ __device__ __forceinline__ void render_tile(const FrameArgs& fa, uint32_t tile, 
     rgb[3 * pixel + 1] = acc[1] * inv;
     rgb[3 * pixel + 2] = acc[2] * inv;
   }
+}
+
+// Warp tile: the 32 / grp pixels one warp renders (wtw x wth); a pixel's
+// samples on `grp` adjacent lanes, summed with a fixed XOR-shuffle tree.
+// Called by whole warps.
+template <int KMAX, int PREC, bool COUNT>
+__device__ __forceinline__ void render_warp_tile(const FrameArgs& fa, uint32_t x0, uint32_t y0,
+                                                 uint32_t wtw, const float4 rect,
+                                                 float* __restrict__ rgb, Counts& cn,
+                                                 bool& overflow) {
+  const uint32_t G = fa.grp;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t lane_g = lane & (G - 1);
+  const uint32_t p = lane / G;
+  const uint32_t x = x0 + p % wtw, y = y0 + p / wtw;
+  const bool valid = x < (uint32_t)fa.cam.W && y < (uint32_t)fa.cam.H;
+  const bool inside = valid && (float)x + 1.f >= rect.x && (float)x <= rect.z &&
+                      (float)y + 1.f >= rect.y && (float)y <= rect.w;
+  const uint64_t pixel = (uint64_t)y * (uint32_t)fa.cam.W + x;
+  float acc[3] = {0.f, 0.f, 0.f};
+  if (inside) {
+    for (uint32_t s = lane_g; s < fa.spp; s += G) {
+      float v[3];
+      bool ok;
+      float3 o, d;
+      camera_ray_xy(fa.cam, fa.seed, pixel * fa.spp + s, x, y, o, d);
+      render_ray<KMAX, PREC, COUNT>(fa, o, d, v, nullptr, ok, cn);
+      if (COUNT) ++cn.rays;
+      overflow |= !ok;
+      acc[0] += v[0];
+      acc[1] += v[1];
+      acc[2] += v[2];
+    }
+  }
+  for (uint32_t o = 1; o < G; o <<= 1) {
+    acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
+    acc[1] += __shfl_xor_sync(0xffffffffu, acc[1], o);
+    acc[2] += __shfl_xor_sync(0xffffffffu, acc[2], o);
+  }
+  if (inside && lane_g == 0) {
+    const float inv = 1.0f / (float)fa.spp;
+    rgb[3 * pixel] = acc[0] * inv;
+    rgb[3 * pixel + 1] = acc[1] * inv;
+    rgb[3 * pixel + 2] = acc[2] * inv;
+  }
+}
+
+template <int KMAX, int PREC, bool COUNT>
+__device__ __forceinline__ void render_tile(const FrameArgs& fa, uint32_t tile, const float4 rect,
+                                            float* __restrict__ rgb, Counts& cn, bool& overflow) {
+  const uint32_t tiles_x = ((uint32_t)fa.cam.W + fa.tile_w - 1) / fa.tile_w;
+  render_tile_xy<KMAX, PREC, COUNT>(fa, tile % tiles_x, tile / tiles_x, rect, rgb, cn, overflow);
 }
 
 }  // namespace tr
