@@ -397,7 +397,8 @@ def stress(n: int = 500000, S: int = 64, width: int = 3840, height: int = 2160,
            spp: int = 16, n_clusters: int = 16384, seed: int = 0) -> Workload:
     """500k long straight strands x 64 segments, eccentricity 0.9, 16,384
     clusters; 3840x2160, 16 spp, 4 lights, k-buffer depth 8, FP16 tables."""
-    v = make_strands(n, S, seed=seed, length=2.0, jitter=0.0, radius=1e-3, droop=1.2)
+    v = make_strands(n, S, seed=seed, length=2.0, jitter=0.0, radius=1e-3, cap_deg=35.0,
+                     hang=0.05, spread=0.25)
     st = Stream(seed, 14)
     psi = 2.0 * math.pi * st.uniform(n)
     mel = 0.1 + 0.8 * st.uniform(n)
@@ -405,7 +406,7 @@ def stress(n: int = 500000, S: int = 64, width: int = 3840, height: int = 2160,
     sc = Scene(v, material_from_melanin(mel, rough),
                np.stack([np.full(n, 0.9), psi], -1).astype(np.float32), "stress")
     lo, hi = sc.aabb()
-    cam = frame_camera(lo, hi, width, height, perspective=True, fill=0.5)
+    cam = frame_camera(lo, hi, width, height, perspective=True, fill=0.3)
     lights = point_lights(4, 0.5 * (lo + hi), seed=seed)
     return Workload(f"stress_{n}x{S}_{width}x{height}_{spp}spp", sc, cam, lights, spp, 8,
                     n_clusters, lod_setting="select", precision=1)

@@ -344,3 +344,39 @@ def test_full_head_full_size_sampled(ctx):
         assert num <= RMSE_FP32 * np.linalg.norm(want[agree_px]) + 1e-12
     finally:
         hr.hr_asset_destroy(ctx, a)
+
+
+def _sampled_pixels(W, H, n_any, n_center, half_frac, seed):
+    st = scenegen.Stream(seed, 99)
+    pix = list((st.u64(n_any) % np.uint64(W * H)).astype(np.int64))
+    half = max(1, int(half_frac * H))
+    xs = (W // 2 - half + (st.u64(n_center) % np.uint64(2 * half))).astype(np.int64)
+    ys = (H // 2 - half + (st.u64(n_center) % np.uint64(2 * half))).astype(np.int64)
+    pix += list(ys * W + xs)
+    return np.unique(np.asarray(pix, np.int64))
+
+
+@pytest.mark.parametrize("setting", ["strands", "half", "eth"])
+def test_clustered_full_size_sampled(ctx, setting):
+    """The clustered workload at its full size (10,000 strands x 32 segments,
+    256 clusters, 512x512, 4 spp, 2 lights, K = 4) in each LoD setting, on
+    every sample of 256 seeded pixels."""
+    w = scenegen.clustered(lod_setting=setting)
+    W, H = w.camera.width, w.camera.height
+    pix = _sampled_pixels(W, H, 64, 192, 0.3, 5)
+    sids = scenegen.pixel_samples(W, w.spp, pix)
+    rg, hg, ro, ho = _render_check(ctx, w, sids)
+    assert (ho[:, 0] >= 0).mean() > 0.2
+
+
+def test_stress_sampled(ctx):
+    """The stress workload (500,000 long straight strands x 64 segments,
+    16,384 clusters, eccentricity 0.9, 3840x2160, 16 spp, 4 lights, K = 8, FP16
+    tables, LoD selected) on every sample of 12 seeded pixels on the hair: the
+    oracle runs brute force over tens of millions of primitives per sample."""
+    w = scenegen.stress()
+    W, H = w.camera.width, w.camera.height
+    pix = _sampled_pixels(W, H, 0, 12, 0.2, 6)
+    sids = scenegen.pixel_samples(W, w.spp, pix)
+    rg, hg, ro, ho = _render_check(ctx, w, sids)
+    print(f"stress: hit fraction {(ho[:, 0] >= 0).mean():.3f}")

@@ -478,3 +478,43 @@ def test_degenerate_cross_section_axis():
             _, _, f1, _, fa, fb = oracle.fit_cross_section(P[mem, k], T[mem, k], R[mem, 0])
             assert abs(abs(np.dot(eth.e1[e, k], f1)) - 1) < 1e-9
             assert eth.a[e, k] == pytest.approx(fa, rel=1e-9)
+
+
+def _thick_hair_row(c0, c1, e1, a, b, ntot, r):
+    return np.array([*c0, *c1, *e1, a, b, 1, 1, ntot, r], np.float64)
+
+
+def test_composite_front_to_back_with_closed_form_opacity():
+    # One circular thick hair (radius R, n_tot members of radius r) in front of
+    # an opaque strand.  A ray through the thick hair's axis has chord 2R, so
+    # its opacity is alpha = 1 - exp(-2 r (2R) n_tot / (pi R^2)); compositing
+    # must give render(thick hair alone) + (1 - alpha) * render(strand alone).
+    R, r, ntot = 0.05, 0.002, 20.0
+    eth = _thick_hair_row([0, -0.5, 0], [0, 0.5, 0], [1, 0, 0], R, R, ntot, r)
+    strand = np.array([0, -0.5, -0.2, 0, 0.5, -0.2, 1, 0, 0, 0.01, 0.01, 0, 0, 1, 0.01],
+                      np.float64)
+    mats = np.tile(scenegen.material_from_melanin(np.array([0.5]), np.array([0.2]))
+                   .astype(np.float64), (2, 1))
+    cam = scenegen.Camera(0, 1, 1, np.array([0, 0, 3], np.float32),
+                          np.array([1, 0, 0], np.float32), np.array([0, 1, 0], np.float32),
+                          np.array([0, 0, -1], np.float32), 1e6).pack()
+    lights = scenegen.directional_light((0.3, 0.5, 1.0))
+
+    def render(rows, ids):
+        prep = oracle.Prepared(np.ascontiguousarray(rows), np.asarray(ids, np.int64), mats,
+                               None, None, None)
+        rad, hit = oracle.render_samples(prep, cam, lights, np.array([0]), 1, 4, 1, threads=1)
+        return rad[0], hit[0]
+
+    both, hit = render(np.stack([eth, strand]), [5, 9])
+    a_only, ha = render(eth[None], [5])
+    s_only, hs = render(strand[None], [9])
+    alpha = 1 - math.exp(-2 * r * (2 * R) * ntot / (math.pi * R * R))
+    assert hit.tolist() == [5, 9, -1, -1] and ha[0] == 5 and hs[0] == 9
+    assert np.allclose(both, a_only + (1 - alpha) * s_only, rtol=1e-9)
+    # an opaque strand in front hides everything behind it
+    front = strand.copy()
+    front[[2, 5]] = 0.3
+    occl, h2 = render(np.stack([eth, front]), [5, 9])
+    f_only, _ = render(front[None], [9])
+    assert h2.tolist() == [9, -1, -1, -1] and np.allclose(occl, f_only, rtol=1e-12)
