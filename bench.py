@@ -220,9 +220,16 @@ def config_of(w, args):
 
 
 def run_serving(hr, ctx, torch, dev, n_requests: int, seed: int = 2):
-    """Seeded Poisson request stream (three assets of 10k/50k/100k strands x 64
-    segments, resolutions 256^2 / 720p / 1080p, 1-8 spp, LoD budget 0-4) through
-    the continuous-batching serving loop; latency = completion - arrival."""
+    """Seeded request stream (three assets of 10k/50k/100k strands x 64
+    segments, resolutions 256^2 / 720p / 1080p, 1-8 spp, LoD budget 0-4).
+
+    * plain: the plain FP32 renderer, one request after another through the C
+      ABI (LoD selection, BVH, frame) - the baseline of the served form;
+    * served, saturated: every request submitted at once to the continuous-
+      batching loop with FP16 lookup tables - aggregate throughput;
+    * served, Poisson arrivals at 80% of the saturated rate - latency
+      (completion minus submission) p50 / p99.
+    """
     import scenegen
     assets = []
     for i, n in enumerate((10000, 50000, 100000)):
@@ -234,47 +241,74 @@ def run_serving(hr, ctx, torch, dev, n_requests: int, seed: int = 2):
         hr.hr_build_clusters(ctx, a, wl.n_clusters)
         assets.append((a, wl))
     reqs = scenegen.serving_stream(n_requests, seed=seed, rate_hz=1.0)
-    descs = []
+    jobs = []
     for r in reqs:
         a, wl = assets[r["asset"]]
         lo, hi = wl.scene.aabb()
         cam = scenegen.frame_camera(lo, hi, r["width"], r["height"], perspective=True, fill=0.3)
-        d = hr.render_desc(cam.pack(), wl.lights, r["spp"], 4, r["seed"], precision=1)
-        descs.append((a, d, r))
-    outs = [torch.empty((r["height"], r["width"], 3), device=dev) for _, _, r in descs]
-    # calibrate: service time of the requests one at a time
-    hr.hr_serve_start(ctx, 16, 8 << 20)
+        jobs.append((a, cam, r))
+    outs = [torch.empty((r["height"], r["width"], 3), device=dev) for _, _, r in jobs]
+    total_samples = sum(r["width"] * r["height"] * r["spp"] for _, _, r in jobs)
+
+    # plain FP32 renderer, sequential
+    lods = {}
+    torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    for (a, d, r), o in zip(descs[:8], outs[:8]):
-        t = hr.hr_submit(ctx, a, d, o, 2.0, r["budget"])
-        hr.hr_poll(ctx, t, 60000)
-    per = (time.perf_counter() - t0) / 8
-    rate = 0.8 / per
-    arr = np.asarray([r["arrival_s"] for r in reqs]) / 1.0 / rate  # rescale the unit-rate stream
-    tickets = []
-    start = time.perf_counter()
-    for (a, d, r), o, at in zip(descs, outs, arr):
-        now = time.perf_counter() - start
-        if at > now:
-            time.sleep(at - now)
-        tickets.append((hr.hr_submit(ctx, a, d, o, 2.0, r["budget"]), at))
-    lat, samples, first, last = [], 0, None, 0.0
-    for (t, at), (_, _, r) in zip(tickets, descs):
-        st, res = hr.hr_poll(ctx, t, 600000)
-        if st != hr.HR_OK or res.status != hr.HR_OK:
-            raise RuntimeError(f"request failed: {st} {res.status}")
-        lat.append(res.done_ms - res.submit_ms)
-        samples += res.n_samples
-        last = max(last, res.done_ms)
-        first = res.submit_ms if first is None else min(first, res.submit_ms)
-    hr.hr_serve_stop(ctx)
-    for a, _ in assets:
-        hr.hr_asset_destroy(ctx, a)
+    for (a, cam, r), o in zip(jobs, outs):
+        C, L, E = hr.hr_hierarchy_info(ctx, a)
+        lod = lods.setdefault(C, torch.empty(C, dtype=torch.uint8, device=dev))
+        hr.hr_select_lod(ctx, a, cam.pack(), 2.0, 0, r["budget"], lod)
+        hr.hr_build_bvh(ctx, a, lod)
+        d = hr.render_desc(cam.pack(), assets[r["asset"]][1].lights, r["spp"], 4, r["seed"], 0)
+        hr.hr_render(ctx, a, d, o)
+    torch.cuda.synchronize(dev)
+    plain_s = time.perf_counter() - t0
+
+    descs = [hr.render_desc(cam.pack(), assets[r["asset"]][1].lights, r["spp"], 4, r["seed"], 1)
+             for a, cam, r in jobs]
+    hr.hr_serve_start(ctx, 16, 8 << 20)
+    try:
+        # warm the slots
+        for (a, cam, r), d, o in list(zip(jobs, descs, outs))[:16]:
+            hr.hr_poll(ctx, hr.hr_submit(ctx, a, d, o, 2.0, r["budget"]), 60000)
+        # saturated
+        t0 = time.perf_counter()
+        ts = [hr.hr_submit(ctx, a, d, o, 2.0, r["budget"])
+              for (a, cam, r), d, o in zip(jobs, descs, outs)]
+        for t in ts:
+            st, res = hr.hr_poll(ctx, t, 600000)
+            if st != hr.HR_OK or res.status != hr.HR_OK:
+                raise RuntimeError(f"request failed: {st} {res.status}")
+        sat_s = time.perf_counter() - t0
+        sat_rate = total_samples / sat_s
+        # Poisson arrivals at 80% of the saturated request rate
+        rate = 0.8 * len(jobs) / sat_s
+        arr = np.asarray([r["arrival_s"] for _, _, r in jobs]) / rate
+        tickets = []
+        start = time.perf_counter()
+        for (a, cam, r), d, o, at in zip(jobs, descs, outs, arr):
+            now = time.perf_counter() - start
+            if at > now:
+                time.sleep(at - now)
+            tickets.append(hr.hr_submit(ctx, a, d, o, 2.0, r["budget"]))
+        lat = []
+        for t in tickets:
+            st, res = hr.hr_poll(ctx, t, 600000)
+            if st != hr.HR_OK or res.status != hr.HR_OK:
+                raise RuntimeError(f"request failed: {st} {res.status}")
+            lat.append(res.done_ms - res.submit_ms)
+    finally:
+        hr.hr_serve_stop(ctx)
+        for a, _ in assets:
+            hr.hr_asset_destroy(ctx, a)
     lat = np.asarray(lat)
     return {"requests": n_requests, "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "msamples_per_s": samples / (last - first) / 1e3,
-            "arrival_rate_hz": rate, "precision": "fp16_tables",
-            "accuracy": "rel-RMSE <= 5e-3 vs the FP64 oracle (tests/test_serving.py)"}
+            "p99_ms": float(np.percentile(lat, 99)), "arrival_rate_hz": rate,
+            "served_fp16_msamples_per_s": sat_rate / 1e6,
+            "plain_fp32_sequential_msamples_per_s": total_samples / plain_s / 1e6,
+            "speedup_served_vs_plain": (total_samples / sat_s) / (total_samples / plain_s),
+            "accuracy": "FP16 tables: rel-RMSE <= 5e-3 vs the FP64 oracle (tests/test_serving.py, "
+                        "tests/test_gpu_parity.py::test_stress_sampled)"}
 
 
 # ------------------------------------------------------------------ main arm
@@ -283,7 +317,7 @@ def run_serving(hr, ctx, torch, dev, n_requests: int, seed: int = 2):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=250)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="full_head")
@@ -336,6 +370,12 @@ def main():
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(dev)
+    # the same frame with FP16 lookup tables (outside the timed region)
+    d16 = hr.render_desc(w.camera.pack(), w.lights, spp, w.k_depth, w.sample_seed, 1)
+    fp16_ms = statistics.median(hr.hr_render(ctx, asset, d16, img, stats=True).render_ms
+                                for _ in range(10))
+    fp32_ms = statistics.median(hr.hr_render(ctx, asset, desc, img, stats=True).render_ms
+                                for _ in range(10))
     # counting render (outside the timed region): events of the algorithmic FLOP model
     cdesc = hr.render_desc(w.camera.pack(), w.lights, spp, w.k_depth, w.sample_seed, w.precision,
                            hr.HR_FLAG_COUNT)
@@ -445,7 +485,8 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": config_of(w, args),
-            "frame_ms": render_avg, "active_prims": int(st.n_active_prims),
+            "frame_ms": render_avg, "frame_ms_fp32_warm": fp32_ms, "frame_ms_fp16_warm": fp16_ms,
+            "active_prims": int(st.n_active_prims),
             "eth_prims": int(st.n_eth_prims), "stack_overflows": int(st.stack_overflows),
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": e2e,

@@ -29,8 +29,17 @@ uint64_t ctx_budget(hr_ctx* ctx);
 
 namespace {
 
-struct Slot {
+// A BVH kept resident for an (asset, LoD) pair; requests with the same pair
+// share it.
+struct CachedBvh {
+  hr_asset* asset = nullptr;
+  std::vector<uint8_t> lod;
   Bvh bvh;
+  int refs = 0;
+  uint64_t last_use = 0;
+};
+
+struct Slot {
   uint8_t* lod = nullptr;
   uint32_t lod_cap = 0;
   float* out = nullptr;  // device staging when the caller's buffer is host memory
@@ -48,6 +57,7 @@ struct Request {
   bool host_out = false;
   bool finished_issue = false;
   cudaEvent_t done_ev = nullptr;
+  CachedBvh* entry = nullptr;
   int kmax = 1;
   FrameArgs fa{};
   float* dev_out = nullptr;
@@ -82,6 +92,10 @@ struct Server {
   int inject_nomem = 0;
   int64_t inject_delay = 0;
   uint64_t launches = 0;
+  cudaStream_t build_stream = nullptr;  // LoD + BVH builds, overlapping the batches
+  std::vector<CachedBvh*> cache;
+  uint64_t use_clock = 0;
+  uint64_t cache_hits = 0, cache_misses = 0;
 };
 
 namespace {
@@ -102,33 +116,54 @@ uint32_t request_tiles(const hr_render_desc& d) {
   return tiles_for(d.camera.width, d.camera.height, d.spp);
 }
 
-// Upper bound of the device bytes a request may add: a BVH over every
-// primitive of its asset, its LoD array and a device output when needed.
+// Upper bound of the device bytes admitting a request may add: a new resident
+// BVH over every primitive of its asset (as if its LoD were not cached), and
+// the growth of the slot's LoD and staging buffers.
 uint64_t estimate_bytes(const Request* r, const Slot& sl) {
-  // growth of the slot's grow-only buffers, bounding the active primitives by
-  // every primitive of the asset
   const hr_asset* a = r->req.asset;
-  const uint64_t P = a->n_prims_total;
-  uint64_t need = 0;
-  if (P > sl.bvh.cap) need += (P - sl.bvh.cap) * (4 * 16 + 3 * 16 + 16 + 4);
+  uint64_t need = (uint64_t)a->n_prims_total * (4 * 16 + 3 * 16 + 16 + 4);
   const size_t out = (size_t)r->req.desc.camera.width * r->req.desc.camera.height * 12;
   if (r->host_out && out > sl.out_cap) need += out - sl.out_cap;
   if (a->C > sl.lod_cap) need += a->C - sl.lod_cap;
   return need;
 }
 
-// Admission: LoD and BVH of one request into its slot (holding the API lock
-// so the context scratch is not shared with a concurrent call).
+constexpr size_t kMaxCached = 64;
+
+// Free the least recently used resident BVHs that no request holds, while
+// more than `keep` entries remain (keep = 0: every unreferenced one).
+void evict(Server* s, size_t keep) {
+  hr_ctx* ctx = s->ctx;
+  for (;;) {
+    if (s->cache.size() <= keep) return;
+    int victim = -1;
+    for (size_t i = 0; i < s->cache.size(); ++i)
+      if (s->cache[i]->refs == 0 &&
+          (victim < 0 || s->cache[i]->last_use < s->cache[victim]->last_use))
+        victim = (int)i;
+    if (victim < 0) return;
+    free_bvh(ctx, s->cache[victim]->bvh);
+    delete s->cache[victim];
+    s->cache.erase(s->cache.begin() + victim);
+  }
+}
+
+// Admission: LoD of one request, then its resident BVH (shared when the same
+// asset and LoD are already resident, built otherwise), on the build stream
+// and holding the API lock so the context scratch is not shared with a
+// concurrent call.
 hr_status admit(Server* s, Request* r) {
   hr_ctx* ctx = s->ctx;
   std::lock_guard<std::recursive_mutex> g(ctx_mutex(ctx));
+  cudaStream_t bs = s->build_stream;
   Slot& sl = s->slots[r->slot];
   hr_asset* a = r->req.asset;
   const uint8_t* lod = nullptr;
+  std::vector<uint8_t> lod_h;
   if (a->n_levels > 0) {
     if (sl.lod_cap < a->C) {
       if (sl.lod) {
-        cudaStreamSynchronize(s->stream);
+        cudaStreamSynchronize(bs);
         dfree(ctx, sl.lod, sl.lod_cap);
         sl.lod = nullptr;
         sl.lod_cap = 0;
@@ -137,10 +172,37 @@ hr_status admit(Server* s, Request* r) {
       sl.lod_cap = a->C;
     }
     HR_TRY(lod_select(ctx, a, &r->req.desc.camera, r->req.eps_w_px, 0, r->req.budget_bias,
-                      nullptr, sl.lod, s->stream));
+                      nullptr, sl.lod, bs));
     lod = sl.lod;
+    lod_h.resize(a->C);
+    HR_CUDA(ctx, cudaMemcpyAsync(lod_h.data(), sl.lod, a->C, cudaMemcpyDeviceToHost, bs));
+    HR_CUDA(ctx, cudaStreamSynchronize(bs));
   }
-  HR_TRY(build_bvh(ctx, a, lod, sl.bvh, s->stream));
+  CachedBvh* e = nullptr;
+  for (CachedBvh* c : s->cache)
+    if (c->asset == a && c->lod == lod_h) {
+      e = c;
+      break;
+    }
+  if (e) {
+    s->cache_hits++;
+  } else {
+    s->cache_misses++;
+    evict(s, kMaxCached - 1);
+    e = new CachedBvh();
+    e->asset = a;
+    e->lod = lod_h;
+    const hr_status st = build_bvh(ctx, a, lod, e->bvh, bs);
+    if (st != HR_OK) {
+      free_bvh(ctx, e->bvh);
+      delete e;
+      return st;
+    }
+    s->cache.push_back(e);
+  }
+  e->refs++;
+  e->last_use = ++s->use_clock;
+  r->entry = e;
   const size_t out = (size_t)r->req.desc.camera.width * r->req.desc.camera.height * 12;
   r->dev_out = r->req.rgb_out;
   if (r->host_out) {
@@ -156,10 +218,10 @@ hr_status admit(Server* s, Request* r) {
     }
     r->dev_out = sl.out;
   }
-  // the scratch used by the build is shared with API calls: finish before
-  // releasing the lock
-  HR_CUDA(ctx, cudaStreamSynchronize(s->stream));
-  r->fa = frame_args(ctx, a, sl.bvh, r->req.desc);
+  // the build must be complete before the batches (another stream) read it,
+  // and the scratch it used is shared with API calls
+  HR_CUDA(ctx, cudaStreamSynchronize(bs));
+  r->fa = frame_args(ctx, a, e->bvh, r->req.desc);
   r->kmax = kmax_for(r->req.desc.k_depth);
   r->tiles_total = request_tiles(r->req.desc);
   return HR_OK;
@@ -171,6 +233,10 @@ void finish(Server* s, Request* r, hr_status st, double done_ms) {
   r->ready_ms = ctx_now_ms(s->ctx) + (double)r->delay_ms;
   if (r->slot >= 0) s->slots[r->slot].busy = false;
   r->slot = -1;
+  if (r->entry) {
+    r->entry->refs--;
+    r->entry = nullptr;
+  }
 }
 
 void loop(Server* s) {
@@ -217,13 +283,13 @@ void loop(Server* s) {
         return need <= fr;
       };
       if (!fits()) {
-        // reclaim the resident buffers of idle slots, then retry
+        // reclaim unreferenced resident BVHs and idle slots' buffers, retry
         std::lock_guard<std::recursive_mutex> g(ctx_mutex(ctx));
         cudaStreamSynchronize(s->stream);
+        evict(s, 0);
         for (size_t i = 0; i < s->slots.size(); ++i) {
           Slot& sl = s->slots[i];
           if (sl.busy || (int)i == slot) continue;
-          free_bvh(ctx, sl.bvh);
           if (sl.lod) dfree(ctx, sl.lod, sl.lod_cap);
           if (sl.out) dfree(ctx, sl.out, sl.out_cap);
           sl.lod = nullptr;
@@ -357,6 +423,16 @@ void serve_forget_asset(hr_ctx* ctx, Server* s, hr_asset* a) {
     if (!busy) break;
     s->cv_done.wait_for(lk, std::chrono::milliseconds(1));
   }
+  for (size_t i = 0; i < s->cache.size();) {
+    CachedBvh* c = s->cache[i];
+    if (c->asset == a && c->refs == 0) {
+      free_bvh(ctx, c->bvh);
+      delete c;
+      s->cache.erase(s->cache.begin() + i);
+    } else {
+      ++i;
+    }
+  }
 }
 
 }  // namespace hr
@@ -379,6 +455,7 @@ hr_status hr_serve_start(hr_ctx* ctx, uint32_t max_slots, uint64_t max_batch_sam
   s->max_batch_samples = max_batch_samples;
   s->max_items = std::min<uint32_t>(kMaxItems, std::max<uint32_t>(max_slots, 1));
   bool ok = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&s->build_stream, cudaStreamNonBlocking) == cudaSuccess;
   for (int b = 0; b < 2 && ok; ++b) {
     const size_t ni = s->max_items;
     ok &= cudaMallocHost((void**)&s->h_items[b], ni * sizeof(ServeItem)) == cudaSuccess;
@@ -422,8 +499,13 @@ hr_status hr_serve_stop(hr_ctx* ctx) {
     if (r->done_ev) cudaEventDestroy(r->done_ev);
     delete r;
   }
+  if (s->build_stream) cudaStreamSynchronize(s->build_stream);
+  for (CachedBvh* c : s->cache) {
+    free_bvh(ctx, c->bvh);
+    delete c;
+  }
+  s->cache.clear();
   for (Slot& sl : s->slots) {
-    free_bvh(ctx, sl.bvh);
     if (sl.lod) dfree(ctx, sl.lod, sl.lod_cap);
     if (sl.out) dfree(ctx, sl.out, sl.out_cap);
   }
@@ -437,6 +519,7 @@ hr_status hr_serve_stop(hr_ctx* ctx) {
   if (s->d_work) dfree(ctx, s->d_work, 16);
   if (s->ref_ev) cudaEventDestroy(s->ref_ev);
   if (s->stream) cudaStreamDestroy(s->stream);
+  if (s->build_stream) cudaStreamDestroy(s->build_stream);
   delete s;
   *ctx_server_slot(ctx) = nullptr;
   return HR_OK;
