@@ -54,6 +54,17 @@ FLOPS_PER_STRAND_SHADE = 100  # light vector, angles, f_single (3 Gaussians), ac
 FLOPS_PER_ETH_SHADE = 250     # + albedo lookups, widened lobes, B lobe, S
 FLOPS_PER_HIT = 40            # tangent, outgoing angles, opacity, composite
 FLOPS_PER_SAMPLE = 30         # camera ray
+# FP64 operations of the cross-section fit (k_fit_cross_sections), same rules
+# (fabs free): per member the shifted centring sums (3 subtractions, 3
+# additions, 6 FMA) = 18; per cross-section the mean, centre and tangent (17),
+# covariance (18), trace scaling (13), Gram-Schmidt (40), V^T C V (90), gap
+# tests (14), first-order correction (39), axis order and choice (25), e1/e2
+# (30) = 286.  The FP32 seed and projections are not counted, nor the FP64
+# Jacobi fallback of near-degenerate sections: the model is a lower bound.
+FP64_FLOPS_PER_MEMBER = 18
+FP64_FLOPS_PER_SECTION = 286
+# Nominal FP64 rate of GB300 (the profiling recipe's table); nothing measures it.
+FP64_PEAK_TFLOPS = 1.25
 
 
 def sources_hash(names):
@@ -65,6 +76,22 @@ def sources_hash(names):
 
 
 TRACE_SOURCES = ["trace_core.cuh", "trace_frame.cu", "common.cuh"]
+FIT_SOURCES = ["hierarchy.cu", "common.cuh"]
+
+
+def traffic_record(name, sources, workload_name):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel's
+    sources are unchanged since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    try:
+        pj = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if pj.get("sources") == sources_hash(sources) and pj.get("workload") == workload_name:
+        return pj.get("dram_bytes_per_launch")
+    return None
 
 
 # ------------------------------------------------------------------ clocks
@@ -380,6 +407,7 @@ def main():
     cdesc = hr.render_desc(w.camera.pack(), w.lights, spp, w.k_depth, w.sample_seed, w.precision,
                            hr.HR_FLAG_COUNT)
     cst = hr.hr_render(ctx, asset, cdesc, img, stats=True)
+    n_levels_info = hr.hr_hierarchy_info(ctx, asset)
     flops = (FLOPS_PER_NODE * cst.node_visits + FLOPS_PER_TEST * cst.prim_tests +
              FLOPS_PER_STRAND_SHADE * cst.strand_shades + FLOPS_PER_ETH_SHADE * cst.eth_shades +
              FLOPS_PER_HIT * cst.shaded_hits + FLOPS_PER_SAMPLE * cst.traced_samples)
@@ -394,7 +422,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize(dev)
     launches0 = hr.hr_kernel_launches(ctx)
-    render_ms = []
+    render_ms, fit_ms = [], []
     with ClockSampler(uuid) as clk:
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -402,6 +430,7 @@ def main():
         for _ in range(args.steps):
             st = step()
             render_ms.append(st.render_ms)
+            fit_ms.append(st.fit_ms)
         e1.record(stream)
         e1.synchronize()
         torch.cuda.synchronize(dev)
@@ -458,26 +487,36 @@ def main():
     sm_max = clocks.get("sm_max_mhz") or 2070.0
     peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
     achieved = flops / (render_avg * 1e-3) / 1e12
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "k_frame_full_head_traffic.json")
-    if os.path.exists(prof):
-        try:
-            pj = json.load(open(prof))
-            if pj.get("sources") == sources_hash(TRACE_SOURCES) and pj.get("workload") == w.name:
-                traffic = pj.get("dram_bytes_per_launch")
-        except (OSError, ValueError):
-            traffic = None
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": traffic, "kernel": "k_frame (trace/shade/composite)",
-            "kernel_ms": render_avg, "flops_per_launch": flops,
-            "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 (FMA) x "
-                          f"{sm_max:.0f} MHz",
-            "frac_at_sampled_clock": (achieved / (peak * (clocks["sm_mhz"] or sm_max) / sm_max))
-            if clocks.get("sm_mhz") else None,
-            "events": {"node_visits": cst.node_visits, "prim_tests": cst.prim_tests,
-                       "strand_shades": cst.strand_shades, "eth_shades": cst.eth_shades,
-                       "hits": cst.shaded_hits, "traced_samples": cst.traced_samples,
-                       "samples": samples}}
+    roof_frame = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                  "frac": achieved / peak,
+                  "traffic": traffic_record("k_frame_full_head_traffic.json", TRACE_SOURCES, w.name),
+                  "kernel": "k_frame (trace/shade/composite, FP32)", "kernel_ms": render_avg,
+                  "flops_per_launch": flops,
+                  "peak_basis": f"FP32: {props.multi_processor_count} SMs x 128 lanes x 2 (FMA) x "
+                                f"{sm_max:.0f} MHz (derived from unit counts and clock)",
+                  "events": {"node_visits": cst.node_visits, "prim_tests": cst.prim_tests,
+                             "strand_shades": cst.strand_shades, "eth_shades": cst.eth_shades,
+                             "hits": cst.shaded_hits, "traced_samples": cst.traced_samples,
+                             "samples": samples}}
+    # FP64 work of the cross-section fit: every strand is a member of one thick
+    # hair per level, so the members sum to N * levels over S+1 sections
+    C_, L_, E_ = n_levels_info
+    fit_avg = statistics.mean(fit_ms)
+    fit_flops = (w.scene.n_segments + 1) * (FP64_FLOPS_PER_SECTION * E_ +
+                                            FP64_FLOPS_PER_MEMBER * w.scene.n_strands * L_)
+    fit_ach = fit_flops / (fit_avg * 1e-3) / 1e12 if fit_avg > 0 else 0.0
+    roof_fit = {"bound": "alu", "achieved": fit_ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": fit_ach / FP64_PEAK_TFLOPS,
+                "traffic": traffic_record("k_fit_cross_sections_full_head_traffic.json",
+                                          FIT_SOURCES, w.name),
+                "kernel": "k_fit_cross_sections (thick-hair fit, FP64)", "kernel_ms": fit_avg,
+                "flops_per_launch": fit_flops,
+                "peak_basis": "FP64: nominal GB300 rate from the profiling recipe's table "
+                              "(no measured FP64 peak)"}
+    dominant_fit = fit_avg >= render_avg
+    roof = dict(roof_fit if dominant_fit else roof_frame)
+    roof["dominant_by_time_in_step"] = True
+    other = roof_frame if dominant_fit else roof_fit
     cpu = None
     if not args.no_cpu_baseline:
         cpu = oracle_baseline(w, args.cpu_seconds)
@@ -488,7 +527,10 @@ def main():
             "frame_ms": render_avg, "frame_ms_fp32_warm": fp32_ms, "frame_ms_fp16_warm": fp16_ms,
             "active_prims": int(st.n_active_prims),
             "eth_prims": int(st.n_eth_prims), "stack_overflows": int(st.stack_overflows),
-            "roofline": roof, "cpu_baseline": cpu,
+            "roofline": roof, "roofline_other": other,
+            "phase_ms": {"hierarchy": st.hierarchy_ms, "fit": st.fit_ms, "lod": st.lod_ms,
+                         "bvh": st.bvh_ms, "render": st.render_ms},
+            "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks, "serving": serving}
     print(json.dumps(line))

@@ -145,6 +145,11 @@ typedef struct hr_stats {
   uint64_t shaded_hits;     /* hits composited */
   uint64_t traced_samples;  /* samples traced (pixels outside the scene's
                                projected bounds are background untraced) */
+  /* filled by hr_render_frame (CUDA events on the context stream, ms) */
+  double hierarchy_ms;      /* clusters, thick-hair fit, records (K1, K2) */
+  double fit_ms;            /* of which the FP64 cross-section fit kernel */
+  double lod_ms;            /* LoD widths and rule (K4) */
+  double bvh_ms;            /* compaction and LBVH (K5, K6) */
 } hr_stats;
 
 /* ---------------------------------------------------------------- context */

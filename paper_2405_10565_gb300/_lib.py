@@ -69,7 +69,9 @@ class hr_stats(ctypes.Structure):
     _fields_ = [("render_ms", ctypes.c_double), ("n_samples", c_u64), ("n_active_prims", c_u32),
                 ("n_eth_prims", c_u32), ("n_strand_prims", c_u32), ("stack_overflows", c_u32),
                 ("node_visits", c_u64), ("prim_tests", c_u64), ("strand_shades", c_u64),
-                ("eth_shades", c_u64), ("shaded_hits", c_u64), ("traced_samples", c_u64)]
+                ("eth_shades", c_u64), ("shaded_hits", c_u64), ("traced_samples", c_u64),
+                ("hierarchy_ms", ctypes.c_double), ("fit_ms", ctypes.c_double),
+                ("lod_ms", ctypes.c_double), ("bvh_ms", ctypes.c_double)]
 
 
 class hr_request(ctypes.Structure):

@@ -26,6 +26,7 @@ struct hr_ctx {
   std::string last_error;
   std::recursive_mutex api_mu;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ph[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   uint32_t* d_overflow = nullptr;
   unsigned long long* d_counters = nullptr;
   std::chrono::steady_clock::time_point t0;
@@ -222,6 +223,8 @@ hr_status hr_create(hr_ctx** out, int device, uint64_t hbm_budget, void* cuda_st
   hr_status st = HR_OK;
   if (cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess)
     st = HR_ECUDA;
+  for (int i = 0; i < 6 && st == HR_OK; ++i)
+    if (cudaEventCreate(&ctx->ph[i]) != cudaSuccess) st = HR_ECUDA;
   if (st == HR_OK) st = dalloc(ctx, (void**)&ctx->d_overflow, 64, "flags");
   if (st == HR_OK) st = dalloc(ctx, (void**)&ctx->d_counters, 8 * sizeof(unsigned long long), "counters");
   if (st == HR_OK) st = bake_tables(ctx, &ctx->im32, &ctx->im16, &ctx->gz16);
@@ -249,6 +252,8 @@ hr_status hr_destroy(hr_ctx* ctx) {
     if (ctx->d_counters) cudaFree(ctx->d_counters);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    for (int i = 0; i < 6; ++i)
+      if (ctx->ph[i]) cudaEventDestroy(ctx->ph[i]);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   }
   delete ctx;
@@ -553,17 +558,38 @@ hr_status hr_render_frame(hr_ctx* ctx, hr_asset* a, uint32_t n_clusters, float e
   HR_TRY(check_desc(ctx, desc));
   cudaStream_t st = ctx->stream;
   const uint8_t* lod_dev = nullptr;
+  // phase events: 0 start, 1 fit begin, 2 fit end, 3 hierarchy end, 4 LoD end, 5 BVH end
+  cudaEvent_t* ph = ctx->ph;
+  if (stats) HR_CUDA(ctx, cudaEventRecord(ph[0], st));
+  bool fit_ran = false;
   if (n_clusters > 0) {
     if (n_clusters > a->N) return set_error(ctx, HR_EINVAL, "n_clusters out of range");
-    HR_TRY(build_hierarchy(ctx, a, n_clusters, 0));
-    if (a->n_levels > 0) {
-      HR_TRY(lod_select(ctx, a, &desc->camera, eps_w_px, 0, budget_bias, nullptr, a->lod, st));
-      a->lod_valid = 1;
-      lod_dev = a->lod;
-    }
+    HR_TRY(build_hierarchy(ctx, a, n_clusters, 0, stats ? ph[1] : nullptr,
+                           stats ? ph[2] : nullptr));
+    fit_ran = a->E > 0;
   }
+  if (stats) HR_CUDA(ctx, cudaEventRecord(ph[3], st));
+  if (n_clusters > 0 && a->n_levels > 0) {
+    HR_TRY(lod_select(ctx, a, &desc->camera, eps_w_px, 0, budget_bias, nullptr, a->lod, st));
+    a->lod_valid = 1;
+    lod_dev = a->lod;
+  }
+  if (stats) HR_CUDA(ctx, cudaEventRecord(ph[4], st));
   HR_TRY(build_bvh(ctx, a, lod_dev, a->bvh, st));
-  return render_impl(ctx, a, desc, rgb_out, stats);
+  if (stats) HR_CUDA(ctx, cudaEventRecord(ph[5], st));
+  HR_TRY(render_impl(ctx, a, desc, rgb_out, stats));
+  if (stats) {
+    float h = 0.f, f = 0.f, l = 0.f, b = 0.f;
+    HR_CUDA(ctx, cudaEventElapsedTime(&h, ph[0], ph[3]));
+    if (fit_ran) HR_CUDA(ctx, cudaEventElapsedTime(&f, ph[1], ph[2]));
+    HR_CUDA(ctx, cudaEventElapsedTime(&l, ph[3], ph[4]));
+    HR_CUDA(ctx, cudaEventElapsedTime(&b, ph[4], ph[5]));
+    stats->hierarchy_ms = h;
+    stats->fit_ms = f;
+    stats->lod_ms = l;
+    stats->bvh_ms = b;
+  }
+  return HR_OK;
 }
 
 }  // extern "C"

@@ -138,7 +138,8 @@ cudaError_t morton_clusters_with(const float4* verts, uint32_t N, uint32_t S, ui
 
 // --- hierarchy.cu
 hr_status build_strand_prims(hr_ctx* ctx, hr_asset* a);
-hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_levels);
+hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_levels,
+                          cudaEvent_t fit_begin = nullptr, cudaEvent_t fit_end = nullptr);
 
 // --- lod.cu
 hr_status lod_widths(hr_ctx* ctx, hr_asset* a, const hr_camera* cam, float* wcl_dev,

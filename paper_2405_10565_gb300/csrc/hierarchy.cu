@@ -577,7 +577,8 @@ hr_status build_strand_prims(hr_ctx* ctx, hr_asset* a) {
   return scene_bounds(ctx, a, n);
 }
 
-hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_levels) {
+hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_levels,
+                          cudaEvent_t fit_begin, cudaEvent_t fit_end) {
   cudaStream_t st = ctx_stream(ctx);
   const uint32_t N = a->N, S = a->S;
   // level count: 1 + max k with 4^k <= floor(N/C)/2, capped
@@ -680,10 +681,12 @@ hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_lev
   HR_TRY(scratch(ctx, 4, (size_t)E * (S + 1) * 8 * sizeof(double), (void**)&fit64));
   HR_TRY(scratch(ctx, 5, (size_t)E * sizeof(float), (void**)&eth_r));
   const uint64_t nx = E * (S + 1);
+  if (fit_begin) HR_CUDA(ctx, cudaEventRecord(fit_begin, st));
   k_fit_cross_sections<<<(unsigned)((nx + 127) / 128), 128, 0, st>>>(a->verts, S, a->order,
                                                                     a->cl_first, li, (uint32_t)E,
                                                                     a->xsec, fit64);
   HR_LAUNCHED(ctx);
+  if (fit_end) HR_CUDA(ctx, cudaEventRecord(fit_end, st));
   k_eth_material<<<(unsigned)((E + 127) / 128), 128, 0, st>>>(a->verts, N, S, a->order,
                                                              a->cl_first, li, (uint32_t)E,
                                                              a->mat, eth_r);
