@@ -11,7 +11,9 @@
 // centroids in the scene bounds, stable radix sort of (code, id), one thread
 // per internal node finds its key range and split from the longest common
 // prefix (ties between equal codes broken by index), then bounds are
-// propagated bottom-up with one arrival counter per internal node.
+// propagated bottom-up with one arrival counter per internal node: in shared
+// memory for the nodes whose leaf range lies inside the thread block's leaves
+// (nearly all of them), in global memory for the few that span blocks.
 //
 // Node layout (4 x float4 = 64 bytes), children's boxes stored in the parent:
 //   n0 = (lo0.x, hi0.x, lo0.y, hi0.y)  n1 = (lo1.x, hi1.x, lo1.y, hi1.y)
@@ -126,7 +128,7 @@ __global__ void k_karras(const uint32_t* __restrict__ keys, int n, int4* child,
     c1 = gamma + 1;
     parent_int[gamma + 1] = i;
   }
-  child[i] = make_int4(c0, c1, 0, 0);
+  child[i] = make_int4(c0, c1, lo, hi);  // children and the node's leaf range
 }
 
 // Gather leaf records in Morton order.
@@ -164,14 +166,23 @@ __device__ __forceinline__ void lbox_read(const float4* lbox, int leaf, float* b
 // Leaf gather and bottom-up bounds in one pass: a thread copies its leaf's
 // record into Morton order, publishes the leaf box (leaf order, read by the
 // sibling's thread) and climbs; at every internal node the first arrival
-// stops, the second writes both child boxes.
-__global__ void k_gather_refit(const int4* __restrict__ child, const int* __restrict__ parent_int,
-                               const int* __restrict__ parent_leaf, const float4* __restrict__ box,
-                               const uint32_t* __restrict__ sorted_ids,
-                               const float4* __restrict__ xf, const float4* __restrict__ aux,
-                               int n, float4* nodes, float4* lbox, float4* leaf_xf,
-                               float4* leaf_aux, uint32_t* leaf_id, unsigned* arrivals) {
-  const int leaf = blockIdx.x * blockDim.x + threadIdx.x;
+// stops, the second writes both child boxes.  Node i's leaf range starts or
+// ends at leaf i, so a node whose range lies inside this block's leaves has
+// both arrivals in this block and counts them in shared memory (index
+// i - first leaf) behind block-scope fences; a node that spans blocks counts
+// them in global memory behind device-scope fences.
+template <int B>
+__global__ void __launch_bounds__(B) k_gather_refit(
+    const int4* __restrict__ child, const int* __restrict__ parent_int,
+    const int* __restrict__ parent_leaf, const float4* __restrict__ box,
+    const uint32_t* __restrict__ sorted_ids, const float4* __restrict__ xf,
+    const float4* __restrict__ aux, int n, float4* nodes, float4* lbox, float4* leaf_xf,
+    float4* leaf_aux, uint32_t* leaf_id, unsigned* arrivals) {
+  __shared__ unsigned s_arrivals[B];
+  s_arrivals[threadIdx.x] = 0u;
+  __syncthreads();
+  const int b0 = blockIdx.x * B;
+  const int leaf = b0 + threadIdx.x;
   if (leaf >= n) return;
   const uint32_t id = sorted_ids[leaf];
   leaf_xf[3 * (size_t)leaf] = xf[3 * (size_t)id];
@@ -183,17 +194,23 @@ __global__ void k_gather_refit(const int4* __restrict__ child, const int* __rest
   __stcg(lbox + 2 * leaf + 1, box[2 * (size_t)id + 1]);
   int node = parent_leaf[leaf];
   while (node >= 0) {
-    __threadfence();
-    if (atomicAdd(&arrivals[node], 1u) == 0) return;
-    __threadfence();
-    const int4 ch = child[node];
-    float b0[6], b1[6];
-    if (ch.x < 0) lbox_read(lbox, ~ch.x, b0); else node_union(nodes, ch.x, b0);
-    if (ch.y < 0) lbox_read(lbox, ~ch.y, b1); else node_union(nodes, ch.y, b1);
+    const int4 ch = __ldg(child + node);
+    if (ch.z >= b0 && ch.w < b0 + B) {
+      __threadfence_block();
+      if (atomicAdd(&s_arrivals[node - b0], 1u) == 0) return;
+      __threadfence_block();
+    } else {
+      __threadfence();
+      if (atomicAdd(&arrivals[node], 1u) == 0) return;
+      __threadfence();
+    }
+    float b0v[6], b1v[6];
+    if (ch.x < 0) lbox_read(lbox, ~ch.x, b0v); else node_union(nodes, ch.x, b0v);
+    if (ch.y < 0) lbox_read(lbox, ~ch.y, b1v); else node_union(nodes, ch.y, b1v);
     float4* o = nodes + 4 * node;
-    __stcg(o, make_float4(b0[0], b0[1], b0[2], b0[3]));
-    __stcg(o + 1, make_float4(b1[0], b1[1], b1[2], b1[3]));
-    __stcg(o + 2, make_float4(b0[4], b0[5], b1[4], b1[5]));
+    __stcg(o, make_float4(b0v[0], b0v[1], b0v[2], b0v[3]));
+    __stcg(o + 1, make_float4(b1v[0], b1v[1], b1v[2], b1v[3]));
+    __stcg(o + 2, make_float4(b0v[4], b0v[5], b1v[4], b1v[5]));
     __stcg(o + 3, make_float4(__int_as_float(ch.x), __int_as_float(ch.y), 0.f, 0.f));
     node = node == 0 ? -1 : parent_int[node];
   }
@@ -298,7 +315,7 @@ hr_status build_bvh(hr_ctx* ctx, hr_asset* a, const uint8_t* lod_dev, Bvh& bv, c
   HR_CUDA(ctx, cudaMemsetAsync(arrivals, 0, (size_t)n * 4, st));
   k_karras<<<(n - 1 + 255) / 256, 256, 0, st>>>(keys, (int)n, child, par_int, par_leaf);
   HR_LAUNCHED(ctx);
-  k_gather_refit<<<(n + 255) / 256, 256, 0, st>>>(child, par_int, par_leaf, a->prim_box, ids,
+  k_gather_refit<256><<<(n + 255) / 256, 256, 0, st>>>(child, par_int, par_leaf, a->prim_box, ids,
                                                   a->prim_xf, a->prim_aux, (int)n, bv.nodes,
                                                   lbox, bv.leaf_xf, bv.leaf_aux, bv.leaf_id,
                                                   arrivals);

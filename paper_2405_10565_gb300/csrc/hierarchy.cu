@@ -7,15 +7,17 @@
 //    the segment direction.
 //  * Clusters: deterministic Morton buckets of the strand roots (rank r of the
 //    (code, id) order joins cluster floor(r C / N)), split 4^k ways at level k.
-//  * Thick hairs: per cross-section k, FP64 mean centre, mean unit tangent,
-//    PCA of the members' k-th points (cyclic Jacobi), the axis closest to the
-//    tangent dropped, e1 the remaining axis with the larger eigenvalue, and
-//    semi-axes covering every member (Section 5.1 step 3 "Cross-section
-//    fitting").
+//  * Thick hairs: per cross-section k, mean centre, mean unit tangent, PCA of
+//    the members' k-th points, the axis closest to the tangent dropped, e1 the
+//    remaining axis with the larger eigenvalue, and semi-axes covering every
+//    member (Section 5.1 step 3 "Cross-section fitting").  The covariance and
+//    its eigen-decomposition are FP64; the members' centring sums are exact
+//    FP32 double-word sums (the FP64 rate of GB300 is 1/64 of its FP32 rate).
 //
 // A primitive record is the affine map from world space to the cylinder's
 // unit frame: rows (e1/a, -c0.e1/a), (e2/b, -c0.e2/b), (t/L, -c0.t/L); a ray
-// hits the open cylinder where u^2 + v^2 = 1 with w in [0, 1].
+// hits the open cylinder where u^2 + v^2 = 1 with w in [0, 1].  Records are
+// built in FP32 with compensated offsets (below); no FP64 outside the fit.
 #include <algorithm>
 #include <vector>
 
@@ -28,44 +30,107 @@ struct d3 {
   double x, y, z;
 };
 __device__ __forceinline__ d3 mk(double x, double y, double z) { return {x, y, z}; }
-__device__ __forceinline__ d3 operator+(d3 a, d3 b) { return mk(a.x + b.x, a.y + b.y, a.z + b.z); }
 __device__ __forceinline__ d3 operator-(d3 a, d3 b) { return mk(a.x - b.x, a.y - b.y, a.z - b.z); }
 __device__ __forceinline__ d3 operator*(d3 a, double s) { return mk(a.x * s, a.y * s, a.z * s); }
 __device__ __forceinline__ double dot(d3 a, d3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 __device__ __forceinline__ d3 cross(d3 a, d3 b) {
   return mk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
-__device__ __forceinline__ d3 normalize(d3 a) { return a * (1.0 / sqrt(dot(a, a))); }
 __device__ __forceinline__ d3 ld3(float4 v) { return mk(v.x, v.y, v.z); }
 
+// ------------------------------------------------ FP32 error-free transforms
+// Knuth's TwoSum: returns s = fl(a + b) and sets e with s + e == a + b
+// exactly (round to nearest, no overflow).  The _rn intrinsics keep the
+// compiler from contracting or reordering the steps.
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return s;
+}
+
+// Double-word FP32 sum hi + lo: hi is the running rounded sum, lo collects
+// every rounding error (Ogita, Rump and Oishi 2005, "Accurate sum and dot
+// product", algorithm Sum2).  Over n terms the error is about n^2 2^-48 of
+// the sum of magnitudes.
+struct ffsum {
+  float hi, lo;
+};
+__device__ __forceinline__ void ff_add(ffsum& s, float x, float x_lo) {
+  float e;
+  s.hi = two_sum(s.hi, x, e);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(e, x_lo));
+}
+// a[j] for j in {0, 1, 2} by selects (no local-memory indexing)
+__device__ __forceinline__ float pick3(const float a[3], int j) {
+  return j == 0 ? a[0] : (j == 1 ? a[1] : a[2]);
+}
+
+// Renormalise so |lo| <= ulp(hi) / 2 (keeps lo's own rounding small).
+__device__ __forceinline__ void ff_renorm(ffsum& s) {
+  float e;
+  s.hi = two_sum(s.hi, s.lo, e);
+  s.lo = e;
+}
+__device__ __forceinline__ double ff_value(const ffsum& s) { return (double)s.hi + (double)s.lo; }
+// s += (xh + xl) (yh + yl), with the exact product xh yh (the FMA form of
+// Dekker's TwoProduct) and the cross terms; xl yl (2^-48 relative) dropped.
+__device__ __forceinline__ void ff_add_prod(ffsum& s, float xh, float xl, float yh, float yl) {
+  const float p = __fmul_rn(xh, yh);
+  const float pe = fmaf(xh, yh, -p);
+  const float c = fmaf(xh, yl, __fmul_rn(xl, yh));
+  ff_add(s, p, __fadd_rn(pe, c));
+}
+
+// Compensated dot product of FP32 3-vectors (Ogita, Rump and Oishi, Dot2):
+// as accurate as if computed in twice the working precision, then rounded.
+__device__ __forceinline__ float dot_comp(float3 a, float3 b) {
+  ffsum s{0.f, 0.f};
+  ff_add_prod(s, a.x, 0.f, b.x, 0.f);
+  ff_add_prod(s, a.y, 0.f, b.y, 0.f);
+  ff_add_prod(s, a.z, 0.f, b.z, 0.f);
+  return __fadd_rn(s.hi, s.lo);
+}
+
+__device__ __forceinline__ float3 sub3(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 mul3(float3 a, float s) { return make_float3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float dotf(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ float3 crossf(float3 a, float3 b) {
+  return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
 // World -> unit elliptic cylinder rows and a conservative AABB of the
-// segment c0 -> c1 with semi-axis a along e1 and b along e2 = t x e1.
-__device__ void write_prim(float4* xf, float4* box, d3 c0, d3 c1, d3 e1, double a, double b) {
-  d3 ax = c1 - c0;
-  const double L2 = dot(ax, ax);
-  if (!(L2 > 0.0)) {
+// segment c0 -> c1 with semi-axis a along e1 (unit, normal to the axis) and b
+// along e2 = t x e1.  FP32 throughout: every row is within a few ulps of the
+// correctly rounded value, and each offset is the compensated dot product of
+// the stored row with c0, so the stored cylinder passes through c0 to within
+// the offset's own rounding.
+__device__ void write_prim(float4* xf, float4* box, float3 c0, float3 c1, float3 e1, float a, float b) {
+  const float3 ax = sub3(c1, c0);
+  const float L2 = dotf(ax, ax);
+  if (!(L2 > 0.f)) {
     xf[0] = xf[1] = xf[2] = make_float4(0.f, 0.f, 0.f, 0.f);
-    box[0] = make_float4((float)c0.x, (float)c0.y, (float)c0.z, 0.f);
+    box[0] = make_float4(c0.x, c0.y, c0.z, 0.f);
     box[1] = box[0];
     return;
   }
-  const double iL = rsqrt(L2);
-  const d3 t = ax * iL;
-  const d3 e2 = cross(t, e1);
-  const double ia = 1.0 / a, ib = 1.0 / b;
-  const d3 r0 = e1 * ia, r1 = e2 * ib, r2 = t * iL;
-  xf[0] = make_float4((float)r0.x, (float)r0.y, (float)r0.z, (float)(-dot(c0, e1) * ia));
-  xf[1] = make_float4((float)r1.x, (float)r1.y, (float)r1.z, (float)(-dot(c0, e2) * ib));
-  xf[2] = make_float4((float)r2.x, (float)r2.y, (float)r2.z, (float)(-dot(c0, t) * iL));
-  // half extents of the elliptic disc per axis, grown by 1e-6 relative so the
-  // FP32 square root stays conservative; the corners are rounded outward
-  const float hx = sqrtf((float)(a * a * e1.x * e1.x + b * b * e2.x * e2.x)) * 1.000001f;
-  const float hy = sqrtf((float)(a * a * e1.y * e1.y + b * b * e2.y * e2.y)) * 1.000001f;
-  const float hz = sqrtf((float)(a * a * e1.z * e1.z + b * b * e2.z * e2.z)) * 1.000001f;
-  box[0] = make_float4(__double2float_rd(fmin(c0.x, c1.x) - hx), __double2float_rd(fmin(c0.y, c1.y) - hy),
-                       __double2float_rd(fmin(c0.z, c1.z) - hz), 0.f);
-  box[1] = make_float4(__double2float_ru(fmax(c0.x, c1.x) + hx), __double2float_ru(fmax(c0.y, c1.y) + hy),
-                       __double2float_ru(fmax(c0.z, c1.z) + hz), 0.f);
+  const float3 t = mul3(ax, 1.0f / sqrtf(L2));
+  const float3 e2 = crossf(t, e1);
+  const float ia = 1.0f / a, ib = 1.0f / b;
+  const float3 r0 = mul3(e1, ia), r1 = mul3(e2, ib), r2 = mul3(ax, 1.0f / L2);
+  xf[0] = make_float4(r0.x, r0.y, r0.z, -dot_comp(r0, c0));
+  xf[1] = make_float4(r1.x, r1.y, r1.z, -dot_comp(r1, c0));
+  xf[2] = make_float4(r2.x, r2.y, r2.z, -dot_comp(r2, c0));
+  // half extents of the elliptic disc per axis, grown by 2e-6 relative (the
+  // FP32 terms carry a few ulps); the corners are rounded outward
+  const float ga = 1.000002f;
+  const float hx = sqrtf(fmaf(a * e1.x, a * e1.x, (b * e2.x) * (b * e2.x))) * ga;
+  const float hy = sqrtf(fmaf(a * e1.y, a * e1.y, (b * e2.y) * (b * e2.y))) * ga;
+  const float hz = sqrtf(fmaf(a * e1.z, a * e1.z, (b * e2.z) * (b * e2.z))) * ga;
+  box[0] = make_float4(__fsub_rd(fminf(c0.x, c1.x), hx), __fsub_rd(fminf(c0.y, c1.y), hy),
+                       __fsub_rd(fminf(c0.z, c1.z), hz), 0.f);
+  box[1] = make_float4(__fadd_ru(fmaxf(c0.x, c1.x), hx), __fadd_ru(fmaxf(c0.y, c1.y), hy),
+                       __fadd_ru(fmaxf(c0.z, c1.z), hz), 0.f);
 }
 
 // Orthonormal basis around a unit vector (Duff, Burgess, Christensen, Hery,
@@ -77,42 +142,50 @@ __device__ void duff_basis(d3 n, d3* b1, d3* b2) {
   *b1 = mk(1.0 + sign * n.x * n.x * a, sign * b, -sign * n.x);
   *b2 = mk(b, sign + n.y * n.y * a, -n.y);
 }
-
-// Per strand (FP64): cos(psi), sin(psi) and the semi-axes a, b of its
-// cross-section, so the segment kernel does no transcendental per segment.
-__global__ void k_strand_shape(const float4* __restrict__ verts, const float2* __restrict__ shape,
-                               uint32_t N, uint32_t S, double4_32a* out) {
-  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= N) return;
-  const double r = verts[(size_t)s * (S + 1)].w;
-  const float2 sh = shape[s];
-  const double e = sh.x, psi = sh.y;
-  double sp, cp;
-  sincos(psi, &sp, &cp);
-  const double q = sqrt(sqrt(1.0 - e * e));
-  out[s] = make_double4_32a(cp, sp, r / q, r * q);
+__device__ void duff_basis_f(float3 n, float3* b1, float3* b2) {
+  const float sign = copysignf(1.0f, n.z);
+  const float a = -1.0f / (sign + n.z);
+  const float b = n.x * n.y * a;
+  *b1 = make_float3(1.0f + sign * n.x * n.x * a, sign * b, -sign * n.x);
+  *b2 = make_float3(b, sign + n.y * n.y * a, -n.y);
 }
 
-__global__ void k_strand_prims(const float4* __restrict__ verts, const double4_32a* __restrict__ sh4,
+// Per strand: cos(psi), sin(psi) and the semi-axes a, b of its cross-section
+// (equal area to the circle of radius r), so the segment kernel does no
+// transcendental per segment.
+__global__ void k_strand_shape(const float4* __restrict__ verts, const float2* __restrict__ shape,
+                               uint32_t N, uint32_t S, float4* out) {
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  const float r = verts[(size_t)s * (S + 1)].w;
+  const float2 sh = shape[s];
+  float sp, cp;
+  sincosf(sh.y, &sp, &cp);
+  const float q = sqrtf(sqrtf(fmaf(-sh.x, sh.x, 1.0f)));
+  out[s] = make_float4(cp, sp, r / q, r * q);
+}
+
+__global__ void k_strand_prims(const float4* __restrict__ verts, const float4* __restrict__ sh4,
                                uint32_t N, uint32_t S, float4* xf, float4* box, float4* aux) {
   const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (uint64_t)N * S) return;
   const uint32_t s = (uint32_t)(idx / S), k = (uint32_t)(idx % S);
   const float4* P = verts + (size_t)s * (S + 1);
-  const d3 p0 = ld3(P[k]), p1 = ld3(P[k + 1]);
-  const double r = P[0].w;
-  const double4_32a sh = sh4[s];
-  d3 ax = p1 - p0;
-  const double L = sqrt(dot(ax, ax));
-  d3 e1 = mk(1, 0, 0);
-  if (L > 0.0) {
-    d3 b1, b2;
-    duff_basis(ax * (1.0 / L), &b1, &b2);
-    e1 = b1 * sh.x + b2 * sh.y;
+  const float4 v0 = __ldg(P + k), v1 = __ldg(P + k + 1);
+  const float3 p0 = make_float3(v0.x, v0.y, v0.z), p1 = make_float3(v1.x, v1.y, v1.z);
+  const float r = __ldg(&P[0].w);
+  const float4 sh = __ldg(sh4 + s);
+  const float3 ax = sub3(p1, p0);
+  const float L2 = dotf(ax, ax);
+  float3 e1 = make_float3(1.f, 0.f, 0.f);
+  if (L2 > 0.f) {
+    float3 b1, b2;
+    duff_basis_f(mul3(ax, 1.0f / sqrtf(L2)), &b1, &b2);
+    e1 = make_float3(fmaf(b1.x, sh.x, b2.x * sh.y), fmaf(b1.y, sh.x, b2.y * sh.y),
+                     fmaf(b1.z, sh.x, b2.z * sh.y));
   }
-  const double a = sh.z, b = sh.w;
-  write_prim(xf + idx * 3, box + idx * 2, p0, p1, e1, a, b);
-  aux[idx] = make_float4(__uint_as_float(s), 0.f, (float)r, (float)(a * b));
+  write_prim(xf + idx * 3, box + idx * 2, p0, p1, e1, sh.z, sh.w);
+  aux[idx] = make_float4(__uint_as_float(s), 0.f, r, sh.z * sh.w);
 }
 
 // ------------------------------------------------------------ Morton clusters
@@ -261,26 +334,41 @@ __device__ void jacobi_sweeps(T A[3][3], T V[3][3], int max_sweeps, T rel_tol) {
   }
 }
 
-// Eigen-decomposition of a symmetric 3x3 covariance to FP64 accuracy: an FP32
-// Jacobi solve of the trace-normalised matrix gives a basis that is already
-// diagonalising to ~1e-7, the basis is re-orthonormalised in FP64, the matrix
-// is rotated into it in FP64 and FP64 Jacobi sweeps finish the job (they
-// converge quadratically from there, so one or two sweeps suffice).  The FP64
-// rate of this part is the limit of the fit, hence the FP32 start.
-__device__ void eigen3(const double C[3][3], double A[3][3], double V[3][3]) {
-  const double tr = C[0][0] + C[1][1] + C[2][2];
-  float Af[3][3], Vf[3][3];
-  const double inv = tr > 0.0 ? 1.0 / tr : 0.0;
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) {
-      Af[i][j] = (float)(C[i][j] * inv);
-      Vf[i][j] = (i == j) ? 1.f : 0.f;
-    }
-  if (tr > 0.0) jacobi_sweeps<float>(Af, Vf, 8, 1e-12f);
+// 1/g for a double g whose magnitude lies in [1e-30, 1e30]: the FP32
+// reciprocal refined by one Newton-Raphson step r (2 - g r) in FP64, which
+// squares its relative error (~6e-8 -> ~4e-15).
+__device__ __forceinline__ double recip_nr(double g) {
+  const double r = (double)(1.0f / (float)g);
+  return r * fma(-g, r, 2.0);
+}
+// 1/sqrt(x) for x in [1e-30, 1e30]: the FP32 estimate refined by one Newton
+// step y (3 - x y^2) / 2 in FP64 (relative error ~1.5 d^2 for an estimate
+// error d of a few 1e-7).
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  const double y = (double)rsqrtf((float)x);
+  return y * fma(-0.5 * x * y, y, 1.5);
+}
+// Normalise a vector whose length is already 1 to about 1e-6 (the columns of
+// an FP32 rotation): 1/sqrt(1 + h) = 1 - h/2 + 3h^2/8 - ..., whose first
+// omitted term is below 0.32 |h|^3 (< 4e-19 here); otherwise an exact division.
+__device__ __forceinline__ d3 normalize_near_unit(d3 v) {
+  const double h = dot(v, v) - 1.0;
+  if (fabs(h) < 1e-6) return v * fma(h, fma(0.375, h, -0.5), 1.0);
+  return v * (1.0 / sqrt(h + 1.0));
+}
+
+// FP64 refinement of an FP32 eigenbasis Vf of the symmetric 3x3 covariance C
+// (used where the eigenvalues are too close for the FP32 basis): the basis is
+// re-orthonormalised in FP64, C is rotated into it in FP64, and a first-order
+// FP64 correction of the basis (or, for nearly equal eigenvalues, FP64 Jacobi
+// sweeps) finishes the job.  On return A's diagonal holds the eigenvalues and
+// V's columns the vectors.
+__device__ void eigen3_refine(const double C[3][3], const float Vf[3][3], double A[3][3],
+                              double V[3][3]) {
   // FP64 Gram-Schmidt of the FP32 basis
-  d3 v0 = normalize(mk(Vf[0][0], Vf[1][0], Vf[2][0]));
+  const d3 v0 = normalize_near_unit(mk(Vf[0][0], Vf[1][0], Vf[2][0]));
   d3 v1 = mk(Vf[0][1], Vf[1][1], Vf[2][1]);
-  v1 = normalize(v1 - v0 * dot(v1, v0));
+  v1 = normalize_near_unit(v1 - v0 * dot(v1, v0));
   const d3 v2 = cross(v0, v1);
   const d3 cols[3] = {v0, v1, v2};
   for (int j = 0; j < 3; ++j) {
@@ -288,22 +376,25 @@ __device__ void eigen3(const double C[3][3], double A[3][3], double V[3][3]) {
     V[1][j] = cols[j].y;
     V[2][j] = cols[j].z;
   }
-  // A = V^T C V
-  double CV[3][3];
+  // A = V^T C V (symmetric: the upper triangle is computed and mirrored)
+  d3 CV[3];
+  for (int j = 0; j < 3; ++j)
+    CV[j] = mk(C[0][0] * cols[j].x + C[0][1] * cols[j].y + C[0][2] * cols[j].z,
+               C[1][0] * cols[j].x + C[1][1] * cols[j].y + C[1][2] * cols[j].z,
+               C[2][0] * cols[j].x + C[2][1] * cols[j].y + C[2][2] * cols[j].z);
   for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) CV[i][j] = C[i][0] * V[0][j] + C[i][1] * V[1][j] + C[i][2] * V[2][j];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) A[i][j] = V[0][i] * CV[0][j] + V[1][i] * CV[1][j] + V[2][i] * CV[2][j];
-  // A is diagonal up to ~1e-7 relative.  With well-separated diagonal entries
-  // the first-order correction v_i += sum_j A_ji / (A_ii - A_jj) v_j leaves an
-  // error of (off / gap)^2; otherwise finish with FP64 Jacobi sweeps.
+    for (int j = i; j < 3; ++j) A[i][j] = A[j][i] = dot(cols[i], CV[j]);
+  // With well-separated diagonal entries the first-order correction
+  // v_i += sum_j A_ji / (A_ii - A_jj) v_j leaves an error of (off / gap)^2;
+  // otherwise finish with FP64 Jacobi sweeps.
   const double d0 = A[0][0], d1 = A[1][1], d2 = A[2][2];
   const double g01 = d0 - d1, g02 = d0 - d2, g12 = d1 - d2;
   const double scale = fmax(fabs(d0), fmax(fabs(d1), fabs(d2)));
   const double off = fmax(fabs(A[0][1]), fmax(fabs(A[0][2]), fabs(A[1][2])));
   const double gap = fmin(fabs(g01), fmin(fabs(g02), fabs(g12)));
-  if (scale > 0.0 && gap > 1e-3 * scale && off < 1e-5 * gap) {
-    const double c01 = A[0][1] / g01, c02 = A[0][2] / g02, c12 = A[1][2] / g12;
+  if (scale > 1e-27 && scale < 1e27 && gap > 1e-3 * scale && off < 1e-5 * gap) {
+    const double c01 = A[0][1] * recip_nr(g01), c02 = A[0][2] * recip_nr(g02),
+                 c12 = A[1][2] * recip_nr(g12);
     double W[3][3];
     for (int r = 0; r < 3; ++r) {
       W[r][0] = V[r][0] + c01 * V[r][1] + c02 * V[r][2];
@@ -320,46 +411,19 @@ __device__ void eigen3(const double C[3][3], double A[3][3], double V[3][3]) {
   }
 }
 
-// One thread per (thick hair, cross-section).  Writes the FP32 cross-section
-// record used by the LoD widths and the FP64 values the segments are built from.
-// The centring sums, the eigen-decomposition and the semi-axes are FP64; the
-// members' unit tangents (which only pick the dropped axis and orient e1, e2)
-// are summed in FP32.
-__global__ void k_fit_cross_sections(const float4* __restrict__ verts, uint32_t S,
-                                     const uint32_t* __restrict__ order,
-                                     const uint32_t* __restrict__ cl_first, LevelInfo li,
-                                     uint32_t E, float4* xsec, double* fit64) {
-  const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (uint64_t)E * (S + 1)) return;
-  const uint32_t e = (uint32_t)(idx / (S + 1)), k = (uint32_t)(idx % (S + 1));
-  uint32_t first, cnt, c, lv;
-  eth_members(li, cl_first, e, &first, &cnt, &c, &lv);
-  const double n = cnt, inv_n = 1.0 / n;
-  const uint32_t k0 = k > 0 ? k - 1 : 0, k1 = k < S ? k + 1 : S;
-  // pass 1: sums of the offsets from the first member (centring in FP64 with
-  // a shift, so the second moments do not cancel) and of the unit tangents
-  const d3 p0 = ld3(__ldg(verts + (size_t)order[first] * (S + 1) + k));
-  double s1x = 0, s1y = 0, s1z = 0, sxx = 0, sxy = 0, sxz = 0, syy = 0, syz = 0, szz = 0;
-  float tx = 0.f, ty = 0.f, tz = 0.f;
-  for (uint32_t i = 0; i < cnt; ++i) {
-    const float4* P = verts + (size_t)__ldg(order + first + i) * (S + 1);
-    const float4 pk = __ldg(P + k), pa = __ldg(P + k0), pb = __ldg(P + k1);
-    const double dx = (double)pk.x - p0.x, dy = (double)pk.y - p0.y, dz = (double)pk.z - p0.z;
-    s1x += dx; s1y += dy; s1z += dz;
-    sxx = fma(dx, dx, sxx); sxy = fma(dx, dy, sxy); sxz = fma(dx, dz, sxz);
-    syy = fma(dy, dy, syy); syz = fma(dy, dz, syz); szz = fma(dz, dz, szz);
-    const float gx = pb.x - pa.x, gy = pb.y - pa.y, gz = pb.z - pa.z;
-    const float ig = rsqrtf(gx * gx + gy * gy + gz * gz);
-    tx += gx * ig; ty += gy * ig; tz += gz * ig;
-  }
-  const double mx = s1x * inv_n, my = s1y * inv_n, mz = s1z * inv_n;
-  const d3 ctr = mk(p0.x + mx, p0.y + my, p0.z + mz);
-  const d3 t = normalize(mk(tx, ty, tz));
-  const double C[3][3] = {{sxx * inv_n - mx * mx, sxy * inv_n - mx * my, sxz * inv_n - mx * mz},
-                          {sxy * inv_n - mx * my, syy * inv_n - my * my, syz * inv_n - my * mz},
-                          {sxz * inv_n - mx * mz, syz * inv_n - my * mz, szz * inv_n - mz * mz}};
+// e1 of a cross-section from the FP64 eigen-decomposition (the careful path:
+// nearly equal eigenvalues, a near tie for the dropped axis, a covariance out
+// of FP32 range).  The eigenvector most aligned with the tangent t is
+// dropped and e1 is the remaining one with the larger eigenvalue; when the
+// two kept eigenvalues are equal, e1 points to the member farthest from the
+// centre in the plane normal to t (first in rank order), else along the Duff
+// basis vector b1 of t.
+__device__ d3 major_axis_fp64(const double C[3][3], const float Vf[3][3], const d3 t,
+                              const d3 ctr, const float4* __restrict__ verts, uint32_t S,
+                              uint32_t k, const uint32_t* __restrict__ order, uint32_t first,
+                              uint32_t cnt) {
   double A[3][3], V[3][3];
-  eigen3(C, A, V);
+  eigen3_refine(C, Vf, A, V);
   // ascending eigenvalues (stable for ties)
   int ord[3] = {0, 1, 2};
   for (int i = 1; i < 3; ++i)
@@ -382,9 +446,6 @@ __global__ void k_fit_cross_sections(const float4* __restrict__ verts, uint32_t 
   d3 e1 = mk(V[0][keep], V[1][keep], V[2][keep]);
   const double lmax = A[ord[2]][ord[2]];
   if (A[keep][keep] - A[keep0][keep0] <= 1e-9 * lmax || !(lmax > 0.0)) {
-    // the two kept axes have equal variance: e1 toward the member farthest
-    // from the centre in the plane normal to t (first in rank order), else the
-    // Duff basis vector b1 of t
     double best_d2 = 0.0;
     d3 far = mk(0, 0, 0);
     for (uint32_t i = 0; i < cnt; ++i) {
@@ -404,16 +465,151 @@ __global__ void k_fit_cross_sections(const float4* __restrict__ verts, uint32_t 
       e1 = b1;
     }
   }
-  e1 = normalize(e1 - t * dot(e1, t));
-  const d3 e2 = cross(t, e1);
+  return e1;
+}
+
+// One thread per (thick hair, cross-section).  Writes the FP32 cross-section
+// record (c, a) (e1, b) (e2, 0) that the LoD widths and the thick-hair
+// segments are built from.
+//  * Centring sums: the members' offsets d = p - p0 from the first member are
+//    exact FP32 pairs (TwoSum) and their first and second moments double-word
+//    FP32 sums (exact products, every rounding error kept, renormalised every
+//    64 members), folded into FP64 once: within ~2^-48 of exact, like FP64
+//    sums, at a fraction of their cost.
+//  * Covariance: FP64.  Eigenbasis: cyclic Jacobi in FP32 on the
+//    trace-normalised covariance; the kept axis e1 is then corrected to first
+//    order from its FP64 residual r = C v - (v.Cv) v, which is where the
+//    conditioning needs FP64 (the residual is a small difference of large
+//    terms).  The FP32 basis is off by e ~ 3e-7 / gap and the correction
+//    leaves ~e^2, so it is taken while every gap between e1's eigenvalue and
+//    the others is at least 1e-2 of the largest (e^2 < 1e-9);
+//    closer eigenvalues, a near tie for the dropped axis and covariances out
+//    of FP32 range take the full FP64 solve above.
+//  * Unit tangents (which only pick the dropped axis and orient e1, e2) and
+//    the member projections for the semi-axes: FP32.
+__global__ void k_fit_cross_sections(const float4* __restrict__ verts, uint32_t S,
+                                     const uint32_t* __restrict__ order,
+                                     const uint32_t* __restrict__ cl_first, LevelInfo li,
+                                     uint32_t E, float4* xsec) {
+  const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (uint64_t)E * (S + 1)) return;
+  const uint32_t e = (uint32_t)(idx / (S + 1)), k = (uint32_t)(idx % (S + 1));
+  uint32_t first, cnt, c, lv;
+  eth_members(li, cl_first, e, &first, &cnt, &c, &lv);
+  const uint32_t k0 = k > 0 ? k - 1 : 0, k1 = k < S ? k + 1 : S;
+  const float4 q0 = __ldg(verts + (size_t)__ldg(order + first) * (S + 1) + k);
+  const float p0x = q0.x, p0y = q0.y, p0z = q0.z;
+  // pass 1: sums of the offsets from the first member and of the unit tangents
+  ffsum fx{0.f, 0.f}, fy{0.f, 0.f}, fz{0.f, 0.f};
+  ffsum fxx{0.f, 0.f}, fxy{0.f, 0.f}, fxz{0.f, 0.f}, fyy{0.f, 0.f}, fyz{0.f, 0.f}, fzz{0.f, 0.f};
+  float tx = 0.f, ty = 0.f, tz = 0.f;
+  for (uint32_t i = 0; i < cnt; ++i) {
+    const float4* P = verts + (size_t)__ldg(order + first + i) * (S + 1);
+    const float4 pk = __ldg(P + k), pa = __ldg(P + k0), pb = __ldg(P + k1);
+    float dxl, dyl, dzl;
+    const float dx = two_sum(pk.x, -p0x, dxl), dy = two_sum(pk.y, -p0y, dyl),
+                dz = two_sum(pk.z, -p0z, dzl);
+    ff_add(fx, dx, dxl);
+    ff_add(fy, dy, dyl);
+    ff_add(fz, dz, dzl);
+    ff_add_prod(fxx, dx, dxl, dx, dxl);
+    ff_add_prod(fxy, dx, dxl, dy, dyl);
+    ff_add_prod(fxz, dx, dxl, dz, dzl);
+    ff_add_prod(fyy, dy, dyl, dy, dyl);
+    ff_add_prod(fyz, dy, dyl, dz, dzl);
+    ff_add_prod(fzz, dz, dzl, dz, dzl);
+    const float gx = pb.x - pa.x, gy = pb.y - pa.y, gz = pb.z - pa.z;
+    const float ig = rsqrtf(gx * gx + gy * gy + gz * gz);
+    tx += gx * ig;
+    ty += gy * ig;
+    tz += gz * ig;
+    if ((i & 63u) == 63u) {
+      ff_renorm(fx); ff_renorm(fy); ff_renorm(fz);
+      ff_renorm(fxx); ff_renorm(fxy); ff_renorm(fxz);
+      ff_renorm(fyy); ff_renorm(fyz); ff_renorm(fzz);
+    }
+  }
+  const double inv_n = recip_nr((double)cnt);
+  const double mx = ff_value(fx) * inv_n, my = ff_value(fy) * inv_n, mz = ff_value(fz) * inv_n;
+  const double sxx = ff_value(fxx), sxy = ff_value(fxy), sxz = ff_value(fxz);
+  const double syy = ff_value(fyy), syz = ff_value(fyz), szz = ff_value(fzz);
+  const d3 ctr = mk(p0x + mx, p0y + my, p0z + mz);
+  const float itn = rsqrtf(tx * tx + ty * ty + tz * tz);
+  const float tfx = tx * itn, tfy = ty * itn, tfz = tz * itn;
+  const double C[3][3] = {{sxx * inv_n - mx * mx, sxy * inv_n - mx * my, sxz * inv_n - mx * mz},
+                          {sxy * inv_n - mx * my, syy * inv_n - my * my, syz * inv_n - my * mz},
+                          {sxz * inv_n - mx * mz, syz * inv_n - my * mz, szz * inv_n - mz * mz}};
+  // FP32 Jacobi on the trace-normalised covariance
+  const double tr = C[0][0] + C[1][1] + C[2][2];
+  const bool seed = tr > 1e-30 && tr < 1e30;
+  const float inv_tr = seed ? 1.0f / (float)tr : 0.f;
+  float Af[3][3], Vf[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      Af[i][j] = (float)C[i][j] * inv_tr;
+      Vf[i][j] = (i == j) ? 1.f : 0.f;
+    }
+  if (seed) jacobi_sweeps<float>(Af, Vf, 10, 1e-13f);
+  // FP32 choice of the dropped and kept axes (as in the FP64 path); columns
+  // are picked with selects so the basis stays in registers
+  const float lam3[3] = {Af[0][0], Af[1][1], Af[2][2]};
+  int o0 = 0, o1 = 1, o2 = 2;  // ascending eigenvalue order (stable)
+  if (pick3(lam3, o1) < pick3(lam3, o0)) { const int tt = o0; o0 = o1; o1 = tt; }
+  if (pick3(lam3, o2) < pick3(lam3, o1)) { const int tt = o1; o1 = o2; o2 = tt; }
+  if (pick3(lam3, o1) < pick3(lam3, o0)) { const int tt = o0; o0 = o1; o1 = tt; }
+  float dd3[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) dd3[j] = fabsf(Vf[0][j] * tfx + Vf[1][j] * tfy + Vf[2][j] * tfz);
+  const float da = pick3(dd3, o0), db = pick3(dd3, o1), dc = pick3(dd3, o2);
+  int drop = 0;
+  float best = da, second = -1.f;
+  if (db > best) { second = best; best = db; drop = 1; } else { second = db; }
+  if (dc > best) { second = best; best = dc; drop = 2; } else if (dc > second) { second = dc; }
+  const int keep = drop == 2 ? o1 : o2, keep0 = drop == 0 ? o1 : o0;
+  const int dcol = drop == 0 ? o0 : (drop == 1 ? o1 : o2);
+  const float lk = pick3(lam3, keep), lmax = pick3(lam3, o2);
+  const float ga = lk - pick3(lam3, keep0), gb = lk - pick3(lam3, dcol);
+  float e1x, e1y, e1z;
+  if (seed && lmax > 0.f && fminf(ga, fabsf(gb)) >= 1e-2f * lmax && best - second > 1e-4f) {
+    // FP64 residual of the FP32 vector v, then v += sum_j (v_j . r) / (l_k - l_j) v_j
+    const float vx = pick3(Vf[0], keep), vy = pick3(Vf[1], keep), vz = pick3(Vf[2], keep);
+    const float ax = pick3(Vf[0], keep0), ay = pick3(Vf[1], keep0), az = pick3(Vf[2], keep0);
+    const float bx = pick3(Vf[0], dcol), by = pick3(Vf[1], dcol), bz = pick3(Vf[2], dcol);
+    const d3 v = mk(vx, vy, vz);
+    const d3 w = mk(C[0][0] * v.x + C[0][1] * v.y + C[0][2] * v.z,
+                    C[1][0] * v.x + C[1][1] * v.y + C[1][2] * v.z,
+                    C[2][0] * v.x + C[2][1] * v.y + C[2][2] * v.z);
+    const double lam = dot(v, w), sc = (double)inv_tr;
+    const float rx = (float)((w.x - lam * v.x) * sc), ry = (float)((w.y - lam * v.y) * sc),
+                rz = (float)((w.z - lam * v.z) * sc);
+    const float ca = (ax * rx + ay * ry + az * rz) / ga;
+    const float cb = (bx * rx + by * ry + bz * rz) / gb;
+    e1x = vx + ca * ax + cb * bx;
+    e1y = vy + ca * ay + cb * by;
+    e1z = vz + ca * az + cb * bz;
+  } else {
+    const d3 e1 = major_axis_fp64(C, Vf, mk(tfx, tfy, tfz), ctr, verts, S, k, order, first, cnt);
+    e1x = (float)e1.x;
+    e1y = (float)e1.y;
+    e1z = (float)e1.z;
+  }
+  // e1 made normal to t and unit, e2 = t x e1
+  {
+    const float d = e1x * tfx + e1y * tfy + e1z * tfz;
+    e1x -= d * tfx;
+    e1y -= d * tfy;
+    e1z -= d * tfz;
+    const float in1 = 1.0f / sqrtf(e1x * e1x + e1y * e1y + e1z * e1z);
+    e1x *= in1;
+    e1y *= in1;
+    e1z *= in1;
+  }
+  const float e2x = tfy * e1z - tfz * e1y, e2y = tfz * e1x - tfx * e1z, e2z = tfx * e1y - tfy * e1x;
   // pass 2: semi-axes; pass 3: the coverage scale (one square root).  A
   // member's offset from the centre is (p - p0) - (c - p0): the first
-  // difference of nearby floats is exact in FP32, the second term is the FP64
-  // mean shift rounded once, so the projections can run in FP32 (the results
-  // are stored as FP32 anyway).
-  const float e1x = (float)e1.x, e1y = (float)e1.y, e1z = (float)e1.z;
-  const float e2x = (float)e2.x, e2y = (float)e2.y, e2z = (float)e2.z;
-  const float p0x = (float)p0.x, p0y = (float)p0.y, p0z = (float)p0.z;
+  // difference is rounded once in FP32 (exact when the two floats are within
+  // a factor of two), the second term is the FP64 mean shift rounded once, so
+  // the projections run in FP32 (the results are stored as FP32 anyway).
   const float mfx = (float)mx, mfy = (float)my, mfz = (float)mz;
   float af = 0.f, bf = 0.f;
   for (uint32_t i = 0; i < cnt; ++i) {
@@ -433,23 +629,20 @@ __global__ void k_fit_cross_sections(const float4* __restrict__ verts, uint32_t 
     const float v = fmaf(qx, e2x, fmaf(qy, e2y, qz * e2z)) * ib;
     s2 = fmaxf(s2, fmaf(u, u, v * v));
   }
-  double a = af, b = bf;
+  float a = af, b = bf;
   if (s2 > 1.f) {
     const float sc = sqrtf(s2);
-    a = (double)(af * sc);
-    b = (double)(bf * sc);
+    a = af * sc;
+    b = bf * sc;
   }
   float4* o = xsec + idx * 3;
-  o[0] = make_float4((float)ctr.x, (float)ctr.y, (float)ctr.z, (float)a);
-  o[1] = make_float4((float)e1.x, (float)e1.y, (float)e1.z, (float)b);
-  o[2] = make_float4((float)e2.x, (float)e2.y, (float)e2.z, 0.f);
-  double* f = fit64 + idx * 8;
-  f[0] = ctr.x; f[1] = ctr.y; f[2] = ctr.z;
-  f[3] = e1.x; f[4] = e1.y; f[5] = e1.z;
-  f[6] = a; f[7] = b;
+  o[0] = make_float4((float)ctr.x, (float)ctr.y, (float)ctr.z, a);
+  o[1] = make_float4(e1x, e1y, e1z, b);
+  o[2] = make_float4(e2x, e2y, e2z, 0.f);
 }
 
-// Mean member material and radius of every thick hair (FP64 sums).
+// Mean member material and radius of every thick hair (double-word FP32
+// sums, so the mean is the correctly rounded one to within an ulp).
 __global__ void k_eth_material(const float4* __restrict__ verts, uint32_t N, uint32_t S,
                                const uint32_t* __restrict__ order,
                                const uint32_t* __restrict__ cl_first, LevelInfo li, uint32_t E,
@@ -458,45 +651,46 @@ __global__ void k_eth_material(const float4* __restrict__ verts, uint32_t N, uin
   if (e >= E) return;
   uint32_t first, cnt, c, lv;
   eth_members(li, cl_first, e, &first, &cnt, &c, &lv);
-  double acc[HR_MAT_FLOATS];
-  for (int j = 0; j < HR_MAT_FLOATS; ++j) acc[j] = 0.0;
-  double rs = 0.0;
+  ffsum acc[HR_MAT_FLOATS];
+  for (int j = 0; j < HR_MAT_FLOATS; ++j) acc[j] = ffsum{0.f, 0.f};
+  ffsum rs{0.f, 0.f};
   for (uint32_t i = 0; i < cnt; ++i) {
     const uint32_t s = order[first + i];
-    for (int j = 0; j < HR_MAT_FLOATS; ++j) acc[j] += mat[(size_t)s * HR_MAT_FLOATS + j];
-    rs += verts[(size_t)s * (S + 1)].w;
+    for (int j = 0; j < HR_MAT_FLOATS; ++j) ff_add(acc[j], mat[(size_t)s * HR_MAT_FLOATS + j], 0.f);
+    ff_add(rs, verts[(size_t)s * (S + 1)].w, 0.f);
   }
+  const float fn = (float)cnt;
   for (int j = 0; j < HR_MAT_FLOATS; ++j)
-    mat[(size_t)(N + e) * HR_MAT_FLOATS + j] = (float)(acc[j] / cnt);
-  eth_r[e] = (float)(rs / cnt);
+    mat[(size_t)(N + e) * HR_MAT_FLOATS + j] = __fadd_rn(acc[j].hi, acc[j].lo) / fn;
+  eth_r[e] = __fadd_rn(rs.hi, rs.lo) / fn;
 }
 
 // Thick-hair segment (e, k): axis c_k -> c_{k+1}, e1 = e1_k made orthogonal to
 // the axis, semi-axes the larger of the two cross-sections'.
-__global__ void k_eth_prims(const double* __restrict__ fit64, uint32_t N, uint32_t S, uint32_t E,
+__global__ void k_eth_prims(const float4* __restrict__ xsec, uint32_t N, uint32_t S, uint32_t E,
                             const uint32_t* __restrict__ cl_first, LevelInfo li,
                             const float* __restrict__ eth_r, float4* xf, float4* box,
                             float4* aux) {
   const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (uint64_t)E * S) return;
   const uint32_t e = (uint32_t)(idx / S), k = (uint32_t)(idx % S);
-  const double* f0 = fit64 + ((size_t)e * (S + 1) + k) * 8;
-  const double* f1 = f0 + 8;
-  const d3 c0 = mk(f0[0], f0[1], f0[2]), c1 = mk(f1[0], f1[1], f1[2]);
-  d3 ax = c1 - c0;
-  const double L2 = dot(ax, ax);
-  d3 e1 = mk(f0[3], f0[4], f0[5]);
-  if (L2 > 0.0) {
-    ax = ax * rsqrt(L2);
-    e1 = e1 - ax * dot(e1, ax);
-    e1 = e1 * rsqrt(dot(e1, e1));
+  const float4* x0 = xsec + ((size_t)e * (S + 1) + k) * 3;
+  const float4 q0 = __ldg(x0), q1 = __ldg(x0 + 1), r0 = __ldg(x0 + 3), r1 = __ldg(x0 + 4);
+  const float3 c0 = make_float3(q0.x, q0.y, q0.z), c1 = make_float3(r0.x, r0.y, r0.z);
+  const float3 ax = sub3(c1, c0);
+  const float L2 = dotf(ax, ax);
+  float3 e1 = make_float3(q1.x, q1.y, q1.z);
+  if (L2 > 0.f) {
+    const float3 t = mul3(ax, 1.0f / sqrtf(L2));
+    e1 = sub3(e1, mul3(t, dotf(e1, t)));
+    e1 = mul3(e1, 1.0f / sqrtf(dotf(e1, e1)));
   }
-  const double a = fmax(f0[6], f1[6]), b = fmax(f0[7], f1[7]);
+  const float a = fmaxf(q0.w, r0.w), b = fmaxf(q1.w, r1.w);
   const uint64_t p = (uint64_t)N * S + idx;
   write_prim(xf + p * 3, box + p * 2, c0, c1, e1, a, b);
   uint32_t first, cnt, c, lv;
   eth_members(li, cl_first, e, &first, &cnt, &c, &lv);
-  aux[p] = make_float4(__uint_as_float(N + e), (float)cnt, eth_r[e], (float)(a * b));
+  aux[p] = make_float4(__uint_as_float(N + e), (float)cnt, eth_r[e], a * b);
 }
 
 // Scene bounds over all primitive boxes (ordered-bit atomics).
@@ -566,8 +760,8 @@ hr_status build_strand_prims(hr_ctx* ctx, hr_asset* a) {
   HR_TRY(dalloc(ctx, (void**)&a->prim_box, n * 2 * sizeof(float4), "strand boxes"));
   HR_TRY(dalloc(ctx, (void**)&a->prim_aux, n * sizeof(float4), "strand aux"));
   a->bytes += n * 6 * sizeof(float4);
-  double4_32a* sh4 = nullptr;
-  HR_TRY(scratch(ctx, 6, (size_t)a->N * sizeof(double4_32a), (void**)&sh4));
+  float4* sh4 = nullptr;
+  HR_TRY(scratch(ctx, 6, (size_t)a->N * sizeof(float4), (void**)&sh4));
   k_strand_shape<<<(a->N + 255) / 256, 256, 0, st>>>(a->verts, a->shape, a->N, a->S, sh4);
   HR_LAUNCHED(ctx);
   k_strand_prims<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a->verts, sh4, a->N, a->S,
@@ -674,17 +868,16 @@ hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_lev
   }
   if (E == 0) return scene_bounds(ctx, a, total);
 
-  // K2: FP64 cross-section fits, materials and thick-hair segment records
+  // K2: cross-section fits (FP64 covariance and eigenvectors), materials and
+  // thick-hair segment records
   HR_TRY(dalloc(ctx, (void**)&a->xsec, (size_t)E * (S + 1) * 3 * sizeof(float4), "cross-sections"));
-  double* fit64 = nullptr;
   float* eth_r = nullptr;
-  HR_TRY(scratch(ctx, 4, (size_t)E * (S + 1) * 8 * sizeof(double), (void**)&fit64));
   HR_TRY(scratch(ctx, 5, (size_t)E * sizeof(float), (void**)&eth_r));
   const uint64_t nx = E * (S + 1);
   if (fit_begin) HR_CUDA(ctx, cudaEventRecord(fit_begin, st));
   k_fit_cross_sections<<<(unsigned)((nx + 127) / 128), 128, 0, st>>>(a->verts, S, a->order,
                                                                     a->cl_first, li, (uint32_t)E,
-                                                                    a->xsec, fit64);
+                                                                    a->xsec);
   HR_LAUNCHED(ctx);
   if (fit_end) HR_CUDA(ctx, cudaEventRecord(fit_end, st));
   k_eth_material<<<(unsigned)((E + 127) / 128), 128, 0, st>>>(a->verts, N, S, a->order,
@@ -692,7 +885,7 @@ hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_lev
                                                              a->mat, eth_r);
   HR_LAUNCHED(ctx);
   const uint64_t ne = E * S;
-  k_eth_prims<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(fit64, N, S, (uint32_t)E,
+  k_eth_prims<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(a->xsec, N, S, (uint32_t)E,
                                                            a->cl_first, li, eth_r, a->prim_xf,
                                                            a->prim_box, a->prim_aux);
   HR_LAUNCHED(ctx);
