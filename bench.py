@@ -54,15 +54,15 @@ FLOPS_PER_STRAND_SHADE = 100  # light vector, angles, f_single (3 Gaussians), ac
 FLOPS_PER_ETH_SHADE = 250     # + albedo lookups, widened lobes, B lobe, S
 FLOPS_PER_HIT = 40            # tangent, outgoing angles, opacity, composite
 FLOPS_PER_SAMPLE = 30         # camera ray
-# FP64 operations of the cross-section fit (k_fit_cross_sections), same rules
-# (fabs free): per member the shifted centring sums (3 subtractions, 3
-# additions, 6 FMA) = 18; per cross-section the mean, centre and tangent (17),
-# covariance (18), trace scaling (13), Gram-Schmidt (40), V^T C V (90), gap
-# tests (14), first-order correction (39), axis order and choice (25), e1/e2
-# (30) = 286.  The FP32 seed and projections are not counted, nor the FP64
-# Jacobi fallback of near-degenerate sections: the model is a lower bound.
-FP64_FLOPS_PER_MEMBER = 18
-FP64_FLOPS_PER_SECTION = 286
+# FP64 operations of the cross-section fit (k_fit_cross_sections), same rules:
+# per member none (the centring sums are exact FP32 double-word sums); per
+# cross-section the fold of the 9 sums (9), 1/n and the mean and centre (9),
+# the covariance (18), its trace (2) and the FP64 residual of the kept axis
+# (C v, v.Cv, r, scaling: 29) = 67.  The FP32 eigen-solve, tangents and
+# projections are not counted, nor the full FP64 solve that nearly
+# degenerate sections take: the model is a lower bound.
+FP64_FLOPS_PER_MEMBER = 0
+FP64_FLOPS_PER_SECTION = 67
 # Nominal FP64 rate of GB300 (the profiling recipe's table); nothing measures it.
 FP64_PEAK_TFLOPS = 1.25
 

@@ -163,14 +163,49 @@ __device__ __forceinline__ void lbox_read(const float4* lbox, int leaf, float* b
   b[0] = l.x; b[1] = h.x; b[2] = l.y; b[3] = h.y; b[4] = l.z; b[5] = h.z;
 }
 
-// Leaf gather and bottom-up bounds in one pass: a thread copies its leaf's
-// record into Morton order, publishes the leaf box (leaf order, read by the
-// sibling's thread) and climbs; at every internal node the first arrival
-// stops, the second writes both child boxes.  Node i's leaf range starts or
-// ends at leaf i, so a node whose range lies inside this block's leaves has
-// both arrivals in this block and counts them in shared memory (index
-// i - first leaf) behind block-scope fences; a node that spans blocks counts
-// them in global memory behind device-scope fences.
+// Bounds of an internal node, from two child boxes (lo.x, hi.x, lo.y, hi.y,
+// lo.z, hi.z), as the node record and as the union.
+__device__ __forceinline__ void store_node(float4* nodes, int node, int4 ch, const float* c0,
+                                           const float* c1) {
+  float4* o = nodes + 4 * node;
+  __stcg(o, make_float4(c0[0], c0[1], c0[2], c0[3]));
+  __stcg(o + 1, make_float4(c1[0], c1[1], c1[2], c1[3]));
+  __stcg(o + 2, make_float4(c0[4], c0[5], c1[4], c1[5]));
+  __stcg(o + 3, make_float4(__int_as_float(ch.x), __int_as_float(ch.y), 0.f, 0.f));
+}
+
+// Bottom-up bounds from a node that spans blocks: one global arrival counter
+// per node behind device-scope fences; the second arrival reads both child
+// boxes from the node records / published leaf boxes and goes on up.
+__device__ __forceinline__ void climb_global(int node, const int4* __restrict__ child,
+                                             const int* __restrict__ parent_int, float4* nodes,
+                                             const float4* lbox, unsigned* arrivals) {
+  while (node >= 0) {
+    __threadfence();
+    if (atomicAdd(&arrivals[node], 1u) == 0) return;
+    __threadfence();
+    const int4 ch = __ldg(child + node);
+    float c0[6], c1[6];
+    if (ch.x < 0) lbox_read(lbox, ~ch.x, c0); else node_union(nodes, ch.x, c0);
+    if (ch.y < 0) lbox_read(lbox, ~ch.y, c1); else node_union(nodes, ch.y, c1);
+    store_node(nodes, node, ch, c0, c1);
+    node = node == 0 ? -1 : __ldg(parent_int + node);
+  }
+}
+
+// Leaf gather and bottom-up bounds in one kernel.  Thread j of block b owns
+// leaf b0 + j and internal node b0 + j (b0 = b * B).
+//  1. Gather: each thread copies its leaf's record into Morton order and
+//     keeps the leaf box in shared memory.
+//  2. Local subtrees: node i's leaf range starts or ends at leaf i, so a node
+//     whose range lies inside the block's leaves ("local") is owned by a
+//     thread of the block and so are its children.  These are finished in
+//     rounds separated by barriers: a node whose children are done takes
+//     their boxes from shared memory, writes its record and its union.  The
+//     rounds number the local subtrees' height; no fences, no atomics.
+//  3. The few nodes that span blocks are finished with global arrival
+//     counters: the owner of each local node (or leaf) whose parent spans
+//     blocks publishes its box and climbs.
 template <int B>
 __global__ void __launch_bounds__(B) k_gather_refit(
     const int4* __restrict__ child, const int* __restrict__ parent_int,
@@ -178,41 +213,84 @@ __global__ void __launch_bounds__(B) k_gather_refit(
     const uint32_t* __restrict__ sorted_ids, const float4* __restrict__ xf,
     const float4* __restrict__ aux, int n, float4* nodes, float4* lbox, float4* leaf_xf,
     float4* leaf_aux, uint32_t* leaf_id, unsigned* arrivals) {
-  __shared__ unsigned s_arrivals[B];
-  s_arrivals[threadIdx.x] = 0u;
-  __syncthreads();
+  __shared__ int4 s_child[B];
+  __shared__ float s_lbox[B][6];  // leaf boxes (lo.x, hi.x, lo.y, hi.y, lo.z, hi.z)
+  __shared__ float s_nbox[B][6];  // unions of the block's local nodes
+  __shared__ unsigned char s_done[B];
   const int b0 = blockIdx.x * B;
-  const int leaf = b0 + threadIdx.x;
-  if (leaf >= n) return;
-  const uint32_t id = sorted_ids[leaf];
-  leaf_xf[3 * (size_t)leaf] = xf[3 * (size_t)id];
-  leaf_xf[3 * (size_t)leaf + 1] = xf[3 * (size_t)id + 1];
-  leaf_xf[3 * (size_t)leaf + 2] = xf[3 * (size_t)id + 2];
-  leaf_aux[leaf] = aux[id];
-  leaf_id[leaf] = id;
-  __stcg(lbox + 2 * leaf, box[2 * (size_t)id]);
-  __stcg(lbox + 2 * leaf + 1, box[2 * (size_t)id + 1]);
-  int node = parent_leaf[leaf];
-  while (node >= 0) {
-    const int4 ch = __ldg(child + node);
-    if (ch.z >= b0 && ch.w < b0 + B) {
-      __threadfence_block();
-      if (atomicAdd(&s_arrivals[node - b0], 1u) == 0) return;
-      __threadfence_block();
-    } else {
-      __threadfence();
-      if (atomicAdd(&arrivals[node], 1u) == 0) return;
-      __threadfence();
+  const int j = threadIdx.x;
+  const int leaf = b0 + j, node = b0 + j;
+  const bool has_node = node <= n - 2;
+  int4 ch = make_int4(0, 0, -1, -1);
+  if (has_node) ch = __ldg(child + node);
+  s_child[j] = ch;
+  s_done[j] = 0;
+  const bool node_local = has_node && ch.z >= b0 && ch.w < b0 + B;
+  // 1. gather
+  float4 bl = make_float4(0.f, 0.f, 0.f, 0.f), bh = bl;
+  int lparent = -1;
+  if (leaf < n) {
+    const uint32_t id = sorted_ids[leaf];
+    const float4 r0 = xf[3 * (size_t)id], r1 = xf[3 * (size_t)id + 1], r2 = xf[3 * (size_t)id + 2];
+    const float4 ax = aux[id];
+    bl = box[2 * (size_t)id];
+    bh = box[2 * (size_t)id + 1];
+    lparent = parent_leaf[leaf];
+    leaf_xf[3 * (size_t)leaf] = r0;
+    leaf_xf[3 * (size_t)leaf + 1] = r1;
+    leaf_xf[3 * (size_t)leaf + 2] = r2;
+    leaf_aux[leaf] = ax;
+    leaf_id[leaf] = id;
+    s_lbox[j][0] = bl.x; s_lbox[j][1] = bh.x; s_lbox[j][2] = bl.y;
+    s_lbox[j][3] = bh.y; s_lbox[j][4] = bl.z; s_lbox[j][5] = bh.z;
+  }
+  __syncthreads();
+  // 2. local subtrees, one level of readiness per round
+  bool pending = node_local;
+  for (;;) {
+    bool ready = false;
+    if (pending)
+      ready = (ch.x < 0 || s_done[ch.x - b0]) && (ch.y < 0 || s_done[ch.y - b0]);
+    if (ready) {
+      const float* p0 = ch.x < 0 ? s_lbox[~ch.x - b0] : s_nbox[ch.x - b0];
+      const float* p1 = ch.y < 0 ? s_lbox[~ch.y - b0] : s_nbox[ch.y - b0];
+      float c0[6], c1[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        c0[q] = p0[q];
+        c1[q] = p1[q];
+      }
+      store_node(nodes, node, ch, c0, c1);
+      s_nbox[j][0] = fminf(c0[0], c1[0]);
+      s_nbox[j][1] = fmaxf(c0[1], c1[1]);
+      s_nbox[j][2] = fminf(c0[2], c1[2]);
+      s_nbox[j][3] = fmaxf(c0[3], c1[3]);
+      s_nbox[j][4] = fminf(c0[4], c1[4]);
+      s_nbox[j][5] = fmaxf(c0[5], c1[5]);
     }
-    float b0v[6], b1v[6];
-    if (ch.x < 0) lbox_read(lbox, ~ch.x, b0v); else node_union(nodes, ch.x, b0v);
-    if (ch.y < 0) lbox_read(lbox, ~ch.y, b1v); else node_union(nodes, ch.y, b1v);
-    float4* o = nodes + 4 * node;
-    __stcg(o, make_float4(b0v[0], b0v[1], b0v[2], b0v[3]));
-    __stcg(o + 1, make_float4(b1v[0], b1v[1], b1v[2], b1v[3]));
-    __stcg(o + 2, make_float4(b0v[4], b0v[5], b1v[4], b1v[5]));
-    __stcg(o + 3, make_float4(__int_as_float(ch.x), __int_as_float(ch.y), 0.f, 0.f));
-    node = node == 0 ? -1 : parent_int[node];
+    const int any = __syncthreads_or(ready);  // this round's reads of s_done are over
+    if (ready) {
+      s_done[j] = 1;
+      pending = false;
+    }
+    if (!any) break;
+    __syncthreads();  // this round's flags are visible
+  }
+  // 3. nodes that span blocks: leaves, then local nodes, whose parent does
+  if (leaf < n) {
+    const bool parent_local = lparent >= b0 && lparent < b0 + B && s_child[lparent - b0].z >= b0 &&
+                              s_child[lparent - b0].w < b0 + B;
+    if (!parent_local) {
+      __stcg(lbox + 2 * leaf, bl);
+      __stcg(lbox + 2 * leaf + 1, bh);
+      climb_global(lparent, child, parent_int, nodes, lbox, arrivals);
+    }
+  }
+  if (node_local && node != 0) {
+    const int p = __ldg(parent_int + node);
+    const bool parent_local = p >= b0 && p < b0 + B && s_child[p - b0].z >= b0 &&
+                              s_child[p - b0].w < b0 + B;
+    if (!parent_local) climb_global(p, child, parent_int, nodes, lbox, arrivals);
   }
 }
 
