@@ -4,18 +4,20 @@
 One step is one pass of the whole hot path over the full-head workload
 (100,000 strands x 64 segments, 1920x1080, 8 samples per pixel, 8 point
 lights, 4096 clusters, LoD chosen per cluster by projected width with
-epsilon_w = 2 px): Morton clusters, FP64 thick-hair fit, LoD selection,
+epsilon_w = 2 px): Morton clusters, thick-hair fit, LoD selection,
 active-primitive compaction, LBVH build, and the trace / shade / composite
 kernel.  The metric is samples per second of that step (Msamples/s) with the
 inputs resident on the device; ms/frame is printed beside it.
 
 Also measured in the same run:
-  * e2e    - the same step through the C ABI with host buffers: the strand
-             upload from pinned memory and the image read-back inside the
+  * e2e    - the same step through the C ABI with host buffers, as an
+             animated frame: the strand positions uploaded from pinned
+             memory (hr_asset_update) and the image read back, inside the
              timed region;
-  * roofline - the trace kernel (dominant) against the FP32 pipe peak, with
-             algorithmic FLOPs from a counting render (node visits, primitive
-             tests, shading evaluations times fixed per-operation costs);
+  * roofline - the kernel that takes more of the step, the trace kernel or
+             the cross-section fit, against its ALU peak (FP32 for the trace
+             kernel, with algorithmic FLOPs from a counting render; FP64 for
+             the fit), and the other kernel beside it;
   * cpu_baseline - the FP64 brute-force CPU oracle on a bounded sample of the
              same workload, on this host's cores;
   * serving - a seeded Poisson request stream through hr_submit / hr_poll
@@ -446,18 +448,17 @@ def main():
     render_avg = statistics.mean(render_ms)
     clocks = clk.summary()
 
-    # e2e: the same step through the C ABI with host buffers
+    # e2e: the same step through the C ABI with host buffers, as an animated
+    # frame: the strand positions come from pinned host memory every step
+    # (hr_asset_update), the image goes back to pinned host memory
     pv = torch.from_numpy(w.scene.verts).pin_memory()
-    pm = torch.from_numpy(w.scene.mat).pin_memory()
-    ps = torch.from_numpy(w.scene.shape).pin_memory()
     hout = torch.empty((H, W, 3), dtype=torch.float32).pin_memory()
-    h2d = pv.numel() * 4 + pm.numel() * 4 + ps.numel() * 4
+    h2d = pv.numel() * 4
     d2h = hout.numel() * 4
 
     def e2e_step():
-        a = hr.hr_asset_create(ctx, pv, pm, ps)
-        hr.hr_render_frame(ctx, a, w.n_clusters, w.eps_w, 0, desc, hout)
-        hr.hr_asset_destroy(ctx, a)
+        hr.hr_asset_update(ctx, asset, pv)
+        hr.hr_render_frame(ctx, asset, w.n_clusters, w.eps_w, 0, desc, hout)
 
     e2e = None
     if not args.no_e2e:

@@ -176,6 +176,19 @@ uint64_t hr_kernel_launches(hr_ctx* ctx);
 hr_status hr_asset_create(hr_ctx* ctx, const hr_hair_desc* desc, hr_asset** out);
 hr_status hr_asset_destroy(hr_ctx* ctx, hr_asset* asset);
 
+/* New strand positions for an existing asset: the per-frame input of animated
+ * hair (Section 6, "Animated hairs": every strand moves each frame, with the
+ * same strands, materials and cross-sections).  vertices: host or device,
+ * [n_strands][n_segments + 1] float4 (x, y, z, r) in the asset's sizes,
+ * copied on the context stream; the strand segment records are rebuilt in
+ * place (no allocation).  The hierarchy, thick hairs and BVH of the old
+ * positions are stale afterwards: hr_render_frame rebuilds them, or call
+ * hr_build_clusters and hr_build_bvh.  The LoD kept for Eq. 14's deferred
+ * rule is the previous frame's, as the paper intends.  With serving running,
+ * the asset's queued requests end with HR_ESTATE, running ones are waited
+ * for, and its cached BVHs are dropped. */
+hr_status hr_asset_update(hr_ctx* ctx, hr_asset* asset, const float* vertices);
+
 /* Build the hair hierarchy and fit the thick hairs (Section 5.1 steps 2-3).
  * Clustering rule (deterministic Morton buckets): strands are sorted by
  * (30-bit Morton code of the root quantised to 10 bits per axis in the roots'

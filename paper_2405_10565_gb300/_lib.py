@@ -93,6 +93,7 @@ _SIGS = {
     "hr_kernel_launches": (c_u64, [P]),
     "hr_asset_create": (c_int, [P, ctypes.POINTER(hr_hair_desc), ctypes.POINTER(c_void_p)]),
     "hr_asset_destroy": (c_int, [P, P]),
+    "hr_asset_update": (c_int, [P, P, P]),
     "hr_build_clusters": (c_int, [P, P, c_u32, c_u32, P, P]),
     "hr_hierarchy_info": (c_int, [P, P, ctypes.POINTER(c_u32), ctypes.POINTER(c_u32),
                                   ctypes.POINTER(c_u32)]),
@@ -237,6 +238,11 @@ def hr_asset_create(ctx: int, vertices, material, shape) -> int:
 
 def hr_asset_destroy(ctx: int, asset: int) -> None:
     _check(ctx, load().hr_asset_destroy(ctx, asset), "hr_asset_destroy")
+
+
+def hr_asset_update(ctx: int, asset: int, vertices) -> None:
+    """New vertices [N, S+1, 4] float32 (host or device) in the asset's sizes."""
+    _check(ctx, load().hr_asset_update(ctx, asset, ptr(vertices)), "hr_asset_update")
 
 
 def hr_build_clusters(ctx: int, asset: int, n_clusters: int, max_levels: int = 0,

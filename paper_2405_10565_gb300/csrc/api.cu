@@ -300,6 +300,17 @@ hr_status hr_asset_create(hr_ctx* ctx, const hr_hair_desc* d, hr_asset** out) {
   return HR_OK;
 }
 
+hr_status hr_asset_update(hr_ctx* ctx, hr_asset* a, const float* vertices) {
+  API_ENTER(ctx);
+  if (!a || !vertices) return set_error(ctx, HR_EINVAL, "hr_asset_update: null argument");
+  if (ctx->server) serve_forget_asset(ctx, ctx->server, a);
+  cudaStream_t st = ctx->stream;
+  HR_TRY(to_device(ctx, a->verts, vertices, (size_t)a->N * (a->S + 1) * sizeof(float4), st));
+  HR_TRY(refresh_strand_prims(ctx, a));
+  a->bvh.valid = 0;
+  return HR_OK;
+}
+
 hr_status hr_asset_destroy(hr_ctx* ctx, hr_asset* a) {
   API_ENTER(ctx);
   if (!a) return HR_EINVAL;
@@ -318,6 +329,7 @@ hr_status hr_asset_destroy(hr_ctx* ctx, hr_asset* a) {
   if (a->prim_xf) dfree(ctx, a->prim_xf, P * 3 * sizeof(float4));
   if (a->prim_box) dfree(ctx, a->prim_box, P * 2 * sizeof(float4));
   if (a->prim_aux) dfree(ctx, a->prim_aux, P * sizeof(float4));
+  if (a->d_bounds) dfree(ctx, a->d_bounds, 8 * sizeof(uint32_t));
   free_bvh(ctx, a->bvh);
   delete a;
   return HR_OK;

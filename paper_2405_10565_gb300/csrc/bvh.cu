@@ -27,12 +27,15 @@
 namespace hr {
 namespace {
 
+// Active primitives per cluster, and the thick-hair total in counts[C + 1]
+// (zeroed by the caller) for the statistics.
 __global__ void k_cluster_counts(const uint8_t* __restrict__ lod, const uint32_t* __restrict__ cl_first,
                                  uint32_t C, uint32_t L, uint32_t S, uint32_t* counts) {
   const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
   const uint32_t l = min((uint32_t)lod[c], L);
   counts[c] = (l == L) ? (cl_first[c + 1] - cl_first[c]) * S : (1u << (2 * l)) * S;
+  if (l < L) atomicAdd(counts + C + 1, (1u << (2 * l)) * S);
 }
 
 __global__ void k_cluster_fill(const uint8_t* __restrict__ lod, const uint32_t* __restrict__ cl_first,
@@ -71,9 +74,16 @@ __device__ __forceinline__ uint32_t spread10(uint32_t v) {
 }
 
 __global__ void k_prim_morton(const float4* __restrict__ box, const uint32_t* __restrict__ ids,
-                              uint32_t n, float3 lo, float3 inv_ext, uint32_t* keys) {
+                              uint32_t n, const uint32_t* __restrict__ bounds, uint32_t* keys) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  float3 lo, hi, inv_ext;
+  lo.x = from_ordered(__ldg(bounds)), lo.y = from_ordered(__ldg(bounds + 1));
+  lo.z = from_ordered(__ldg(bounds + 2)), hi.x = from_ordered(__ldg(bounds + 3));
+  hi.y = from_ordered(__ldg(bounds + 4)), hi.z = from_ordered(__ldg(bounds + 5));
+  inv_ext.x = hi.x > lo.x ? 1.f / (hi.x - lo.x) : 0.f;
+  inv_ext.y = hi.y > lo.y ? 1.f / (hi.y - lo.y) : 0.f;
+  inv_ext.z = hi.z > lo.z ? 1.f / (hi.z - lo.z) : 0.f;
   const uint32_t id = ids[i];
   const float4 l = box[2 * (size_t)id], h = box[2 * (size_t)id + 1];
   const float cx = (0.5f * (l.x + h.x) - lo.x) * inv_ext.x;
@@ -321,27 +331,22 @@ hr_status build_bvh(hr_ctx* ctx, hr_asset* a, const uint8_t* lod_dev, Bvh& bv, c
   } else {
     const uint32_t C = a->C, L = a->n_levels;
     uint32_t* cnt = nullptr;
-    HR_TRY(scratch(ctx, 31, (size_t)(C + 1) * 4, (void**)&cnt));
+    HR_TRY(scratch(ctx, 31, (size_t)(C + 2) * 4, (void**)&cnt));
+    HR_CUDA(ctx, cudaMemsetAsync(cnt + C, 0, 8, st));
     k_cluster_counts<<<(C + 255) / 256, 256, 0, st>>>(lod_dev, a->cl_first, C, L, S, cnt);
     HR_LAUNCHED(ctx);
-    HR_CUDA(ctx, cudaMemsetAsync(cnt + C, 0, 4, st));
     HR_TRY(scan_u32(ctx, cnt, C + 1, st));
-    HR_CUDA(ctx, cudaMemcpyAsync(&n, cnt + C, 4, cudaMemcpyDeviceToHost, st));
+    uint32_t tot[2] = {0, 0};  // active primitives, of which thick-hair segments
+    HR_CUDA(ctx, cudaMemcpyAsync(tot, cnt + C, 8, cudaMemcpyDeviceToHost, st));
     HR_CUDA(ctx, cudaStreamSynchronize(st));
+    n = tot[0];
+    bv.n_eth = tot[1];
     uint32_t* eoff = nullptr;
     HR_TRY(scratch(ctx, 32, 16 * 4, (void**)&eoff));
     HR_CUDA(ctx, cudaMemcpyAsync(eoff, a->eth_offset, 16 * 4, cudaMemcpyHostToDevice, st));
     HR_TRY(scratch(ctx, 30, (size_t)std::max(n, 1u) * 4, (void**)&ids));
     k_cluster_fill<<<C, 256, 0, st>>>(lod_dev, a->cl_first, a->order, cnt, eoff, C, L, N, S, ids);
     HR_LAUNCHED(ctx);
-    // count thick-hair primitives for the statistics
-    std::vector<uint8_t> hl(C);
-    HR_CUDA(ctx, cudaMemcpyAsync(hl.data(), lod_dev, C, cudaMemcpyDeviceToHost, st));
-    HR_CUDA(ctx, cudaStreamSynchronize(st));
-    uint64_t ne = 0;
-    for (uint32_t c = 0; c < C; ++c)
-      if (hl[c] < L) ne += (uint64_t)(1u << (2 * hl[c])) * S;
-    bv.n_eth = (uint32_t)ne;
   }
   // 2. storage (grow only)
   if (n > bv.cap) {
@@ -365,12 +370,7 @@ hr_status build_bvh(hr_ctx* ctx, hr_asset* a, const uint8_t* lod_dev, Bvh& bv, c
   HR_TRY(scratch(ctx, 33, (size_t)n * 4, (void**)&keys));
   HR_TRY(scratch(ctx, 34, (size_t)n * 4, (void**)&k2));
   HR_TRY(scratch(ctx, 35, (size_t)n * 4, (void**)&v2));
-  float3 lo = make_float3(a->scene_lo[0], a->scene_lo[1], a->scene_lo[2]);
-  float3 inv;
-  inv.x = a->scene_hi[0] > a->scene_lo[0] ? 1.f / (a->scene_hi[0] - a->scene_lo[0]) : 0.f;
-  inv.y = a->scene_hi[1] > a->scene_lo[1] ? 1.f / (a->scene_hi[1] - a->scene_lo[1]) : 0.f;
-  inv.z = a->scene_hi[2] > a->scene_lo[2] ? 1.f / (a->scene_hi[2] - a->scene_lo[2]) : 0.f;
-  k_prim_morton<<<(n + 255) / 256, 256, 0, st>>>(a->prim_box, ids, n, lo, inv, keys);
+  k_prim_morton<<<(n + 255) / 256, 256, 0, st>>>(a->prim_box, ids, n, a->d_bounds, keys);
   HR_LAUNCHED(ctx);
   HR_TRY(radix_sort_pairs(ctx, keys, ids, k2, v2, n, 30, st));
   if (n == 1) {
@@ -393,7 +393,7 @@ hr_status build_bvh(hr_ctx* ctx, hr_asset* a, const uint8_t* lod_dev, Bvh& bv, c
   HR_CUDA(ctx, cudaMemsetAsync(arrivals, 0, (size_t)n * 4, st));
   k_karras<<<(n - 1 + 255) / 256, 256, 0, st>>>(keys, (int)n, child, par_int, par_leaf);
   HR_LAUNCHED(ctx);
-  k_gather_refit<256><<<(n + 255) / 256, 256, 0, st>>>(child, par_int, par_leaf, a->prim_box, ids,
+  k_gather_refit<128><<<(n + 127) / 128, 128, 0, st>>>(child, par_int, par_leaf, a->prim_box, ids,
                                                   a->prim_xf, a->prim_aux, (int)n, bv.nodes,
                                                   lbox, bv.leaf_xf, bv.leaf_aux, bv.leaf_id,
                                                   arrivals);

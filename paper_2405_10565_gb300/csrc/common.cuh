@@ -74,7 +74,7 @@ struct hr_asset {
   float4* prim_xf = nullptr;   // [P_total * 3]
   float4* prim_box = nullptr;  // [P_total * 2]
   float4* prim_aux = nullptr;  // [P_total]
-  float scene_lo[3] = {0, 0, 0}, scene_hi[3] = {0, 0, 0};
+  uint32_t* d_bounds = nullptr;  // [8] strand boxes' bounds, ordered float bits (lo xyz, hi xyz)
   // LoD
   uint8_t* lod = nullptr;  // [C] current selection on the device
   int lod_valid = 0;
@@ -138,6 +138,16 @@ cudaError_t morton_clusters_with(const float4* verts, uint32_t N, uint32_t S, ui
 
 // --- hierarchy.cu
 hr_status build_strand_prims(hr_ctx* ctx, hr_asset* a);
+hr_status refresh_strand_prims(hr_ctx* ctx, hr_asset* a);
+
+// Float <-> unsigned with the same order (atomic min / max of floats).
+__device__ __forceinline__ uint32_t ordered_bits(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float from_ordered(uint32_t u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
 hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_levels,
                           cudaEvent_t fit_begin = nullptr, cudaEvent_t fit_end = nullptr);
 

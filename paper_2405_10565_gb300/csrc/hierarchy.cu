@@ -190,13 +190,6 @@ __global__ void k_strand_prims(const float4* __restrict__ verts, const float4* _
 
 // ------------------------------------------------------------ Morton clusters
 
-__device__ __forceinline__ uint32_t ordered_bits(float f) {
-  const uint32_t u = __float_as_uint(f);
-  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
-__device__ __forceinline__ float from_ordered(uint32_t u) {
-  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
-}
 
 // bounds[0..2] = min (ordered bits), bounds[3..5] = max
 __global__ void k_root_bounds(const float4* __restrict__ verts, uint32_t N, uint32_t S,
@@ -724,42 +717,36 @@ __global__ void k_init_bounds(uint32_t* bounds) {
   else if (threadIdx.x < 6) bounds[threadIdx.x] = 0u;
 }
 
-float host_from_ordered(uint32_t u) {
-  uint32_t v = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
-  float f;
-  memcpy(&f, &v, 4);
-  return f;
-}
-
+// Bounds of the first n primitive boxes into a->d_bounds (ordered float
+// bits: lo xyz, hi xyz), on the stream; nothing is read back.
 hr_status scene_bounds(hr_ctx* ctx, hr_asset* a, uint64_t n) {
   cudaStream_t st = ctx_stream(ctx);
-  uint32_t* b = nullptr;
-  HR_TRY(scratch(ctx, 20, 64, (void**)&b));
-  const uint32_t init[6] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u};
-  HR_CUDA(ctx, cudaMemcpyAsync(b, init, sizeof(init), cudaMemcpyHostToDevice, st));
-  const int blocks = (int)std::min<uint64_t>((n + 255) / 256, 152 * 8);
-  k_prim_bounds<<<std::max(1, blocks), 256, 0, st>>>(a->prim_box, n, b);
+  k_init_bounds<<<1, 32, 0, st>>>(a->d_bounds);
   HR_LAUNCHED(ctx);
-  uint32_t hb[6];
-  HR_CUDA(ctx, cudaMemcpyAsync(hb, b, sizeof(hb), cudaMemcpyDeviceToHost, st));
-  HR_CUDA(ctx, cudaStreamSynchronize(st));
-  for (int i = 0; i < 3; ++i) {
-    a->scene_lo[i] = host_from_ordered(hb[i]);
-    a->scene_hi[i] = host_from_ordered(hb[3 + i]);
-  }
+  const int blocks = (int)std::min<uint64_t>((n + 255) / 256, 152 * 8);
+  k_prim_bounds<<<std::max(1, blocks), 256, 0, st>>>(a->prim_box, n, a->d_bounds);
+  HR_LAUNCHED(ctx);
   return HR_OK;
 }
 
 }  // namespace
 
 hr_status build_strand_prims(hr_ctx* ctx, hr_asset* a) {
-  cudaStream_t st = ctx_stream(ctx);
   const uint64_t n = (uint64_t)a->N * a->S;
   a->n_prims_total = (uint32_t)n;
   HR_TRY(dalloc(ctx, (void**)&a->prim_xf, n * 3 * sizeof(float4), "strand records"));
   HR_TRY(dalloc(ctx, (void**)&a->prim_box, n * 2 * sizeof(float4), "strand boxes"));
   HR_TRY(dalloc(ctx, (void**)&a->prim_aux, n * sizeof(float4), "strand aux"));
+  HR_TRY(dalloc(ctx, (void**)&a->d_bounds, 8 * sizeof(uint32_t), "scene bounds"));
   a->bytes += n * 6 * sizeof(float4);
+  return refresh_strand_prims(ctx, a);
+}
+
+// Strand segment records and scene bounds from the current vertices, into
+// the asset's existing arrays (the first N * S records).
+hr_status refresh_strand_prims(hr_ctx* ctx, hr_asset* a) {
+  cudaStream_t st = ctx_stream(ctx);
+  const uint64_t n = (uint64_t)a->N * a->S;
   float4* sh4 = nullptr;
   HR_TRY(scratch(ctx, 6, (size_t)a->N * sizeof(float4), (void**)&sh4));
   k_strand_shape<<<(a->N + 255) / 256, 256, 0, st>>>(a->verts, a->shape, a->N, a->S, sh4);
@@ -822,8 +809,8 @@ hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_lev
   HR_TRY(scratch(ctx, 2, (size_t)N * 4, (void**)&k2));
   HR_TRY(scratch(ctx, 3, (size_t)N * 4, (void**)&v2));
   vals = a->order;
-  const uint32_t init[6] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u};
-  HR_CUDA(ctx, cudaMemcpyAsync(bounds, init, sizeof(init), cudaMemcpyHostToDevice, st));
+  k_init_bounds<<<1, 32, 0, st>>>(bounds);
+  HR_LAUNCHED(ctx);
   k_root_bounds<<<(N + 255) / 256, 256, 0, st>>>(a->verts, N, S, bounds);
   HR_LAUNCHED(ctx);
   k_root_morton<<<(N + 255) / 256, 256, 0, st>>>(a->verts, N, S, bounds, keys, vals);
@@ -866,7 +853,10 @@ hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_lev
     a->prim_aux = ax;
     a->n_prims_total = (uint32_t)total;
   }
-  if (E == 0) return scene_bounds(ctx, a, total);
+  // The scene bounds (for the BVH's Morton codes) are those of the strand
+  // segments' boxes, taken when the asset was created: a thick-hair segment's
+  // box centre is the mean of member vertices, so it lies inside them.
+  if (E == 0) return HR_OK;
 
   // K2: cross-section fits (FP64 covariance and eigenvectors), materials and
   // thick-hair segment records
@@ -889,7 +879,7 @@ hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_lev
                                                            a->cl_first, li, eth_r, a->prim_xf,
                                                            a->prim_box, a->prim_aux);
   HR_LAUNCHED(ctx);
-  return scene_bounds(ctx, a, total);
+  return HR_OK;
 }
 
 // Morton clustering of strand roots on caller-provided scratch (no

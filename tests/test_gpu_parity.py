@@ -380,3 +380,38 @@ def test_stress_sampled(ctx):
     sids = scenegen.pixel_samples(W, w.spp, pix)
     rg, hg, ro, ho = _render_check(ctx, w, sids)
     print(f"stress: hit fraction {(ho[:, 0] >= 0).mean():.3f}")
+
+
+def test_asset_update_matches_a_fresh_asset(ctx):
+    """hr_asset_update (new strand positions, as in animation) followed by a
+    full frame gives the frame of an asset created from those positions:
+    the hierarchy, thick hairs, LoD and BVH are rebuilt from the new
+    vertices, with host and with device vertex buffers."""
+    torch = pytest.importorskip("torch")
+    w0 = scenegen.full_head(n=6000, S=16, width=64, height=48, spp=2, n_lights=2, n_clusters=256)
+    w1 = scenegen.full_head(n=6000, S=16, width=64, height=48, spp=2, n_lights=2, n_clusters=256,
+                            seed=5)
+    d = desc_of(w0)
+    a = upload(ctx, w0.scene)
+    b = hr.hr_asset_create(ctx, np.ascontiguousarray(w1.scene.verts),
+                           np.ascontiguousarray(w0.scene.mat), np.ascontiguousarray(w0.scene.shape))
+    try:
+        img = np.zeros((48, 64, 3), np.float32)
+        hr.hr_render_frame(ctx, a, w0.n_clusters, w0.eps_w, 0, d, img)
+        ref = np.zeros_like(img)
+        hr.hr_render_frame(ctx, b, w0.n_clusters, w0.eps_w, 0, d, ref)
+        assert ref.max() > 0
+        hr.hr_asset_update(ctx, a, np.ascontiguousarray(w1.scene.verts))
+        hr.hr_render_frame(ctx, a, w0.n_clusters, w0.eps_w, 0, d, img)
+        assert np.array_equal(img, ref)
+        # device vertices, back to the first positions and forth again
+        hr.hr_asset_update(ctx, a, torch.from_numpy(w0.scene.verts).to("cuda:0"))
+        hr.hr_render_frame(ctx, a, w0.n_clusters, w0.eps_w, 0, d, img)
+        assert not np.array_equal(img, ref)
+        hr.hr_asset_update(ctx, a, torch.from_numpy(w1.scene.verts).to("cuda:0"))
+        torch.cuda.synchronize()
+        hr.hr_render_frame(ctx, a, w0.n_clusters, w0.eps_w, 0, d, img)
+        assert np.array_equal(img, ref)
+    finally:
+        hr.hr_asset_destroy(ctx, a)
+        hr.hr_asset_destroy(ctx, b)
