@@ -472,6 +472,44 @@ def main():
         e2e = {"value": world * samples / e2e_s / 1e6, "unit": "Msamples/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3}
 
+    # animated frames: the strands alternate between two poses (a smooth
+    # displacement field of amplitude `amp`), uploaded from pinned memory each
+    # frame; full BVH rebuild against a refit when the LoD (Eq. 14 deferred
+    # selection) is unchanged.  Subtle motion keeps every cluster's level and
+    # the BVH is refit; larger motion moves some of the 4096 clusters across
+    # a level boundary every frame and the frame call rebuilds.
+    animation = None
+    if not args.no_e2e:
+        p = w.scene.verts[..., :3].astype(np.float64)
+        animation = {"frames": args.e2e_steps * 4}
+        for amp in (2e-5, 2e-3):
+            moved = np.array(w.scene.verts, copy=True)
+            moved[..., 0] += (amp * np.sin(7.0 * p[..., 1] + 1.3)).astype(np.float32)
+            moved[..., 2] += (amp * np.cos(5.0 * p[..., 0] - 1.3)).astype(np.float32)
+            poses = [torch.from_numpy(moved).pin_memory(), pv]
+            res = {}
+            for key, flags in (("rebuild", 0), ("refit", hr.HR_FLAG_REFIT | hr.HR_FLAG_DEFERRED_LOD)):
+                da = hr.render_desc(w.camera.pack(), w.lights, w.spp, w.k_depth, w.sample_seed,
+                                    w.precision, flags)
+                for i in range(2):  # warm-up
+                    hr.hr_asset_update(ctx, asset, poses[i])
+                    hr.hr_render_frame(ctx, asset, w.n_clusters, w.eps_w, 0, da, hout)
+                torch.cuda.synchronize(dev)
+                refits, bvh = 0, []
+                t0 = time.perf_counter()
+                for i in range(animation["frames"]):
+                    hr.hr_asset_update(ctx, asset, poses[i % 2])
+                    sa = hr.hr_render_frame(ctx, asset, w.n_clusters, w.eps_w, 0, da, hout,
+                                            stats=True)
+                    refits += sa.bvh_refit
+                    bvh.append(sa.bvh_ms)
+                torch.cuda.synchronize(dev)
+                dt = (time.perf_counter() - t0) / animation["frames"]
+                res[key] = {"ms_per_frame": dt * 1e3, "bvh_ms": statistics.median(bvh),
+                            "bvh_refits": refits}
+            animation[f"displacement_{amp:g}"] = res
+        hr.hr_asset_update(ctx, asset, pv)
+
     serving = None
     if not args.no_serve and rank == 0 and world == 1:
         serving = run_serving(hr, ctx, torch, dev, args.serve_requests)
@@ -532,7 +570,7 @@ def main():
             "phase_ms": {"hierarchy": st.hierarchy_ms, "fit": st.fit_ms, "lod": st.lod_ms,
                          "bvh": st.bvh_ms, "render": st.render_ms},
             "cpu_baseline": cpu,
-            "e2e": e2e,
+            "e2e": e2e, "animation": animation,
             "gpu_launches": launches, "clocks": clocks, "serving": serving}
     print(json.dumps(line))
     if dist:

@@ -118,6 +118,17 @@ typedef struct hr_light {
  * shading evaluations into hr_stats (slower; used to derive the algorithmic
  * FLOP count of a frame). */
 #define HR_FLAG_COUNT 256u
+/* hr_render_frame options for animated hair (a new frame of the same asset
+ * after hr_asset_update):
+ *  - HR_FLAG_REFIT: when the hierarchy's shape and the LoD selection equal
+ *    those the asset's BVH was built for, refit the BVH's bounds and leaf
+ *    records to the current primitives (same topology and leaf order)
+ *    instead of rebuilding it.  The hits are the same; traversal may slow
+ *    down after large motion.  Otherwise the BVH is rebuilt.
+ *  - HR_FLAG_DEFERRED_LOD: choose the LoD with Eq. 14 from the previous
+ *    frame's selection when there is one (else the initial rule). */
+#define HR_FLAG_REFIT 512u
+#define HR_FLAG_DEFERRED_LOD 1024u
 
 typedef struct hr_render_desc {
   hr_camera camera;
@@ -149,7 +160,9 @@ typedef struct hr_stats {
   double hierarchy_ms;      /* clusters, thick-hair fit, records (K1, K2) */
   double fit_ms;            /* of which the FP64 cross-section fit kernel */
   double lod_ms;            /* LoD widths and rule (K4) */
-  double bvh_ms;            /* compaction and LBVH (K5, K6) */
+  double bvh_ms;            /* compaction and LBVH (K5, K6), or the refit */
+  uint32_t bvh_refit;       /* 1 when hr_render_frame refit the BVH (HR_FLAG_REFIT) */
+  uint32_t lod_deferred;    /* 1 when it chose the LoD with Eq. 14 (HR_FLAG_DEFERRED_LOD) */
 } hr_stats;
 
 /* ---------------------------------------------------------------- context */

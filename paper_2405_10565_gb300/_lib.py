@@ -35,6 +35,8 @@ HR_PREC_FP16 = 1
 HR_FLAG_NO_S = 1
 HR_FLAG_SINGLE_ON_ETH = 2
 HR_FLAG_COUNT = 256
+HR_FLAG_REFIT = 512
+HR_FLAG_DEFERRED_LOD = 1024
 
 
 class HairRTError(RuntimeError):
@@ -71,7 +73,8 @@ class hr_stats(ctypes.Structure):
                 ("node_visits", c_u64), ("prim_tests", c_u64), ("strand_shades", c_u64),
                 ("eth_shades", c_u64), ("shaded_hits", c_u64), ("traced_samples", c_u64),
                 ("hierarchy_ms", ctypes.c_double), ("fit_ms", ctypes.c_double),
-                ("lod_ms", ctypes.c_double), ("bvh_ms", ctypes.c_double)]
+                ("lod_ms", ctypes.c_double), ("bvh_ms", ctypes.c_double),
+                ("bvh_refit", c_u32), ("lod_deferred", c_u32)]
 
 
 class hr_request(ctypes.Structure):

@@ -581,13 +581,21 @@ hr_status hr_render_frame(hr_ctx* ctx, hr_asset* a, uint32_t n_clusters, float e
     fit_ran = a->E > 0;
   }
   if (stats) HR_CUDA(ctx, cudaEventRecord(ph[3], st));
+  const bool deferred = (desc->flags & HR_FLAG_DEFERRED_LOD) && a->lod_valid;
   if (n_clusters > 0 && a->n_levels > 0) {
-    HR_TRY(lod_select(ctx, a, &desc->camera, eps_w_px, 0, budget_bias, nullptr, a->lod, st));
+    // Eq. 14 reads the previous selection and writes the new one in place
+    HR_TRY(lod_select(ctx, a, &desc->camera, eps_w_px, deferred ? 1 : 0, budget_bias,
+                      deferred ? a->lod : nullptr, a->lod, st));
     a->lod_valid = 1;
     lod_dev = a->lod;
   }
   if (stats) HR_CUDA(ctx, cudaEventRecord(ph[4], st));
-  HR_TRY(build_bvh(ctx, a, lod_dev, a->bvh, st));
+  bool refit = false;
+  if (desc->flags & HR_FLAG_REFIT) {
+    refit = refit_bvh(ctx, a, lod_dev, a->bvh, st) == HR_OK;
+    if (!refit) set_error(ctx, HR_OK, "");  // not refittable: rebuild
+  }
+  if (!refit) HR_TRY(build_bvh(ctx, a, lod_dev, a->bvh, st));
   if (stats) HR_CUDA(ctx, cudaEventRecord(ph[5], st));
   HR_TRY(render_impl(ctx, a, desc, rgb_out, stats));
   if (stats) {
@@ -600,6 +608,8 @@ hr_status hr_render_frame(hr_ctx* ctx, hr_asset* a, uint32_t n_clusters, float e
     stats->fit_ms = f;
     stats->lod_ms = l;
     stats->bvh_ms = b;
+    stats->bvh_refit = refit ? 1u : 0u;
+    stats->lod_deferred = deferred && n_clusters > 0 && a->n_levels > 0 ? 1u : 0u;
   }
   return HR_OK;
 }

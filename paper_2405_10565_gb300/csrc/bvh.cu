@@ -304,6 +304,29 @@ __global__ void __launch_bounds__(B) k_gather_refit(
   }
 }
 
+__global__ void k_bytes_differ(const uint8_t* __restrict__ x, const uint8_t* __restrict__ y,
+                               uint32_t n, uint32_t* diff) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && x[i] != y[i]) *diff = 1u;
+}
+
+// Leaf records of the primitives `ids` (in leaf order) and every node's
+// bounds, over the topology in bv.
+hr_status gather_refit(hr_ctx* ctx, hr_asset* a, Bvh& bv, const uint32_t* ids, cudaStream_t st) {
+  const uint32_t n = bv.n;
+  unsigned* arrivals = nullptr;
+  float4* lbox = nullptr;
+  HR_TRY(scratch(ctx, 39, (size_t)n * 4, (void**)&arrivals));
+  HR_TRY(scratch(ctx, 46, (size_t)n * 2 * sizeof(float4), (void**)&lbox));
+  HR_CUDA(ctx, cudaMemsetAsync(arrivals, 0, (size_t)n * 4, st));
+  k_gather_refit<128><<<(n + 127) / 128, 128, 0, st>>>(bv.child, bv.par_int, bv.par_leaf,
+                                                       a->prim_box, ids, a->prim_xf, a->prim_aux,
+                                                       (int)n, bv.nodes, lbox, bv.leaf_xf,
+                                                       bv.leaf_aux, bv.leaf_id, arrivals);
+  HR_LAUNCHED(ctx);
+  return HR_OK;
+}
+
 }  // namespace
 
 void free_bvh(hr_ctx* ctx, Bvh& bv) {
@@ -312,7 +335,11 @@ void free_bvh(hr_ctx* ctx, Bvh& bv) {
     dfree(ctx, bv.leaf_xf, (size_t)bv.cap * 3 * sizeof(float4));
     dfree(ctx, bv.leaf_aux, (size_t)bv.cap * sizeof(float4));
     dfree(ctx, bv.leaf_id, (size_t)bv.cap * 4);
+    dfree(ctx, bv.child, (size_t)bv.cap * sizeof(int4));
+    dfree(ctx, bv.par_int, (size_t)bv.cap * 4);
+    dfree(ctx, bv.par_leaf, (size_t)bv.cap * 4);
   }
+  if (bv.lod_built) dfree(ctx, bv.lod_built, bv.lod_cap);
   bv = Bvh();
 }
 
@@ -358,11 +385,31 @@ hr_status build_bvh(hr_ctx* ctx, hr_asset* a, const uint8_t* lod_dev, Bvh& bv, c
     HR_TRY(dalloc(ctx, (void**)&bv.leaf_xf, (size_t)n * 3 * sizeof(float4), "BVH leaf records"));
     HR_TRY(dalloc(ctx, (void**)&bv.leaf_aux, (size_t)n * sizeof(float4), "BVH leaf aux"));
     HR_TRY(dalloc(ctx, (void**)&bv.leaf_id, (size_t)n * 4, "BVH leaf ids"));
+    HR_TRY(dalloc(ctx, (void**)&bv.child, (size_t)n * sizeof(int4), "BVH children"));
+    HR_TRY(dalloc(ctx, (void**)&bv.par_int, (size_t)n * 4, "BVH parents"));
+    HR_TRY(dalloc(ctx, (void**)&bv.par_leaf, (size_t)n * 4, "BVH leaf parents"));
     bv.cap = n;
   }
   bv.n = n;
+  // what the topology is built for (checked by refit_bvh)
+  bv.topo = 0;
+  bv.built_C = a->C;
+  bv.built_E = a->E;
+  bv.built_total = a->n_prims_total;
+  bv.built_with_lod = lod_dev != nullptr;
+  if (lod_dev) {
+    if (bv.lod_cap < a->C) {
+      if (bv.lod_built) dfree(ctx, bv.lod_built, bv.lod_cap);
+      bv.lod_built = nullptr;
+      bv.lod_cap = 0;
+      HR_TRY(dalloc(ctx, (void**)&bv.lod_built, a->C, "BVH LoD"));
+      bv.lod_cap = a->C;
+    }
+    HR_CUDA(ctx, cudaMemcpyAsync(bv.lod_built, lod_dev, a->C, cudaMemcpyDeviceToDevice, st));
+  }
   if (n == 0) {
     bv.valid = 1;
+    bv.topo = 1;
     return HR_OK;
   }
   // 3. Morton codes and sort
@@ -378,26 +425,42 @@ hr_status build_bvh(hr_ctx* ctx, hr_asset* a, const uint8_t* lod_dev, Bvh& bv, c
                                bv.leaf_id);
     HR_LAUNCHED(ctx);
     bv.valid = 1;
+    bv.topo = 1;
     return HR_OK;
   }
   // 4. hierarchy, then leaf records and bounds in one bottom-up pass
-  int4* child = nullptr;
-  int *par_int = nullptr, *par_leaf = nullptr;
-  unsigned* arrivals = nullptr;
-  float4* lbox = nullptr;
-  HR_TRY(scratch(ctx, 36, (size_t)n * sizeof(int4), (void**)&child));
-  HR_TRY(scratch(ctx, 37, (size_t)n * 4, (void**)&par_int));
-  HR_TRY(scratch(ctx, 38, (size_t)n * 4, (void**)&par_leaf));
-  HR_TRY(scratch(ctx, 39, (size_t)n * 4, (void**)&arrivals));
-  HR_TRY(scratch(ctx, 46, (size_t)n * 2 * sizeof(float4), (void**)&lbox));
-  HR_CUDA(ctx, cudaMemsetAsync(arrivals, 0, (size_t)n * 4, st));
-  k_karras<<<(n - 1 + 255) / 256, 256, 0, st>>>(keys, (int)n, child, par_int, par_leaf);
+  k_karras<<<(n - 1 + 255) / 256, 256, 0, st>>>(keys, (int)n, bv.child, bv.par_int, bv.par_leaf);
   HR_LAUNCHED(ctx);
-  k_gather_refit<128><<<(n + 127) / 128, 128, 0, st>>>(child, par_int, par_leaf, a->prim_box, ids,
-                                                  a->prim_xf, a->prim_aux, (int)n, bv.nodes,
-                                                  lbox, bv.leaf_xf, bv.leaf_aux, bv.leaf_id,
-                                                  arrivals);
-  HR_LAUNCHED(ctx);
+  HR_TRY(gather_refit(ctx, a, bv, ids, st));
+  bv.valid = 1;
+  bv.topo = 1;
+  return HR_OK;
+}
+
+hr_status refit_bvh(hr_ctx* ctx, hr_asset* a, const uint8_t* lod_dev, Bvh& bv, cudaStream_t st) {
+  if (!bv.topo || bv.built_C != a->C || bv.built_E != a->E || bv.built_total != a->n_prims_total ||
+      bv.built_with_lod != (lod_dev != nullptr))
+    return set_error(ctx, HR_ESTATE, "refit: the BVH was built for another hierarchy");
+  if (lod_dev) {
+    uint32_t* diff = nullptr;
+    HR_TRY(scratch(ctx, 36, 4, (void**)&diff));
+    HR_CUDA(ctx, cudaMemsetAsync(diff, 0, 4, st));
+    k_bytes_differ<<<(a->C + 255) / 256, 256, 0, st>>>(lod_dev, bv.lod_built, a->C, diff);
+    HR_LAUNCHED(ctx);
+    uint32_t h = 0;
+    HR_CUDA(ctx, cudaMemcpyAsync(&h, diff, 4, cudaMemcpyDeviceToHost, st));
+    HR_CUDA(ctx, cudaStreamSynchronize(st));
+    if (h) return set_error(ctx, HR_ESTATE, "refit: the LoD selection changed since the build");
+  }
+  bv.valid = 0;
+  const uint32_t n = bv.n;
+  if (n == 1) {
+    k_gather<<<1, 32, 0, st>>>(bv.leaf_id, n, a->prim_xf, a->prim_aux, bv.leaf_xf, bv.leaf_aux,
+                               bv.leaf_id);
+    HR_LAUNCHED(ctx);
+  } else if (n > 1) {
+    HR_TRY(gather_refit(ctx, a, bv, bv.leaf_id, st));
+  }
   bv.valid = 1;
   return HR_OK;
 }

@@ -42,7 +42,16 @@ struct Bvh {
   float4* leaf_aux = nullptr;  // [n] (material index bits, n_tot, r, a*b)
   uint32_t* leaf_id = nullptr; // [n] global primitive id
   uint32_t n_eth = 0;
-  int valid = 0;
+  int valid = 0;               // bounds and leaf records match the primitives
+  // topology kept for refits: children + leaf range, parents; the LoD and
+  // hierarchy shape it was built for
+  int4* child = nullptr;       // [cap]
+  int* par_int = nullptr;      // [cap]
+  int* par_leaf = nullptr;     // [cap]
+  uint8_t* lod_built = nullptr;  // [lod_cap] copy of the LoD of the build (none: all strands)
+  uint32_t lod_cap = 0, built_C = 0, built_E = 0, built_total = 0;
+  int built_with_lod = 0;
+  int topo = 0;                // a topology exists
 };
 
 // Device scratch that grows on demand (owned by the context).
@@ -161,6 +170,10 @@ hr_status lod_select(hr_ctx* ctx, hr_asset* a, const hr_camera* cam, float eps, 
 // Build `out` over the active primitives of LoD `lod_dev` (nullptr: all
 // strands) on stream `st`.
 hr_status build_bvh(hr_ctx* ctx, hr_asset* a, const uint8_t* lod_dev, Bvh& out, cudaStream_t st);
+// Refit `bv` to the asset's current primitive records, keeping its topology
+// and leaf order.  HR_ESTATE unless the hierarchy shape and the LoD `lod_dev`
+// (nullptr: all strands) are those bv was built for (one read-back).
+hr_status refit_bvh(hr_ctx* ctx, hr_asset* a, const uint8_t* lod_dev, Bvh& bv, cudaStream_t st);
 void free_bvh(hr_ctx* ctx, Bvh& b);
 
 // --- tables.cu

@@ -784,19 +784,24 @@ hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_lev
   if (total >= (1ull << 31) || E >= (1ull << 28))
     return set_error(ctx, HR_EINVAL, "hierarchy too large for 31-bit primitive ids");
 
-  // free a previous hierarchy
-  if (a->order) dfree(ctx, a->order, (size_t)N * 4), a->order = nullptr;
-  if (a->cluster_of) dfree(ctx, a->cluster_of, (size_t)N * 4), a->cluster_of = nullptr;
-  if (a->cl_first) dfree(ctx, a->cl_first, (size_t)(a->C + 1) * 4), a->cl_first = nullptr;
-  if (a->xsec) dfree(ctx, a->xsec, (size_t)a->E * (S + 1) * 3 * sizeof(float4)), a->xsec = nullptr;
-  if (a->lod) dfree(ctx, a->lod, a->C), a->lod = nullptr;
-  a->lod_valid = 0;
+  // A hierarchy of the same shape (a new frame of the same hair) reuses the
+  // arrays, and keeps the LoD selection as the previous frame's (Eq. 14);
+  // another shape frees and reallocates them.
+  const bool same_shape = a->order && a->C == C && a->n_levels == L && a->E == (uint32_t)E &&
+                          (E == 0 || a->xsec);
   a->bvh.valid = 0;
-
-  HR_TRY(dalloc(ctx, (void**)&a->order, (size_t)N * 4, "order"));
-  HR_TRY(dalloc(ctx, (void**)&a->cluster_of, (size_t)N * 4, "cluster_of"));
-  HR_TRY(dalloc(ctx, (void**)&a->cl_first, (size_t)(C + 1) * 4, "cluster first"));
-  HR_TRY(dalloc(ctx, (void**)&a->lod, C, "lod"));
+  if (!same_shape) {
+    if (a->order) dfree(ctx, a->order, (size_t)N * 4), a->order = nullptr;
+    if (a->cluster_of) dfree(ctx, a->cluster_of, (size_t)N * 4), a->cluster_of = nullptr;
+    if (a->cl_first) dfree(ctx, a->cl_first, (size_t)(a->C + 1) * 4), a->cl_first = nullptr;
+    if (a->xsec) dfree(ctx, a->xsec, (size_t)a->E * (S + 1) * 3 * sizeof(float4)), a->xsec = nullptr;
+    if (a->lod) dfree(ctx, a->lod, a->C), a->lod = nullptr;
+    a->lod_valid = 0;
+    HR_TRY(dalloc(ctx, (void**)&a->order, (size_t)N * 4, "order"));
+    HR_TRY(dalloc(ctx, (void**)&a->cluster_of, (size_t)N * 4, "cluster_of"));
+    HR_TRY(dalloc(ctx, (void**)&a->cl_first, (size_t)(C + 1) * 4, "cluster first"));
+    HR_TRY(dalloc(ctx, (void**)&a->lod, C, "lod"));
+  }
   a->C = C;
   a->n_levels = L;
   a->E = (uint32_t)E;
@@ -860,7 +865,8 @@ hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_lev
 
   // K2: cross-section fits (FP64 covariance and eigenvectors), materials and
   // thick-hair segment records
-  HR_TRY(dalloc(ctx, (void**)&a->xsec, (size_t)E * (S + 1) * 3 * sizeof(float4), "cross-sections"));
+  if (!a->xsec)
+    HR_TRY(dalloc(ctx, (void**)&a->xsec, (size_t)E * (S + 1) * 3 * sizeof(float4), "cross-sections"));
   float* eth_r = nullptr;
   HR_TRY(scratch(ctx, 5, (size_t)E * sizeof(float), (void**)&eth_r));
   const uint64_t nx = E * (S + 1);

@@ -415,3 +415,76 @@ def test_asset_update_matches_a_fresh_asset(ctx):
     finally:
         hr.hr_asset_destroy(ctx, a)
         hr.hr_asset_destroy(ctx, b)
+
+
+def _moved(verts, amp, seed=3):
+    """The same strands displaced by a smooth field (radius column kept)."""
+    v = np.array(verts, np.float32, copy=True)
+    p = v[..., :3].astype(np.float64)
+    ph = 1.0 + 0.1 * seed
+    v[..., 0] += (amp * np.sin(7.0 * p[..., 1] + ph)).astype(np.float32)
+    v[..., 2] += (amp * np.cos(5.0 * p[..., 0] - ph)).astype(np.float32)
+    return v
+
+
+def test_frame_refit_matches_rebuild(ctx):
+    """HR_FLAG_REFIT after hr_asset_update: with the LoD unchanged the BVH is
+    refit (same topology, new bounds and records) and the frame equals a
+    rebuilt one; with the LoD changed the frame call rebuilds."""
+    w = scenegen.full_head(n=6000, S=16, width=96, height=64, spp=2, n_lights=2, n_clusters=256)
+    d = desc_of(w)
+    moved = _moved(w.scene.verts, 2e-5)
+    a = upload(ctx, w.scene)
+    b = hr.hr_asset_create(ctx, moved, np.ascontiguousarray(w.scene.mat),
+                           np.ascontiguousarray(w.scene.shape))
+    try:
+        img = np.zeros((64, 96, 3), np.float32)
+        st = hr.hr_render_frame(ctx, a, w.n_clusters, w.eps_w, 0, d, img, stats=True)
+        assert st.bvh_refit == 0
+        hr.hr_asset_update(ctx, a, moved)
+        dr = desc_of(w, flags=hr.HR_FLAG_REFIT)
+        st = hr.hr_render_frame(ctx, a, w.n_clusters, w.eps_w, 0, dr, img, stats=True)
+        ref = np.zeros_like(img)
+        hr.hr_render_frame(ctx, b, w.n_clusters, w.eps_w, 0, d, ref)
+        assert st.bvh_refit == 1
+        assert ref.max() > 0
+        assert np.allclose(img, ref, rtol=1e-6, atol=1e-7), np.abs(img - ref).max()
+        # another LoD (a larger width threshold): no refit, same frame as a rebuild
+        st = hr.hr_render_frame(ctx, a, w.n_clusters, 4.0 * w.eps_w, 0, dr, img, stats=True)
+        hr.hr_render_frame(ctx, b, w.n_clusters, 4.0 * w.eps_w, 0, d, ref)
+        assert st.bvh_refit == 0
+        assert np.array_equal(img, ref)
+    finally:
+        hr.hr_asset_destroy(ctx, a)
+        hr.hr_asset_destroy(ctx, b)
+
+
+def test_frame_deferred_lod_follows_eq14(ctx):
+    """HR_FLAG_DEFERRED_LOD: the second frame's LoD comes from Eq. 14 applied
+    to the first frame's selection, as the oracle's deferred rule gives it."""
+    w = scenegen.full_head(n=6000, S=16, width=96, height=64, spp=1, n_lights=1, n_clusters=256)
+    a = upload(ctx, w.scene)
+    try:
+        img = np.zeros((64, 96, 3), np.float32)
+        d = desc_of(w, flags=hr.HR_FLAG_DEFERRED_LOD)
+        st = hr.hr_render_frame(ctx, a, w.n_clusters, w.eps_w, 0, d, img, stats=True)
+        assert st.lod_deferred == 0  # no previous selection yet
+        C, L, E = hr.hr_hierarchy_info(ctx, a)
+        first = np.zeros(C, np.uint8)
+        hr.hr_select_lod(ctx, a, w.camera.pack(), w.eps_w, 0, 0, first)
+        # a closer camera for the second frame, so Eq. 14 has work to do
+        cam2 = scenegen.frame_camera(*w.scene.aabb(), 96, 64, perspective=True, fill=0.3).pack()
+        d2 = hr.render_desc(cam2, w.lights, 1, w.k_depth, w.sample_seed, 0,
+                            hr.HR_FLAG_DEFERRED_LOD)
+        st = hr.hr_render_frame(ctx, a, w.n_clusters, w.eps_w, 0, d2, img, stats=True)
+        assert st.lod_deferred == 1
+        prep = oracle_prepare(w)
+        wcl = oracle.cluster_level_widths(prep.hier, prep.eth, cam2)
+        want = oracle.select_lod_deferred(wcl, first.astype(np.int64), w.eps_w, L)
+        n = hr.hr_bvh_export(ctx, a)
+        ids = np.zeros(n, np.uint32)
+        hr.hr_bvh_export(ctx, a, ids)
+        prep2 = oracle_prepare(w, lod=np.asarray(want, np.uint8))
+        assert np.array_equal(np.sort(ids.astype(np.int64)), np.sort(prep2.ids))
+    finally:
+        hr.hr_asset_destroy(ctx, a)
