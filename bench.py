@@ -405,6 +405,12 @@ def main():
                                 for _ in range(10))
     fp32_ms = statistics.median(hr.hr_render(ctx, asset, desc, img, stats=True).render_ms
                                 for _ in range(10))
+    # the same frame with dual-scattering light paths (a shadow ray per hit and
+    # light, HR_FLAG_SHADOWS), outside the timed region
+    dsh = hr.render_desc(w.camera.pack(), w.lights, spp, w.k_depth, w.sample_seed, w.precision,
+                         hr.HR_FLAG_SHADOWS)
+    shadow_ms = statistics.median(hr.hr_render(ctx, asset, dsh, img, stats=True).render_ms
+                                  for _ in range(5))
     # counting render (outside the timed region): events of the algorithmic FLOP model
     cdesc = hr.render_desc(w.camera.pack(), w.lights, spp, w.k_depth, w.sample_seed, w.precision,
                            hr.HR_FLAG_COUNT)
@@ -564,6 +570,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": config_of(w, args),
             "frame_ms": render_avg, "frame_ms_fp32_warm": fp32_ms, "frame_ms_fp16_warm": fp16_ms,
+            "frame_ms_shadow_rays": shadow_ms,
             "active_prims": int(st.n_active_prims),
             "eth_prims": int(st.n_eth_prims), "stack_overflows": int(st.stack_overflows),
             "roofline": roof, "roofline_other": other,

@@ -114,6 +114,14 @@ typedef struct hr_light {
 /* Render flags (ablations of Section 7, "S-term" figure). */
 #define HR_FLAG_NO_S 1u          /* drop the shadowing-masking term S of Eq. 13 */
 #define HR_FLAG_SINGLE_ON_ETH 2u /* shade thick hairs with the single-fibre BCSDF */
+/* Dual-scattering light paths (Section 3.2; the hairs on a shadow path found
+ * by ray shooting as in Section 6): per hit and light a shadow ray toward the
+ * light crosses hairs; T = d_F prod a_F^n over them (d_F = 0.7, a strand
+ * counts one hair, a thick hair n = rho l sqrt(n_tot / (pi a b)) for its
+ * chord l, a_F at incidence |asin(w . t)|; the shading hair itself is
+ * skipped) scales the light, and the hairs' forward spread variances widen
+ * every lobe of the shading BCSDF.  Off: primary hits only. */
+#define HR_FLAG_SHADOWS 4u
 /* Counting build: hr_render also counts node visits, primitive tests and
  * shading evaluations into hr_stats (slower; used to derive the algorithmic
  * FLOP count of a frame). */
@@ -342,7 +350,8 @@ typedef struct hr_result {
 hr_status hr_serve_start(hr_ctx* ctx, uint32_t max_slots, uint64_t max_batch_samples);
 hr_status hr_serve_stop(hr_ctx* ctx);
 /* Non-blocking submit; *ticket identifies the request.  HR_EBUSY when the
- * queue holds too many pending requests. */
+ * queue holds too many pending requests; HR_EINVAL for HR_FLAG_SHADOWS or
+ * HR_FLAG_COUNT (served frames are primary hits only). */
 hr_status hr_submit(hr_ctx* ctx, const hr_request* req, uint64_t* ticket);
 /* Wait up to timeout_ms (0: do not wait) for a request.  HR_OK and *result
  * filled when done; HR_ENOTREADY if timeout_ms == 0 and not done;

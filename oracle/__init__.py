@@ -30,6 +30,7 @@ _lib = None
 
 FLAG_NO_S = 1
 FLAG_SINGLE_ON_ETH = 2
+FLAG_SHADOWS = 4
 PRIM_STRIDE = 15
 
 
@@ -66,6 +67,9 @@ def _load():
         lib.oracle_albedo.argtypes = [PD, ctypes.c_int, PD, PD, D, PD, PD, PD]
         lib.oracle_albedo_2d.argtypes = [PD, ctypes.c_int, PD, PD, D, PD, PD]
         lib.oracle_f_single.argtypes = [PD, D, D, D, PD]
+        lib.oracle_f_single_spread.argtypes = [PD, D, D, D, D, PD]
+        lib.oracle_shadow_path.argtypes = [PD, ctypes.c_int64, PD, ctypes.c_int64, ctypes.c_int,
+                                           PD, PD, PD, PD, D, ctypes.c_int, PD, PD]
         lib.oracle_f_ours.argtypes = [PD, ctypes.c_int, PD, PD, D, D, D, D, D, ctypes.c_uint, PD]
         lib.oracle_intersect.argtypes = [PD, PD, PD, PD, PD]
         lib.oracle_intersect.restype = ctypes.c_int
@@ -135,6 +139,31 @@ def f_single(mat12, th_i, th_o, cphi):
     out = np.zeros(3)
     _load().oracle_f_single(_pd(m), th_i, th_o, cphi, _pd(out))
     return out
+
+
+def f_single_spread(mat12, th_i, th_o, cphi, sg2):
+    """f_single with every lobe's variance grown by sg2 (the spread of the
+    light path under shadow rays)."""
+    out = np.zeros(3)
+    m = np.ascontiguousarray(mat12, np.float64)
+    _load().oracle_f_single_spread(_pd(m), th_i, th_o, cphi, sg2, _pd(out))
+    return out
+
+
+def shadow_path(rows, mats, x, wi, t_light, self_mat, nq: int = 384):
+    """(T [3], sg2): the dual-scattering transmittance and spread variance of
+    the light path from x along wi up to t_light, over primitive rows (15
+    doubles each) with material rows `mats`, skipping material `self_mat`."""
+    r = np.ascontiguousarray(rows, np.float64).reshape(-1, 15)
+    mt = np.ascontiguousarray(mats, np.float64).reshape(-1, 12)
+    qx, qw = gauss_legendre(nq)
+    xx = np.ascontiguousarray(x, np.float64)
+    ww = np.ascontiguousarray(wi, np.float64)
+    T = np.zeros(3)
+    sg2 = np.zeros(1)
+    _load().oracle_shadow_path(_pd(r), r.shape[0], _pd(mt), mt.shape[0], nq, _pd(qx), _pd(qw),
+                               _pd(xx), _pd(ww), float(t_light), int(self_mat), _pd(T), _pd(sg2))
+    return T, float(sg2[0])
 
 
 def f_ours(mat12, th_i, th_o, cphi, rho, n_view, flags=0, nq: int = 384):

@@ -25,6 +25,10 @@
 /* flag bits (same values as the library's render flags) */
 #define FLAG_NO_S 1u          /* drop the shadowing-masking term S (ablation, Fig. "S-term") */
 #define FLAG_SINGLE_ON_ETH 2u /* shade thick hairs with f_single (ablation, Fig. "S-term") */
+#define FLAG_SHADOWS 4u       /* dual-scattering transmittance along shadow rays (Section 3.2, 6) */
+/* READING: the forward scattering density d_F of dual scattering (Section
+ * 3.2 names it, without a value); Zinke et al. 2008 use 0.7.                */
+#define D_F 0.7
 
 typedef struct { double x, y, z; } v3;
 static v3 mk(double x, double y, double z) { v3 r = {x, y, z}; return r; }
@@ -81,12 +85,16 @@ double oracle_im(int nq, const double* qx, const double* qw, double theta, doubl
 /* Single-fibre BCSDF, Eq. (1): sum over R, TT, D of A_p M_p(theta_h) N_p(phi)
  * with M_R = G(beta_R), N_R = 1/2pi; M_TT = G(beta_TT), N_TT = G(gamma_TT,
  * phi - pi); M_D = 1/pi, N_D = 1/2pi (the n = 1 case of Eq. 6).
- * phi is taken in [0, pi] from cos(phi) (the model is even in phi).          */
-static void f_single(const material* m, double th_i, double th_o, double cphi, double out[3]) {
+ * phi is taken in [0, pi] from cos(phi) (the model is even in phi).
+ * sg2 is the forward spread variance gathered along the light's path (zero
+ * without shadow rays); READING: it adds to every lobe's variance.          */
+static void f_single(const material* m, double th_i, double th_o, double cphi, double sg2,
+                     double out[3]) {
   double th_h = 0.5 * (th_i + th_o);
   double phi = acos(clampd(cphi, -1.0, 1.0));
-  double mR = oracle_gauss(m->bR, th_h) / (2.0 * PI);
-  double mTT = oracle_gauss(m->bTT, th_h) * oracle_gauss(m->gTT, phi - PI);
+  double mR = oracle_gauss(sqrt(m->bR * m->bR + sg2), th_h) / (2.0 * PI);
+  double mTT = oracle_gauss(sqrt(m->bTT * m->bTT + sg2), th_h) *
+               oracle_gauss(sqrt(m->gTT * m->gTT + sg2), phi - PI);
   double mD = 1.0 / (PI * 2.0 * PI);
   for (int c = 0; c < 3; ++c) out[c] = m->A[0][c] * mR + m->A[1][c] * mTT + m->A[2][c] * mD;
 }
@@ -166,7 +174,7 @@ void oracle_back_atten(double aF, double aB, double n, double* out3) {
  * P_m = c_m (1 - rho), c_m = 0.2, P_n = 1 - P_m - P_s, applied for
  * phi in (-pi/2, pi/2) only (READING: P_n floored at 0).                     */
 static void f_ours(const material* m, const quad* q, double th_i, double th_o, double cphi,
-                   double rho, double n_view, unsigned flags, double out[3]) {
+                   double rho, double n_view, unsigned flags, double sg2, double out[3]) {
   double th_h = 0.5 * (th_i + th_o);
   double th_d = th_i - th_o;
   double phi = acos(clampd(cphi, -1.0, 1.0));
@@ -174,9 +182,9 @@ static void f_ours(const material* m, const quad* q, double th_i, double th_o, d
   double aF[3], aB[3], s2;
   albedo_split(m, q, th_d, aF, aB, &s2);
   double n = back ? 1.0 : n_view;
-  double bR = sqrt(m->bR * m->bR + (n - 1.0) * s2);
-  double bT = sqrt(m->bTT * m->bTT + (n - 1.0) * s2);
-  double gT = sqrt(m->gTT * m->gTT + (n - 1.0) * s2);
+  double bR = sqrt(m->bR * m->bR + (n - 1.0) * s2 + sg2);
+  double bT = sqrt(m->bTT * m->bTT + (n - 1.0) * s2 + sg2);
+  double gT = sqrt(m->gTT * m->gTT + (n - 1.0) * s2 + sg2);
   double mR = oracle_gauss(bR, th_h) / (2.0 * PI);
   double mTT = oracle_gauss(bT, th_h) * oracle_gauss(gT, phi - PI);
   double mD = 1.0 / (PI * 2.0 * PI);
@@ -196,7 +204,7 @@ static void f_ours(const material* m, const quad* q, double th_i, double th_o, d
     double bR2 = m->bR * m->bR;
     double vB = (w1 * (bR2 + 2.0 * s2) + w3 * (3.0 * bR2 + 2.0 * s2) +
                  w1p * (bR2 + (n_view + 1.0) * s2)) / (w1 + w3 + w1p);
-    double mB = oracle_gauss(sqrt(vB), th_h) / PI;
+    double mB = oracle_gauss(sqrt(vB + sg2), th_h) / PI;
     for (int c = 0; c < 3; ++c) lob[c] += (A1p[c] + A1[c] + A3[c]) * mB;
     if (!(flags & FLAG_NO_S)) {
       double Ps = (1.0 - rho) * (1.0 - cphi);
@@ -220,7 +228,14 @@ static void load_material(const double* row, material* m) {
 void oracle_f_single(const double* mat12, double th_i, double th_o, double cphi, double* out3) {
   material m;
   load_material(mat12, &m);
-  f_single(&m, th_i, th_o, cphi, out3);
+  f_single(&m, th_i, th_o, cphi, 0.0, out3);
+}
+
+void oracle_f_single_spread(const double* mat12, double th_i, double th_o, double cphi,
+                            double sg2, double* out3) {
+  material m;
+  load_material(mat12, &m);
+  f_single(&m, th_i, th_o, cphi, sg2, out3);
 }
 
 void oracle_f_ours(const double* mat12, int nq, const double* qx, const double* qw, double th_i,
@@ -229,7 +244,7 @@ void oracle_f_ours(const double* mat12, int nq, const double* qx, const double* 
   material m;
   load_material(mat12, &m);
   quad q = {nq, qx, qw};
-  f_ours(&m, &q, th_i, th_o, cphi, rho, n_view, flags, out3);
+  f_ours(&m, &q, th_i, th_o, cphi, rho, n_view, flags, 0.0, out3);
 }
 
 /* Directional albedo of f_single by direct 2-D midpoint-free Gauss-Legendre
@@ -250,7 +265,7 @@ void oracle_albedo_2d(const double* mat12, int nq, const double* qx, const doubl
         double phi = 0.25 * PI * (qx[j] + 1.0) + (half ? 0.5 * PI : 0.0);
         double wp = 0.25 * PI * qw[j] * 2.0;
         double f[3];
-        f_single(&m, theta_i, to, cos(phi), f);
+        f_single(&m, theta_i, to, cos(phi), 0.0, f);
         for (int c = 0; c < 3; ++c) (half ? front3 : back3)[c] += wt * wp * f[c];
       }
     }
@@ -327,6 +342,77 @@ int oracle_intersect(const double* row, const double* o3, const double* d3, doub
   return intersect(&p, mk(o3[0], o3[1], o3[2]), mk(d3[0], d3[1], d3[2]), 0.0, t_out, chord_out);
 }
 
+/* Ray interval inside the finite cylinder volume of one primitive: the part
+ * of the infinite elliptic cylinder's interval [t-, t+] whose axial
+ * coordinate lies in [0, L].  Returns 0 when the ray misses it.              */
+static int span(const prim* p, v3 o, v3 d, double* lo, double* hi) {
+  v3 r = sub(o, p->c0);
+  double u0 = dot(r, p->e1) / p->a, v0 = dot(r, p->e2) / p->b, w0 = dot(r, p->t);
+  double du = dot(d, p->e1) / p->a, dv = dot(d, p->e2) / p->b, dw = dot(d, p->t);
+  double A = du * du + dv * dv;
+  if (A <= 0.0) return 0;
+  double B = 2.0 * (u0 * du + v0 * dv);
+  double C = u0 * u0 + v0 * v0 - 1.0;
+  double disc = B * B - 4.0 * A * C;
+  if (disc < 0.0) return 0;
+  double sq = sqrt(disc);
+  double tm = (-B - sq) / (2.0 * A), tp = (-B + sq) / (2.0 * A);
+  double wlo = -INFINITY, whi = INFINITY;
+  if (dw != 0.0) {
+    double ta = (0.0 - w0) / dw, tb = (p->L - w0) / dw;
+    wlo = ta < tb ? ta : tb;
+    whi = ta < tb ? tb : ta;
+  } else if (w0 < 0.0 || w0 > p->L) {
+    return 0;
+  }
+  *lo = tm > wlo ? tm : wlo;
+  *hi = tp < whi ? tp : whi;
+  return *hi > *lo;
+}
+
+/* Transmittance of the light path of dual scattering (Section 3.2: the light
+ * reaching a hair is attenuated by the forward scattering of every hair it
+ * passes; Section 6 finds those hairs by ray shooting).  READING:
+ *  - the shadow ray leaves x along wi and ends at the light (t_light, +inf
+ *    for a directional light); every primitive of the shading hair itself
+ *    (the same material row: the same strand or thick hair) is skipped;
+ *  - a primitive is crossed when the ray's interval inside its cylinder
+ *    meets (0, t_light); a strand segment counts one hair, a thick-hair
+ *    segment n = rho l sqrt(n_tot / (pi a b)) hairs (the hair-number estimate
+ *    of Section 4, l its chord within (0, t_light));
+ *  - each crossed hair attenuates by its forward albedo a_F at incidence
+ *    |asin(wi . t)| (the mirror configuration of the a_F reading) and adds
+ *    its forward spread variance sigma_f^2, n times;
+ *  - T = d_F * prod a_F^n when at least one hair is crossed, else 1.        */
+static void shadow_path(const prim* P, int64_t n_prims, const material* M, const quad* q, v3 x,
+                        v3 wi, double t_light, int self_mat, double T[3], double* sg2) {
+  int crossed = 0;
+  T[0] = T[1] = T[2] = 1.0;
+  *sg2 = 0.0;
+  for (int64_t j = 0; j < n_prims; ++j) {
+    const prim* p = &P[j];
+    if (p->mat == self_mat) continue;
+    double lo, hi;
+    if (!span(p, x, wi, &lo, &hi)) continue;
+    double a = lo > 0.0 ? lo : 0.0, b = hi < t_light ? hi : t_light;
+    if (!(b > a)) continue;
+    double n = 1.0;
+    if (p->kind == 1) {
+      double rho = p->ntot * p->r * p->r / (p->a * p->b);
+      if (rho > 1.0) rho = 1.0;
+      n = rho * (b - a) * sqrt(p->ntot / (PI * p->a * p->b));
+    }
+    double th = asin(clampd(dot(wi, p->t), -1.0, 1.0));
+    double aF[3], aB[3], s2;
+    albedo_split(&M[p->mat], q, 2.0 * th, aF, aB, &s2);
+    for (int c = 0; c < 3; ++c) T[c] *= pow(aF[c], n);
+    *sg2 += n * s2;
+    crossed = 1;
+  }
+  if (crossed)
+    for (int c = 0; c < 3; ++c) T[c] *= D_F;
+}
+
 /* ------------------------------------------------------------ camera */
 
 static uint64_t splitmix_out(uint64_t seed, uint64_t i) {
@@ -364,6 +450,27 @@ static void camera_ray(const camera* c, uint64_t seed, int64_t sid, int spp, v3*
 
 /* ------------------------------------------------------------ renderer */
 
+static void load_prims(const double* prim_rows, int64_t n_prims, const int64_t* prim_ids,
+                       prim* P) {
+  for (int64_t j = 0; j < n_prims; ++j) {
+    const double* r = prim_rows + PRIM_STRIDE * j;
+    v3 c0 = mk(r[0], r[1], r[2]), c1 = mk(r[3], r[4], r[5]);
+    v3 ax = sub(c1, c0);
+    P[j].c0 = c0;
+    P[j].L = len(ax);
+    P[j].t = scl(ax, 1.0 / P[j].L);
+    P[j].e1 = mk(r[6], r[7], r[8]);
+    P[j].e2 = cross(P[j].t, P[j].e1);
+    P[j].a = r[9];
+    P[j].b = r[10];
+    P[j].kind = (int)r[11];
+    P[j].mat = (int)r[12];
+    P[j].ntot = r[13];
+    P[j].r = r[14];
+    P[j].id = prim_ids ? prim_ids[j] : j;
+  }
+}
+
 typedef struct {
   const prim* prims;
   int64_t n_prims;
@@ -383,8 +490,10 @@ typedef struct {
 } job;
 
 /* Radiance leaving hit point x toward -d: sum over lights of
- * f(omega_i, omega_o) E cos(theta_i) (READING: no shadow rays; directional
- * light E = rgb, point light E = rgb / distance^2).  The angles are measured
+ * T f(omega_i, omega_o) E cos(theta_i) (directional light E = rgb, point
+ * light E = rgb / distance^2).  T = 1 and f unwidened without FLAG_SHADOWS
+ * (READING: primary hits only); with it, T and the spread variance come
+ * from the light path (shadow_path).  The angles are measured
  * against the segment axis t: sin(theta) = omega . t, cos(phi) from the
  * projections onto the normal plane (Section 3).                            */
 static void shade(const job* jb, const prim* p, v3 x, v3 d, double chord, double* rgb,
@@ -431,13 +540,17 @@ static void shade(const job* jb, const prim* p, v3 x, v3 d, double chord, double
     v3 wip = sub(wi, scl(p->t, si));
     double nip = len(wip);
     double cphi = (nip > 0.0 && nop > 0.0) ? clampd(dot(wip, wop) / (nip * nop), -1.0, 1.0) : 1.0;
+    double T[3] = {1.0, 1.0, 1.0}, sg2 = 0.0;
+    if (jb->flags & FLAG_SHADOWS)
+      shadow_path(jb->prims, jb->n_prims, jb->mats, &jb->q, x, wi,
+                  L[3] == 0.0 ? INFINITY : 1.0 / sqrt(E), p->mat, T, &sg2);
     double f[3];
     if (p->kind == 1 && !(jb->flags & FLAG_SINGLE_ON_ETH))
-      f_ours(m, &jb->q, th_i, th_o, cphi, rho, n_view, jb->flags, f);
+      f_ours(m, &jb->q, th_i, th_o, cphi, rho, n_view, jb->flags, sg2, f);
     else
-      f_single(m, th_i, th_o, cphi, f);
+      f_single(m, th_i, th_o, cphi, sg2, f);
     double g = E * sqrt(1.0 - si * si);
-    for (int c = 0; c < 3; ++c) rgb[c] += f[c] * g * L[4 + c];
+    for (int c = 0; c < 3; ++c) rgb[c] += f[c] * T[c] * g * L[4 + c];
   }
   /* READING: a thick hair's opacity is the Poisson probability 1 - exp(-n_c)
    * that the view chord meets at least one member strand; a strand is opaque. */
@@ -503,23 +616,7 @@ int oracle_render(const double* prim_rows, const int64_t* prim_ids, int64_t n_pr
   prim* P = (prim*)malloc(sizeof(prim) * (size_t)(n_prims > 0 ? n_prims : 1));
   material* M = (material*)malloc(sizeof(material) * (size_t)(n_mats > 0 ? n_mats : 1));
   if (!P || !M) return 2;
-  for (int64_t j = 0; j < n_prims; ++j) {
-    const double* r = prim_rows + PRIM_STRIDE * j;
-    v3 c0 = mk(r[0], r[1], r[2]), c1 = mk(r[3], r[4], r[5]);
-    v3 ax = sub(c1, c0);
-    P[j].c0 = c0;
-    P[j].L = len(ax);
-    P[j].t = scl(ax, 1.0 / P[j].L);
-    P[j].e1 = mk(r[6], r[7], r[8]);
-    P[j].e2 = cross(P[j].t, P[j].e1);
-    P[j].a = r[9];
-    P[j].b = r[10];
-    P[j].kind = (int)r[11];
-    P[j].mat = (int)r[12];
-    P[j].ntot = r[13];
-    P[j].r = r[14];
-    P[j].id = prim_ids[j];
-  }
+  load_prims(prim_rows, n_prims, prim_ids, P);
   for (int64_t j = 0; j < n_mats; ++j) load_material(mat_rows + 12 * j, &M[j]);
   camera cam;
   cam.kind = (int)cam_rec[0];
@@ -583,4 +680,26 @@ void oracle_camera_ray(const double* cam_rec, uint64_t seed, int64_t sid, int sp
   camera_ray(&cam, seed, sid, spp, &o, &d);
   o3[0] = o.x; o3[1] = o.y; o3[2] = o.z;
   d3[0] = d.x; d3[1] = d.y; d3[2] = d.z;
+}
+
+/* The light-path transmittance of one point, exported for the pins. */
+void oracle_shadow_path(const double* prim_rows, int64_t n_prims, const double* mat_rows,
+                        int64_t n_mats, int nq, const double* qx, const double* qw,
+                        const double* x3, const double* wi3, double t_light, int self_mat,
+                        double* T3, double* sg2) {
+  prim* P = (prim*)malloc(sizeof(prim) * (size_t)(n_prims > 0 ? n_prims : 1));
+  material* M = (material*)malloc(sizeof(material) * (size_t)(n_mats > 0 ? n_mats : 1));
+  if (!P || !M) {
+    free(P);
+    free(M);
+    T3[0] = T3[1] = T3[2] = -1.0;
+    return;
+  }
+  load_prims(prim_rows, n_prims, 0, P);
+  for (int64_t j = 0; j < n_mats; ++j) load_material(mat_rows + 12 * j, &M[j]);
+  quad q = {nq, qx, qw};
+  shadow_path(P, n_prims, M, &q, mk(x3[0], x3[1], x3[2]), mk(wi3[0], wi3[1], wi3[2]), t_light,
+              self_mat, T3, sg2);
+  free(P);
+  free(M);
 }

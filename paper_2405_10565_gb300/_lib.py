@@ -34,6 +34,7 @@ HR_PREC_FP32 = 0
 HR_PREC_FP16 = 1
 HR_FLAG_NO_S = 1
 HR_FLAG_SINGLE_ON_ETH = 2
+HR_FLAG_SHADOWS = 4
 HR_FLAG_COUNT = 256
 HR_FLAG_REFIT = 512
 HR_FLAG_DEFERRED_LOD = 1024

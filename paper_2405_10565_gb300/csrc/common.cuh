@@ -230,6 +230,8 @@ inline uint32_t tiles_for(uint32_t W, uint32_t H, uint32_t spp) {
 }
 hr_status launch_frame(hr_ctx* ctx, const FrameArgs& fa, int precision, bool count,
                        float* rgb_dev, cudaStream_t st);
+hr_status launch_frame_shadow(hr_ctx* ctx, const FrameArgs& fa, int precision, bool count,
+                       float* rgb_dev, cudaStream_t st);
 hr_status launch_samples(hr_ctx* ctx, const FrameArgs& fa, int precision, const uint32_t* sids,
                          uint32_t m, float* rad_dev, int32_t* hit_dev, cudaStream_t st);
 

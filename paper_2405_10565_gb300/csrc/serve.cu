@@ -532,6 +532,8 @@ hr_status hr_submit(hr_ctx* ctx, const hr_request* req, uint64_t* ticket) {
   if (!req->asset || !req->rgb_out) return set_error(ctx, HR_EINVAL, "request asset / output");
   HR_TRY(check_desc(ctx, &req->desc));
   if (req->budget_bias < 0) return set_error(ctx, HR_EINVAL, "budget_bias");
+  if (req->desc.flags & (HR_FLAG_SHADOWS | HR_FLAG_COUNT))
+    return set_error(ctx, HR_EINVAL, "serving renders primary hits only (no shadow rays, no counting)");
   Request* r = new Request();
   r->req = *req;
   r->host_out = !is_device_ptr(req->rgb_out);

@@ -237,6 +237,16 @@ __device__ __forceinline__ bool traverse(const FrameArgs& fa, const float3 o, co
   return ok;
 }
 
+// Slab reciprocals of a ray: a zero direction component would turn the slab
+// products into inf - inf, so its sign is kept and its magnitude floored.
+__device__ __forceinline__ void ray_slabs(const float3 o, const float3 d, float3& inv,
+                                          float3& ooi) {
+  inv = f3(1.0f / (fabsf(d.x) > 1e-12f ? d.x : copysignf(1e-12f, d.x)),
+           1.0f / (fabsf(d.y) > 1e-12f ? d.y : copysignf(1e-12f, d.y)),
+           1.0f / (fabsf(d.z) > 1e-12f ? d.z : copysignf(1e-12f, d.z)));
+  ooi = f3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
+}
+
 // ------------------------------------------------------------------ scattering
 
 struct Mat {
@@ -300,14 +310,19 @@ constexpr float kInv2Pi = 0.15915494309189535f;
 constexpr float kInvPi = 0.3183098861837907f;
 constexpr float kInv2Pi2 = 0.05066059182116889f;  // 1 / (2 pi^2)
 
-// Single-fibre BCSDF, Eq. (1).
+// Single-fibre BCSDF, Eq. (1).  sg2: the spread variance gathered on the
+// light's path (0 without shadow rays), added to every lobe's variance.
 template <int PREC>
 __device__ __forceinline__ void f_single(const Tables& tb, const Mat& m, float th_i, float th_o,
-                                         float cphi, float out[3]) {
+                                         float cphi, float sg2, float out[3]) {
   const float th_h = 0.5f * (th_i + th_o);
   const float phi = acosf(clampf(cphi, -1.f, 1.f));
-  const float mR = gauss<PREC>(tb, m.bR, th_h) * kInv2Pi;
-  const float mT = gauss<PREC>(tb, m.bT, th_h) * gauss<PREC>(tb, m.gT, phi - kPi);
+  const bool wide = sg2 > 0.f;
+  const float bR = wide ? sqrtf(fmaf(m.bR, m.bR, sg2)) : m.bR;
+  const float bT = wide ? sqrtf(fmaf(m.bT, m.bT, sg2)) : m.bT;
+  const float gT = wide ? sqrtf(fmaf(m.gT, m.gT, sg2)) : m.gT;
+  const float mR = gauss<PREC>(tb, bR, th_h) * kInv2Pi;
+  const float mT = gauss<PREC>(tb, bT, th_h) * gauss<PREC>(tb, gT, phi - kPi);
 #pragma unroll
   for (int c = 0; c < 3; ++c)
     out[c] = fmaf(m.A[0][c], mR, fmaf(m.A[1][c], mT, m.A[2][c] * kInv2Pi2));
@@ -326,7 +341,7 @@ struct EthHit {
 template <int PREC>
 __device__ __forceinline__ void f_ours(const Tables& tb, const Mat& m, const EthHit& eh,
                                        float th_i, float th_o, float cphi, uint32_t flags,
-                                       float out[3]) {
+                                       float sg2, float out[3]) {
   const float th_h = 0.5f * (th_i + th_o);
   const float ta = 0.5f * fabsf(th_i - th_o);
   const float phi = acosf(clampf(cphi, -1.f, 1.f));
@@ -348,9 +363,9 @@ __device__ __forceinline__ void f_ours(const Tables& tb, const Mat& m, const Eth
   const bool back = cphi > 0.f;
   const float n = back ? 1.f : eh.n_view;
   const float nm1 = n - 1.f;
-  const float mR = gauss<PREC>(tb, sqrtf(fmaf(nm1, s2, bR2)), th_h) * kInv2Pi;
-  const float mT = gauss<PREC>(tb, sqrtf(fmaf(nm1, s2, bT2)), th_h) *
-                   gauss<PREC>(tb, sqrtf(fmaf(nm1, s2, m.gT * m.gT)), phi - kPi);
+  const float mR = gauss<PREC>(tb, sqrtf(fmaf(nm1, s2, bR2) + sg2), th_h) * kInv2Pi;
+  const float mT = gauss<PREC>(tb, sqrtf(fmaf(nm1, s2, bT2) + sg2), th_h) *
+                   gauss<PREC>(tb, sqrtf(fmaf(nm1, s2, m.gT * m.gT) + sg2), phi - kPi);
   float lob[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -374,7 +389,7 @@ __device__ __forceinline__ void f_ours(const Tables& tb, const Mat& m, const Eth
     }
     const float vB = (w1 * (bR2 + 2.f * s2) + w3 * (3.f * bR2 + 2.f * s2) +
                       w1p * (bR2 + (eh.n_view + 1.f) * s2)) / (w1 + w3 + w1p);
-    const float mB = gauss<PREC>(tb, sqrtf(vB), th_h) * kInvPi;
+    const float mB = gauss<PREC>(tb, sqrtf(vB + sg2), th_h) * kInvPi;
 #pragma unroll
     for (int c = 0; c < 3; ++c) lob[c] = fmaf(A1p[c] + A1[c] + A3[c], mB, lob[c]);
     if (!(flags & HR_FLAG_NO_S)) {
@@ -389,9 +404,159 @@ __device__ __forceinline__ void f_ours(const Tables& tb, const Mat& m, const Eth
   for (int c = 0; c < 3; ++c) out[c] = lob[c];
 }
 
-// Radiance of one hit toward -d (sum over lights of f E cos(theta_i)) and its
-// opacity (strand 1; thick hair 1 - exp(-2 r l n_tot / (pi a b))).
+// Forward albedo a_F (rgb) and forward spread variance of a fibre for light
+// at incidence |theta| (the a_F reading of the aggregated model).
+template <int PREC>
+__device__ __forceinline__ void forward_albedo(const Tables& tb, const Mat& m, float theta_abs,
+                                               float aF[3], float& s2) {
+  const float imR = im_lookup<PREC>(tb, theta_abs, m.bR);
+  const float imT = im_lookup<PREC>(tb, theta_abs, m.bT);
+  const float nF = erff(kPi / (2.f * 1.41421356f * m.gT));
+  float wR = 0.f, wT = 0.f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float r = m.A[0][c] * imR * 0.5f;
+    const float tt = m.A[1][c] * imT * nF;
+    aF[c] = r + tt + m.A[2][c] * 0.25f;
+    wR += r;
+    wT += tt;
+  }
+  s2 = (wR * m.bR * m.bR + wT * m.bT * m.bT) / (wR + wT);
+}
+
+// The hair a shadow ray crosses in one leaf: the ray's interval inside the
+// leaf's finite cylinder, clipped to (0, tmax).  Returns false when empty.
+__device__ __forceinline__ bool leaf_span(const float4* __restrict__ xf, const float3 o,
+                                          const float3 d, const float tmax, float& lo, float& hi) {
+  const float4 r0 = __ldg(xf), r1 = __ldg(xf + 1), r2 = __ldg(xf + 2);
+  const float u0 = fmaf(r0.x, o.x, fmaf(r0.y, o.y, fmaf(r0.z, o.z, r0.w)));
+  const float v0 = fmaf(r1.x, o.x, fmaf(r1.y, o.y, fmaf(r1.z, o.z, r1.w)));
+  const float du = fmaf(r0.x, d.x, fmaf(r0.y, d.y, r0.z * d.z));
+  const float dv = fmaf(r1.x, d.x, fmaf(r1.y, d.y, r1.z * d.z));
+  const float A = fmaf(du, du, dv * dv);
+  if (!(A > 0.f)) return false;
+  const float inv = 1.0f / A;
+  const float tc = -fmaf(u0, du, v0 * dv) * inv;
+  const float uc = fmaf(tc, du, u0), vc = fmaf(tc, dv, v0);
+  const float h2 = fmaf(uc, uc, vc * vc);
+  if (h2 > 1.f) return false;
+  const float half = sqrtf((1.f - h2) * inv);
+  lo = tc - half;
+  hi = tc + half;
+  const float w0 = fmaf(r2.x, o.x, fmaf(r2.y, o.y, fmaf(r2.z, o.z, r2.w)));
+  const float dw = fmaf(r2.x, d.x, fmaf(r2.y, d.y, r2.z * d.z));
+  if (dw != 0.f) {
+    const float idw = 1.0f / dw;
+    const float ta = -w0 * idw, tb = (1.f - w0) * idw;
+    lo = fmaxf(lo, fminf(ta, tb));
+    hi = fminf(hi, fmaxf(ta, tb));
+  } else if (w0 < 0.f || w0 > 1.f) {
+    return false;
+  }
+  lo = fmaxf(lo, 0.f);
+  hi = fminf(hi, tmax);
+  return hi > lo;
+}
+
+// Transmittance of the light path of dual scattering (readings as in the
+// oracle): the shadow ray from x along wi up to tmax crosses hairs; every
+// primitive of the shading hair itself (material row self_mat) is skipped; a
+// strand segment counts one hair, a thick-hair segment rho l sqrt(n_tot /
+// (pi a b)) for its chord l; each hair multiplies T by its forward albedo at
+// incidence |asin(wi . t)| and adds its forward spread variance; T = d_F prod
+// a_F^n (d_F = 0.7) once a hair is crossed.  The walk visits every box on the
+// path (all crossings count) and stops early once T < 1e-7 in every channel,
+// where the light's contribution is below FP32 resolution of the pixel.
+constexpr float kDF = 0.7f;
 template <int PREC, bool COUNT>
+__device__ __forceinline__ void shadow_path(const FrameArgs& fa, const float3 x, const float3 wi,
+                                            const float tmax, const uint32_t self_mat, float T[3],
+                                            float& sg2, bool& ok, Counts& cn) {
+  T[0] = T[1] = T[2] = 1.f;
+  sg2 = 0.f;
+  if (fa.n_prims == 0) return;
+  float3 inv, ooi;
+  ray_slabs(x, wi, inv, ooi);
+  int stack[kStack];
+  int sp = 0;
+  int node = fa.n_prims == 1 ? ~0 : 0;
+  bool crossed = false;
+  for (;;) {
+    if (node >= 0) {
+      const float4* nd = fa.nodes + 4 * (size_t)node;
+      const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+      if (COUNT) ++cn.nodes;
+      float lx = fmaf(n0.x, inv.x, -ooi.x), hx = fmaf(n0.y, inv.x, -ooi.x);
+      float ly = fmaf(n0.z, inv.y, -ooi.y), hy = fmaf(n0.w, inv.y, -ooi.y);
+      float lz = fmaf(n2.x, inv.z, -ooi.z), hz = fmaf(n2.y, inv.z, -ooi.z);
+      const float a0 = fmaxf(fmaxf(fminf(lx, hx), fminf(ly, hy)), fmaxf(fminf(lz, hz), 0.f));
+      const float b0 = fminf(fminf(fmaxf(lx, hx), fmaxf(ly, hy)), fminf(fmaxf(lz, hz), tmax));
+      lx = fmaf(n1.x, inv.x, -ooi.x); hx = fmaf(n1.y, inv.x, -ooi.x);
+      ly = fmaf(n1.z, inv.y, -ooi.y); hy = fmaf(n1.w, inv.y, -ooi.y);
+      lz = fmaf(n2.z, inv.z, -ooi.z); hz = fmaf(n2.w, inv.z, -ooi.z);
+      const float a1 = fmaxf(fmaxf(fminf(lx, hx), fminf(ly, hy)), fmaxf(fminf(lz, hz), 0.f));
+      const float b1 = fminf(fminf(fmaxf(lx, hx), fmaxf(ly, hy)), fminf(fmaxf(lz, hz), tmax));
+      const bool h0 = a0 <= b0, h1 = a1 <= b1;
+      const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+      if (h0 && h1) {
+        if (sp < kStack)
+          stack[sp++] = c1;
+        else
+          ok = false;
+        node = c0;
+        continue;
+      }
+      if (h0 || h1) {
+        node = h0 ? c0 : c1;
+        continue;
+      }
+    } else {
+      const uint32_t leaf = (uint32_t)(~node);
+      const float4 aux = __ldg(fa.leaf_aux + leaf);
+      float lo, hi;
+      if (COUNT) ++cn.tests;
+      if (__float_as_uint(aux.x) != self_mat &&
+          leaf_span(fa.leaf_xf + 3 * (size_t)leaf, x, wi, tmax, lo, hi)) {
+        const float4 r2 = __ldg(fa.leaf_xf + 3 * (size_t)leaf + 2);
+        const float si = clampf(dot3(wi, f3(r2.x, r2.y, r2.z)) *
+                                    rsqrtf(r2.x * r2.x + r2.y * r2.y + r2.z * r2.z),
+                                -1.f, 1.f);
+        Mat m;
+        load_mat(fa.mat + (size_t)__float_as_uint(aux.x) * HR_MAT_FLOATS, m);
+        float aF[3], s2;
+        forward_albedo<PREC>(fa.tables, m, fabsf(asinf(si)), aF, s2);
+        if (aux.y > 0.f) {  // thick hair: its hair number over the chord
+          const float ntot = aux.y, r = aux.z, ab = aux.w;
+          const float rho = fminf(1.f, ntot * r * r / ab);
+          const float n = rho * (hi - lo) * sqrtf(ntot / (kPi * ab));
+#pragma unroll
+          for (int c = 0; c < 3; ++c) T[c] *= exp2f(n * __log2f(aF[c]));
+          sg2 = fmaf(n, s2, sg2);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) T[c] *= aF[c];
+          sg2 += s2;
+        }
+        crossed = true;
+        if (fmaxf(T[0], fmaxf(T[1], T[2])) < 1e-7f) break;
+      }
+    }
+    if (sp == 0) break;
+    node = stack[--sp];
+  }
+  if (crossed) {
+    T[0] *= kDF;
+    T[1] *= kDF;
+    T[2] *= kDF;
+  }
+}
+
+// Radiance of one hit toward -d (sum over lights of T f E cos(theta_i), T and
+// the spread of f from shadow_path when SHADOW (HR_FLAG_SHADOWS), else T = 1)
+// and its opacity (strand 1; thick hair 1 - exp(-2 r l n_tot / (pi a b))).
+// SHADOW is a template parameter so kernels without shadow rays carry none
+// of their registers.
+template <int PREC, bool COUNT, bool SHADOW = false>
 __device__ __forceinline__ void shade_hit(const FrameArgs& fa, uint32_t leaf, float t, float chord,
                                           const float3 o, const float3 d, float rgb[3],
                                           float& alpha, Counts& cn) {
@@ -438,24 +603,31 @@ __device__ __forceinline__ void shade_hit(const FrameArgs& fa, uint32_t leaf, fl
     const float nip = sqrtf(dot3(wip, wip));
     const float cphi =
         (nip > 0.f && nop > 0.f) ? clampf(dot3(wip, wop) / (nip * nop), -1.f, 1.f) : 1.f;
+    float Tl[3] = {1.f, 1.f, 1.f}, sg2 = 0.f;
+    if (SHADOW) {
+      bool sok = true;
+      shadow_path<PREC, COUNT>(fa, x, wi, L.w == 0.f ? kInf : sqrtf(1.f / E),
+                               __float_as_uint(aux.x), Tl, sg2, sok, cn);
+      if (!sok) atomicAdd(fa.overflow, 1u);
+    }
     float f[3];
     if (eth) {
-      f_ours<PREC>(fa.tables, m, eh, th_i, th_o, cphi, fa.flags, f);
+      f_ours<PREC>(fa.tables, m, eh, th_i, th_o, cphi, fa.flags, sg2, f);
       if (COUNT) ++cn.eshade;
     } else {
-      f_single<PREC>(fa.tables, m, th_i, th_o, cphi, f);
+      f_single<PREC>(fa.tables, m, th_i, th_o, cphi, sg2, f);
       if (COUNT) ++cn.sshade;
     }
     const float g = E * sqrtf(fmaxf(0.f, 1.f - si * si));
     const float4 Lc = fa.lights.rgb[l];
-    rgb[0] = fmaf(f[0] * g, Lc.x, rgb[0]);
-    rgb[1] = fmaf(f[1] * g, Lc.y, rgb[1]);
-    rgb[2] = fmaf(f[2] * g, Lc.z, rgb[2]);
+    rgb[0] = fmaf(f[0] * Tl[0] * g, Lc.x, rgb[0]);
+    rgb[1] = fmaf(f[1] * Tl[1] * g, Lc.y, rgb[1]);
+    rgb[2] = fmaf(f[2] * Tl[2] * g, Lc.z, rgb[2]);
   }
 }
 
 // One sample: ray, K nearest hits, shading and front-to-back compositing.
-template <int KMAX, int PREC, bool COUNT>
+template <int KMAX, int PREC, bool COUNT, bool SHADOW = false>
 __device__ __forceinline__ void render_ray(const FrameArgs& fa, const float3 o, const float3 d,
                                            float out[3], int32_t* ids, bool& ok, Counts& cn) {
   KBuf<KMAX> kb;
@@ -476,7 +648,7 @@ __device__ __forceinline__ void render_ray(const FrameArgs& fa, const float3 o, 
   for (int j = 0; j < KMAX; ++j) {
     if (j < (int)fa.k && kb.t[j] < kInf && T > 0.f) {
       float rgb[3], a;
-      shade_hit<PREC, COUNT>(fa, kb.leaf[j], kb.t[j], kb.ch[j], o, d, rgb, a, cn);
+      shade_hit<PREC, COUNT, SHADOW>(fa, kb.leaf[j], kb.t[j], kb.ch[j], o, d, rgb, a, cn);
       if (COUNT) ++cn.hits;
       const float ta = T * a;
       out[0] = fmaf(ta, rgb[0], out[0]);
@@ -487,12 +659,12 @@ __device__ __forceinline__ void render_ray(const FrameArgs& fa, const float3 o, 
   }
 }
 
-template <int KMAX, int PREC, bool COUNT>
+template <int KMAX, int PREC, bool COUNT, bool SHADOW = false>
 __device__ __forceinline__ void render_sample(const FrameArgs& fa, uint64_t sid, float out[3],
                                               int32_t* ids, bool& ok, Counts& cn) {
   float3 o, d;
   camera_ray(fa.cam, fa.seed, sid, fa.spp, o, d);
-  render_ray<KMAX, PREC, COUNT>(fa, o, d, out, ids, ok, cn);
+  render_ray<KMAX, PREC, COUNT, SHADOW>(fa, o, d, out, ids, ok, cn);
 }
 
 __device__ __forceinline__ void flush_counts(const FrameArgs& fa, const Counts& cn) {
@@ -563,7 +735,7 @@ __device__ __forceinline__ void scene_rect(const FrameArgs& fa, float4* rect) {
 // mean is a fixed XOR-shuffle sum over the group divided by spp.  Pixels
 // outside `rect` are background.  All 32 lanes of every warp reach the
 // shuffles (no early return).
-template <int KMAX, int PREC, bool COUNT>
+template <int KMAX, int PREC, bool COUNT, bool SHADOW = false>
 __device__ __forceinline__ void render_tile_xy(const FrameArgs& fa, uint32_t tx, uint32_t ty,
                                                const float4 rect, float* __restrict__ rgb,
                                                Counts& cn, bool& overflow) {
@@ -583,7 +755,7 @@ __device__ __forceinline__ void render_tile_xy(const FrameArgs& fa, uint32_t tx,
       bool ok;
       float3 o, d;
       camera_ray_xy(fa.cam, fa.seed, pixel * fa.spp + s, x, y, o, d);
-      render_ray<KMAX, PREC, COUNT>(fa, o, d, v, nullptr, ok, cn);
+      render_ray<KMAX, PREC, COUNT, SHADOW>(fa, o, d, v, nullptr, ok, cn);
       if (COUNT) ++cn.rays;
       overflow |= !ok;
       acc[0] += v[0];
@@ -607,7 +779,7 @@ __device__ __forceinline__ void render_tile_xy(const FrameArgs& fa, uint32_t tx,
 // Warp tile: the 32 / grp pixels one warp renders (wtw x wth); a pixel's
 // samples on `grp` adjacent lanes, summed with a fixed XOR-shuffle tree.
 // Called by whole warps.
-template <int KMAX, int PREC, bool COUNT>
+template <int KMAX, int PREC, bool COUNT, bool SHADOW = false>
 __device__ __forceinline__ void render_warp_tile(const FrameArgs& fa, uint32_t x0, uint32_t y0,
                                                  uint32_t wtw, const float4 rect,
                                                  float* __restrict__ rgb, Counts& cn,
@@ -628,7 +800,7 @@ __device__ __forceinline__ void render_warp_tile(const FrameArgs& fa, uint32_t x
       bool ok;
       float3 o, d;
       camera_ray_xy(fa.cam, fa.seed, pixel * fa.spp + s, x, y, o, d);
-      render_ray<KMAX, PREC, COUNT>(fa, o, d, v, nullptr, ok, cn);
+      render_ray<KMAX, PREC, COUNT, SHADOW>(fa, o, d, v, nullptr, ok, cn);
       if (COUNT) ++cn.rays;
       overflow |= !ok;
       acc[0] += v[0];
@@ -649,11 +821,11 @@ __device__ __forceinline__ void render_warp_tile(const FrameArgs& fa, uint32_t x
   }
 }
 
-template <int KMAX, int PREC, bool COUNT>
+template <int KMAX, int PREC, bool COUNT, bool SHADOW = false>
 __device__ __forceinline__ void render_tile(const FrameArgs& fa, uint32_t tile, const float4 rect,
                                             float* __restrict__ rgb, Counts& cn, bool& overflow) {
   const uint32_t tiles_x = ((uint32_t)fa.cam.W + fa.tile_w - 1) / fa.tile_w;
-  render_tile_xy<KMAX, PREC, COUNT>(fa, tile % tiles_x, tile / tiles_x, rect, rgb, cn, overflow);
+  render_tile_xy<KMAX, PREC, COUNT, SHADOW>(fa, tile % tiles_x, tile / tiles_x, rect, rgb, cn, overflow);
 }
 
 }  // namespace tr

@@ -1,114 +1,16 @@
-// Frame kernel: one 128-thread block per 16 x 8 pixel tile, one pixel per
-// thread, all of the pixel's samples in that thread (hot path of hr_render).
-#include <algorithm>
-
-#include "trace_core.cuh"
+// Frame kernel (hot path of hr_render): persistent warps, one sample per
+// lane; this unit instantiates it without shadow rays (trace_frame_shadow.cu
+// with them) and holds the host-side camera and light conversions.
+#include "trace_frame.cuh"
 
 namespace hr {
-namespace {
-
-// Projected scene rectangle of the frame and a cleared work counter, once per
-// launch (one warp).
-__global__ void k_scene_rect(const FrameArgs fa, float4* rect, uint32_t* work) {
-  tr::scene_rect_warp(fa, rect);
-  if (threadIdx.x == 0) *work = 0u;
-}
-
-// Persistent frame kernel.  The image has been cleared to background; the
-// warp tiles (32 / grp pixels each) that overlap the projected scene rectangle
-// are handed out one at a time through an atomic counter, so the few tiles
-// that see hair spread over every warp of the GPU and a warp that drew cheap
-// tiles takes more.  No warp ever waits for another.
-template <int KMAX, int PREC, bool COUNT>
-__global__ void __launch_bounds__(kBlock)
-    k_frame(const FrameArgs fa, const float4* __restrict__ rect_p, uint32_t* work,
-            float* __restrict__ rgb) {
-  const float4 rect = *rect_p;
-  const uint32_t P = 32u / fa.grp;  // pixels per warp tile
-  uint32_t wtw = 1;
-  while (wtw * wtw < P) wtw <<= 1;
-  const uint32_t wth = P / wtw;
-  const uint32_t W = (uint32_t)fa.cam.W, H = (uint32_t)fa.cam.H;
-  const float fx0 = fmaxf(0.f, floorf(rect.x)), fy0 = fmaxf(0.f, floorf(rect.y));
-  const float fx1 = fminf(rect.z, (float)W - 1.f), fy1 = fminf(rect.w, (float)H - 1.f);
-  uint32_t n = 0, nx = 0, x0 = 0, y0 = 0;
-  if (fx0 <= fx1 && fy0 <= fy1) {
-    x0 = (uint32_t)fx0 / wtw * wtw;
-    y0 = (uint32_t)fy0 / wth * wth;
-    nx = ((uint32_t)fx1 - x0) / wtw + 1;
-    n = nx * (((uint32_t)fy1 - y0) / wth + 1);
-  }
-  tr::Counts cn{0, 0, 0, 0, 0, 0};
-  bool overflow = false;
-  const uint32_t lane = threadIdx.x & 31;
-  for (;;) {
-    uint32_t t = 0;
-    if (lane == 0) t = atomicAdd(work, 1u);
-    t = __shfl_sync(0xffffffffu, t, 0);
-    if (t >= n) break;
-    tr::render_warp_tile<KMAX, PREC, COUNT>(fa, x0 + (t % nx) * wtw, y0 + (t / nx) * wth, wtw,
-                                            rect, rgb, cn, overflow);
-  }
-  if (COUNT) tr::flush_counts(fa, cn);
-  if (overflow) atomicAdd(fa.overflow, 1u);
-}
-
-template <int KMAX, int PREC, bool COUNT>
-int frame_grid() {
-  static int grid = 0;
-  if (!grid) {
-    int dev = 0, sms = 1, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_frame<KMAX, PREC, COUNT>, kBlock,
-                                                      0) != cudaSuccess) {
-      cudaGetLastError();
-      per = 4;
-    }
-    grid = sms * (per > 0 ? per : 1);
-  }
-  return grid;
-}
-
-template <int KMAX, int PREC>
-hr_status launch_k(hr_ctx* ctx, const FrameArgs& fa, bool count, float* rgb, cudaStream_t st) {
-  const uint32_t tiles = tiles_for(fa.cam.W, fa.cam.H, fa.spp);
-  float4* rect = nullptr;
-  HR_TRY(scratch(ctx, 47, 2 * sizeof(float4), (void**)&rect));
-  uint32_t* work = reinterpret_cast<uint32_t*>(rect + 1);
-  HR_CUDA(ctx, cudaMemsetAsync(rgb, 0, (size_t)fa.cam.W * fa.cam.H * 3 * sizeof(float), st));
-  k_scene_rect<<<1, 32, 0, st>>>(fa, rect, work);
-  HR_LAUNCHED(ctx);
-  if (count) {
-    const int g = (int)std::min<uint32_t>(tiles, frame_grid<KMAX, PREC, true>());
-    k_frame<KMAX, PREC, true><<<g, kBlock, 0, st>>>(fa, rect, work, rgb);
-  } else {
-    const int g = (int)std::min<uint32_t>(tiles, frame_grid<KMAX, PREC, false>());
-    k_frame<KMAX, PREC, false><<<g, kBlock, 0, st>>>(fa, rect, work, rgb);
-  }
-  HR_LAUNCHED(ctx);
-  return HR_OK;
-}
-
-template <int PREC>
-hr_status launch_p(hr_ctx* ctx, const FrameArgs& fa, bool count, float* rgb, cudaStream_t st) {
-  switch (kmax_for(fa.k)) {
-    case 1: return launch_k<1, PREC>(ctx, fa, count, rgb, st);
-    case 2: return launch_k<2, PREC>(ctx, fa, count, rgb, st);
-    case 4: return launch_k<4, PREC>(ctx, fa, count, rgb, st);
-    default: return launch_k<8, PREC>(ctx, fa, count, rgb, st);
-  }
-}
-
-}  // namespace
 
 int kmax_for(uint32_t k) { return k <= 1 ? 1 : (k <= 2 ? 2 : (k <= 4 ? 4 : 8)); }
 
 hr_status launch_frame(hr_ctx* ctx, const FrameArgs& fa, int precision, bool count,
                        float* rgb_dev, cudaStream_t st) {
-  if (fa.cam.W <= 0 || fa.cam.H <= 0) return HR_OK;
-  return precision == HR_PREC_FP16 ? launch_p<HR_PREC_FP16>(ctx, fa, count, rgb_dev, st)
-                                   : launch_p<HR_PREC_FP32>(ctx, fa, count, rgb_dev, st);
+  if (fa.flags & HR_FLAG_SHADOWS) return launch_frame_shadow(ctx, fa, precision, count, rgb_dev, st);
+  return launch_frame_t<false>(ctx, fa, precision, count, rgb_dev, st);
 }
 
 LaunchCam to_launch_cam(const hr_camera& c) {

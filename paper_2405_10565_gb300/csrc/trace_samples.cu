@@ -6,7 +6,7 @@
 namespace hr {
 namespace {
 
-template <int KMAX, int PREC>
+template <int KMAX, int PREC, bool SHADOW>
 __global__ void __launch_bounds__(128)
     k_samples(const FrameArgs fa, const uint32_t* __restrict__ sids, uint32_t m,
               float* __restrict__ rad, int32_t* __restrict__ hit) {
@@ -16,7 +16,7 @@ __global__ void __launch_bounds__(128)
   float v[3];
   int32_t ids[KMAX];
   bool ok;
-  tr::render_sample<KMAX, PREC, false>(fa, sids[i], v, ids, ok, cn);
+  tr::render_sample<KMAX, PREC, false, SHADOW>(fa, sids[i], v, ids, ok, cn);
   rad[3 * (size_t)i] = v[0];
   rad[3 * (size_t)i + 1] = v[1];
   rad[3 * (size_t)i + 2] = v[2];
@@ -26,18 +26,25 @@ __global__ void __launch_bounds__(128)
   if (!ok) atomicAdd(fa.overflow, 1u);
 }
 
-template <int PREC>
+template <int PREC, bool SHADOW>
 hr_status launch_p(hr_ctx* ctx, const FrameArgs& fa, const uint32_t* sids, uint32_t m,
                    float* rad, int32_t* hit, cudaStream_t st) {
   const uint32_t g = (m + 127) / 128;
   switch (kmax_for(fa.k)) {
-    case 1: k_samples<1, PREC><<<g, 128, 0, st>>>(fa, sids, m, rad, hit); break;
-    case 2: k_samples<2, PREC><<<g, 128, 0, st>>>(fa, sids, m, rad, hit); break;
-    case 4: k_samples<4, PREC><<<g, 128, 0, st>>>(fa, sids, m, rad, hit); break;
-    default: k_samples<8, PREC><<<g, 128, 0, st>>>(fa, sids, m, rad, hit); break;
+    case 1: k_samples<1, PREC, SHADOW><<<g, 128, 0, st>>>(fa, sids, m, rad, hit); break;
+    case 2: k_samples<2, PREC, SHADOW><<<g, 128, 0, st>>>(fa, sids, m, rad, hit); break;
+    case 4: k_samples<4, PREC, SHADOW><<<g, 128, 0, st>>>(fa, sids, m, rad, hit); break;
+    default: k_samples<8, PREC, SHADOW><<<g, 128, 0, st>>>(fa, sids, m, rad, hit); break;
   }
   HR_LAUNCHED(ctx);
   return HR_OK;
+}
+
+template <bool SHADOW>
+hr_status launch_t(hr_ctx* ctx, const FrameArgs& fa, int precision, const uint32_t* sids,
+                   uint32_t m, float* rad, int32_t* hit, cudaStream_t st) {
+  return precision == HR_PREC_FP16 ? launch_p<HR_PREC_FP16, SHADOW>(ctx, fa, sids, m, rad, hit, st)
+                                   : launch_p<HR_PREC_FP32, SHADOW>(ctx, fa, sids, m, rad, hit, st);
 }
 
 }  // namespace
@@ -45,8 +52,8 @@ hr_status launch_p(hr_ctx* ctx, const FrameArgs& fa, const uint32_t* sids, uint3
 hr_status launch_samples(hr_ctx* ctx, const FrameArgs& fa, int precision, const uint32_t* sids,
                          uint32_t m, float* rad_dev, int32_t* hit_dev, cudaStream_t st) {
   if (m == 0) return HR_OK;
-  return precision == HR_PREC_FP16 ? launch_p<HR_PREC_FP16>(ctx, fa, sids, m, rad_dev, hit_dev, st)
-                                   : launch_p<HR_PREC_FP32>(ctx, fa, sids, m, rad_dev, hit_dev, st);
+  return (fa.flags & HR_FLAG_SHADOWS) ? launch_t<true>(ctx, fa, precision, sids, m, rad_dev, hit_dev, st)
+                                      : launch_t<false>(ctx, fa, precision, sids, m, rad_dev, hit_dev, st);
 }
 
 }  // namespace hr

@@ -488,3 +488,53 @@ def test_frame_deferred_lod_follows_eq14(ctx):
         assert np.array_equal(np.sort(ids.astype(np.int64)), np.sort(prep2.ids))
     finally:
         hr.hr_asset_destroy(ctx, a)
+
+
+# ---------------------------------------------------------------- shadow rays
+SHADOW_AGREE_MIN = 0.99  # samples whose radiance agrees to 1e-3 (shadow crossings decided alike)
+
+
+@pytest.mark.parametrize("wl", ["tiny", "clusters_half", "full_head"])
+def test_shadow_rays_against_the_oracle(ctx, wl):
+    """HR_FLAG_SHADOWS (dual-scattering light paths): the GPU's transmittance
+    and spread along every shadow ray against the oracle's brute force over
+    all primitives.  A shadow ray grazing a hair can cross it in FP64 and
+    miss it in FP32, which changes that light's term by a_F: such samples are
+    counted apart (at most 1%), the rest must agree to the FP32 bar."""
+    rng = np.random.default_rng(11)
+    if wl == "tiny":
+        w = scenegen.tiny_strands()
+        sids = np.arange(w.camera.width * w.camera.height * w.spp)
+    elif wl == "clusters_half":
+        w = scenegen.clustered(n=3000, S=12, res=48, spp=4, lod_setting="half", n_clusters=64)
+        sids = rng.choice(w.camera.width * w.camera.height * w.spp, 3000, replace=False)
+    else:
+        w = scenegen.full_head(n=8000, S=16, width=96, height=64, spp=2, n_lights=4,
+                               n_clusters=320, fill=0.25)
+        sids = rng.choice(w.camera.width * w.camera.height * w.spp, 1000, replace=False)
+    a = upload(ctx, w.scene)
+    try:
+        lod_g = gpu_lod(ctx, a, w)
+        prep = _oracle_with_lod(w, None, lod_g)
+        d = desc_of(w, flags=hr.HR_FLAG_SHADOWS)
+        rg, hg = gpu_samples(ctx, a, d, sids)
+        r0, _ = gpu_samples(ctx, a, desc_of(w), sids)
+        ro, ho = oracle.render_samples(prep, w.camera.pack(), w.lights, sids, w.spp, w.k_depth,
+                                       w.sample_seed, flags=oracle.FLAG_SHADOWS)
+        frac, full, _, _ = compare(rg, hg, ro, ho)
+        same = np.all(np.asarray(hg, np.int64) == ho, axis=1)
+        on = np.linalg.norm(ro, axis=1)
+        err = np.linalg.norm(rg.astype(np.float64) - ro, axis=1) / np.maximum(on, 1e-3 * on.mean())
+        ok = same & (err <= 1e-3)
+        agree = ok.sum() / max(1, same.sum())
+        rmse = np.linalg.norm(rg[ok].astype(np.float64) - ro[ok]) / np.linalg.norm(ro[ok])
+        msg = (f"{w.name}: k-buffer agreement {full:.5f}, shadow agreement {agree:.5f}, "
+               f"rel-RMSE {rmse:.2e}, light kept {rg.sum() / r0.sum():.3f}")
+        print(msg)
+        assert full >= KBUF_AGREE_MIN, msg
+        assert agree >= SHADOW_AGREE_MIN, msg
+        assert rmse <= RMSE_FP32, msg
+        if wl != "tiny":  # hair shadows hair: less light than without shadow rays
+            assert rg.sum() < 0.95 * r0.sum(), msg
+    finally:
+        hr.hr_asset_destroy(ctx, a)

@@ -145,6 +145,11 @@ def test_injected_faults(ctx):
         assert st == hr.HR_OK and res.status == hr.HR_OK
         with pytest.raises(hr.HairRTError):
             hr.hr_poll(ctx, 987654321, 0)
+        # served frames are primary hits only: shadow rays are refused at submit
+        ds = hr.render_desc(cam.pack(), w.lights, d.spp, d.k_depth, d.seed, d.precision,
+                            hr.HR_FLAG_SHADOWS)
+        with pytest.raises(hr.HairRTError):
+            hr.hr_submit(ctx, a, ds, img, 2.0, bias)
     finally:
         hr.hr_serve_stop(ctx)
         for a_, _ in assets:
