@@ -199,6 +199,23 @@ def oracle_baseline(w, seconds: float, seed: int = 11):
             "seconds": dt}
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The maximum of a per-rank time over all ranks (x itself on one rank):
+    a multi-GPU step lasts as long as its slowest rank."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_msamples_per_s(world: int, samples_per_rank: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput: every rank renders its own replica, so the job
+    processes world x samples per step in the slowest rank's time."""
+    return world * samples_per_rank * steps / seconds / 1e6
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle as it stands, on this host's cores."""
     rank = int(os.environ.get("RANK", "0"))
@@ -443,14 +460,11 @@ def main():
         e1.synchronize()
         torch.cuda.synchronize(dev)
     launches = hr.hr_kernel_launches(ctx) - launches0
-    elapsed = e0.elapsed_time(e1) / 1e3
+    elapsed = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist, dev)
     if dist:
-        t = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
         dist.barrier()
     ms_step = 1e3 * elapsed / args.steps
-    value = world * samples * args.steps / elapsed / 1e6
+    value = job_msamples_per_s(world, samples, args.steps, elapsed)
     render_avg = statistics.mean(render_ms)
     clocks = clk.summary()
 
@@ -470,12 +484,14 @@ def main():
     if not args.no_e2e:
         e2e_step()
         torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             e2e_step()
         torch.cuda.synchronize(dev)
-        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-        e2e = {"value": world * samples / e2e_s / 1e6, "unit": "Msamples/s",
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, dist, dev)
+        e2e = {"value": job_msamples_per_s(world, samples, 1, e2e_s), "unit": "Msamples/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3}
 
     # animated frames: the strands alternate between two poses (a smooth
