@@ -538,3 +538,35 @@ def test_shadow_rays_against_the_oracle(ctx, wl):
             assert rg.sum() < 0.95 * r0.sum(), msg
     finally:
         hr.hr_asset_destroy(ctx, a)
+
+
+def test_invalid_calls_are_refused_with_a_status(ctx):
+    """Argument and state errors come back as status codes (no fault, no
+    crash) and leave the context usable."""
+    w = scenegen.tiny_strands()
+
+    def status_of(fn, *a, **k):
+        with pytest.raises(hr.HairRTError) as e:
+            fn(*a, **k)
+        return e.value.status
+
+    v = np.ascontiguousarray(w.scene.verts)
+    assert status_of(hr.hr_asset_create, ctx, v[:0], w.scene.mat[:0], w.scene.shape[:0]) == hr.HR_EINVAL
+    a = upload(ctx, w.scene)
+    try:
+        img = np.zeros((w.camera.height, w.camera.width, 3), np.float32)
+        # no BVH yet
+        assert status_of(hr.hr_render, ctx, a, desc_of(w), img) == hr.HR_ESTATE
+        assert status_of(hr.hr_build_clusters, ctx, a, w.scene.n_strands + 1) == hr.HR_EINVAL
+        hr.hr_build_bvh(ctx, a, None)
+        bad = desc_of(w)
+        bad.spp = 0
+        assert status_of(hr.hr_render, ctx, a, bad, img) == hr.HR_EINVAL
+        bad = desc_of(w)
+        bad.k_depth = hr.HR_MAX_K + 1
+        assert status_of(hr.hr_render, ctx, a, bad, img) == hr.HR_EINVAL
+        # the context still renders
+        hr.hr_render(ctx, a, desc_of(w), img)
+        assert img.max() > 0
+    finally:
+        hr.hr_asset_destroy(ctx, a)
