@@ -199,6 +199,50 @@ def oracle_baseline(w, seconds: float, seed: int = 11):
             "seconds": dt}
 
 
+def measure_config(hr, ctx, torch, dev, w, steps: int, warmup: int = 2):
+    """Step time of another configuration (not the headline line): for a
+    fixed LoD setting (all strands, half, all thick hairs) the clusters, BVH
+    and frame per step, for a selected LoD the whole hr_render_frame step."""
+    import scenegen
+    verts = torch.from_numpy(w.scene.verts).to(dev)
+    mat = torch.from_numpy(w.scene.mat).to(dev)
+    shape = torch.from_numpy(w.scene.shape).to(dev)
+    a = hr.hr_asset_create(ctx, verts, mat, shape)
+    d = hr.render_desc(w.camera.pack(), w.lights, w.spp, w.k_depth, w.sample_seed, w.precision)
+    img = torch.empty((w.camera.height, w.camera.width, 3), device=dev)
+    try:
+        if w.n_clusters and w.lod_setting != "select":
+            hr.hr_build_clusters(ctx, a, w.n_clusters)
+            C, L, _ = hr.hr_hierarchy_info(ctx, a)
+            lod = torch.from_numpy(scenegen.lod_preset(w.lod_setting, C, L)).to(dev)
+
+            def one():
+                hr.hr_build_clusters(ctx, a, w.n_clusters)
+                hr.hr_build_bvh(ctx, a, lod)
+                hr.hr_render(ctx, a, d, img)
+        elif w.n_clusters:
+            def one():
+                hr.hr_render_frame(ctx, a, w.n_clusters, w.eps_w, 0, d, img)
+        else:
+            def one():
+                hr.hr_build_bvh(ctx, a, None)
+                hr.hr_render(ctx, a, d, img)
+        for _ in range(warmup):
+            one()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            one()
+        torch.cuda.synchronize(dev)
+        dt = (time.perf_counter() - t0) / steps
+    finally:
+        hr.hr_asset_destroy(ctx, a)
+    n = w.camera.width * w.camera.height * w.spp
+    return {"workload": w.name, "ms_per_step": dt * 1e3, "Msamples_per_s": n / dt / 1e6,
+            "strands": w.scene.n_strands, "segments": w.scene.n_segments,
+            "lod": w.lod_setting, "precision": "fp16" if w.precision else "fp32", "k_depth": w.k_depth}
+
+
 def max_over_ranks(x: float, dist, device) -> float:
     """The maximum of a per-rank time over all ranks (x itself on one rank):
     a multi-GPU step lasts as long as its slowest rank."""
@@ -374,6 +418,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-configs", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -536,6 +581,17 @@ def main():
     if not args.no_serve and rank == 0 and world == 1:
         serving = run_serving(hr, ctx, torch, dev, args.serve_requests)
 
+    # the other configurations, one step each (host-timed, synchronous calls)
+    other_configs = None
+    if not args.no_configs and rank == 0:
+        import scenegen
+        other_configs = [measure_config(hr, ctx, torch, dev, cw, 5) for cw in (
+            scenegen.tiny_strands(),
+            scenegen.clustered(lod_setting="strands"), scenegen.clustered(lod_setting="half"),
+            scenegen.clustered(lod_setting="eth"),
+            scenegen.full_head(precision=1),
+            scenegen.stress())]
+
     hr.hr_asset_destroy(ctx, asset)
     hr.hr_destroy(ctx)
 
@@ -593,7 +649,7 @@ def main():
             "phase_ms": {"hierarchy": st.hierarchy_ms, "fit": st.fit_ms, "lod": st.lod_ms,
                          "bvh": st.bvh_ms, "render": st.render_ms},
             "cpu_baseline": cpu,
-            "e2e": e2e, "animation": animation,
+            "e2e": e2e, "animation": animation, "other_configs": other_configs,
             "gpu_launches": launches, "clocks": clocks, "serving": serving}
     print(json.dumps(line))
     if dist:
