@@ -77,7 +77,7 @@ def sources_hash(names):
     return h.hexdigest()[:16]
 
 
-TRACE_SOURCES = ["trace_core.cuh", "trace_frame.cu", "common.cuh"]
+TRACE_SOURCES = ["trace_core.cuh", "trace_frame.cuh", "trace_frame.cu", "common.cuh"]
 FIT_SOURCES = ["hierarchy.cu", "common.cuh"]
 
 

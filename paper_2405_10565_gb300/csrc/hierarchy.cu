@@ -480,7 +480,9 @@ __device__ d3 major_axis_fp64(const double C[3][3], const float Vf[3][3], const 
 //    of FP32 range take the full FP64 solve above.
 //  * Unit tangents (which only pick the dropped axis and orient e1, e2) and
 //    the member projections for the semi-axes: FP32.
-__global__ void k_fit_cross_sections(const float4* __restrict__ verts, uint32_t S,
+// 64 registers (8 blocks of 128 per SM): more warps in flight hide the FP64
+// pipe's latency better than the spills of the rare full-FP64 path cost.
+__global__ void __launch_bounds__(128, 8) k_fit_cross_sections(const float4* __restrict__ verts, uint32_t S,
                                      const uint32_t* __restrict__ order,
                                      const uint32_t* __restrict__ cl_first, LevelInfo li,
                                      uint32_t E, float4* xsec) {
