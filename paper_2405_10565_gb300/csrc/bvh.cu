@@ -203,6 +203,18 @@ __device__ __forceinline__ void climb_global(int node, const int4* __restrict__ 
   }
 }
 
+// Warp-aggregated append of one node index per lane (-1: nothing) to the
+// list of climb starts; every lane of the warp calls it.
+__device__ __forceinline__ void append_start(int v, unsigned* count, int* list) {
+  const unsigned m = __ballot_sync(0xffffffffu, v >= 0);
+  if (!m) return;
+  const int lane = threadIdx.x & 31, lead = __ffs(m) - 1;
+  unsigned base = 0;
+  if (lane == lead) base = atomicAdd(count, (unsigned)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, lead);
+  if (v >= 0) list[base + __popc(m & ((1u << lane) - 1u))] = v;
+}
+
 // Leaf gather and bottom-up bounds in one kernel.  Thread j of block b owns
 // leaf b0 + j and internal node b0 + j (b0 = b * B).
 //  1. Gather: each thread copies its leaf's record into Morton order and
@@ -213,16 +225,17 @@ __device__ __forceinline__ void climb_global(int node, const int4* __restrict__ 
 //     rounds separated by barriers: a node whose children are done takes
 //     their boxes from shared memory, writes its record and its union.  The
 //     rounds number the local subtrees' height; no fences, no atomics.
-//  3. The few nodes that span blocks are finished with global arrival
-//     counters: the owner of each local node (or leaf) whose parent spans
-//     blocks publishes its box and climbs.
+//  3. The few nodes that span blocks are left to k_climb: the owner of each
+//     local node (or leaf) whose parent spans blocks publishes its box and
+//     appends the parent to a list, so that no block stays resident behind a
+//     climb through the upper tree.
 template <int B>
 __global__ void __launch_bounds__(B) k_gather_refit(
     const int4* __restrict__ child, const int* __restrict__ parent_int,
     const int* __restrict__ parent_leaf, const float4* __restrict__ box,
     const uint32_t* __restrict__ sorted_ids, const float4* __restrict__ xf,
     const float4* __restrict__ aux, int n, float4* nodes, float4* lbox, float4* leaf_xf,
-    float4* leaf_aux, uint32_t* leaf_id, unsigned* arrivals) {
+    float4* leaf_aux, uint32_t* leaf_id, unsigned* n_starts, int* starts) {
   __shared__ int4 s_child[B];
   __shared__ float s_lbox[B][6];  // leaf boxes (lo.x, hi.x, lo.y, hi.y, lo.z, hi.z)
   __shared__ float s_nbox[B][6];  // unions of the block's local nodes
@@ -287,21 +300,34 @@ __global__ void __launch_bounds__(B) k_gather_refit(
     __syncthreads();  // this round's flags are visible
   }
   // 3. nodes that span blocks: leaves, then local nodes, whose parent does
+  int start_leaf = -1, start_node = -1;
   if (leaf < n) {
     const bool parent_local = lparent >= b0 && lparent < b0 + B && s_child[lparent - b0].z >= b0 &&
                               s_child[lparent - b0].w < b0 + B;
     if (!parent_local) {
       __stcg(lbox + 2 * leaf, bl);
       __stcg(lbox + 2 * leaf + 1, bh);
-      climb_global(lparent, child, parent_int, nodes, lbox, arrivals);
+      start_leaf = lparent;
     }
   }
   if (node_local && node != 0) {
     const int p = __ldg(parent_int + node);
     const bool parent_local = p >= b0 && p < b0 + B && s_child[p - b0].z >= b0 &&
                               s_child[p - b0].w < b0 + B;
-    if (!parent_local) climb_global(p, child, parent_int, nodes, lbox, arrivals);
+    if (!parent_local) start_node = p;
   }
+  append_start(start_leaf, n_starts, starts);
+  append_start(start_node, n_starts, starts);
+}
+
+// Bottom-up bounds of the nodes that span blocks, from the arrivals listed by
+// k_gather_refit (every record below them is complete when it starts).
+__global__ void k_climb(const unsigned* __restrict__ n_starts, const int* __restrict__ starts,
+                        const int4* __restrict__ child, const int* __restrict__ parent_int,
+                        float4* nodes, const float4* lbox, unsigned* arrivals) {
+  const unsigned m = *n_starts;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    climb_global(__ldg(starts + i), child, parent_int, nodes, lbox, arrivals);
 }
 
 __global__ void k_bytes_differ(const uint8_t* __restrict__ x, const uint8_t* __restrict__ y,
@@ -314,15 +340,32 @@ __global__ void k_bytes_differ(const uint8_t* __restrict__ x, const uint8_t* __r
 // bounds, over the topology in bv.
 hr_status gather_refit(hr_ctx* ctx, hr_asset* a, Bvh& bv, const uint32_t* ids, cudaStream_t st) {
   const uint32_t n = bv.n;
-  unsigned* arrivals = nullptr;
+  unsigned* arrivals = nullptr;  // n node counters, then the number of climb starts
   float4* lbox = nullptr;
-  HR_TRY(scratch(ctx, 39, (size_t)n * 4, (void**)&arrivals));
+  int* starts = nullptr;  // at most one per leaf and one per internal node
+  HR_TRY(scratch(ctx, 39, ((size_t)n + 1) * 4, (void**)&arrivals));
   HR_TRY(scratch(ctx, 46, (size_t)n * 2 * sizeof(float4), (void**)&lbox));
-  HR_CUDA(ctx, cudaMemsetAsync(arrivals, 0, (size_t)n * 4, st));
+  HR_TRY(scratch(ctx, 48, (size_t)n * 2 * 4, (void**)&starts));
+  HR_CUDA(ctx, cudaMemsetAsync(arrivals, 0, ((size_t)n + 1) * 4, st));
   k_gather_refit<128><<<(n + 127) / 128, 128, 0, st>>>(bv.child, bv.par_int, bv.par_leaf,
                                                        a->prim_box, ids, a->prim_xf, a->prim_aux,
                                                        (int)n, bv.nodes, lbox, bv.leaf_xf,
-                                                       bv.leaf_aux, bv.leaf_id, arrivals);
+                                                       bv.leaf_aux, bv.leaf_id, arrivals + n, starts);
+  HR_LAUNCHED(ctx);
+  static int climb_grid = 0;
+  if (!climb_grid) {
+    int dev = 0, sms = 1, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_climb, 256, 0) != cudaSuccess || per < 1) {
+      cudaGetLastError();
+      per = 1;
+    }
+    climb_grid = sms * per;
+  }
+  const unsigned grid = (unsigned)std::min<size_t>((size_t)climb_grid, ((size_t)n * 2 + 255) / 256);
+  k_climb<<<grid, 256, 0, st>>>(arrivals + n, starts, bv.child, bv.par_int, bv.nodes, lbox,
+                                arrivals);
   HR_LAUNCHED(ctx);
   return HR_OK;
 }
