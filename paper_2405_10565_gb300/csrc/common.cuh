@@ -130,8 +130,9 @@ void note_launch(hr_ctx* ctx);
 // --- primitives (sort.cu)
 // exclusive scan of n uint32 values in place (device); uses scratch slots 10-12
 hr_status scan_u32(hr_ctx* ctx, uint32_t* data, uint32_t n, cudaStream_t st);
-// stable LSD radix sort of (key, value) pairs on the low `bits` key bits;
-// result in keys/vals; tmp buffers of n entries; uses scratch slots 13-15
+// stable LSD radix sort of (key, value) pairs on the low `bits` key bits,
+// one kernel per 8-bit digit pass (decoupled look-back); result in
+// keys/vals; tmp buffers of n entries; scratch slot 14; n < 2^30
 hr_status radix_sort_pairs(hr_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp,
                            uint32_t* vals_tmp, uint32_t n, int bits, cudaStream_t st);
 

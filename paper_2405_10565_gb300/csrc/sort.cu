@@ -1,6 +1,10 @@
 // Device-wide exclusive scan and stable LSD radix sort of (uint32 key, uint32
 // value) pairs.  Used by the Morton clustering of strands and by the linear
-// BVH build.
+// BVH build.  Two forms of the sort: a single sweep per digit pass (the
+// library's), and histogram / scan / scatter kernels per pass on
+// caller-provided buffers (the allocation-free clustering entry point).
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace hr {
@@ -146,6 +150,173 @@ __global__ void __launch_bounds__(kSortThreads)
   }
 }
 
+// ------------------------------------------------ single-sweep radix sort
+//
+// The stable LSD sort with one kernel per digit pass (Merrill and Garland's
+// decoupled look-back applied to radix sorting, as in Adinets and Merrill's
+// Onesweep): the digit totals of every pass come from one histogram kernel,
+// and each tile finds the offsets of its digits among the earlier tiles by
+// reading their published counts instead of through a device-wide scan.
+
+constexpr uint32_t kFlagAgg = 1u << 30;  // tile's own digit count
+constexpr uint32_t kFlagInc = 2u << 30;  // count of this and every earlier tile
+constexpr uint32_t kCountMask = kFlagAgg - 1u;
+constexpr int kLookbackPolls = 1 << 16;  // then the tile counts the earlier keys itself
+constexpr int kLookbackWindow = 8;
+constexpr int kSweepItems = 12;  // keys per thread
+constexpr uint32_t kSweepTile = kSortThreads * kSweepItems;
+
+// Digit totals of every pass in one read of the keys: hist[q * 256 + d].
+__global__ void k_pass_hist(const uint32_t* __restrict__ keys, uint32_t n, int passes,
+                            uint32_t* __restrict__ hist) {
+  __shared__ uint32_t h[4][kRadix];
+  for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&h[0][0])[i] = 0;
+  __syncthreads();
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const uint32_t k = keys[p];
+    for (int q = 0; q < passes; ++q) atomicAdd(&h[q][(k >> (8 * q)) & 0xffu], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) {
+    const uint32_t v = (&h[0][0])[i];
+    if (v) atomicAdd(hist + i, v);
+  }
+}
+
+// One digit pass.  Tiles are numbered in the order their blocks start, so a
+// tile only ever waits for tiles whose blocks are already running.  Tile t
+// ranks its keys stably (per-warp digit counts; lanes with equal digits found
+// by one vote per digit bit), publishes its digit counts, then
+// (thread d for digit d) walks back over the earlier tiles' published words,
+// adding counts until it meets a word that already holds an inclusive count.
+// If a wait outlasts kLookbackPolls reads the block counts the digits of all
+// earlier keys itself, which gives the same offsets.
+__global__ void __launch_bounds__(kSortThreads)
+    k_sweep(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+            uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, uint32_t n, int shift,
+            const uint32_t* __restrict__ totals, uint32_t* status, uint32_t* tile_ctr) {
+  static_assert(kSortThreads == kRadix && kSortThreads == kScanThreads, "one thread per digit");
+  __shared__ uint32_t whist[kSortWarps][kRadix];
+  __shared__ uint32_t s_off[kRadix];
+  __shared__ uint32_t s_tile;
+  __shared__ uint32_t s_key[kSweepTile], s_val[kSweepTile];  // the tile in digit order
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
+  for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&whist[0][0])[i] = 0;
+  __syncthreads();
+  const uint32_t t = s_tile;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  const uint32_t base = t * kSweepTile + wid * (32 * kSweepItems);
+  uint32_t k[kSweepItems], v[kSweepItems], local[kSweepItems];
+#pragma unroll
+  for (int j = 0; j < kSweepItems; ++j) {  // every load in flight before the ranking
+    const uint32_t p = base + j * 32 + lane;
+    k[j] = p < n ? keys[p] : 0u;
+    v[j] = p < n ? vals[p] : 0u;
+  }
+#pragma unroll
+  for (int j = 0; j < kSweepItems; ++j) {
+    const bool valid = base + j * 32 + lane < n;
+    const uint32_t d = valid ? ((k[j] >> shift) & 0xffu) : 0u;
+    // lanes with the same digit: one vote per digit bit, and one for validity
+    uint32_t peers = __ballot_sync(0xffffffffu, valid);
+    if (!valid) peers = ~peers;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const bool bit = (d >> b) & 1u;
+      const uint32_t vote = __ballot_sync(0xffffffffu, bit);
+      peers &= bit ? vote : ~vote;
+    }
+    const uint32_t rank_in = __popc(peers & lt_mask);
+    uint32_t prior = 0;
+    if (valid) prior = whist[wid][d];
+    local[j] = prior + rank_in;
+    __syncwarp();
+    if (valid && rank_in == 0) whist[wid][d] = prior + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  const uint32_t d = threadIdx.x;
+  uint32_t c = 0;
+#pragma unroll
+  for (int w = 0; w < kSortWarps; ++w) {
+    const uint32_t x = whist[w][d];
+    whist[w][d] = c;
+    c += x;
+  }
+  volatile uint32_t* vs = status;
+  vs[(size_t)t * kRadix + d] = (t == 0 ? kFlagInc : kFlagAgg) | c;
+  uint32_t all;
+  const uint32_t dstart = block_excl_scan(__ldg(totals + d), &all);
+  uint32_t excl = 0;
+  bool gave_up = false;
+  if (t > 0) {
+    // kLookbackWindow earlier tiles per read, nearest first: counts are added
+    // up to the first inclusive word; a tile not yet published stops the walk
+    // there until a later read finds it
+    int kt = (int)t - 1;
+    int polls = 0;
+    for (;;) {
+      uint32_t w[kLookbackWindow];
+#pragma unroll
+      for (int i = 0; i < kLookbackWindow; ++i)
+        w[i] = kt - i >= 0 ? (uint32_t)vs[(size_t)(kt - i) * kRadix + d] : (uint32_t)kFlagInc;
+      int used = 0;
+      bool inc = false;
+#pragma unroll
+      for (int i = 0; i < kLookbackWindow; ++i) {
+        if (used == i && w[i] != 0u && !inc) {
+          excl += w[i] & kCountMask;
+          inc = (w[i] & kFlagInc) != 0u;
+          ++used;
+        }
+      }
+      if (inc) break;
+      kt -= used;  // tile 0 publishes an inclusive count, so kt stays >= 0
+      if (used == 0 && ++polls > kLookbackPolls) {
+        gave_up = true;
+        break;
+      }
+    }
+  }
+  if (__syncthreads_or(gave_up)) {
+    uint32_t* cnt = s_off;
+    cnt[d] = 0;
+    __syncthreads();
+    for (uint32_t p = threadIdx.x; p < t * kSweepTile; p += kSortThreads)
+      atomicAdd(&cnt[(keys[p] >> shift) & 0xffu], 1u);
+    __syncthreads();
+    excl = cnt[d];
+    __syncthreads();
+  }
+  if (t > 0) vs[(size_t)t * kRadix + d] = kFlagInc | (excl + c);
+  // digit d's keys take places [tstart, tstart + c) of the tile in digit
+  // order, and the output from dstart + excl on
+  const uint32_t tstart = block_excl_scan(c, &all);
+  s_off[d] = dstart + excl - tstart;  // output index = s_off[digit] + tile place
+#pragma unroll
+  for (int w = 0; w < kSortWarps; ++w) whist[w][d] += tstart;
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kSweepItems; ++j) {
+    if (base + j * 32 + lane < n) {
+      const uint32_t q = whist[wid][(k[j] >> shift) & 0xffu] + local[j];
+      s_key[q] = k[j];
+      s_val[q] = v[j];
+    }
+  }
+  __syncthreads();
+  // the tile in digit order: consecutive threads write consecutive places of
+  // each digit's run
+  const uint32_t tile_n = min(kSweepTile, n - t * kSweepTile);
+  for (uint32_t i = threadIdx.x; i < tile_n; i += kSortThreads) {
+    const uint32_t key = s_key[i];
+    const uint32_t dst = s_off[(key >> shift) & 0xffu] + i;
+    keys_out[dst] = key;
+    vals_out[dst] = s_val[i];
+  }
+}
+
 }  // namespace
 
 hr_status scan_u32(hr_ctx* ctx, uint32_t* data, uint32_t n, cudaStream_t st) {
@@ -187,16 +358,25 @@ hr_status scan_u32(hr_ctx* ctx, uint32_t* data, uint32_t n, cudaStream_t st) {
 hr_status radix_sort_pairs(hr_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp,
                            uint32_t* vals_tmp, uint32_t n, int bits, cudaStream_t st) {
   if (n <= 1) return HR_OK;
-  const uint32_t nb = (n + kSortTile - 1) / kSortTile;
-  uint32_t* counts = nullptr;
-  HR_TRY(scratch(ctx, 13, (size_t)nb * kRadix * 4, (void**)&counts));
+  if (n >= kFlagAgg || bits < 1 || bits > 32) return set_error(ctx, HR_EINVAL, "sort: size out of range");
+  const int passes = (bits + 7) / 8;
+  const uint32_t nb = (n + kSweepTile - 1) / kSweepTile;
+  // pass totals (passes x 256), tile counters (64 words), then the tiles'
+  // published counts (passes x nb x 256), all cleared here
+  const size_t words = (size_t)passes * kRadix + 64 + (size_t)passes * nb * kRadix;
+  uint32_t* ws = nullptr;
+  HR_TRY(scratch(ctx, 14, words * 4, (void**)&ws));
+  HR_CUDA(ctx, cudaMemsetAsync(ws, 0, words * 4, st));
+  uint32_t* totals = ws;
+  uint32_t* ctr = ws + (size_t)passes * kRadix;
+  uint32_t* status = ctr + 64;
+  const uint32_t hb = std::min<uint32_t>(nb, 1024u);
+  k_pass_hist<<<hb, kSortThreads, 0, st>>>(keys, n, passes, totals);
+  HR_LAUNCHED(ctx);
   uint32_t *ki = keys, *vi = vals, *ko = keys_tmp, *vo = vals_tmp;
-  int passes = 0;
-  for (int shift = 0; shift < bits; shift += 8, ++passes) {
-    k_digit_hist<<<nb, kSortThreads, 0, st>>>(ki, n, shift, counts, nb);
-    HR_LAUNCHED(ctx);
-    HR_TRY(scan_u32(ctx, counts, nb * kRadix, st));
-    k_digit_scatter<<<nb, kSortThreads, 0, st>>>(ki, vi, ko, vo, n, shift, counts, nb);
+  for (int q = 0; q < passes; ++q) {
+    k_sweep<<<nb, kSortThreads, 0, st>>>(ki, vi, ko, vo, n, 8 * q, totals + q * kRadix,
+                                         status + (size_t)q * nb * kRadix, ctr + q);
     HR_LAUNCHED(ctx);
     uint32_t* t;
     t = ki; ki = ko; ko = t;
