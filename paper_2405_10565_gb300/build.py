@@ -22,6 +22,18 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", 
          "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]
 
 
+# The ray-tracing translation units (trace_*.cu) divide and take square roots
+# with the hardware's approximate instructions and flush FP32 denormals: the
+# traversal and shading are latency-bound, and their results stay well inside
+# the FP32 parity bounds.  Everything else (the fit above all) keeps IEEE
+# division and square root.
+TRACE_FLAGS = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
+
+
+def _tu_flags(src: str):
+    return TRACE_FLAGS if os.path.basename(src).startswith("trace_") else []
+
+
 def _nvcc() -> str:
     for cand in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
         if cand and os.path.exists(cand):
@@ -48,7 +60,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *_tu_flags(src), *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
