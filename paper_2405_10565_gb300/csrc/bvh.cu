@@ -184,35 +184,29 @@ __device__ __forceinline__ void store_node(float4* nodes, int node, int4 ch, con
   __stcg(o + 3, make_float4(__int_as_float(ch.x), __int_as_float(ch.y), 0.f, 0.f));
 }
 
-// Bottom-up bounds from a node that spans blocks: one global arrival counter
-// per node behind device-scope fences; the second arrival reads both child
-// boxes from the node records / published leaf boxes and goes on up.
-__device__ __forceinline__ void climb_global(int node, const int4* __restrict__ child,
-                                             const int* __restrict__ parent_int, float4* nodes,
-                                             const float4* lbox, unsigned* arrivals) {
-  while (node >= 0) {
-    __threadfence();
-    if (atomicAdd(&arrivals[node], 1u) == 0) return;
-    __threadfence();
-    const int4 ch = __ldg(child + node);
-    float c0[6], c1[6];
-    if (ch.x < 0) lbox_read(lbox, ~ch.x, c0); else node_union(nodes, ch.x, c0);
-    if (ch.y < 0) lbox_read(lbox, ~ch.y, c1); else node_union(nodes, ch.y, c1);
-    store_node(nodes, node, ch, c0, c1);
-    node = node == 0 ? -1 : __ldg(parent_int + node);
-  }
+// Float min / max as one integer atomic on the float's bits (non-negative
+// floats order like signed ints; negative ones order like unsigned ints in
+// reverse).  -0 must not reach them: callers pass +0.  Returns whether the
+// stored value changed.
+__device__ __forceinline__ bool atomic_min_f(float* a, float v) {
+  if (v >= 0.f) return atomicMin(reinterpret_cast<int*>(a), __float_as_int(v)) > __float_as_int(v);
+  return atomicMax(reinterpret_cast<unsigned*>(a), __float_as_uint(v)) < __float_as_uint(v);
+}
+__device__ __forceinline__ bool atomic_max_f(float* a, float v) {
+  if (v >= 0.f) return atomicMax(reinterpret_cast<int*>(a), __float_as_int(v)) < __float_as_int(v);
+  return atomicMin(reinterpret_cast<unsigned*>(a), __float_as_uint(v)) > __float_as_uint(v);
 }
 
-// Warp-aggregated append of one node index per lane (-1: nothing) to the
-// list of climb starts; every lane of the warp calls it.
-__device__ __forceinline__ void append_start(int v, unsigned* count, int* list) {
-  const unsigned m = __ballot_sync(0xffffffffu, v >= 0);
+// Warp-aggregated append of one child (node index, or ~leaf) per lane that
+// has one to the list of climb starts; every lane of the warp calls it.
+__device__ __forceinline__ void append_start(bool has, int v, unsigned* count, int* list) {
+  const unsigned m = __ballot_sync(0xffffffffu, has);
   if (!m) return;
   const int lane = threadIdx.x & 31, lead = __ffs(m) - 1;
   unsigned base = 0;
   if (lane == lead) base = atomicAdd(count, (unsigned)__popc(m));
   base = __shfl_sync(0xffffffffu, base, lead);
-  if (v >= 0) list[base + __popc(m & ((1u << lane) - 1u))] = v;
+  if (has) list[base + __popc(m & ((1u << lane) - 1u))] = v;
 }
 
 // Leaf gather and bottom-up bounds in one kernel.  Thread j of block b owns
@@ -225,10 +219,10 @@ __device__ __forceinline__ void append_start(int v, unsigned* count, int* list) 
 //     rounds separated by barriers: a node whose children are done takes
 //     their boxes from shared memory, writes its record and its union.  The
 //     rounds number the local subtrees' height; no fences, no atomics.
-//  3. The few nodes that span blocks are left to k_climb: the owner of each
-//     local node (or leaf) whose parent spans blocks publishes its box and
-//     appends the parent to a list, so that no block stays resident behind a
-//     climb through the upper tree.
+//  3. The few nodes that span blocks are left to k_climb: their owners set
+//     their child boxes empty, and the owner of each local node (or leaf)
+//     whose parent spans blocks publishes its box and lists it as a climb
+//     start, so that no block stays resident behind a climb.
 template <int B>
 __global__ void __launch_bounds__(B) k_gather_refit(
     const int4* __restrict__ child, const int* __restrict__ parent_int,
@@ -299,35 +293,77 @@ __global__ void __launch_bounds__(B) k_gather_refit(
     if (!any) break;
     __syncthreads();  // this round's flags are visible
   }
-  // 3. nodes that span blocks: leaves, then local nodes, whose parent does
-  int start_leaf = -1, start_node = -1;
-  if (leaf < n) {
+  // 3. nodes that span blocks: empty child boxes, widened by k_climb
+  if (has_node && !node_local) {
+    float4* o = nodes + 4 * (size_t)node;
+    const float inf = __int_as_float(0x7f800000);
+    const float4 e = make_float4(inf, -inf, inf, -inf);
+    __stcg(o, e);
+    __stcg(o + 1, e);
+    __stcg(o + 2, e);
+    __stcg(o + 3, make_float4(__int_as_float(ch.x), __int_as_float(ch.y), 0.f, 0.f));
+  }
+  bool start_leaf = false, start_node = false;
+  if (leaf < n && lparent >= 0) {
     const bool parent_local = lparent >= b0 && lparent < b0 + B && s_child[lparent - b0].z >= b0 &&
                               s_child[lparent - b0].w < b0 + B;
     if (!parent_local) {
       __stcg(lbox + 2 * leaf, bl);
       __stcg(lbox + 2 * leaf + 1, bh);
-      start_leaf = lparent;
+      start_leaf = true;
     }
   }
   if (node_local && node != 0) {
     const int p = __ldg(parent_int + node);
-    const bool parent_local = p >= b0 && p < b0 + B && s_child[p - b0].z >= b0 &&
-                              s_child[p - b0].w < b0 + B;
-    if (!parent_local) start_node = p;
+    start_node = !(p >= b0 && p < b0 + B && s_child[p - b0].z >= b0 && s_child[p - b0].w < b0 + B);
   }
-  append_start(start_leaf, n_starts, starts);
-  append_start(start_node, n_starts, starts);
+  append_start(start_leaf, ~leaf, n_starts, starts);
+  append_start(start_node, node, n_starts, starts);
 }
 
-// Bottom-up bounds of the nodes that span blocks, from the arrivals listed by
-// k_gather_refit (every record below them is complete when it starts).
+// Bounds of the nodes that span blocks.  Each climb start (a leaf or local
+// node whose parent spans blocks; its record is complete) widens, with float
+// atomics, its own slot in its parent, then its parent's slot in the
+// grandparent, and so on to the root.  Each of the six coordinates stops at
+// the first ancestor slot that it does not change: that slot already holds a
+// value at least as wide from another start below it, which carries it on
+// up.  No ordering between starts is needed.
 __global__ void k_climb(const unsigned* __restrict__ n_starts, const int* __restrict__ starts,
                         const int4* __restrict__ child, const int* __restrict__ parent_int,
-                        float4* nodes, const float4* lbox, unsigned* arrivals) {
+                        const int* __restrict__ parent_leaf, float4* nodes, const float4* lbox) {
   const unsigned m = *n_starts;
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
-    climb_global(__ldg(starts + i), child, parent_int, nodes, lbox, arrivals);
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    int cur = __ldg(starts + i);
+    float b[6];
+    int p;
+    if (cur < 0) {
+      lbox_read(lbox, ~cur, b);
+      p = __ldg(parent_leaf + ~cur);
+    } else {
+      node_union(nodes, cur, b);
+      p = __ldg(parent_int + cur);
+    }
+#pragma unroll
+    for (int q = 0; q < 6; ++q) b[q] = b[q] + 0.f;  // -0 -> +0
+    unsigned live = 0x3fu;
+    while (p >= 0) {
+      const int4 ch = __ldg(child + p);
+      const int up = p == 0 ? -1 : __ldg(parent_int + p);
+      float* r = reinterpret_cast<float*>(nodes + 4 * (size_t)p);
+      // record slots of (lo.x, hi.x, lo.y, hi.y, lo.z, hi.z) for child 0 / child 1
+      const int o = ch.x == cur ? 0 : 4, oz = ch.x == cur ? 8 : 10;
+      const int off[6] = {o, o + 1, o + 2, o + 3, oz, oz + 1};
+#pragma unroll
+      for (int q = 0; q < 6; ++q)
+        if ((live >> q) & 1u) {
+          const bool changed = (q & 1) ? atomic_max_f(r + off[q], b[q]) : atomic_min_f(r + off[q], b[q]);
+          if (!changed) live &= ~(1u << q);
+        }
+      if (!live) break;
+      cur = p;
+      p = up;
+    }
+  }
 }
 
 __global__ void k_bytes_differ(const uint8_t* __restrict__ x, const uint8_t* __restrict__ y,
@@ -340,17 +376,17 @@ __global__ void k_bytes_differ(const uint8_t* __restrict__ x, const uint8_t* __r
 // bounds, over the topology in bv.
 hr_status gather_refit(hr_ctx* ctx, hr_asset* a, Bvh& bv, const uint32_t* ids, cudaStream_t st) {
   const uint32_t n = bv.n;
-  unsigned* arrivals = nullptr;  // n node counters, then the number of climb starts
+  unsigned* n_starts = nullptr;
   float4* lbox = nullptr;
   int* starts = nullptr;  // at most one per leaf and one per internal node
-  HR_TRY(scratch(ctx, 39, ((size_t)n + 1) * 4, (void**)&arrivals));
+  HR_TRY(scratch(ctx, 39, 16, (void**)&n_starts));
   HR_TRY(scratch(ctx, 46, (size_t)n * 2 * sizeof(float4), (void**)&lbox));
   HR_TRY(scratch(ctx, 48, (size_t)n * 2 * 4, (void**)&starts));
-  HR_CUDA(ctx, cudaMemsetAsync(arrivals, 0, ((size_t)n + 1) * 4, st));
+  HR_CUDA(ctx, cudaMemsetAsync(n_starts, 0, 4, st));
   k_gather_refit<128><<<(n + 127) / 128, 128, 0, st>>>(bv.child, bv.par_int, bv.par_leaf,
                                                        a->prim_box, ids, a->prim_xf, a->prim_aux,
                                                        (int)n, bv.nodes, lbox, bv.leaf_xf,
-                                                       bv.leaf_aux, bv.leaf_id, arrivals + n, starts);
+                                                       bv.leaf_aux, bv.leaf_id, n_starts, starts);
   HR_LAUNCHED(ctx);
   static int climb_grid = 0;
   if (!climb_grid) {
@@ -364,8 +400,7 @@ hr_status gather_refit(hr_ctx* ctx, hr_asset* a, Bvh& bv, const uint32_t* ids, c
     climb_grid = sms * per;
   }
   const unsigned grid = (unsigned)std::min<size_t>((size_t)climb_grid, ((size_t)n * 2 + 255) / 256);
-  k_climb<<<grid, 256, 0, st>>>(arrivals + n, starts, bv.child, bv.par_int, bv.nodes, lbox,
-                                arrivals);
+  k_climb<<<grid, 256, 0, st>>>(n_starts, starts, bv.child, bv.par_int, bv.par_leaf, bv.nodes, lbox);
   HR_LAUNCHED(ctx);
   return HR_OK;
 }
