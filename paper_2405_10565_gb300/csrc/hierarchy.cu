@@ -10,14 +10,16 @@
 //  * Thick hairs: per cross-section k, mean centre, mean unit tangent, PCA of
 //    the members' k-th points, the axis closest to the tangent dropped, e1 the
 //    remaining axis with the larger eigenvalue, and semi-axes covering every
-//    member (Section 5.1 step 3 "Cross-section fitting").  The covariance and
-//    its eigen-decomposition are FP64; the members' centring sums are exact
-//    FP32 double-word sums (the FP64 rate of GB300 is 1/64 of its FP32 rate).
+//    member (Section 5.1 step 3 "Cross-section fitting").  The centring sums,
+//    the covariance and the eigenvector residual are double-word FP32 (the
+//    FP64 rate of GB300 is 1/64 of its FP32 rate); near-degenerate sections
+//    take a full FP64 eigen-solve.
 //
 // A primitive record is the affine map from world space to the cylinder's
 // unit frame: rows (e1/a, -c0.e1/a), (e2/b, -c0.e2/b), (t/L, -c0.t/L); a ray
 // hits the open cylinder where u^2 + v^2 = 1 with w in [0, 1].  Records are
-// built in FP32 with compensated offsets (below); no FP64 outside the fit.
+// built in FP32 with compensated offsets (below); no FP64 outside the fit's
+// near-degenerate path.
 #include <algorithm>
 #include <vector>
 
@@ -73,6 +75,44 @@ __device__ __forceinline__ void ff_renorm(ffsum& s) {
   s.lo = e;
 }
 __device__ __forceinline__ double ff_value(const ffsum& s) { return (double)s.hi + (double)s.lo; }
+
+// Double-word FP32 numbers hi + lo, |lo| <= ulp(hi) / 2 (Dekker 1971; the
+// accurate addition of Li et al., "Design, implementation and testing of
+// extended and mixed precision BLAS", 2002): about 2^-44 relative error per
+// operation, at a few FP32 operations each instead of one FP64 operation
+// (1/64 of the FP32 rate on this GPU).
+struct df {
+  float hi, lo;
+};
+__device__ __forceinline__ df df_fast(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df df_of(const ffsum& s) {
+  float e;
+  const float h = two_sum(s.hi, s.lo, e);
+  return {h, e};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+  float e1, e2;
+  const float s = two_sum(a.hi, b.hi, e1);
+  const float t = two_sum(a.lo, b.lo, e2);
+  const df u = df_fast(s, __fadd_rn(e1, t));
+  return df_fast(u.hi, __fadd_rn(u.lo, e2));
+}
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, {-b.hi, -b.lo}); }
+__device__ __forceinline__ df df_mul(df a, df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  const float e = fmaf(a.hi, b.hi, -p);
+  return df_fast(p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e)));
+}
+__device__ __forceinline__ df df_mul(df a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  const float e = fmaf(a.hi, b, -p);
+  return df_fast(p, fmaf(a.lo, b, e));
+}
+__device__ __forceinline__ float df_float(df a) { return __fadd_rn(a.hi, a.lo); }
+__device__ __forceinline__ double df_double(df a) { return (double)a.hi + (double)a.lo; }
 // s += (xh + xl) (yh + yl), with the exact product xh yh (the FMA form of
 // Dekker's TwoProduct) and the cross terms; xl yl (2^-48 relative) dropped.
 __device__ __forceinline__ void ff_add_prod(ffsum& s, float xh, float xl, float yh, float yl) {
@@ -467,13 +507,14 @@ __device__ d3 major_axis_fp64(const double C[3][3], const float Vf[3][3], const 
 //  * Centring sums: the members' offsets d = p - p0 from the first member are
 //    exact FP32 pairs (TwoSum) and their first and second moments double-word
 //    FP32 sums (exact products, every rounding error kept, renormalised every
-//    64 members), folded into FP64 once: within ~2^-48 of exact, like FP64
-//    sums, at a fraction of their cost.
-//  * Covariance: FP64.  Eigenbasis: cyclic Jacobi in FP32 on the
-//    trace-normalised covariance; the kept axis e1 is then corrected to first
-//    order from its FP64 residual r = C v - (v.Cv) v, which is where the
-//    conditioning needs FP64 (the residual is a small difference of large
-//    terms).  The FP32 basis is off by e ~ 3e-7 / gap and the correction
+//    64 members): within ~2^-48 of exact, like FP64 sums, at a fraction of
+//    their cost.
+//  * Mean and covariance: double-word FP32 (about 2^-44 relative).
+//    Eigenbasis: cyclic Jacobi in FP32 on the trace-normalised covariance;
+//    the kept axis e1 is then corrected to first order from its double-word
+//    residual r = C v - (v.Cv) v, which is where the conditioning needs more
+//    than FP32 (the residual is a small difference of large terms).  The
+//    FP32 basis is off by e ~ 3e-7 / gap and the correction
 //    leaves ~e^2, so it is taken while every gap between e1's eigenvalue and
 //    the others is at least 1e-2 of the largest (e^2 < 1e-9);
 //    closer eigenvalues, a near tie for the dropped axis and covariances out
@@ -524,24 +565,32 @@ __global__ void __launch_bounds__(128, 8) k_fit_cross_sections(const float4* __r
       ff_renorm(fyy); ff_renorm(fyz); ff_renorm(fzz);
     }
   }
-  const double inv_n = recip_nr((double)cnt);
-  const double mx = ff_value(fx) * inv_n, my = ff_value(fy) * inv_n, mz = ff_value(fz) * inv_n;
-  const double sxx = ff_value(fxx), sxy = ff_value(fxy), sxz = ff_value(fxz);
-  const double syy = ff_value(fyy), syz = ff_value(fyz), szz = ff_value(fzz);
-  const d3 ctr = mk(p0x + mx, p0y + my, p0z + mz);
+  // mean offset and covariance in double-word FP32
+  const float fn = (float)cnt, rn = 1.0f / fn;
+  const df inv_n = {rn, fmaf(-fn, rn, 1.0f) * rn};
+  const df mx = df_mul(df_of(fx), inv_n), my = df_mul(df_of(fy), inv_n), mz = df_mul(df_of(fz), inv_n);
+  const df m3[3] = {mx, my, mz};
+  const df s3[3][3] = {{df_of(fxx), df_of(fxy), df_of(fxz)},
+                       {df_of(fxy), df_of(fyy), df_of(fyz)},
+                       {df_of(fxz), df_of(fyz), df_of(fzz)}};
+  df C[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      C[i][j] = df_sub(df_mul(s3[i][j], inv_n), df_mul(m3[i], m3[j]));
+      C[j][i] = C[i][j];
+    }
   const float itn = rsqrtf(tx * tx + ty * ty + tz * tz);
   const float tfx = tx * itn, tfy = ty * itn, tfz = tz * itn;
-  const double C[3][3] = {{sxx * inv_n - mx * mx, sxy * inv_n - mx * my, sxz * inv_n - mx * mz},
-                          {sxy * inv_n - mx * my, syy * inv_n - my * my, syz * inv_n - my * mz},
-                          {sxz * inv_n - mx * mz, syz * inv_n - my * mz, szz * inv_n - mz * mz}};
   // FP32 Jacobi on the trace-normalised covariance
-  const double tr = C[0][0] + C[1][1] + C[2][2];
-  const bool seed = tr > 1e-30 && tr < 1e30;
-  const float inv_tr = seed ? 1.0f / (float)tr : 0.f;
+  const float tr = df_float(C[0][0]) + df_float(C[1][1]) + df_float(C[2][2]);
+  const bool seed = tr > 1e-30f && tr < 1e30f;
+  const float inv_tr = seed ? 1.0f / tr : 0.f;
   float Af[3][3], Vf[3][3];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
-      Af[i][j] = (float)C[i][j] * inv_tr;
+      Af[i][j] = df_float(C[i][j]) * inv_tr;
       Vf[i][j] = (i == j) ? 1.f : 0.f;
     }
   if (seed) jacobi_sweeps<float>(Af, Vf, 10, 1e-13f);
@@ -566,24 +615,30 @@ __global__ void __launch_bounds__(128, 8) k_fit_cross_sections(const float4* __r
   const float ga = lk - pick3(lam3, keep0), gb = lk - pick3(lam3, dcol);
   float e1x, e1y, e1z;
   if (seed && lmax > 0.f && fminf(ga, fabsf(gb)) >= 1e-2f * lmax && best - second > 1e-4f) {
-    // FP64 residual of the FP32 vector v, then v += sum_j (v_j . r) / (l_k - l_j) v_j
+    // double-word residual of the FP32 vector v, then
+    // v += sum_j (v_j . r) / (l_k - l_j) v_j
     const float vx = pick3(Vf[0], keep), vy = pick3(Vf[1], keep), vz = pick3(Vf[2], keep);
     const float ax = pick3(Vf[0], keep0), ay = pick3(Vf[1], keep0), az = pick3(Vf[2], keep0);
     const float bx = pick3(Vf[0], dcol), by = pick3(Vf[1], dcol), bz = pick3(Vf[2], dcol);
-    const d3 v = mk(vx, vy, vz);
-    const d3 w = mk(C[0][0] * v.x + C[0][1] * v.y + C[0][2] * v.z,
-                    C[1][0] * v.x + C[1][1] * v.y + C[1][2] * v.z,
-                    C[2][0] * v.x + C[2][1] * v.y + C[2][2] * v.z);
-    const double lam = dot(v, w), sc = (double)inv_tr;
-    const float rx = (float)((w.x - lam * v.x) * sc), ry = (float)((w.y - lam * v.y) * sc),
-                rz = (float)((w.z - lam * v.z) * sc);
+    df w[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      w[i] = df_add(df_add(df_mul(C[i][0], vx), df_mul(C[i][1], vy)), df_mul(C[i][2], vz));
+    const df lam = df_add(df_add(df_mul(w[0], vx), df_mul(w[1], vy)), df_mul(w[2], vz));
+    const float rx = df_float(df_sub(w[0], df_mul(lam, vx))) * inv_tr;
+    const float ry = df_float(df_sub(w[1], df_mul(lam, vy))) * inv_tr;
+    const float rz = df_float(df_sub(w[2], df_mul(lam, vz))) * inv_tr;
     const float ca = (ax * rx + ay * ry + az * rz) / ga;
     const float cb = (bx * rx + by * ry + bz * rz) / gb;
     e1x = vx + ca * ax + cb * bx;
     e1y = vy + ca * ay + cb * by;
     e1z = vz + ca * az + cb * bz;
   } else {
-    const d3 e1 = major_axis_fp64(C, Vf, mk(tfx, tfy, tfz), ctr, verts, S, k, order, first, cnt);
+    double Cd[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) Cd[i][j] = df_double(C[i][j]);
+    const d3 ctr = mk(p0x + df_double(mx), p0y + df_double(my), p0z + df_double(mz));
+    const d3 e1 = major_axis_fp64(Cd, Vf, mk(tfx, tfy, tfz), ctr, verts, S, k, order, first, cnt);
     e1x = (float)e1.x;
     e1y = (float)e1.y;
     e1z = (float)e1.z;
@@ -603,9 +658,9 @@ __global__ void __launch_bounds__(128, 8) k_fit_cross_sections(const float4* __r
   // pass 2: semi-axes; pass 3: the coverage scale (one square root).  A
   // member's offset from the centre is (p - p0) - (c - p0): the first
   // difference is rounded once in FP32 (exact when the two floats are within
-  // a factor of two), the second term is the FP64 mean shift rounded once, so
+  // a factor of two), the second term is the mean shift rounded once, so
   // the projections run in FP32 (the results are stored as FP32 anyway).
-  const float mfx = (float)mx, mfy = (float)my, mfz = (float)mz;
+  const float mfx = df_float(mx), mfy = df_float(my), mfz = df_float(mz);
   float af = 0.f, bf = 0.f;
   for (uint32_t i = 0; i < cnt; ++i) {
     const float4* P = verts + (size_t)__ldg(order + first + i) * (S + 1);
@@ -631,7 +686,9 @@ __global__ void __launch_bounds__(128, 8) k_fit_cross_sections(const float4* __r
     b = bf * sc;
   }
   float4* o = xsec + idx * 3;
-  o[0] = make_float4((float)ctr.x, (float)ctr.y, (float)ctr.z, a);
+  // centre p0 + mean offset, rounded once from double-word FP32
+  const df cx = df_add({p0x, 0.f}, mx), cy = df_add({p0y, 0.f}, my), cz = df_add({p0z, 0.f}, mz);
+  o[0] = make_float4(df_float(cx), df_float(cy), df_float(cz), a);
   o[1] = make_float4(e1x, e1y, e1z, b);
   o[2] = make_float4(e2x, e2y, e2z, 0.f);
 }
