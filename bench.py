@@ -16,7 +16,7 @@ Also measured in the same run:
              timed region;
   * roofline - the kernel that takes more of the step, the trace kernel or
              the cross-section fit, against its ALU peak (FP32 for the trace
-             kernel, with algorithmic FLOPs from a counting render; FP64 for
+             kernel, with algorithmic FLOPs from a counting render; FP32 for
              the fit), and the other kernel beside it;
   * cpu_baseline - the FP64 brute-force CPU oracle on a bounded sample of the
              same workload, on this host's cores;
@@ -56,17 +56,19 @@ FLOPS_PER_STRAND_SHADE = 100  # light vector, angles, f_single (3 Gaussians), ac
 FLOPS_PER_ETH_SHADE = 250     # + albedo lookups, widened lobes, B lobe, S
 FLOPS_PER_HIT = 40            # tangent, outgoing angles, opacity, composite
 FLOPS_PER_SAMPLE = 30         # camera ray
-# FP64 operations of the cross-section fit (k_fit_cross_sections), same rules:
-# per member none (the centring sums are exact FP32 double-word sums); per
-# cross-section the fold of the 9 sums (9), 1/n and the mean and centre (9),
-# the covariance (18), its trace (2) and the FP64 residual of the kept axis
-# (C v, v.Cv, r, scaling: 29) = 67.  The FP32 eigen-solve, tangents and
-# projections are not counted, nor the full FP64 solve that nearly
-# degenerate sections take: the model is a lower bound.
-FP64_FLOPS_PER_MEMBER = 0
-FP64_FLOPS_PER_SECTION = 67
-# Nominal FP64 rate of GB300 (the profiling recipe's table); nothing measures it.
-FP64_PEAK_TFLOPS = 1.25
+# FP32 operations of the cross-section fit (k_fit_cross_sections), same rules
+# (hierarchy.cu).  Per member and section: the exact offsets and their
+# double-word first and second moments (3 TwoSum, 3 double-word adds, 6
+# double-word product accumulations: 132), the unit tangent (15), and the two
+# projection passes for the semi-axes and the coverage scale (22 + 22) = 191.
+# Per section: folding the 9 sums (54), 1/n and the mean (34), the double-word
+# covariance (240), the mean tangent, trace and FP32 copy (33), two cyclic
+# Jacobi sweeps (444: the fewest a section takes, so a lower bound), axis
+# choice (48), the double-word residual and first-order correction of the
+# kept axis (370), the frame and semi-axis scalars (39) and the centre (63)
+# = 1325.  The rare full FP64 solve of near-degenerate sections is not counted.
+FIT_FLOPS_PER_MEMBER = 191
+FIT_FLOPS_PER_SECTION = 1325
 
 
 def sources_hash(names):
@@ -615,21 +617,20 @@ def main():
                              "strand_shades": cst.strand_shades, "eth_shades": cst.eth_shades,
                              "hits": cst.shaded_hits, "traced_samples": cst.traced_samples,
                              "samples": samples}}
-    # FP64 work of the cross-section fit: every strand is a member of one thick
+    # FP32 work of the cross-section fit: every strand is a member of one thick
     # hair per level, so the members sum to N * levels over S+1 sections
     C_, L_, E_ = n_levels_info
     fit_avg = statistics.mean(fit_ms)
-    fit_flops = (w.scene.n_segments + 1) * (FP64_FLOPS_PER_SECTION * E_ +
-                                            FP64_FLOPS_PER_MEMBER * w.scene.n_strands * L_)
+    fit_flops = (w.scene.n_segments + 1) * (FIT_FLOPS_PER_SECTION * E_ +
+                                            FIT_FLOPS_PER_MEMBER * w.scene.n_strands * L_)
     fit_ach = fit_flops / (fit_avg * 1e-3) / 1e12 if fit_avg > 0 else 0.0
-    roof_fit = {"bound": "alu", "achieved": fit_ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": fit_ach / FP64_PEAK_TFLOPS,
+    roof_fit = {"bound": "alu", "achieved": fit_ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": fit_ach / peak,
                 "traffic": traffic_record("k_fit_cross_sections_full_head_traffic.json",
                                           FIT_SOURCES, w.name),
-                "kernel": "k_fit_cross_sections (thick-hair fit, FP64)", "kernel_ms": fit_avg,
-                "flops_per_launch": fit_flops,
-                "peak_basis": "FP64: nominal GB300 rate from the profiling recipe's table "
-                              "(no measured FP64 peak)"}
+                "kernel": "k_fit_cross_sections (thick-hair fit, double-word FP32)",
+                "kernel_ms": fit_avg, "flops_per_launch": fit_flops,
+                "peak_basis": roof_frame["peak_basis"]}
     dominant_fit = fit_avg >= render_avg
     roof = dict(roof_fit if dominant_fit else roof_frame)
     roof["dominant_by_time_in_step"] = True
