@@ -699,22 +699,24 @@ __global__ void k_eth_material(const float4* __restrict__ verts, uint32_t N, uin
                                const uint32_t* __restrict__ order,
                                const uint32_t* __restrict__ cl_first, LevelInfo li, uint32_t E,
                                float* mat, float* eth_r) {
-  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= E) return;
+  // one thread per (thick hair, material float); the last float is the radius
+  constexpr uint32_t F = HR_MAT_FLOATS + 1;
+  const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (uint64_t)E * F) return;
+  const uint32_t e = (uint32_t)(idx / F), j = (uint32_t)(idx % F);
   uint32_t first, cnt, c, lv;
   eth_members(li, cl_first, e, &first, &cnt, &c, &lv);
-  ffsum acc[HR_MAT_FLOATS];
-  for (int j = 0; j < HR_MAT_FLOATS; ++j) acc[j] = ffsum{0.f, 0.f};
-  ffsum rs{0.f, 0.f};
+  ffsum acc{0.f, 0.f};
   for (uint32_t i = 0; i < cnt; ++i) {
-    const uint32_t s = order[first + i];
-    for (int j = 0; j < HR_MAT_FLOATS; ++j) ff_add(acc[j], mat[(size_t)s * HR_MAT_FLOATS + j], 0.f);
-    ff_add(rs, verts[(size_t)s * (S + 1)].w, 0.f);
+    const uint32_t s = __ldg(order + first + i);
+    ff_add(acc, j < HR_MAT_FLOATS ? mat[(size_t)s * HR_MAT_FLOATS + j] : __ldg(&verts[(size_t)s * (S + 1)].w),
+           0.f);
   }
-  const float fn = (float)cnt;
-  for (int j = 0; j < HR_MAT_FLOATS; ++j)
-    mat[(size_t)(N + e) * HR_MAT_FLOATS + j] = __fadd_rn(acc[j].hi, acc[j].lo) / fn;
-  eth_r[e] = __fadd_rn(rs.hi, rs.lo) / fn;
+  const float mean = __fadd_rn(acc.hi, acc.lo) / (float)cnt;
+  if (j < HR_MAT_FLOATS)
+    mat[(size_t)(N + e) * HR_MAT_FLOATS + j] = mean;
+  else
+    eth_r[e] = mean;
 }
 
 // Thick-hair segment (e, k): axis c_k -> c_{k+1}, e1 = e1_k made orthogonal to
@@ -935,7 +937,7 @@ hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_lev
                                                                     a->xsec);
   HR_LAUNCHED(ctx);
   if (fit_end) HR_CUDA(ctx, cudaEventRecord(fit_end, st));
-  k_eth_material<<<(unsigned)((E + 127) / 128), 128, 0, st>>>(a->verts, N, S, a->order,
+  k_eth_material<<<(unsigned)((E * (HR_MAT_FLOATS + 1) + 127) / 128), 128, 0, st>>>(a->verts, N, S, a->order,
                                                              a->cl_first, li, (uint32_t)E,
                                                              a->mat, eth_r);
   HR_LAUNCHED(ctx);

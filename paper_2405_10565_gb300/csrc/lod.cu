@@ -50,8 +50,9 @@ struct Levels {
 
 __global__ void k_widths(const float4* __restrict__ xsec, uint32_t E, uint32_t S, Levels lv,
                          CamF cam, uint32_t* wmax /* [C][n_levels] float bits */) {
-  const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (uint64_t)E * (S + 1)) return;
+  const uint64_t idx0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = idx0 < (uint64_t)E * (S + 1);
+  const uint64_t idx = valid ? idx0 : 0;  // every lane stays for the warp reduction
   const uint32_t e = (uint32_t)(idx / (S + 1));
   uint32_t k = 0;
   while (k + 1 < lv.n_levels && e >= lv.off[k + 1]) ++k;
@@ -87,7 +88,11 @@ __global__ void k_widths(const float4* __restrict__ xsec, uint32_t E, uint32_t S
     if (behind) w = __int_as_float(0x7f800000);  // +inf
   }
   if (w != w) w = __int_as_float(0x7f800000);  // NaN (degenerate) counts as too wide
-  atomicMax(&wmax[cluster * lv.n_levels + k], __float_as_uint(w));
+  // lanes of one (cluster, level) take their maximum first: one atomic each
+  const uint32_t slot = valid ? cluster * lv.n_levels + k : 0xffffffffu;
+  const uint32_t peers = __match_any_sync(0xffffffffu, slot);
+  const uint32_t wm = __reduce_max_sync(peers, valid ? __float_as_uint(w) : 0u);
+  if (valid && (threadIdx.x & 31) == (uint32_t)(__ffs(peers) - 1)) atomicMax(&wmax[slot], wm);
 }
 
 __global__ void k_rule(const uint32_t* __restrict__ wmax, uint32_t C, uint32_t L, float eps,
