@@ -247,11 +247,20 @@ __global__ void k_root_bounds(const float4* __restrict__ verts, uint32_t N, uint
       hi[i] = max(hi[i], __shfl_xor_sync(0xffffffffu, hi[i], o));
     }
   }
-  if ((threadIdx.x & 31) == 0) {
+  // then across the block's warps: six atomics per block
+  __shared__ uint32_t s_b[8][6];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0)
     for (int i = 0; i < 3; ++i) {
-      atomicMin(&bounds[i], lo[i]);
-      atomicMax(&bounds[3 + i], hi[i]);
+      s_b[wid][i] = lo[i];
+      s_b[wid][3 + i] = hi[i];
     }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    const int i = threadIdx.x;
+    uint32_t v = s_b[0][i];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = i < 3 ? min(v, s_b[w][i]) : max(v, s_b[w][i]);
+    if (i < 3) atomicMin(&bounds[i], v); else atomicMax(&bounds[i], v);
   }
 }
 
