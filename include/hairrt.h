@@ -202,7 +202,11 @@ hr_status hr_asset_destroy(hr_ctx* ctx, hr_asset* asset);
  * same strands, materials and cross-sections).  vertices: host or device,
  * [n_strands][n_segments + 1] float4 (x, y, z, r) in the asset's sizes,
  * copied on the context stream; the strand segment records are rebuilt in
- * place (no allocation).  The hierarchy, thick hairs and BVH of the old
+ * place (no allocation).  Device memory and page-locked host memory are read
+ * directly by the rebuilding kernel (the transfer overlaps the rebuild);
+ * either must stay unchanged until the context stream has passed it (the
+ * next call that returns results, e.g. hr_render_frame).  Pageable host
+ * memory is copied before the call returns.  The hierarchy, thick hairs and BVH of the old
  * positions are stale afterwards: hr_render_frame rebuilds them, or call
  * hr_build_clusters and hr_build_bvh.  The LoD kept for Eq. 14's deferred
  * rule is the previous frame's, as the paper intends.  With serving running,

@@ -117,6 +117,18 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+const void* device_view(const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return p;
+  if (at.type == cudaMemoryTypeHost) return at.devicePointer;
+  return nullptr;
+}
+
 // Copy `bytes` from a host-or-device source into a device destination.
 hr_status to_device(hr_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_t st) {
   if (!bytes) return HR_OK;
@@ -305,8 +317,16 @@ hr_status hr_asset_update(hr_ctx* ctx, hr_asset* a, const float* vertices) {
   if (!a || !vertices) return set_error(ctx, HR_EINVAL, "hr_asset_update: null argument");
   if (ctx->server) serve_forget_asset(ctx, ctx->server, a);
   cudaStream_t st = ctx->stream;
-  HR_TRY(to_device(ctx, a->verts, vertices, (size_t)a->N * (a->S + 1) * sizeof(float4), st));
-  HR_TRY(refresh_strand_prims(ctx, a));
+  // a device-readable source (device memory, page-locked host memory) is read
+  // once by the kernel that rebuilds the records, so the transfer overlaps
+  // the build; anything else is copied first
+  const float4* view = static_cast<const float4*>(device_view(vertices));
+  if (view && a->S + 1 <= kUpdateMaxVerts) {
+    HR_TRY(update_strands(ctx, a, view));
+  } else {
+    HR_TRY(to_device(ctx, a->verts, vertices, (size_t)a->N * (a->S + 1) * sizeof(float4), st));
+    HR_TRY(refresh_strand_prims(ctx, a));
+  }
   a->bvh.valid = 0;
   return HR_OK;
 }

@@ -383,7 +383,7 @@ hr_status gather_refit(hr_ctx* ctx, hr_asset* a, Bvh& bv, const uint32_t* ids, c
   HR_TRY(scratch(ctx, 46, (size_t)n * 2 * sizeof(float4), (void**)&lbox));
   HR_TRY(scratch(ctx, 48, (size_t)n * 2 * 4, (void**)&starts));
   HR_CUDA(ctx, cudaMemsetAsync(n_starts, 0, 4, st));
-  k_gather_refit<128><<<(n + 127) / 128, 128, 0, st>>>(bv.child, bv.par_int, bv.par_leaf,
+  k_gather_refit<256><<<(n + 255) / 256, 256, 0, st>>>(bv.child, bv.par_int, bv.par_leaf,
                                                        a->prim_box, ids, a->prim_xf, a->prim_aux,
                                                        (int)n, bv.nodes, lbox, bv.leaf_xf,
                                                        bv.leaf_aux, bv.leaf_id, n_starts, starts);

@@ -149,6 +149,15 @@ cudaError_t morton_clusters_with(const float4* verts, uint32_t N, uint32_t S, ui
 // --- hierarchy.cu
 hr_status build_strand_prims(hr_ctx* ctx, hr_asset* a);
 hr_status refresh_strand_prims(hr_ctx* ctx, hr_asset* a);
+// new vertices from a device-readable source (device memory, or page-locked
+// host memory mapped into the device's address space) in one fused kernel:
+// device copy, strand records, Morton bounds; strands of at most
+// kUpdateMaxVerts vertices
+constexpr uint32_t kUpdateMaxVerts = 2048;
+hr_status update_strands(hr_ctx* ctx, hr_asset* a, const float4* src_dev);
+// device address through which kernels can read p (device memory, or mapped
+// page-locked host memory), or nullptr
+const void* device_view(const void* p);
 
 // Float <-> unsigned with the same order (atomic min / max of floats).
 __device__ __forceinline__ uint32_t ordered_bits(float f) {

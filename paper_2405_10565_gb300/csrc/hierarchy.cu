@@ -228,6 +228,58 @@ __global__ void k_strand_prims(const float4* __restrict__ verts, const float4* _
   aux[idx] = make_float4(__uint_as_float(s), 0.f, r, sh.z * sh.w);
 }
 
+// New strand positions in one pass: each block reads the vertices of
+// `per_block` whole strands once, from device memory or from page-locked host
+// memory mapped into the device's address space (so the transfer and the
+// record build overlap), keeps them in shared memory, writes the asset's
+// device copy, and builds every segment record of its strands exactly as
+// k_strand_shape and k_strand_prims do.
+__global__ void k_strand_update(const float4* __restrict__ src, float4* __restrict__ verts,
+                                const float2* __restrict__ shape, uint32_t N, uint32_t S,
+                                uint32_t per_block, float4* xf, float4* box, float4* aux) {
+  extern __shared__ float4 sv[];  // per_block * (S + 1) vertices, then per_block shapes
+  const uint32_t s0 = blockIdx.x * per_block;
+  const uint32_t ns = min(per_block, N - s0);
+  const uint32_t nv = ns * (S + 1);
+  const size_t v0 = (size_t)s0 * (S + 1);
+  for (uint32_t i = threadIdx.x; i < nv; i += blockDim.x) {
+    const float4 v = src[v0 + i];
+    sv[i] = v;
+    verts[v0 + i] = v;
+  }
+  float4* ssh = sv + (size_t)per_block * (S + 1);
+  __syncthreads();
+  if (threadIdx.x < ns) {
+    const float r = sv[threadIdx.x * (S + 1)].w;
+    const float2 sh = shape[s0 + threadIdx.x];
+    float sp, cp;
+    sincosf(sh.y, &sp, &cp);
+    const float q = sqrtf(sqrtf(fmaf(-sh.x, sh.x, 1.0f)));
+    ssh[threadIdx.x] = make_float4(cp, sp, r / q, r * q);
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < ns * S; i += blockDim.x) {
+    const uint32_t ls = i / S, k = i % S;
+    const float4* P = sv + ls * (S + 1);
+    const float4 va = P[k], vb = P[k + 1];
+    const float3 p0 = make_float3(va.x, va.y, va.z), p1 = make_float3(vb.x, vb.y, vb.z);
+    const float r = P[0].w;
+    const float4 sh = ssh[ls];
+    const float3 ax = sub3(p1, p0);
+    const float L2 = dotf(ax, ax);
+    float3 e1 = make_float3(1.f, 0.f, 0.f);
+    if (L2 > 0.f) {
+      float3 b1, b2;
+      duff_basis_f(mul3(ax, 1.0f / sqrtf(L2)), &b1, &b2);
+      e1 = make_float3(fmaf(b1.x, sh.x, b2.x * sh.y), fmaf(b1.y, sh.x, b2.y * sh.y),
+                       fmaf(b1.z, sh.x, b2.z * sh.y));
+    }
+    const size_t idx = (size_t)(s0 + ls) * S + k;
+    write_prim(xf + idx * 3, box + idx * 2, p0, p1, e1, sh.z, sh.w);
+    aux[idx] = make_float4(__uint_as_float(s0 + ls), 0.f, r, sh.z * sh.w);
+  }
+}
+
 // ------------------------------------------------------------ Morton clusters
 
 
@@ -814,6 +866,18 @@ hr_status build_strand_prims(hr_ctx* ctx, hr_asset* a) {
 
 // Strand segment records and scene bounds from the current vertices, into
 // the asset's existing arrays (the first N * S records).
+hr_status update_strands(hr_ctx* ctx, hr_asset* a, const float4* src_dev) {
+  cudaStream_t st = ctx_stream(ctx);
+  const uint32_t S1 = a->S + 1;
+  const uint32_t per_block = std::min<uint32_t>(256u, kUpdateMaxVerts / S1);
+  const size_t smem = ((size_t)per_block * S1 + per_block) * sizeof(float4);
+  const uint32_t blocks = (a->N + per_block - 1) / per_block;
+  k_strand_update<<<blocks, 256, smem, st>>>(src_dev, a->verts, a->shape, a->N, a->S, per_block,
+                                             a->prim_xf, a->prim_box, a->prim_aux);
+  HR_LAUNCHED(ctx);
+  return scene_bounds(ctx, a, (uint64_t)a->N * a->S);
+}
+
 hr_status refresh_strand_prims(hr_ctx* ctx, hr_asset* a) {
   cudaStream_t st = ctx_stream(ctx);
   const uint64_t n = (uint64_t)a->N * a->S;

@@ -386,7 +386,7 @@ def test_asset_update_matches_a_fresh_asset(ctx):
     """hr_asset_update (new strand positions, as in animation) followed by a
     full frame gives the frame of an asset created from those positions:
     the hierarchy, thick hairs, LoD and BVH are rebuilt from the new
-    vertices, with host and with device vertex buffers."""
+    vertices, with pageable host, device and page-locked host vertex buffers."""
     torch = pytest.importorskip("torch")
     w0 = scenegen.full_head(n=6000, S=16, width=64, height=48, spp=2, n_lights=2, n_clusters=256)
     w1 = scenegen.full_head(n=6000, S=16, width=64, height=48, spp=2, n_lights=2, n_clusters=256,
@@ -410,6 +410,14 @@ def test_asset_update_matches_a_fresh_asset(ctx):
         assert not np.array_equal(img, ref)
         hr.hr_asset_update(ctx, a, torch.from_numpy(w1.scene.verts).to("cuda:0"))
         torch.cuda.synchronize()
+        hr.hr_render_frame(ctx, a, w0.n_clusters, w0.eps_w, 0, d, img)
+        assert np.array_equal(img, ref)
+        # page-locked host vertices (read by the update kernel in place)
+        hr.hr_asset_update(ctx, a, torch.from_numpy(w0.scene.verts).pin_memory())
+        hr.hr_render_frame(ctx, a, w0.n_clusters, w0.eps_w, 0, d, img)
+        assert not np.array_equal(img, ref)
+        pinned = torch.from_numpy(w1.scene.verts).pin_memory()
+        hr.hr_asset_update(ctx, a, pinned)
         hr.hr_render_frame(ctx, a, w0.n_clusters, w0.eps_w, 0, d, img)
         assert np.array_equal(img, ref)
     finally:
