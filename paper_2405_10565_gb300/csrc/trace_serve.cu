@@ -12,7 +12,8 @@ namespace hr {
 namespace {
 
 template <int KMAX, int PREC>
-__global__ void __launch_bounds__(kBlock)
+// 5 blocks per SM (at most 96 registers), as for the frame kernel.
+__global__ void __launch_bounds__(kBlock, 5)
     k_serve(const ServeItem* __restrict__ items, const uint32_t* __restrict__ item_start,
             uint32_t n_items, uint32_t total, uint32_t* work) {
   __shared__ uint32_t s_tile;
