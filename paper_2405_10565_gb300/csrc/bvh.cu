@@ -104,30 +104,32 @@ __global__ void k_prim_morton(const float4* __restrict__ box, const uint32_t* __
   keys[i] = ((spread10(qx) << 2) | (spread10(qy) << 1) | spread10(qz)) >> (30 - kMortonBits);
 }
 
-__device__ __forceinline__ int delta(const uint32_t* __restrict__ keys, int n, int i, int j) {
-  if (j < 0 || j >= n) return -1;
-  const uint32_t a = keys[i], b = keys[j];
-  if (a != b) return __clz(a ^ b);
-  return 32 + __clz((uint32_t)i ^ (uint32_t)j);
+// Length of the common prefix of (key, index) at i and j; -1 outside [0, n).
+__device__ __forceinline__ int delta(const uint32_t* __restrict__ keys, int n, uint32_t ki, int i,
+                                     int j) {
+  if ((unsigned)j >= (unsigned)n) return -1;
+  const uint32_t x = ki ^ __ldg(keys + j);
+  return x ? __clz(x) : 32 + __clz((uint32_t)i ^ (uint32_t)j);
 }
 
 __global__ void k_karras(const uint32_t* __restrict__ keys, int n, int4* child,
                          int* parent_int, int* parent_leaf) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n - 1) return;
-  const int d = (delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
-  const int dmin = delta(keys, n, i, i - d);
+  const uint32_t ki = __ldg(keys + i);
+  const int d = (delta(keys, n, ki, i, i + 1) - delta(keys, n, ki, i, i - 1)) >= 0 ? 1 : -1;
+  const int dmin = delta(keys, n, ki, i, i - d);
   int lmax = 2;
-  while (delta(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+  while (delta(keys, n, ki, i, i + lmax * d) > dmin) lmax <<= 1;
   int l = 0;
   for (int t = lmax >> 1; t >= 1; t >>= 1)
-    if (delta(keys, n, i, i + (l + t) * d) > dmin) l += t;
+    if (delta(keys, n, ki, i, i + (l + t) * d) > dmin) l += t;
   const int j = i + l * d;
-  const int dnode = delta(keys, n, i, j);
+  const int dnode = delta(keys, n, ki, i, j);
   int s = 0;
-  for (int div = 2;; div <<= 1) {
-    const int t = (l + div - 1) / div;
-    if (delta(keys, n, i, i + (s + t) * d) > dnode) s += t;
+  for (int k = 1;; ++k) {  // t = ceil(l / 2^k)
+    const int t = (l + (1 << k) - 1) >> k;
+    if (delta(keys, n, ki, i, i + (s + t) * d) > dnode) s += t;
     if (t == 1) break;
   }
   const int gamma = i + s * d + min(d, 0);
