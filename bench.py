@@ -38,6 +38,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -110,8 +111,7 @@ class ClockSampler:
 
     def __init__(self, gpu_id=None):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                                 f".clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"hairrt_clocks_{os.getpid()}.csv")
         self.gpu_id = gpu_id
 
     def __enter__(self):
