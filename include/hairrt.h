@@ -268,6 +268,17 @@ hr_status hr_build_bvh(hr_ctx* ctx, hr_asset* asset, const uint8_t* lod);
 /* Primitive ids in BVH leaf order (host or device, [n_active] uint32) and the
  * number of active primitives; both optional. */
 hr_status hr_bvh_export(hr_ctx* ctx, hr_asset* asset, uint32_t* leaf_ids, uint32_t* n_active);
+/* The library's radix sort (the cluster build's and the BVH build's), for
+ * tests: stable ascending sort of (keys[i], vals[i]) on the low `bits` bits of
+ * the keys (1..32), in place, n < 2^30; keys and vals are device memory and
+ * the call returns when the sort is done.  Each 3,072-pair tile finds where
+ * its digits go by reading the counts that earlier tiles publish; with
+ * count_earlier != 0 every tile counts the earlier keys itself instead (the
+ * path the library takes when a wait for a published count runs out), which
+ * must give the same order.  No counterpart in the paper: it checks Section
+ * 5.1's Morton ordering step and Karras 2012's sorted-key precondition. */
+hr_status hr_sort_pairs(hr_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t n, uint32_t bits,
+                        int count_earlier);
 
 /* ---------------------------------------------------------------- rendering */
 

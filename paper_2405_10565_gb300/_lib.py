@@ -106,6 +106,7 @@ _SIGS = {
     "hr_select_lod": (c_int, [P, P, ctypes.POINTER(hr_camera), c_float, c_int, c_int, P]),
     "hr_build_bvh": (c_int, [P, P, P]),
     "hr_bvh_export": (c_int, [P, P, P, ctypes.POINTER(c_u32)]),
+    "hr_sort_pairs": (c_int, [P, P, P, c_u32, c_u32, c_int]),
     "hr_render": (c_int, [P, P, ctypes.POINTER(hr_render_desc), P, ctypes.POINTER(hr_stats)]),
     "hr_render_samples": (c_int, [P, P, ctypes.POINTER(hr_render_desc), P, c_u32, P, P]),
     "hr_render_frame": (c_int, [P, P, c_u32, c_float, c_int, ctypes.POINTER(hr_render_desc), P,
@@ -282,6 +283,13 @@ def hr_select_lod(ctx: int, asset: int, cam_rec, eps_w_px: float, mode: int, bud
 
 def hr_build_bvh(ctx: int, asset: int, lod=None) -> None:
     _check(ctx, load().hr_build_bvh(ctx, asset, ptr(lod)), "hr_build_bvh")
+
+
+def hr_sort_pairs(ctx: int, keys, vals, n: int, bits: int, count_earlier: bool = False) -> None:
+    """Stable in-place radix sort of device uint32 (key, value) pairs on the
+    low `bits` key bits (test export of the library's sort)."""
+    _check(ctx, load().hr_sort_pairs(ctx, ptr(keys), ptr(vals), n, bits, 1 if count_earlier else 0),
+           "hr_sort_pairs")
 
 
 def hr_bvh_export(ctx: int, asset: int, leaf_ids=None) -> int:

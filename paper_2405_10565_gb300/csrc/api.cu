@@ -495,6 +495,24 @@ hr_status hr_bvh_export(hr_ctx* ctx, hr_asset* a, uint32_t* leaf_ids, uint32_t* 
   return HR_OK;
 }
 
+hr_status hr_sort_pairs(hr_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t n, uint32_t bits,
+                        int count_earlier) {
+  API_ENTER(ctx);
+  if (n == 0) return HR_OK;
+  if (!keys || !vals || !is_device_ptr(keys) || !is_device_ptr(vals))
+    return set_error(ctx, HR_EINVAL, "hr_sort_pairs: keys and vals must be device memory");
+  if (bits < 1 || bits > 32 || n >= (1u << 30))
+    return set_error(ctx, HR_EINVAL, "hr_sort_pairs: bits out of 1..32 or n >= 2^30");
+  cudaStream_t st = ctx->stream;
+  uint32_t *k2 = nullptr, *v2 = nullptr;
+  HR_TRY(scratch(ctx, 49, (size_t)n * 4, (void**)&k2));
+  HR_TRY(scratch(ctx, 50, (size_t)n * 4, (void**)&v2));
+  HR_TRY(radix_sort_pairs(ctx, keys, vals, k2, v2, n, (int)bits, st,
+                          count_earlier ? 0 : kLookbackPolls));
+  HR_CUDA(ctx, cudaStreamSynchronize(st));
+  return HR_OK;
+}
+
 static hr_status render_impl(hr_ctx* ctx, hr_asset* a, const hr_render_desc* desc, float* rgb_out,
                              hr_stats* stats) {
   if (!a || !rgb_out) return set_error(ctx, HR_EINVAL, "null argument");

@@ -133,8 +133,12 @@ hr_status scan_u32(hr_ctx* ctx, uint32_t* data, uint32_t n, cudaStream_t st);
 // stable LSD radix sort of (key, value) pairs on the low `bits` key bits,
 // one kernel per 8-bit digit pass (decoupled look-back); result in
 // keys/vals; tmp buffers of n entries; scratch slot 14; n < 2^30
+// max_polls: reads of an unpublished earlier tile before counting instead
+// (0: count at once, for tests)
+constexpr int kLookbackPolls = 1 << 16;
 hr_status radix_sort_pairs(hr_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp,
-                           uint32_t* vals_tmp, uint32_t n, int bits, cudaStream_t st);
+                           uint32_t* vals_tmp, uint32_t n, int bits, cudaStream_t st,
+                           int max_polls = kLookbackPolls);
 
 // no-allocation variants on caller-provided scratch (sort.cu, hierarchy.cu)
 cudaError_t scan_u32_with(uint32_t* data, uint32_t n, uint32_t* sums, cudaStream_t st);

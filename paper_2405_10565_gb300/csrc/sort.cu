@@ -161,20 +161,21 @@ __global__ void __launch_bounds__(kSortThreads)
 constexpr uint32_t kFlagAgg = 1u << 30;  // tile's own digit count
 constexpr uint32_t kFlagInc = 2u << 30;  // count of this and every earlier tile
 constexpr uint32_t kCountMask = kFlagAgg - 1u;
-constexpr int kLookbackPolls = 1 << 16;  // then the tile counts the earlier keys itself
 constexpr int kLookbackWindow = 8;
 constexpr int kSweepItems = 12;  // keys per thread
 constexpr uint32_t kSweepTile = kSortThreads * kSweepItems;
 
 // Digit totals of every pass in one read of the keys: hist[q * 256 + d].
-__global__ void k_pass_hist(const uint32_t* __restrict__ keys, uint32_t n, int passes,
+__global__ void k_pass_hist(const uint32_t* __restrict__ keys, uint32_t n, int bits,
                             uint32_t* __restrict__ hist) {
+  const int passes = (bits + 7) / 8;
+  const uint32_t low = bits >= 32 ? 0xffffffffu : (1u << bits) - 1u;  // only the low bits count
   __shared__ uint32_t h[4][kRadix];
   for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&h[0][0])[i] = 0;
   __syncthreads();
   for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     const uint32_t k = keys[p];
-    for (int q = 0; q < passes; ++q) atomicAdd(&h[q][(k >> (8 * q)) & 0xffu], 1u);
+    for (int q = 0; q < passes; ++q) atomicAdd(&h[q][((k & low) >> (8 * q)) & 0xffu], 1u);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) {
@@ -189,12 +190,14 @@ __global__ void k_pass_hist(const uint32_t* __restrict__ keys, uint32_t n, int p
 // by one vote per digit bit), publishes its digit counts, then
 // (thread d for digit d) walks back over the earlier tiles' published words,
 // adding counts until it meets a word that already holds an inclusive count.
-// If a wait outlasts kLookbackPolls reads the block counts the digits of all
-// earlier keys itself, which gives the same offsets.
+// If a wait outlasts max_polls reads (kLookbackPolls in the library) the
+// block counts the digits of all earlier keys itself, which gives the same
+// offsets.
 __global__ void __launch_bounds__(kSortThreads)
     k_sweep(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
             uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, uint32_t n, int shift,
-            const uint32_t* __restrict__ totals, uint32_t* status, uint32_t* tile_ctr) {
+            const uint32_t* __restrict__ totals, uint32_t* status, uint32_t* tile_ctr,
+            int max_polls, uint32_t dm) {
   static_assert(kSortThreads == kRadix && kSortThreads == kScanThreads, "one thread per digit");
   __shared__ uint32_t whist[kSortWarps][kRadix];
   __shared__ uint32_t s_off[kRadix];
@@ -217,7 +220,7 @@ __global__ void __launch_bounds__(kSortThreads)
 #pragma unroll
   for (int j = 0; j < kSweepItems; ++j) {
     const bool valid = base + j * 32 + lane < n;
-    const uint32_t d = valid ? ((k[j] >> shift) & 0xffu) : 0u;
+    const uint32_t d = valid ? ((k[j] >> shift) & dm) : 0u;
     // lanes with the same digit: one vote per digit bit, and one for validity
     uint32_t peers = __ballot_sync(0xffffffffu, valid);
     if (!valid) peers = ~peers;
@@ -249,8 +252,8 @@ __global__ void __launch_bounds__(kSortThreads)
   uint32_t all;
   const uint32_t dstart = block_excl_scan(__ldg(totals + d), &all);
   uint32_t excl = 0;
-  bool gave_up = false;
-  if (t > 0) {
+  bool gave_up = t > 0 && max_polls == 0;  // 0: always count (tests the path below)
+  if (t > 0 && !gave_up) {
     // kLookbackWindow earlier tiles per read, nearest first: counts are added
     // up to the first inclusive word; a tile not yet published stops the walk
     // there until a later read finds it
@@ -273,7 +276,7 @@ __global__ void __launch_bounds__(kSortThreads)
       }
       if (inc) break;
       kt -= used;  // tile 0 publishes an inclusive count, so kt stays >= 0
-      if (used == 0 && ++polls > kLookbackPolls) {
+      if (used == 0 && ++polls > max_polls) {
         gave_up = true;
         break;
       }
@@ -284,7 +287,7 @@ __global__ void __launch_bounds__(kSortThreads)
     cnt[d] = 0;
     __syncthreads();
     for (uint32_t p = threadIdx.x; p < t * kSweepTile; p += kSortThreads)
-      atomicAdd(&cnt[(keys[p] >> shift) & 0xffu], 1u);
+      atomicAdd(&cnt[(keys[p] >> shift) & dm], 1u);
     __syncthreads();
     excl = cnt[d];
     __syncthreads();
@@ -300,7 +303,7 @@ __global__ void __launch_bounds__(kSortThreads)
 #pragma unroll
   for (int j = 0; j < kSweepItems; ++j) {
     if (base + j * 32 + lane < n) {
-      const uint32_t q = whist[wid][(k[j] >> shift) & 0xffu] + local[j];
+      const uint32_t q = whist[wid][(k[j] >> shift) & dm] + local[j];
       s_key[q] = k[j];
       s_val[q] = v[j];
     }
@@ -311,7 +314,7 @@ __global__ void __launch_bounds__(kSortThreads)
   const uint32_t tile_n = min(kSweepTile, n - t * kSweepTile);
   for (uint32_t i = threadIdx.x; i < tile_n; i += kSortThreads) {
     const uint32_t key = s_key[i];
-    const uint32_t dst = s_off[(key >> shift) & 0xffu] + i;
+    const uint32_t dst = s_off[(key >> shift) & dm] + i;
     keys_out[dst] = key;
     vals_out[dst] = s_val[i];
   }
@@ -356,7 +359,8 @@ hr_status scan_u32(hr_ctx* ctx, uint32_t* data, uint32_t n, cudaStream_t st) {
 }
 
 hr_status radix_sort_pairs(hr_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp,
-                           uint32_t* vals_tmp, uint32_t n, int bits, cudaStream_t st) {
+                           uint32_t* vals_tmp, uint32_t n, int bits, cudaStream_t st,
+                           int max_polls) {
   if (n <= 1) return HR_OK;
   if (n >= kFlagAgg || bits < 1 || bits > 32) return set_error(ctx, HR_EINVAL, "sort: size out of range");
   const int passes = (bits + 7) / 8;
@@ -371,12 +375,14 @@ hr_status radix_sort_pairs(hr_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t
   uint32_t* ctr = ws + (size_t)passes * kRadix;
   uint32_t* status = ctr + 64;
   const uint32_t hb = std::min<uint32_t>(nb, 1024u);
-  k_pass_hist<<<hb, kSortThreads, 0, st>>>(keys, n, passes, totals);
+  k_pass_hist<<<hb, kSortThreads, 0, st>>>(keys, n, bits, totals);
   HR_LAUNCHED(ctx);
   uint32_t *ki = keys, *vi = vals, *ko = keys_tmp, *vo = vals_tmp;
   for (int q = 0; q < passes; ++q) {
+    // digit q holds key bits [8q, min(8q + 8, bits))
+    const uint32_t dm = bits - 8 * q >= 8 ? 0xffu : (1u << (bits - 8 * q)) - 1u;
     k_sweep<<<nb, kSortThreads, 0, st>>>(ki, vi, ko, vo, n, 8 * q, totals + q * kRadix,
-                                         status + (size_t)q * nb * kRadix, ctr + q);
+                                         status + (size_t)q * nb * kRadix, ctr + q, max_polls, dm);
     HR_LAUNCHED(ctx);
     uint32_t* t;
     t = ki; ki = ko; ko = t;

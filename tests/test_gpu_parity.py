@@ -578,3 +578,31 @@ def test_invalid_calls_are_refused_with_a_status(ctx):
         assert img.max() > 0
     finally:
         hr.hr_asset_destroy(ctx, a)
+
+
+@pytest.mark.parametrize("n,bits,dups", [(1, 30, False), (2, 30, True), (3071, 21, False),
+                                         (3072 * 5 + 17, 21, True), (100_003, 30, False),
+                                         (250_000, 32, True)])
+def test_radix_sort_is_stable_and_matches_numpy(ctx, n, bits, dups):
+    """The library's radix sort (single sweep per digit, decoupled look-back)
+    against numpy's stable argsort of the low `bits` key bits, through the
+    look-back and through the path where every tile counts the earlier keys
+    itself (taken when a wait for an earlier tile runs out)."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(n + bits)
+    hi = 64 if dups else 2 ** 32
+    keys = rng.integers(0, hi, n, dtype=np.uint64).astype(np.uint32)
+    if dups:
+        keys |= rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32) & ~np.uint32(2 ** bits - 1 if bits < 32 else 0xFFFFFFFF)
+    vals = np.arange(n, dtype=np.uint32)[::-1].copy()
+    mask = np.uint32(0xFFFFFFFF) if bits == 32 else np.uint32((1 << bits) - 1)
+    order = np.argsort(keys & mask, kind="stable")
+    for count_earlier in (False, True):
+        k = torch.from_numpy(keys.view(np.int32).copy()).to("cuda:0")
+        v = torch.from_numpy(vals.view(np.int32).copy()).to("cuda:0")
+        torch.cuda.synchronize()
+        hr.hr_sort_pairs(ctx, k, v, n, bits, count_earlier)
+        kk = k.cpu().numpy().view(np.uint32)
+        vv = v.cpu().numpy().view(np.uint32)
+        assert np.array_equal(vv, vals[order]), count_earlier
+        assert np.array_equal(kk, keys[order]), count_earlier
