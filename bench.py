@@ -237,12 +237,18 @@ def measure_config(hr, ctx, torch, dev, w, steps: int, warmup: int = 2):
             one()
         torch.cuda.synchronize(dev)
         dt = (time.perf_counter() - t0) / steps
+        # what the step traced (one counting frame after the timed steps)
+        dc = hr.render_desc(w.camera.pack(), w.lights, w.spp, w.k_depth, w.sample_seed, w.precision,
+                            hr.HR_FLAG_COUNT)
+        st = hr.hr_render(ctx, a, dc, img, stats=True)
     finally:
         hr.hr_asset_destroy(ctx, a)
     n = w.camera.width * w.camera.height * w.spp
     return {"workload": w.name, "ms_per_step": dt * 1e3, "Msamples_per_s": n / dt / 1e6,
             "strands": w.scene.n_strands, "segments": w.scene.n_segments,
-            "lod": w.lod_setting, "precision": "fp16" if w.precision else "fp32", "k_depth": w.k_depth}
+            "lod": w.lod_setting, "precision": "fp16" if w.precision else "fp32", "k_depth": w.k_depth,
+            "active_prims": int(st.n_active_prims), "eth_prims": int(st.n_eth_prims),
+            "traced_samples": int(st.traced_samples)}
 
 
 def max_over_ranks(x: float, dist, device) -> float:
@@ -592,6 +598,7 @@ def main():
             scenegen.clustered(lod_setting="strands"), scenegen.clustered(lod_setting="half"),
             scenegen.clustered(lod_setting="eth"),
             scenegen.full_head(precision=1),
+            scenegen.full_head(fill=0.9),  # close view: hair 90% of the frame height, all strands
             scenegen.stress())]
 
     hr.hr_asset_destroy(ctx, asset)

@@ -389,6 +389,8 @@ def full_head(n: int = 100000, S: int = 64, width: int = 1920, height: int = 108
     cam = frame_camera(lo, hi, width, height, perspective=True, fill=fill)
     lights = point_lights(n_lights, 0.5 * (lo + hi), seed=seed)
     tag = "fp16" if precision else "fp32"
+    if fill != 0.15:
+        tag += f"_fill{round(100 * fill)}"
     return Workload(f"full_head_{n}x{S}_{width}x{height}_{spp}spp_{tag}", sc, cam, lights,
                     spp, 4, n_clusters, lod_setting="select", precision=precision)
 
