@@ -201,7 +201,14 @@ def oracle_baseline(w, seconds: float, seed: int = 11):
             "seconds": dt}
 
 
-def measure_config(hr, ctx, torch, dev, w, steps: int, warmup: int = 2):
+def event_flops(st) -> int:
+    """FP32 operations of a frame from the event counts of a counting render."""
+    return (FLOPS_PER_NODE * st.node_visits + FLOPS_PER_TEST * st.prim_tests +
+            FLOPS_PER_STRAND_SHADE * st.strand_shades + FLOPS_PER_ETH_SHADE * st.eth_shades +
+            FLOPS_PER_HIT * st.shaded_hits + FLOPS_PER_SAMPLE * st.traced_samples)
+
+
+def measure_config(hr, ctx, torch, dev, w, steps: int, warmup: int = 2, peak_tflops=None):
     """Step time of another configuration (not the headline line): for a
     fixed LoD setting (all strands, half, all thick hairs) the clusters, BVH
     and frame per step, for a selected LoD the whole hr_render_frame step."""
@@ -237,18 +244,24 @@ def measure_config(hr, ctx, torch, dev, w, steps: int, warmup: int = 2):
             one()
         torch.cuda.synchronize(dev)
         dt = (time.perf_counter() - t0) / steps
-        # what the step traced (one counting frame after the timed steps)
+        # what the step traced (one counting frame after the timed steps), and
+        # the frame kernel alone on the same BVH (CUDA events, median of 5)
         dc = hr.render_desc(w.camera.pack(), w.lights, w.spp, w.k_depth, w.sample_seed, w.precision,
                             hr.HR_FLAG_COUNT)
         st = hr.hr_render(ctx, a, dc, img, stats=True)
+        frame_ms = statistics.median(hr.hr_render(ctx, a, d, img, stats=True).render_ms for _ in range(5))
     finally:
         hr.hr_asset_destroy(ctx, a)
     n = w.camera.width * w.camera.height * w.spp
-    return {"workload": w.name, "ms_per_step": dt * 1e3, "Msamples_per_s": n / dt / 1e6,
-            "strands": w.scene.n_strands, "segments": w.scene.n_segments,
-            "lod": w.lod_setting, "precision": "fp16" if w.precision else "fp32", "k_depth": w.k_depth,
-            "active_prims": int(st.n_active_prims), "eth_prims": int(st.n_eth_prims),
-            "traced_samples": int(st.traced_samples)}
+    out = {"workload": w.name, "ms_per_step": dt * 1e3, "Msamples_per_s": n / dt / 1e6,
+           "strands": w.scene.n_strands, "segments": w.scene.n_segments,
+           "lod": w.lod_setting, "precision": "fp16" if w.precision else "fp32", "k_depth": w.k_depth,
+           "active_prims": int(st.n_active_prims), "eth_prims": int(st.n_eth_prims),
+           "traced_samples": int(st.traced_samples), "frame_ms": frame_ms}
+    if peak_tflops:
+        tf = event_flops(st) / (frame_ms * 1e-3) / 1e12
+        out["frame_fp32"] = {"achieved_tflops": tf, "frac": tf / peak_tflops}
+    return out
 
 
 def max_over_ranks(x: float, dist, device) -> float:
@@ -486,9 +499,7 @@ def main():
                            hr.HR_FLAG_COUNT)
     cst = hr.hr_render(ctx, asset, cdesc, img, stats=True)
     n_levels_info = hr.hr_hierarchy_info(ctx, asset)
-    flops = (FLOPS_PER_NODE * cst.node_visits + FLOPS_PER_TEST * cst.prim_tests +
-             FLOPS_PER_STRAND_SHADE * cst.strand_shades + FLOPS_PER_ETH_SHADE * cst.eth_shades +
-             FLOPS_PER_HIT * cst.shaded_hits + FLOPS_PER_SAMPLE * cst.traced_samples)
+    flops = event_flops(cst)
     uuid = None
     try:
         uuid = str(torch.cuda.get_device_properties(dev).uuid)
@@ -593,7 +604,9 @@ def main():
     other_configs = None
     if not args.no_configs and rank == 0:
         import scenegen
-        other_configs = [measure_config(hr, ctx, torch, dev, cw, 5) for cw in (
+        props0 = torch.cuda.get_device_properties(dev)
+        peak0 = props0.multi_processor_count * 128 * 2 * (clocks.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
+        other_configs = [measure_config(hr, ctx, torch, dev, cw, 5, peak_tflops=peak0) for cw in (
             scenegen.tiny_strands(),
             scenegen.clustered(lod_setting="strands"), scenegen.clustered(lod_setting="half"),
             scenegen.clustered(lod_setting="eth"),
