@@ -185,14 +185,24 @@ __device__ __forceinline__ void lbox_read(const float4* lbox, int leaf, float* b
 }
 
 // Bounds of an internal node, from two child boxes (lo.x, hi.x, lo.y, hi.y,
-// lo.z, hi.z), as the node record and as the union.
+// lo.z, hi.z), as the node record.  The records are stored with an L2
+// evict-last policy: the frame kernel that follows the build reads them, and
+// keeping them in L2 over the leaf records written beside them took the
+// full-head frame from 0.63 to 0.60 ms (evict-last on the leaf records as
+// well was slower).
 __device__ __forceinline__ void store_node(float4* nodes, int node, int4 ch, const float* c0,
                                            const float* c1) {
   float4* o = nodes + 4 * node;
-  __stcg(o, make_float4(c0[0], c0[1], c0[2], c0[3]));
-  __stcg(o + 1, make_float4(c1[0], c1[1], c1[2], c1[3]));
-  __stcg(o + 2, make_float4(c0[4], c0[5], c1[4], c1[5]));
-  __stcg(o + 3, make_float4(__int_as_float(ch.x), __int_as_float(ch.y), 0.f, 0.f));
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  const float4 v[4] = {make_float4(c0[0], c0[1], c0[2], c0[3]), make_float4(c1[0], c1[1], c1[2], c1[3]),
+                       make_float4(c0[4], c0[5], c1[4], c1[5]),
+                       make_float4(__int_as_float(ch.x), __int_as_float(ch.y), 0.f, 0.f)};
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;"
+                 :: "l"(o + q), "f"(v[q].x), "f"(v[q].y), "f"(v[q].z), "f"(v[q].w), "l"(pol)
+                 : "memory");
 }
 
 // Float min / max as one integer atomic on the float's bits (non-negative
