@@ -10,8 +10,10 @@ READING and is the same reading the library follows.
 
 Pins (tests/test_oracle_*.py) tie each function to something other than
 itself: closed forms, analytic hits, brute force on tiny inputs, the
-separable-albedo identity, reciprocity, the n = 1 reduction and a hand-worked
-Morton example.  Functions without such a pin say "parity unpinned".
+separable-albedo identity, reciprocity, the n = 1 reduction, hand-worked
+Morton, record and light-sum examples, and the convergence of a thick-hair
+image toward the strand image of the same clusters.  Every function names its
+pins in its docstring.
 """
 from __future__ import annotations
 
@@ -35,7 +37,10 @@ PRIM_STRIDE = 15
 
 
 def build(force: bool = False) -> str:
-    """Compile trace.c into liboracle.so with gcc (no FMA contraction)."""
+    """Compile trace.c into liboracle.so with gcc (no FMA contraction).
+
+    Infrastructure (compiles trace.c; no arithmetic of the method).
+    """
     src = os.path.join(_HERE, "trace.c")
     if (not force and os.path.exists(_SO)
             and os.path.getmtime(_SO) >= os.path.getmtime(src)):
@@ -93,7 +98,10 @@ _QUAD = {}
 
 
 def gauss_legendre(n: int = 384):
-    """Gauss-Legendre nodes and weights on [-1, 1] (numpy's leggauss)."""
+    """Gauss-Legendre nodes and weights on [-1, 1] (numpy's leggauss).
+
+    Pinned by test_gauss_legendre_is_exact_for_polynomials_up_to_degree_2n_minus_1.
+    """
     if n not in _QUAD:
         x, w = np.polynomial.legendre.leggauss(n)
         _QUAD[n] = (np.ascontiguousarray(x, np.float64), np.ascontiguousarray(w, np.float64))
@@ -104,17 +112,26 @@ def gauss_legendre(n: int = 384):
 
 
 def gauss(beta: float, x: float) -> float:
+    """Pinned by test_gaussian_definition (the Gaussian's value at 0 and at one beta)."""
     return _load().oracle_gauss(beta, x)
 
 
 def im(theta: float, beta: float, nq: int = 384) -> float:
-    """Longitudinal albedo factor IM(theta; beta) (see trace.c)."""
+    """Longitudinal albedo factor IM(theta; beta) (see trace.c).
+
+    Pinned by test_longitudinal_integral_closed_form and
+    test_longitudinal_integral_quadrature_converged.
+    """
     x, w = gauss_legendre(nq)
     return _load().oracle_im(nq, _pd(x), _pd(w), theta, beta)
 
 
 def albedo(mat12, theta_d: float, nq: int = 384):
-    """(a_F rgb, a_B rgb, sigma_f^2) of a single fibre at theta_d."""
+    """(a_F rgb, a_B rgb, sigma_f^2) of a single fibre at theta_d.
+
+    Pinned by test_separable_albedo_equals_2d_quadrature, test_albedo_white_furnace_c1_material
+    and test_forward_albedo_stays_below_one_over_parameter_box.
+    """
     m = np.ascontiguousarray(mat12, np.float64)
     x, w = gauss_legendre(nq)
     aF = np.zeros(3)
@@ -125,7 +142,10 @@ def albedo(mat12, theta_d: float, nq: int = 384):
 
 
 def albedo_2d(mat12, theta_i: float, nq: int = 256):
-    """(front rgb, back rgb) directional albedo of f_single by 2-D quadrature."""
+    """(front rgb, back rgb) directional albedo of f_single by 2-D quadrature.
+
+    Pinned by test_albedo_2d_diffuse_closed_form (A_D / 4 per half for a diffuse fibre).
+    """
     m = np.ascontiguousarray(mat12, np.float64)
     x, w = gauss_legendre(nq)
     f = np.zeros(3)
@@ -135,6 +155,7 @@ def albedo_2d(mat12, theta_i: float, nq: int = 256):
 
 
 def f_single(mat12, th_i, th_o, cphi):
+    """Pinned by test_f_single_hand_values."""
     m = np.ascontiguousarray(mat12, np.float64)
     out = np.zeros(3)
     _load().oracle_f_single(_pd(m), th_i, th_o, cphi, _pd(out))
@@ -143,7 +164,10 @@ def f_single(mat12, th_i, th_o, cphi):
 
 def f_single_spread(mat12, th_i, th_o, cphi, sg2):
     """f_single with every lobe's variance grown by sg2 (the spread of the
-    light path under shadow rays)."""
+    light path under shadow rays).
+
+    Pinned by test_spread_is_a_wider_lobe.
+    """
     out = np.zeros(3)
     m = np.ascontiguousarray(mat12, np.float64)
     _load().oracle_f_single_spread(_pd(m), th_i, th_o, cphi, sg2, _pd(out))
@@ -153,7 +177,10 @@ def f_single_spread(mat12, th_i, th_o, cphi, sg2):
 def shadow_path(rows, mats, x, wi, t_light, self_mat, nq: int = 384):
     """(T [3], sg2): the dual-scattering transmittance and spread variance of
     the light path from x along wi up to t_light, over primitive rows (15
-    doubles each) with material rows `mats`, skipping material `self_mat`."""
+    doubles each) with material rows `mats`, skipping material `self_mat`.
+
+    Pinned by the hand-worked occluder cases of tests/test_oracle_shadows.py.
+    """
     r = np.ascontiguousarray(rows, np.float64).reshape(-1, 15)
     mt = np.ascontiguousarray(mats, np.float64).reshape(-1, 12)
     qx, qw = gauss_legendre(nq)
@@ -167,6 +194,13 @@ def shadow_path(rows, mats, x, wi, t_light, self_mat, nq: int = 384):
 
 
 def f_ours(mat12, th_i, th_o, cphi, rho, n_view, flags=0, nq: int = 384):
+    """Aggregated BCSDF of a thick hair (see trace.c).
+
+    Pinned by test_aggregated_reciprocity, test_aggregated_reduces_to_single_at_n1_front,
+    test_back_lobe_uniform_over_back_half, test_shadowing_masking_bounds_and_ablation_order,
+    test_attenuation_with_hair_count and the thick-hair / strand convergence of
+    tests/test_oracle_convergence.py.
+    """
     m = np.ascontiguousarray(mat12, np.float64)
     x, w = gauss_legendre(nq)
     out = np.zeros(3)
@@ -176,14 +210,21 @@ def f_ours(mat12, th_i, th_o, cphi, rho, n_view, flags=0, nq: int = 384):
 
 
 def back_atten(aF: float, aB: float, n: float):
-    """(A_1, A_3, A_1+) of one channel (see trace.c)."""
+    """(A_1, A_3, A_1+) of one channel (see trace.c).
+
+    Pinned by test_back_lobe_attenuations_equal_their_series.
+    """
     out = np.zeros(3)
     _load().oracle_back_atten(aF, aB, n, _pd(out))
     return out
 
 
 def intersect(row15, o, d):
-    """(hit, t, chord) of a ray against one primitive row."""
+    """(hit, t, chord) of a ray against one primitive row.
+
+    Pinned by test_circular_cylinder_perpendicular_hit, test_elliptic_cylinder_axis_aligned_hit,
+    test_eccentricity_zero_equals_circle and test_intersection_misses_and_open_ends.
+    """
     r = np.ascontiguousarray(row15, np.float64)
     o = np.ascontiguousarray(o, np.float64)
     d = np.ascontiguousarray(d, np.float64)
@@ -194,6 +235,7 @@ def intersect(row15, o, d):
 
 
 def camera_ray(cam_rec, seed: int, sid: int, spp: int):
+    """Pinned by test_camera_jitter_uses_published_stream and test_perspective_edge_ray_half_fov."""
     c = np.ascontiguousarray(cam_rec, np.float64)
     o = np.zeros(3)
     d = np.zeros(3)
@@ -206,7 +248,11 @@ def camera_ray(cam_rec, seed: int, sid: int, spp: int):
 
 def morton30(q: np.ndarray) -> np.ndarray:
     """30-bit Morton code of 10-bit integer coordinates: bit i of x, y, z goes
-    to bits 3i+2, 3i+1, 3i."""
+    to bits 3i+2, 3i+1, 3i.
+
+    Pinned by test_morton_hand_worked_cube_corners, test_morton_mid_point_and_ties and
+    test_morton_brute_force_random.
+    """
     q = np.asarray(q, np.uint64)
     code = np.zeros(q.shape[0], np.uint64)
     for i in range(10):
@@ -219,7 +265,10 @@ def morton30(q: np.ndarray) -> np.ndarray:
 def quantize_roots(roots: np.ndarray) -> np.ndarray:
     """q = min(1023, floor((p - lo) * (1024 / e))) per axis with lo the root
     AABB's low corner and e its largest extent (the bounding cube, so the grid
-    is isotropic), each operation rounded to float32 in this order."""
+    is isotropic), each operation rounded to float32 in this order.
+
+    Pinned by test_morton_quantises_in_bounding_cube and test_morton_mid_point_and_ties.
+    """
     p = np.asarray(roots, np.float32)
     lo = p.min(0)
     hi = p.max(0)
@@ -234,7 +283,10 @@ def n_eth_levels_for(n_strands: int, n_clusters: int, max_levels: int = 0) -> in
     """Number of thick-hair levels: 1 + max k with 4^k <= floor(N/C) / 2
     (READING: each level splits every cluster into 4x as many thick hairs,
     Section 5.1 "approximately four times"; a level must keep >= 2 strands
-    per thick hair).  ``max_levels`` > 0 caps it."""
+    per thick hair).  ``max_levels`` > 0 caps it.
+
+    Pinned by test_level_count_rule.
+    """
     per = n_strands // n_clusters
     if per < 2:
         return 0
@@ -273,7 +325,10 @@ def build_hierarchy(roots: np.ndarray, n_clusters: int, max_levels: int = 0) -> 
     answer).  Strands are sorted by (30-bit Morton code of the quantised root,
     strand id); the strand of rank r joins cluster floor(r C / N); at level k a
     cluster of m members splits into 4^k thick hairs, rank-in-cluster i going
-    to floor(i 4^k / m)."""
+    to floor(i 4^k / m).
+
+    Pinned by test_morton_hand_worked_cube_corners and test_hierarchy_partition_and_nesting.
+    """
     N = roots.shape[0]
     C = n_clusters
     code = morton30(quantize_roots(roots))
@@ -329,7 +384,10 @@ class ETHs:
 
 def strand_tangents(P: np.ndarray) -> np.ndarray:
     """Unit tangent at every vertex: central difference inside, one-sided at
-    the ends."""
+    the ends.
+
+    Pinned by test_strand_tangents_on_a_circle.
+    """
     d = np.empty_like(P)
     d[:, 1:-1] = P[:, 2:] - P[:, :-2]
     d[:, 0] = P[:, 1] - P[:, 0]
@@ -342,7 +400,10 @@ def degenerate_axis(q: np.ndarray, t: np.ndarray) -> np.ndarray:
     whose offset runs along the tangent, so the principal axis is undefined):
     e1 points to the member farthest from the centre in the plane normal to t
     (first such member in rank order), or along the Duff basis vector b1 of t
-    when every member projects onto the centre."""
+    when every member projects onto the centre.
+
+    Pinned by test_degenerate_cross_section_axis.
+    """
     qp = q - np.outer(q @ t, t)
     d2 = np.sum(qp * qp, 1)
     i = int(np.argmax(d2))
@@ -363,6 +424,10 @@ def fit_cross_section(pts: np.ndarray, tans: np.ndarray, radii: np.ndarray):
     max(|u| + r), b = max(|v| + r) over members, u, v their coordinates along
     e1, e2; both scaled by s = max sqrt((u/a)^2 + (v/b)^2) when s > 1 so the
     ellipse contains every member centre.
+
+    Pinned by test_cross_section_closed_form,
+    test_cross_section_contains_members_and_rotation_invariance and
+    test_degenerate_cross_section_axis.
     """
     c = pts.mean(0)
     t = tans.sum(0)
@@ -395,7 +460,12 @@ def fit_eths(verts: np.ndarray, mat: np.ndarray, hier: Hierarchy, chunk: int = 5
     """Fit every thick hair of every level (FP64).  The thick hairs are
     processed in batches with members padded and masked; per cross-section the
     arithmetic is that of ``fit_cross_section`` (checked against it by the
-    tests)."""
+    tests).
+
+    Pinned by test_batched_fit_matches_single_fit (cross-sections) and, for the segment frame,
+    test_thick_hair_segment_is_the_bundle_cylinder,
+    test_tapered_thick_hair_takes_the_wider_section and test_bent_thick_hair_segment_frame.
+    """
     P = verts[..., :3].astype(np.float64)
     R = verts[..., 3].astype(np.float64)
     T = strand_tangents(P)
@@ -480,7 +550,11 @@ def _f32(x):
 def project_px(p: np.ndarray, cam: np.ndarray):
     """Pixel-plane coordinates of points p [.., 3] (float32, fixed order:
     relative position, then ((x*r0 + y*r1) + z*r2) per camera axis, then the
-    perspective division and the pixel scale).  Returns (X, Y, depth)."""
+    perspective division and the pixel scale).  Returns (X, Y, depth).
+
+    Pinned by test_width_orthographic_facing_camera and
+    test_width_perspective_depth_scaling_and_near_plane.
+    """
     p = _f32(p)
     cam = _f32(cam)
     rx = p[..., 0] - cam[4]
@@ -509,7 +583,11 @@ def cross_section_widths(eth: ETHs, cam: np.ndarray) -> np.ndarray:
     calculation"): the four corner points c +- a e1, c +- b e2 (READING: the
     ends of the fitted axes stand for the corner control points) are projected
     and l_w is the largest pairwise xy distance in pixels.  float32 with a
-    fixed operation order; a corner at or behind the near plane gives +inf."""
+    fixed operation order; a corner at or behind the near plane gives +inf.
+
+    Pinned by test_width_orthographic_facing_camera and
+    test_width_perspective_depth_scaling_and_near_plane.
+    """
     c = _f32(eth.center)
     e1 = _f32(eth.e1)
     e2 = _f32(eth.e2)
@@ -537,7 +615,10 @@ def cross_section_widths(eth: ETHs, cam: np.ndarray) -> np.ndarray:
 
 def cluster_level_widths(hier: Hierarchy, eth: ETHs, cam: np.ndarray) -> np.ndarray:
     """w[c, L]: maximum cross-section width over the level-L thick hairs of
-    cluster c (the per-cluster maximum the paper records with atomicMax)."""
+    cluster c (the per-cluster maximum the paper records with atomicMax).
+
+    Pinned by test_cluster_level_widths_hand_worked.
+    """
     w = cross_section_widths(eth, cam).max(1)
     out = np.zeros((hier.n_clusters, max(1, hier.n_levels)), np.float32)
     for e in range(hier.n_eths):
@@ -549,7 +630,10 @@ def cluster_level_widths(hier: Hierarchy, eth: ETHs, cam: np.ndarray) -> np.ndar
 
 def select_lod_init(wcl: np.ndarray, eps: float, n_levels: int) -> np.ndarray:
     """Section 5.1 step 5: coarsest to finest, the first level whose maximum
-    width is below eps; the strands (level n_levels) if none is."""
+    width is below eps; the strands (level n_levels) if none is.
+
+    Pinned by test_init_rule_hand_worked.
+    """
     eps = np.float32(eps)
     C = wcl.shape[0]
     lod = np.full(C, n_levels, np.uint8)
@@ -565,7 +649,10 @@ def select_lod_deferred(wcl: np.ndarray, prev: np.ndarray, eps: float, n_levels:
     """Eq. (14): L+1 if w_cur > eps; L if w_cur <= eps < w_cur-; L-1 if
     w_cur- <= eps; cases tested in that order.  READING: w_cur- is +inf at
     L = 0; at the strand level only the coarsening case applies; L stays in
-    [0, n_levels]."""
+    [0, n_levels].
+
+    Pinned by test_deferred_rule_hand_worked.
+    """
     eps = np.float32(eps)
     out = np.array(prev, np.uint8).copy()
     for c in range(wcl.shape[0]):
@@ -582,7 +669,10 @@ def select_lod_deferred(wcl: np.ndarray, prev: np.ndarray, eps: float, n_levels:
 
 def apply_budget(lod: np.ndarray, bias: int) -> np.ndarray:
     """READING (serving LoD budget): a bias b >= 0 coarsens every cluster by b
-    levels, L <- max(0, L - b)."""
+    levels, L <- max(0, L - b).
+
+    Pinned by test_budget_bias.
+    """
     return np.maximum(lod.astype(np.int64) - int(bias), 0).astype(np.uint8)
 
 
@@ -591,7 +681,10 @@ def apply_budget(lod: np.ndarray, bias: int) -> np.ndarray:
 
 def duff_basis(n: np.ndarray):
     """Orthonormal basis (b1, b2) around unit vectors n (Duff et al. 2017,
-    "Building an orthonormal basis, revisited")."""
+    "Building an orthonormal basis, revisited").
+
+    Pinned by test_duff_basis_orthonormal_and_right_handed and test_duff_basis_values_at_the_poles.
+    """
     sign = np.copysign(1.0, n[..., 2])
     a = -1.0 / (sign + n[..., 2])
     b = n[..., 0] * n[..., 1] * a
@@ -607,7 +700,11 @@ def strand_prim_rows(verts: np.ndarray, shape: np.ndarray, strands: np.ndarray):
     strand): an ellipse of eccentricity e with the area of the circle of the
     area-equivalent radius r, a = r (1 - e^2)^(-1/4), b = r (1 - e^2)^(1/4),
     whose major axis e1 = cos(psi) b1 + sin(psi) b2 in the Duff basis of the
-    segment direction.  Global id = s * S + k; material index = s."""
+    segment direction.  Global id = s * S + k; material index = s.
+
+    Pinned by test_strand_ellipse_area_and_eccentricity, test_strand_major_axis_orientation,
+    test_strand_semi_axes_as_hit_distances and test_strand_record_fields_and_ids.
+    """
     S = verts.shape[1] - 1
     strands = np.asarray(strands, np.int64)
     P = verts[strands, :, :3].astype(np.float64)
@@ -640,7 +737,11 @@ def strand_prim_rows(verts: np.ndarray, shape: np.ndarray, strands: np.ndarray):
 
 def eth_prim_rows(eth: ETHs, eths: np.ndarray, n_strands: int, S: int):
     """Primitive rows of every segment of the listed thick hairs.  Global id =
-    N S + e S + k; material index = N + e."""
+    N S + e S + k; material index = N + e.
+
+    Pinned by test_thick_hair_segment_is_the_bundle_cylinder,
+    test_tapered_thick_hair_takes_the_wider_section and test_bent_thick_hair_segment_frame.
+    """
     eths = np.asarray(eths, np.int64)
     n = eths.shape[0]
     rows = np.zeros((n, S, PRIM_STRIDE))
@@ -659,7 +760,10 @@ def eth_prim_rows(eth: ETHs, eths: np.ndarray, n_strands: int, S: int):
 
 def active_set(n_strands: int, S: int, hier: Optional[Hierarchy], lod: Optional[np.ndarray]):
     """(strand ids, thick-hair ids) rendered at this LoD: every strand of a
-    cluster at the strand level, the level-L thick hairs of a cluster at L."""
+    cluster at the strand level, the level-L thick hairs of a cluster at L.
+
+    Pinned by test_active_set_hand_counted.
+    """
     if hier is None or lod is None or hier.n_levels == 0:
         return np.arange(n_strands, dtype=np.int64), np.zeros(0, np.int64)
     lod = np.minimum(np.asarray(lod, np.int64), hier.n_levels)
@@ -683,7 +787,11 @@ class Prepared:
 
 def prepare(scene, n_clusters: int, lod_setting: str = "select", cam=None, eps_w: float = 2.0,
             lod: Optional[np.ndarray] = None, max_levels: int = 0, budget: int = 0) -> Prepared:
-    """Hierarchy, fit, LoD and active primitive rows of a scene."""
+    """Hierarchy, fit, LoD and active primitive rows of a scene.
+
+    Pinned by test_active_set_hand_counted (the rows and ids it lists) and, end to end, by the
+    render pins.
+    """
     N, S = scene.n_strands, scene.n_segments
     hier = eth = None
     if n_clusters > 0:
@@ -719,7 +827,14 @@ def render_samples(prep: Prepared, cam: np.ndarray, lights: np.ndarray, samples:
     """Radiance (f64 [m, 3]) and the global ids of the composited hits
     (int64 [m, K]: the K nearest, nearest first, cut after the first opaque
     strand hit, -1 padded) of the listed samples, by brute force over every
-    active primitive."""
+    active primitive.
+
+    Pinned by test_kbuffer_keeps_the_nearest_in_order_and_breaks_ties_by_id,
+    test_composite_front_to_back_with_closed_form_opacity,
+    test_light_sum_point_and_directional_lights,
+    test_thick_hair_shading_uses_the_hair_number_of_its_chord and
+    tests/test_oracle_convergence.py.
+    """
     samples = np.ascontiguousarray(samples, np.int64)
     m = samples.shape[0]
     rad = np.zeros((m, 3))

@@ -20,7 +20,7 @@
 #include <string.h>
 
 #define PI 3.14159265358979323846
-#define MAXK 16
+#define MAXK 64
 
 /* flag bits (same values as the library's render flags) */
 #define FLAG_NO_S 1u          /* drop the shadowing-masking term S (ablation, Fig. "S-term") */
@@ -58,7 +58,9 @@ typedef struct {
   const double* w;
 } quad;
 
-/* Gaussian with standard deviation beta (Section 3.2, definition of G). */
+/* Gaussian with standard deviation beta (Section 3.2, definition of G).
+ * Pinned by test_gaussian_definition.
+ */
 double oracle_gauss(double beta, double x) {
   return exp(-x * x / (2.0 * beta * beta)) / (sqrt(2.0 * PI) * beta);
 }
@@ -66,7 +68,10 @@ double oracle_gauss(double beta, double x) {
 /* IM(theta; beta) = integral over theta_o in [-pi/2, pi/2] of
  * G(beta, (theta + theta_o) / 2) cos^2(theta_o): the longitudinal factor of
  * the directional albedo of a lobe with M = G(beta, theta_h) under the
- * cos^2 measure of the rendering equation (Section 3).                      */
+ * cos^2 measure of the rendering equation (Section 3).
+ * Pinned by test_longitudinal_integral_closed_form,
+ *   test_longitudinal_integral_quadrature_converged.
+ */
 static double im_quad(const quad* q, double theta, double beta) {
   double s = 0.0;
   for (int i = 0; i < q->n; ++i) {
@@ -87,7 +92,9 @@ double oracle_im(int nq, const double* qx, const double* qw, double theta, doubl
  * phi - pi); M_D = 1/pi, N_D = 1/2pi (the n = 1 case of Eq. 6).
  * phi is taken in [0, pi] from cos(phi) (the model is even in phi).
  * sg2 is the forward spread variance gathered along the light's path (zero
- * without shadow rays); READING: it adds to every lobe's variance.          */
+ * without shadow rays); READING: it adds to every lobe's variance.
+ * Pinned by test_f_single_hand_values, test_spread_is_a_wider_lobe.
+ */
 static void f_single(const material* m, double th_i, double th_o, double cphi, double sg2,
                      double out[3]) {
   double th_h = 0.5 * (th_i + th_o);
@@ -107,7 +114,10 @@ static void f_single(const material* m, double th_i, double th_o, double cphi, d
  * under the cos^2 measure; a_B likewise into the back half (cos phi > 0).
  * The separable lobes make this A_p * IM_p * (azimuthal mass in the half).
  * sigma_f^2 is the mean of beta_R^2 and beta_TT^2 weighted by the RGB-mean
- * forward albedo of the R and TT lobes.                                      */
+ * forward albedo of the R and TT lobes.
+ * Pinned by test_separable_albedo_equals_2d_quadrature,
+ *   test_albedo_white_furnace_c1_material.
+ */
 static void albedo_split(const material* m, const quad* q, double theta_d, double aF[3],
                          double aB[3], double* sig2) {
   double ta = 0.5 * fabs(theta_d);
@@ -144,7 +154,9 @@ void oracle_albedo(const double* mat12, int nq, const double* qx, const double* 
  * A_3 = a_B^3 a_F^2 / (1 - a_F^2)^3 those with three backward events.
  * Eq. (8): A_1+ = d_1+ a_B sum_{i=1..n} a_F^(2i-1) with d_1+ = 0.6, in the
  * closed form a_F (1 - a_F^(2n)) / (1 - a_F^2) of the geometric sum.
- * a_F is clamped to 1 - 1e-6 so the sums stay finite.                       */
+ * a_F is clamped to 1 - 1e-6 so the sums stay finite.
+ * Pinned by test_back_lobe_attenuations_equal_their_series.
+ */
 static void back_atten(double aF, double aB, double n, double* A1, double* A3, double* A1p) {
   double f = aF < 1.0 - 1e-6 ? aF : 1.0 - 1e-6;
   double f2 = f * f, g = 1.0 - f2;
@@ -172,7 +184,11 @@ void oracle_back_atten(double aF, double aB, double n, double* out3) {
  * beta_R^2 + (n + 1) s^2 (A_1+).
  * Eq. (10)-(13): S = P_s a_F + P_n with P_s = (1 - rho)(1 - cos phi),
  * P_m = c_m (1 - rho), c_m = 0.2, P_n = 1 - P_m - P_s, applied for
- * phi in (-pi/2, pi/2) only (READING: P_n floored at 0).                     */
+ * phi in (-pi/2, pi/2) only (READING: P_n floored at 0).
+ * Pinned by test_aggregated_reciprocity, test_aggregated_reduces_to_single_at_n1_front,
+ *   test_back_lobe_uniform_over_back_half,
+ *   test_shadowing_masking_bounds_and_ablation_order, tests/test_oracle_convergence.py.
+ */
 static void f_ours(const material* m, const quad* q, double th_i, double th_o, double cphi,
                    double rho, double n_view, unsigned flags, double sg2, double out[3]) {
   double th_h = 0.5 * (th_i + th_o);
@@ -251,7 +267,9 @@ void oracle_f_ours(const double* mat12, int nq, const double* qx, const double* 
  * quadrature over theta_o in [-pi/2, pi/2] and phi in [0, pi] (doubled: the
  * model is even in phi), under the cos^2(theta_o) measure, split at
  * phi = pi/2 into back (phi < pi/2) and front parts.  Used only to check the
- * separable albedo above against the definition.                             */
+ * separable albedo above against the definition.
+ * Pinned by test_albedo_2d_diffuse_closed_form.
+ */
 void oracle_albedo_2d(const double* mat12, int nq, const double* qx, const double* qw,
                       double theta_i, double* front3, double* back3) {
   material m;
@@ -291,7 +309,10 @@ typedef struct {
 /* Ray against an open elliptic cylinder of finite length (READING: no caps,
  * no joint fill).  Returns the nearest root whose axial coordinate lies in
  * [0, L] and whose distance exceeds tmin, and the chord length of the ray
- * inside the finite cylinder (used for the hair count n, Section 4).         */
+ * inside the finite cylinder (used for the hair count n, Section 4).
+ * Pinned by test_circular_cylinder_perpendicular_hit,
+ *   test_elliptic_cylinder_axis_aligned_hit, test_intersection_misses_and_open_ends.
+ */
 static int intersect(const prim* p, v3 o, v3 d, double tmin, double* t_hit, double* chord) {
   v3 r = sub(o, p->c0);
   double u0 = dot(r, p->e1) / p->a, v0 = dot(r, p->e2) / p->b, w0 = dot(r, p->t);
@@ -344,7 +365,9 @@ int oracle_intersect(const double* row, const double* o3, const double* d3, doub
 
 /* Ray interval inside the finite cylinder volume of one primitive: the part
  * of the infinite elliptic cylinder's interval [t-, t+] whose axial
- * coordinate lies in [0, L].  Returns 0 when the ray misses it.              */
+ * coordinate lies in [0, L].  Returns 0 when the ray misses it.
+ * Pinned by test_thick_hair_occluder_counts_its_hair_number_over_the_chord.
+ */
 static int span(const prim* p, v3 o, v3 d, double* lo, double* hi) {
   v3 r = sub(o, p->c0);
   double u0 = dot(r, p->e1) / p->a, v0 = dot(r, p->e2) / p->b, w0 = dot(r, p->t);
@@ -383,7 +406,9 @@ static int span(const prim* p, v3 o, v3 d, double* lo, double* hi) {
  *  - each crossed hair attenuates by its forward albedo a_F at incidence
  *    |asin(wi . t)| (the mirror configuration of the a_F reading) and adds
  *    its forward spread variance sigma_f^2, n times;
- *  - T = d_F * prod a_F^n when at least one hair is crossed, else 1.        */
+ *  - T = d_F * prod a_F^n when at least one hair is crossed, else 1.
+ * Pinned by tests/test_oracle_shadows.py.
+ */
 static void shadow_path(const prim* P, int64_t n_prims, const material* M, const quad* q, v3 x,
                         v3 wi, double t_light, int self_mat, double T[3], double* sg2) {
   int crossed = 0;
@@ -415,6 +440,10 @@ static void shadow_path(const prim* P, int64_t n_prims, const material* M, const
 
 /* ------------------------------------------------------------ camera */
 
+/*
+ * Pinned by test_splitmix64_published_outputs (same stream),
+ *   test_camera_jitter_uses_published_stream.
+ */
 static uint64_t splitmix_out(uint64_t seed, uint64_t i) {
   /* output i (0-based) of SplitMix64 started at seed (Steele et al. 2014) */
   uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
@@ -431,7 +460,9 @@ typedef struct {
 
 /* Sample sid = pixel * spp + s, pixel = y * W + x.  Its position inside the
  * pixel is a pair of 24-bit uniforms drawn from SplitMix64 outputs 2 sid and
- * 2 sid + 1 of the frame seed (READING: stratification left to the spp count). */
+ * 2 sid + 1 of the frame seed (READING: stratification left to the spp count).
+ * Pinned by test_camera_jitter_uses_published_stream, test_perspective_edge_ray_half_fov.
+ */
 static void camera_ray(const camera* c, uint64_t seed, int64_t sid, int spp, v3* o, v3* d) {
   int64_t pixel = sid / spp;
   int64_t x = pixel % c->W, y = pixel / c->W;
@@ -495,7 +526,10 @@ typedef struct {
  * (READING: primary hits only); with it, T and the spread variance come
  * from the light path (shadow_path).  The angles are measured
  * against the segment axis t: sin(theta) = omega . t, cos(phi) from the
- * projections onto the normal plane (Section 3).                            */
+ * projections onto the normal plane (Section 3).
+ * Pinned by test_light_sum_point_and_directional_lights,
+ *   test_thick_hair_shading_uses_the_hair_number_of_its_chord.
+ */
 static void shade(const job* jb, const prim* p, v3 x, v3 d, double chord, double* rgb,
                   double* alpha) {
   const material* m = &jb->mats[p->mat];
@@ -557,6 +591,10 @@ static void shade(const job* jb, const prim* p, v3 x, v3 d, double chord, double
   *alpha = p->kind == 1 ? 1.0 - exp(-n_cross) : 1.0;
 }
 
+/*
+ * Pinned by test_kbuffer_keeps_the_nearest_in_order_and_breaks_ties_by_id,
+ *   test_composite_front_to_back_with_closed_form_opacity.
+ */
 static void* worker(void* arg) {
   job* jb = (job*)arg;
   double kt[MAXK], kc[MAXK];

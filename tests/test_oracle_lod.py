@@ -78,3 +78,26 @@ def test_coarser_levels_are_wider_on_average():
     wcl = oracle.cluster_level_widths(h, eth, w.camera.pack())
     assert h.n_levels == 3
     assert np.all(np.diff(wcl.mean(0)) < 0)
+
+
+def test_cluster_level_widths_hand_worked():
+    # Two clusters with two levels; every thick hair has one cross-section
+    # facing an orthographic camera at 100 px per unit, so its width is
+    # 2 max(a, b) * 100 px.  w[c, L] is the largest width among cluster c's
+    # level-L thick hairs.
+    cam = scenegen.Camera(0, 64, 64, np.array([0, 0, 5], np.float32),
+                          np.array([1, 0, 0], np.float32), np.array([0, 1, 0], np.float32),
+                          np.array([0, 0, -1], np.float32), 100.0).pack()
+    a = np.array([0.03, 0.01, 0.005, 0.02, 0.004, 0.007])
+    cl = np.array([0, 1, 0, 0, 1, 1])
+    lv = np.array([0, 0, 1, 1, 1, 1])
+    E = len(a)
+    z = np.zeros((E, 1, 3))
+    e1 = z + [1.0, 0, 0]
+    e2 = z + [0, 1.0, 0]
+    eth = oracle.ETHs(center=z.copy(), tangent=z + [0, 0, 1.0], e1=e1, e2=e2, a=a[:, None],
+                      b=0.5 * a[:, None], seg_e1=None, seg_a=None, seg_b=None, ntot=None,
+                      radius=None, mat=None)
+    h = oracle.Hierarchy(0, 2, 2, None, None, None, None, None, None, np.ones(E, np.int64), cl, lv)
+    w = oracle.cluster_level_widths(h, eth, cam)
+    assert np.allclose(w, [[6.0, 4.0], [2.0, 1.4]], rtol=1e-6)

@@ -518,3 +518,16 @@ def test_composite_front_to_back_with_closed_form_opacity():
     occl, h2 = render(np.stack([eth, front]), [5, 9])
     f_only, _ = render(front[None], [9])
     assert h2.tolist() == [9, -1, -1, -1] and np.allclose(occl, f_only, rtol=1e-12)
+
+
+def test_albedo_2d_diffuse_closed_form():
+    # A diffuse-only fibre (A_R = A_TT = 0): f = A_D / (2 pi^2) everywhere, so
+    # each half's albedo is A_D / (2 pi^2) * int cos^2 = pi / 2 * (azimuth pi)
+    # = A_D / 4, at every incidence.
+    m = np.zeros(12)
+    m[6:9] = (0.2, 0.5, 0.9)
+    m[9:12] = (0.1, 0.15, 0.3)
+    for th in (0.0, 0.4, 1.2):
+        fr, bk = oracle.albedo_2d(m, th, nq=64)
+        assert np.allclose(fr, m[6:9] / 4, rtol=1e-12)
+        assert np.allclose(bk, m[6:9] / 4, rtol=1e-12)
