@@ -33,6 +33,7 @@ _lib = None
 FLAG_NO_S = 1
 FLAG_SINGLE_ON_ETH = 2
 FLAG_SHADOWS = 4
+FLAG_TRT = 8
 PRIM_STRIDE = 15
 
 
@@ -69,12 +70,13 @@ def _load():
         lib.oracle_gauss.restype = D
         lib.oracle_im.argtypes = [ctypes.c_int, PD, PD, D, D]
         lib.oracle_im.restype = D
-        lib.oracle_albedo.argtypes = [PD, ctypes.c_int, PD, PD, D, PD, PD, PD]
-        lib.oracle_albedo_2d.argtypes = [PD, ctypes.c_int, PD, PD, D, PD, PD]
-        lib.oracle_f_single.argtypes = [PD, D, D, D, PD]
+        lib.oracle_albedo.argtypes = [PD, ctypes.c_int, PD, PD, D, ctypes.c_uint, PD, PD, PD]
+        lib.oracle_albedo_2d.argtypes = [PD, ctypes.c_int, PD, PD, D, ctypes.c_uint, PD, PD]
+        lib.oracle_f_single.argtypes = [PD, D, D, D, ctypes.c_uint, PD]
         lib.oracle_f_single_spread.argtypes = [PD, D, D, D, D, PD]
         lib.oracle_shadow_path.argtypes = [PD, ctypes.c_int64, PD, ctypes.c_int64, ctypes.c_int,
-                                           PD, PD, PD, PD, D, ctypes.c_int, PD, PD]
+                                           PD, PD, PD, PD, D, ctypes.c_int, ctypes.c_uint,
+                                           PD, PD]
         lib.oracle_f_ours.argtypes = [PD, ctypes.c_int, PD, PD, D, D, D, D, D, ctypes.c_uint, PD]
         lib.oracle_intersect.argtypes = [PD, PD, PD, PD, PD]
         lib.oracle_intersect.restype = ctypes.c_int
@@ -126,7 +128,7 @@ def im(theta: float, beta: float, nq: int = 384) -> float:
     return _load().oracle_im(nq, _pd(x), _pd(w), theta, beta)
 
 
-def albedo(mat12, theta_d: float, nq: int = 384):
+def albedo(mat12, theta_d: float, nq: int = 384, flags: int = 0):
     """(a_F rgb, a_B rgb, sigma_f^2) of a single fibre at theta_d.
 
     Pinned by test_separable_albedo_equals_2d_quadrature, test_albedo_white_furnace_c1_material
@@ -137,11 +139,11 @@ def albedo(mat12, theta_d: float, nq: int = 384):
     aF = np.zeros(3)
     aB = np.zeros(3)
     s2 = np.zeros(1)
-    _load().oracle_albedo(_pd(m), nq, _pd(x), _pd(w), theta_d, _pd(aF), _pd(aB), _pd(s2))
+    _load().oracle_albedo(_pd(m), nq, _pd(x), _pd(w), theta_d, flags, _pd(aF), _pd(aB), _pd(s2))
     return aF, aB, float(s2[0])
 
 
-def albedo_2d(mat12, theta_i: float, nq: int = 256):
+def albedo_2d(mat12, theta_i: float, nq: int = 256, flags: int = 0):
     """(front rgb, back rgb) directional albedo of f_single by 2-D quadrature.
 
     Pinned by test_albedo_2d_diffuse_closed_form (A_D / 4 per half for a diffuse fibre).
@@ -150,15 +152,15 @@ def albedo_2d(mat12, theta_i: float, nq: int = 256):
     x, w = gauss_legendre(nq)
     f = np.zeros(3)
     b = np.zeros(3)
-    _load().oracle_albedo_2d(_pd(m), nq, _pd(x), _pd(w), theta_i, _pd(f), _pd(b))
+    _load().oracle_albedo_2d(_pd(m), nq, _pd(x), _pd(w), theta_i, flags, _pd(f), _pd(b))
     return f, b
 
 
-def f_single(mat12, th_i, th_o, cphi):
+def f_single(mat12, th_i, th_o, cphi, flags: int = 0):
     """Pinned by test_f_single_hand_values."""
     m = np.ascontiguousarray(mat12, np.float64)
     out = np.zeros(3)
-    _load().oracle_f_single(_pd(m), th_i, th_o, cphi, _pd(out))
+    _load().oracle_f_single(_pd(m), th_i, th_o, cphi, flags, _pd(out))
     return out
 
 
@@ -174,7 +176,7 @@ def f_single_spread(mat12, th_i, th_o, cphi, sg2):
     return out
 
 
-def shadow_path(rows, mats, x, wi, t_light, self_mat, nq: int = 384):
+def shadow_path(rows, mats, x, wi, t_light, self_mat, nq: int = 384, flags: int = 0):
     """(T [3], sg2): the dual-scattering transmittance and spread variance of
     the light path from x along wi up to t_light, over primitive rows (15
     doubles each) with material rows `mats`, skipping material `self_mat`.
@@ -189,7 +191,8 @@ def shadow_path(rows, mats, x, wi, t_light, self_mat, nq: int = 384):
     T = np.zeros(3)
     sg2 = np.zeros(1)
     _load().oracle_shadow_path(_pd(r), r.shape[0], _pd(mt), mt.shape[0], nq, _pd(qx), _pd(qw),
-                               _pd(xx), _pd(ww), float(t_light), int(self_mat), _pd(T), _pd(sg2))
+                               _pd(xx), _pd(ww), float(t_light), int(self_mat), flags, _pd(T),
+                               _pd(sg2))
     return T, float(sg2[0])
 
 

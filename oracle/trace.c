@@ -26,6 +26,14 @@
 #define FLAG_NO_S 1u          /* drop the shadowing-masking term S (ablation, Fig. "S-term") */
 #define FLAG_SINGLE_ON_ETH 2u /* shade thick hairs with f_single (ablation, Fig. "S-term") */
 #define FLAG_SHADOWS 4u       /* dual-scattering transmittance along shadow rays (Section 3.2, 6) */
+/* Marschner R/TT/TRT single fibre (Section 7, "Extending to Marschner model
+ * with TRT term"): the third lobe is TRT instead of D.  READING (the paper
+ * prints no formula for it): A_TRT takes the D lobe's attenuation slots,
+ * M_TRT = G(beta_TRT, theta_h) with beta_TRT = 2 beta_R (Marschner et al.
+ * 2003's width relation) and no longitudinal shift (none of the paper's
+ * lobes has one), and N_TRT = 1 / 2 pi (the paper's azimuthal simplification
+ * of the R lobe, which leaves the fibre on the same side as TRT).            */
+#define FLAG_TRT 8u
 /* READING: the forward scattering density d_F of dual scattering (Section
  * 3.2 names it, without a value); Zinke et al. 2008 use 0.7.                */
 #define D_F 0.7
@@ -48,8 +56,9 @@ static double clampd(double x, double lo, double hi) { return x < lo ? lo : (x >
 /* Single-fibre lobe parameters: A_p per RGB channel for p in {R, TT, D}, the
  * longitudinal widths beta_R, beta_TT and the TT azimuthal width gamma_TT.   */
 typedef struct {
-  double A[3][3]; /* [lobe R,TT,D][rgb] */
+  double A[3][3]; /* [lobe R,TT,D][rgb]; [R,TT,TRT] with FLAG_TRT */
   double bR, bTT, gTT;
+  int trt;        /* third lobe is TRT (FLAG_TRT) */
 } material;
 
 typedef struct {
@@ -93,7 +102,9 @@ double oracle_im(int nq, const double* qx, const double* qw, double theta, doubl
  * phi is taken in [0, pi] from cos(phi) (the model is even in phi).
  * sg2 is the forward spread variance gathered along the light's path (zero
  * without shadow rays); READING: it adds to every lobe's variance.
- * Pinned by test_f_single_hand_values, test_spread_is_a_wider_lobe.
+ * With FLAG_TRT the third lobe is A_TRT G(2 beta_R, theta_h) / 2 pi.
+ * Pinned by test_f_single_hand_values, test_spread_is_a_wider_lobe,
+ *   test_trt_single_fibre_hand_values.
  */
 static void f_single(const material* m, double th_i, double th_o, double cphi, double sg2,
                      double out[3]) {
@@ -102,7 +113,8 @@ static void f_single(const material* m, double th_i, double th_o, double cphi, d
   double mR = oracle_gauss(sqrt(m->bR * m->bR + sg2), th_h) / (2.0 * PI);
   double mTT = oracle_gauss(sqrt(m->bTT * m->bTT + sg2), th_h) *
                oracle_gauss(sqrt(m->gTT * m->gTT + sg2), phi - PI);
-  double mD = 1.0 / (PI * 2.0 * PI);
+  double mD = m->trt ? oracle_gauss(sqrt(4.0 * m->bR * m->bR + sg2), th_h) / (2.0 * PI)
+                    : 1.0 / (PI * 2.0 * PI);
   for (int c = 0; c < 3; ++c) out[c] = m->A[0][c] * mR + m->A[1][c] * mTT + m->A[2][c] * mD;
 }
 
@@ -114,7 +126,8 @@ static void f_single(const material* m, double th_i, double th_o, double cphi, d
  * under the cos^2 measure; a_B likewise into the back half (cos phi > 0).
  * The separable lobes make this A_p * IM_p * (azimuthal mass in the half).
  * sigma_f^2 is the mean of beta_R^2 and beta_TT^2 weighted by the RGB-mean
- * forward albedo of the R and TT lobes.
+ * forward albedo of the R and TT lobes (and of (2 beta_R)^2, weighted by the
+ * TRT lobe's, with FLAG_TRT).
  * Pinned by test_separable_albedo_equals_2d_quadrature,
  *   test_albedo_white_furnace_c1_material.
  */
@@ -123,27 +136,31 @@ static void albedo_split(const material* m, const quad* q, double theta_d, doubl
   double ta = 0.5 * fabs(theta_d);
   double imR = im_quad(q, ta, m->bR);
   double imT = im_quad(q, ta, m->bTT);
+  double imTRT = m->trt ? im_quad(q, ta, 2.0 * m->bR) : 0.0;
   double nF_TT = erf(PI / (2.0 * sqrt(2.0) * m->gTT));
   double nB_TT = erf(PI / (sqrt(2.0) * m->gTT)) - nF_TT;
-  double wR = 0.0, wT = 0.0;
+  double wR = 0.0, wT = 0.0, w3 = 0.0;
   for (int c = 0; c < 3; ++c) {
     double r = m->A[0][c] * imR * 0.5;
-    aF[c] = r + m->A[1][c] * imT * nF_TT + m->A[2][c] * 0.25;
-    aB[c] = r + m->A[1][c] * imT * nB_TT + m->A[2][c] * 0.25;
+    /* third lobe: D (azimuth and longitude uniform: a quarter per half) or
+     * TRT (uniform azimuth: half of A_TRT IM(2 beta_R) per half) */
+    double third = m->trt ? m->A[2][c] * imTRT * 0.5 : m->A[2][c] * 0.25;
+    aF[c] = r + m->A[1][c] * imT * nF_TT + third;
+    aB[c] = r + m->A[1][c] * imT * nB_TT + third;
     wR += r / 3.0;
     wT += m->A[1][c] * imT * nF_TT / 3.0;
+    if (m->trt) w3 += third / 3.0;
   }
-  *sig2 = (wR * m->bR * m->bR + wT * m->bTT * m->bTT) / (wR + wT);
+  *sig2 = (wR * m->bR * m->bR + wT * m->bTT * m->bTT + w3 * 4.0 * m->bR * m->bR) /
+          (wR + wT + w3);
 }
 
+static void load_material(const double* row, material* m, unsigned flags);
+
 void oracle_albedo(const double* mat12, int nq, const double* qx, const double* qw,
-                   double theta_d, double* aF3, double* aB3, double* sig2) {
+                   double theta_d, unsigned flags, double* aF3, double* aB3, double* sig2) {
   material m;
-  for (int p = 0; p < 3; ++p)
-    for (int c = 0; c < 3; ++c) m.A[p][c] = mat12[3 * p + c];
-  m.bR = mat12[9];
-  m.bTT = mat12[10];
-  m.gTT = mat12[11];
+  load_material(mat12, &m, flags);
   quad q = {nq, qx, qw};
   albedo_split(&m, &q, theta_d, aF3, aB3, sig2);
 }
@@ -185,6 +202,8 @@ void oracle_back_atten(double aF, double aB, double n, double* out3) {
  * Eq. (10)-(13): S = P_s a_F + P_n with P_s = (1 - rho)(1 - cos phi),
  * P_m = c_m (1 - rho), c_m = 0.2, P_n = 1 - P_m - P_s, applied for
  * phi in (-pi/2, pi/2) only (READING: P_n floored at 0).
+ * With FLAG_TRT the third hat lobe is TRT^: a_F^(n-1) A_TRT
+ * G(sqrt(4 beta_R^2 + (n-1) s^2), theta_h) / 2 pi.
  * Pinned by test_aggregated_reciprocity, test_aggregated_reduces_to_single_at_n1_front,
  *   test_back_lobe_uniform_over_back_half,
  *   test_shadowing_masking_bounds_and_ablation_order, tests/test_oracle_convergence.py.
@@ -203,7 +222,9 @@ static void f_ours(const material* m, const quad* q, double th_i, double th_o, d
   double gT = sqrt(m->gTT * m->gTT + (n - 1.0) * s2 + sg2);
   double mR = oracle_gauss(bR, th_h) / (2.0 * PI);
   double mTT = oracle_gauss(bT, th_h) * oracle_gauss(gT, phi - PI);
-  double mD = 1.0 / (PI * 2.0 * PI);
+  double mD = m->trt ? oracle_gauss(sqrt(4.0 * m->bR * m->bR + (n - 1.0) * s2 + sg2), th_h) /
+                          (2.0 * PI)
+                    : 1.0 / (PI * 2.0 * PI);
   double lob[3];
   for (int c = 0; c < 3; ++c) {
     double att = pow(aF[c], n - 1.0);
@@ -233,24 +254,26 @@ static void f_ours(const material* m, const quad* q, double th_i, double th_o, d
   for (int c = 0; c < 3; ++c) out[c] = lob[c];
 }
 
-static void load_material(const double* row, material* m) {
+static void load_material(const double* row, material* m, unsigned flags) {
   for (int p = 0; p < 3; ++p)
     for (int c = 0; c < 3; ++c) m->A[p][c] = row[3 * p + c];
   m->bR = row[9];
   m->bTT = row[10];
   m->gTT = row[11];
+  m->trt = (flags & FLAG_TRT) != 0;
 }
 
-void oracle_f_single(const double* mat12, double th_i, double th_o, double cphi, double* out3) {
+void oracle_f_single(const double* mat12, double th_i, double th_o, double cphi, unsigned flags,
+                     double* out3) {
   material m;
-  load_material(mat12, &m);
+  load_material(mat12, &m, flags);
   f_single(&m, th_i, th_o, cphi, 0.0, out3);
 }
 
 void oracle_f_single_spread(const double* mat12, double th_i, double th_o, double cphi,
                             double sg2, double* out3) {
   material m;
-  load_material(mat12, &m);
+  load_material(mat12, &m, 0u);
   f_single(&m, th_i, th_o, cphi, sg2, out3);
 }
 
@@ -258,7 +281,7 @@ void oracle_f_ours(const double* mat12, int nq, const double* qx, const double* 
                    double th_o, double cphi, double rho, double n_view, unsigned flags,
                    double* out3) {
   material m;
-  load_material(mat12, &m);
+  load_material(mat12, &m, flags);
   quad q = {nq, qx, qw};
   f_ours(&m, &q, th_i, th_o, cphi, rho, n_view, flags, 0.0, out3);
 }
@@ -271,9 +294,9 @@ void oracle_f_ours(const double* mat12, int nq, const double* qx, const double* 
  * Pinned by test_albedo_2d_diffuse_closed_form.
  */
 void oracle_albedo_2d(const double* mat12, int nq, const double* qx, const double* qw,
-                      double theta_i, double* front3, double* back3) {
+                      double theta_i, unsigned flags, double* front3, double* back3) {
   material m;
-  load_material(mat12, &m);
+  load_material(mat12, &m, flags);
   for (int c = 0; c < 3; ++c) front3[c] = back3[c] = 0.0;
   for (int i = 0; i < nq; ++i) {
     double to = 0.5 * PI * qx[i], wt = 0.5 * PI * qw[i] * cos(to) * cos(to);
@@ -655,7 +678,7 @@ int oracle_render(const double* prim_rows, const int64_t* prim_ids, int64_t n_pr
   material* M = (material*)malloc(sizeof(material) * (size_t)(n_mats > 0 ? n_mats : 1));
   if (!P || !M) return 2;
   load_prims(prim_rows, n_prims, prim_ids, P);
-  for (int64_t j = 0; j < n_mats; ++j) load_material(mat_rows + 12 * j, &M[j]);
+  for (int64_t j = 0; j < n_mats; ++j) load_material(mat_rows + 12 * j, &M[j], flags);
   camera cam;
   cam.kind = (int)cam_rec[0];
   cam.W = (int)cam_rec[1];
@@ -724,7 +747,7 @@ void oracle_camera_ray(const double* cam_rec, uint64_t seed, int64_t sid, int sp
 void oracle_shadow_path(const double* prim_rows, int64_t n_prims, const double* mat_rows,
                         int64_t n_mats, int nq, const double* qx, const double* qw,
                         const double* x3, const double* wi3, double t_light, int self_mat,
-                        double* T3, double* sg2) {
+                        unsigned flags, double* T3, double* sg2) {
   prim* P = (prim*)malloc(sizeof(prim) * (size_t)(n_prims > 0 ? n_prims : 1));
   material* M = (material*)malloc(sizeof(material) * (size_t)(n_mats > 0 ? n_mats : 1));
   if (!P || !M) {
@@ -734,7 +757,7 @@ void oracle_shadow_path(const double* prim_rows, int64_t n_prims, const double* 
     return;
   }
   load_prims(prim_rows, n_prims, 0, P);
-  for (int64_t j = 0; j < n_mats; ++j) load_material(mat_rows + 12 * j, &M[j]);
+  for (int64_t j = 0; j < n_mats; ++j) load_material(mat_rows + 12 * j, &M[j], flags);
   quad q = {nq, qx, qw};
   shadow_path(P, n_prims, M, &q, mk(x3[0], x3[1], x3[2]), mk(wi3[0], wi3[1], wi3[2]), t_light,
               self_mat, T3, sg2);

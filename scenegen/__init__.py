@@ -205,6 +205,21 @@ def material_from_melanin(melanin: np.ndarray, roughness: np.ndarray) -> np.ndar
     return m.astype(np.float32)
 
 
+def material_marschner(melanin: np.ndarray, roughness: np.ndarray) -> np.ndarray:
+    """Lobe parameters for the Marschner R / TT / TRT single fibre (the
+    paper's Section 7 extension): R and TT as in material_from_melanin, and the
+    third attenuation triple holds A_TRT instead of A_D.  The paper prints no
+    TRT range; this recipe maps melanin onto a TRT lobe energy from
+    (0.20, 0.14, 0.08) (light) to (0.10, 0.06, 0.03) (dark), halved like the
+    other lobe energies, so the fibre's forward plus backward albedo stays
+    below 1 over the parameter box.
+    """
+    m = material_from_melanin(melanin, roughness).astype(np.float64)
+    t = np.clip((np.asarray(melanin, np.float64) - 0.1) / 0.8, 0.0, 1.0)
+    m[:, 6:9] = 0.5 * _lerp((0.20, 0.14, 0.08), (0.10, 0.06, 0.03), t)
+    return m.astype(np.float32)
+
+
 def material_absorption(n: int, sigma_a: float, beta: float) -> np.ndarray:
     """Grey fibre from an absorption and a longitudinal roughness.
 
