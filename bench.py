@@ -48,15 +48,25 @@ import numpy as np  # noqa: E402
 
 METRIC = "Msamples/s and ms/frame, 100k strands 1080p; p50/p99 served latency at RMSE<=5e-3"
 
-# FP32 operations per counted event, read off the kernel source
-# (trace_core.cuh): an FMA counts 2, every other FP32 arithmetic, min/max or
-# compare 1, a special-function call (rsqrt, exp, asin, acos, erf) 1.
-FLOPS_PER_NODE = 50        # two child slab tests: 12 FMA + 12 min/max each, ordering
-FLOPS_PER_TEST = 41        # ray into the unit frame and the discriminant decision
-FLOPS_PER_STRAND_SHADE = 100  # light vector, angles, f_single (3 Gaussians), accumulate
-FLOPS_PER_ETH_SHADE = 250     # + albedo lookups, widened lobes, B lobe, S
-FLOPS_PER_HIT = 40            # tangent, outgoing angles, opacity, composite
-FLOPS_PER_SAMPLE = 30         # camera ray
+# Algorithmic FP32 operations per counted event of the frame kernel, the
+# per-unit figures of the hot path's measurement plan: 24 per internal-node
+# visit (two slab tests of 12), 60 per primitive test, 150 per (strand hit,
+# light) and 300 per (thick-hair hit, light) shading, 30 per traced sample
+# (camera ray and compositing).  The headline roofline uses these.
+FLOPS_PER_NODE = 24
+FLOPS_PER_TEST = 60
+FLOPS_PER_STRAND_SHADE = 150
+FLOPS_PER_ETH_SHADE = 300
+FLOPS_PER_HIT = 0
+FLOPS_PER_SAMPLE = 30
+# The same events with operation counts read off the kernel source
+# (trace_core.cuh; an FMA counts 2, every other FP32 arithmetic, min/max or
+# compare 1, a special-function call 1): a node visit is 12 FMA (24) plus 12
+# min/max per child box and the ordering (50); a primitive test 41; a strand
+# shade 100; a thick-hair shade 250; a composited hit 40 (tangent, outgoing
+# angles, opacity, blend); a traced sample 30.  Reported beside the headline
+# as "frac_source_count".
+SRC_FLOPS = {"node": 50, "test": 41, "sshade": 100, "eshade": 250, "hit": 40, "sample": 30}
 # FP32 operations of the cross-section fit (k_fit_cross_sections), same rules
 # (hierarchy.cu).  Per member and section: the exact offsets and their
 # double-word first and second moments (3 TwoSum, 3 double-word adds, 6
@@ -202,10 +212,19 @@ def oracle_baseline(w, seconds: float, seed: int = 11):
 
 
 def event_flops(st) -> int:
-    """FP32 operations of a frame from the event counts of a counting render."""
+    """Algorithmic FP32 operations of a frame from the event counts of a
+    counting render (the measurement plan's per-event figures)."""
     return (FLOPS_PER_NODE * st.node_visits + FLOPS_PER_TEST * st.prim_tests +
             FLOPS_PER_STRAND_SHADE * st.strand_shades + FLOPS_PER_ETH_SHADE * st.eth_shades +
             FLOPS_PER_HIT * st.shaded_hits + FLOPS_PER_SAMPLE * st.traced_samples)
+
+
+def event_flops_source(st) -> int:
+    """The same events weighted by the operation counts of the kernel source."""
+    c = SRC_FLOPS
+    return (c["node"] * st.node_visits + c["test"] * st.prim_tests + c["sshade"] * st.strand_shades
+            + c["eshade"] * st.eth_shades + c["hit"] * st.shaded_hits
+            + c["sample"] * st.traced_samples)
 
 
 def measure_config(hr, ctx, torch, dev, w, steps: int, warmup: int = 2, peak_tflops=None):
@@ -258,9 +277,12 @@ def measure_config(hr, ctx, torch, dev, w, steps: int, warmup: int = 2, peak_tfl
            "lod": w.lod_setting, "precision": "fp16" if w.precision else "fp32", "k_depth": w.k_depth,
            "active_prims": int(st.n_active_prims), "eth_prims": int(st.n_eth_prims),
            "traced_samples": int(st.traced_samples), "frame_ms": frame_ms}
+    out["traced_msamples_per_s_frame"] = st.traced_samples / (frame_ms * 1e-3) / 1e6
     if peak_tflops:
         tf = event_flops(st) / (frame_ms * 1e-3) / 1e12
-        out["frame_fp32"] = {"achieved_tflops": tf, "frac": tf / peak_tflops}
+        ts = event_flops_source(st) / (frame_ms * 1e-3) / 1e12
+        out["frame_fp32"] = {"achieved_tflops": tf, "frac": tf / peak_tflops,
+                             "frac_source_count": ts / peak_tflops}
     return out
 
 
@@ -375,6 +397,31 @@ def run_serving(hr, ctx, torch, dev, n_requests: int, seed: int = 2):
     torch.cuda.synchronize(dev)
     plain_s = time.perf_counter() - t0
 
+    # the plain renderer with the same BVH reuse as serving: requests grouped by
+    # (asset, resolution, LoD budget), one LoD selection and BVH build per group,
+    # then one hr_render per request, in FP32 and with FP16 tables (the
+    # comparison isolates batching and the table precision)
+    groups = {}
+    for i, (a, cam, r) in enumerate(jobs):
+        groups.setdefault((r["asset"], r["width"], r["height"], r["budget"]), []).append(i)
+    grouped_s = {}
+    for prec in (0, 1):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for key, idx in groups.items():
+            a, cam, r0 = jobs[idx[0]]
+            C, L, E = hr.hr_hierarchy_info(ctx, a)
+            lod = lods.setdefault(C, torch.empty(C, dtype=torch.uint8, device=dev))
+            hr.hr_select_lod(ctx, a, cam.pack(), 2.0, 0, r0["budget"], lod)
+            hr.hr_build_bvh(ctx, a, lod)
+            for i in idx:
+                _, cam_i, r = jobs[i]
+                d = hr.render_desc(cam_i.pack(), assets[r["asset"]][1].lights, r["spp"], 4,
+                                   r["seed"], prec)
+                hr.hr_render(ctx, a, d, outs[i])
+        torch.cuda.synchronize(dev)
+        grouped_s[prec] = time.perf_counter() - t0
+
     descs = [hr.render_desc(cam.pack(), assets[r["asset"]][1].lights, r["spp"], 4, r["seed"], 1)
              for a, cam, r in jobs]
     hr.hr_serve_start(ctx, 16, 8 << 20)
@@ -418,7 +465,13 @@ def run_serving(hr, ctx, torch, dev, n_requests: int, seed: int = 2):
             "served_fp16_msamples_per_s": sat_rate / 1e6,
             "plain_fp32_sequential_msamples_per_s": total_samples / plain_s / 1e6,
             "speedup_served_vs_plain": (total_samples / sat_s) / (total_samples / plain_s),
-            "accuracy": "FP16 tables: rel-RMSE <= 5e-3 vs the FP64 oracle (tests/test_serving.py, "
+            "bvh_groups": len(groups),
+            "plain_fp32_grouped_msamples_per_s": total_samples / grouped_s[0] / 1e6,
+            "plain_fp16_grouped_msamples_per_s": total_samples / grouped_s[1] / 1e6,
+            "speedup_served_vs_plain_grouped_fp32": grouped_s[0] / sat_s,
+            "accuracy": "FP16 tables: rel-RMSE <= 5e-3 vs the FP64 oracle "
+                        "(tests/test_serving.py::test_served_full_size_asset_vs_oracle: the "
+                        "100k-strand asset served at 1280x720, 4 spp; "
                         "tests/test_gpu_parity.py::test_stress_sampled)"}
 
 
@@ -611,6 +664,7 @@ def main():
             scenegen.clustered(lod_setting="strands"), scenegen.clustered(lod_setting="half"),
             scenegen.clustered(lod_setting="eth"),
             scenegen.full_head(precision=1),
+            scenegen.full_head(fill=0.45),  # middle view: hair 45% of the frame height
             scenegen.full_head(fill=0.9),  # close view: hair 90% of the frame height, all strands
             scenegen.stress())]
 
@@ -626,8 +680,14 @@ def main():
     sm_max = clocks.get("sm_max_mhz") or 2070.0
     peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
     achieved = flops / (render_avg * 1e-3) / 1e12
+    flops_src = event_flops_source(cst)
     roof_frame = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                   "frac": achieved / peak,
+                  "frac_source_count": flops_src / (render_avg * 1e-3) / 1e12 / peak,
+                  "flops_per_event": {"node": FLOPS_PER_NODE, "test": FLOPS_PER_TEST,
+                                      "strand_shade": FLOPS_PER_STRAND_SHADE,
+                                      "eth_shade": FLOPS_PER_ETH_SHADE, "hit": FLOPS_PER_HIT,
+                                      "traced_sample": FLOPS_PER_SAMPLE},
                   "traffic": traffic_record("k_frame_full_head_traffic.json", TRACE_SOURCES, w.name),
                   "kernel": "k_frame (trace/shade/composite, FP32)", "kernel_ms": render_avg,
                   "flops_per_launch": flops,
@@ -662,6 +722,10 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": config_of(w, args),
+            "traced_samples": int(cst.traced_samples),
+            "traced_msamples_per_s": job_msamples_per_s(world, int(cst.traced_samples), args.steps,
+                                                        elapsed),
+            "traced_msamples_per_s_frame": cst.traced_samples / (render_avg * 1e-3) / 1e6,
             "frame_ms": render_avg, "frame_ms_fp32_warm": fp32_ms, "frame_ms_fp16_warm": fp16_ms,
             "frame_ms_shadow_rays": shadow_ms,
             "active_prims": int(st.n_active_prims),

@@ -122,6 +122,14 @@ typedef struct hr_light {
  * skipped) scales the light, and the hairs' forward spread variances widen
  * every lobe of the shading BCSDF.  Off: primary hits only. */
 #define HR_FLAG_SHADOWS 4u
+/* Marschner R / TT / TRT single fibre (Section 7, "Extending to Marschner
+ * model with TRT term"), in f_single and inside the aggregate f_ours: the
+ * material's third attenuation triple is A_TRT and the third lobe is
+ * A_TRT G(2 beta_R, theta_h) / 2 pi (width 2 beta_R after Marschner et al.
+ * 2003, uniform azimuth as the paper's R lobe) instead of the diffuse
+ * A_D / 2 pi^2; it enters a_F, a_B and the forward spread like the other
+ * lobes, and the TRT^ lobe of a thick hair is widened and attenuated as R^. */
+#define HR_FLAG_TRT 8u
 /* Counting build: hr_render also counts node visits, primitive tests and
  * shading evaluations into hr_stats (slower; used to derive the algorithmic
  * FLOP count of a frame). */
@@ -221,9 +229,11 @@ hr_status hr_asset_update(hr_ctx* ctx, hr_asset* asset, const float* vertices);
  * splits each cluster of m members into 4^k thick hairs, rank-in-cluster i
  * going to floor(i * 4^k / m).  Levels: 1 + max k with 4^k <= floor(N/C)/2,
  * capped by max_levels when > 0; the strands are level n_levels.
- * Each thick hair is fitted per cross-section in FP64 (mean centre, mean
- * tangent, PCA, drop the axis closest to the tangent, semi-axes covering the
- * members).  n_clusters: 1..min(N, 2^20).
+ * Each thick hair is fitted per cross-section (mean centre, mean tangent,
+ * PCA, drop the axis closest to the tangent, semi-axes covering the members):
+ * sums, mean and covariance in double-word FP32 (about FP64 accuracy), FP32
+ * eigenvectors corrected from a double-word residual, and a full FP64 solve
+ * for near-degenerate sections.  n_clusters: 1..min(N, 2^20).
  * cluster_of_out: optional, host or device, [N] uint32 cluster per strand.
  * order_out: optional, host or device, [N] uint32 strand ids in Morton order. */
 hr_status hr_build_clusters(hr_ctx* ctx, hr_asset* asset, uint32_t n_clusters,
@@ -280,6 +290,26 @@ hr_status hr_bvh_export(hr_ctx* ctx, hr_asset* asset, uint32_t* leaf_ids, uint32
 hr_status hr_sort_pairs(hr_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t n, uint32_t bits,
                         int count_earlier);
 
+/* The baked scattering table of the shading code, for tests.  IM(theta,
+ * beta) is the integral over theta_o in [-pi/2, pi/2] of G(beta, (theta +
+ * theta_o)/2) cos^2(theta_o): the longitudinal factor of a lobe's directional
+ * albedo, from which the single-fibre attenuations a_F, a_B and the forward
+ * spread of Section 4 (Eq. 6-9) are formed.  The grid is n_theta x n_beta
+ * points, theta_i = (pi/2) i / (n_theta - 1), beta_j = 0.04 + 0.64 j /
+ * (n_beta - 1), stored row-major [beta][theta].
+ * im32_out: optional, host or device, [n_beta][n_theta] floats.
+ * im16_out: optional, host or device, the FP16 copy as IEEE half bit patterns.
+ * n_theta, n_beta: optional, the grid size (256 x 64). */
+hr_status hr_table_export(hr_ctx* ctx, float* im32_out, uint16_t* im16_out, uint32_t* n_theta,
+                          uint32_t* n_beta);
+/* The shading code's bilinear lookup of IM (see hr_table_export) at m points
+ * (theta_k, beta_k), for tests; theta is clamped to [0, pi/2] and beta to
+ * [0.04, 0.68].  precision: HR_PREC_FP32 or HR_PREC_FP16 (the table read).
+ * theta, beta, out: host or device, [m] floats.  HR_EINVAL for a null
+ * pointer or another precision. */
+hr_status hr_im_lookup(hr_ctx* ctx, const float* theta, const float* beta, uint32_t m,
+                       int precision, float* out);
+
 /* ---------------------------------------------------------------- rendering */
 
 /* Render a frame: per sample a camera ray (sample sid = pixel * spp + s,
@@ -314,8 +344,12 @@ hr_status hr_render_frame(hr_ctx* ctx, hr_asset* asset, uint32_t n_clusters, flo
  * owns every allocation under a fixed budget, or a real-time loop in which
  * cudaMalloc / cudaFree are not allowed because they synchronise the device.
  * It computes the same strand order and cluster ids as hr_build_clusters
- * (order_out and cluster_of_out there) with the same kernels, and needs no
- * context.
+ * (order_out and cluster_of_out there) and needs no context.  The root
+ * bounds, Morton-code and cluster kernels are those of hr_build_clusters;
+ * the stable radix sort is a different one, four kernels per 8-bit digit
+ * (digit histogram per 2,048-key tile, scan, scatter), whose scratch fits a
+ * fixed array, where hr_build_clusters runs the single-sweep sort.  Both
+ * sorts are stable, so the outputs are the same.
  *   vertices       : device, [n_strands][n_segments + 1][4] floats (as in
  *                    hr_hair_desc; only the root vertex of each strand is read)
  *   order_out      : device, [n_strands] uint32, strand ids in Morton order

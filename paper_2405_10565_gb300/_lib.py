@@ -35,6 +35,7 @@ HR_PREC_FP16 = 1
 HR_FLAG_NO_S = 1
 HR_FLAG_SINGLE_ON_ETH = 2
 HR_FLAG_SHADOWS = 4
+HR_FLAG_TRT = 8
 HR_FLAG_COUNT = 256
 HR_FLAG_REFIT = 512
 HR_FLAG_DEFERRED_LOD = 1024
@@ -107,6 +108,8 @@ _SIGS = {
     "hr_build_bvh": (c_int, [P, P, P]),
     "hr_bvh_export": (c_int, [P, P, P, ctypes.POINTER(c_u32)]),
     "hr_sort_pairs": (c_int, [P, P, P, c_u32, c_u32, c_int]),
+    "hr_table_export": (c_int, [P, P, P, ctypes.POINTER(c_u32), ctypes.POINTER(c_u32)]),
+    "hr_im_lookup": (c_int, [P, P, P, c_u32, c_int, P]),
     "hr_render": (c_int, [P, P, ctypes.POINTER(hr_render_desc), P, ctypes.POINTER(hr_stats)]),
     "hr_render_samples": (c_int, [P, P, ctypes.POINTER(hr_render_desc), P, c_u32, P, P]),
     "hr_render_frame": (c_int, [P, P, c_u32, c_float, c_int, ctypes.POINTER(hr_render_desc), P,
@@ -290,6 +293,24 @@ def hr_sort_pairs(ctx: int, keys, vals, n: int, bits: int, count_earlier: bool =
     low `bits` key bits (test export of the library's sort)."""
     _check(ctx, load().hr_sort_pairs(ctx, ptr(keys), ptr(vals), n, bits, 1 if count_earlier else 0),
            "hr_sort_pairs")
+
+
+def hr_table_export(ctx: int, im32_out=None, im16_out=None):
+    """Copy the baked IM(theta, beta) tables out (test export): FP32 values and
+    the FP16 copy's half bit patterns, each [n_beta, n_theta] (host or
+    device), either optional.  Returns (n_theta, n_beta)."""
+    nt, nb = c_u32(), c_u32()
+    _check(ctx, load().hr_table_export(ctx, ptr(im32_out), ptr(im16_out), ctypes.byref(nt),
+                                       ctypes.byref(nb)), "hr_table_export")
+    return nt.value, nb.value
+
+
+def hr_im_lookup(ctx: int, theta, beta, out, precision: int = 0) -> None:
+    """The shading code's bilinear IM lookup at the points (theta[k], beta[k])
+    (test export); float32 arrays, host or device."""
+    m = int(theta.shape[0])
+    _check(ctx, load().hr_im_lookup(ctx, ptr(theta), ptr(beta), m, precision, ptr(out)),
+           "hr_im_lookup")
 
 
 def hr_bvh_export(ctx: int, asset: int, leaf_ids=None) -> int:

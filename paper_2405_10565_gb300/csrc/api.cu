@@ -20,7 +20,6 @@ struct hr_ctx {
   std::atomic<uint64_t> used{0};
   float* im32 = nullptr;
   __half* im16 = nullptr;
-  __half* gz16 = nullptr;
   std::vector<hr::Scratch> scratch;
   std::mutex err_mu;
   std::string last_error;
@@ -48,7 +47,7 @@ cudaStream_t ctx_stream(hr_ctx* ctx) { return ctx->stream; }
 
 void note_launch(hr_ctx* ctx) { ctx->launches++; }
 
-Tables ctx_tables(hr_ctx* ctx) { return Tables{ctx->im32, ctx->im16, ctx->gz16}; }
+Tables ctx_tables(hr_ctx* ctx) { return Tables{ctx->im32, ctx->im16}; }
 
 std::recursive_mutex& ctx_mutex(hr_ctx* ctx) { return ctx->api_mu; }
 
@@ -239,7 +238,7 @@ hr_status hr_create(hr_ctx** out, int device, uint64_t hbm_budget, void* cuda_st
     if (cudaEventCreate(&ctx->ph[i]) != cudaSuccess) st = HR_ECUDA;
   if (st == HR_OK) st = dalloc(ctx, (void**)&ctx->d_overflow, 64, "flags");
   if (st == HR_OK) st = dalloc(ctx, (void**)&ctx->d_counters, 8 * sizeof(unsigned long long), "counters");
-  if (st == HR_OK) st = bake_tables(ctx, &ctx->im32, &ctx->im16, &ctx->gz16);
+  if (st == HR_OK) st = bake_tables(ctx, &ctx->im32, &ctx->im16);
   if (st == HR_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) st = HR_ECUDA;
   if (st != HR_OK) {
     hr_destroy(ctx);
@@ -259,7 +258,6 @@ hr_status hr_destroy(hr_ctx* ctx) {
       if (s.p) cudaFree(s.p);
     if (ctx->im32) cudaFree(ctx->im32);
     if (ctx->im16) cudaFree(ctx->im16);
-    if (ctx->gz16) cudaFree(ctx->gz16);
     if (ctx->d_overflow) cudaFree(ctx->d_overflow);
     if (ctx->d_counters) cudaFree(ctx->d_counters);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
@@ -509,6 +507,42 @@ hr_status hr_sort_pairs(hr_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t n,
   HR_TRY(scratch(ctx, 50, (size_t)n * 4, (void**)&v2));
   HR_TRY(radix_sort_pairs(ctx, keys, vals, k2, v2, n, (int)bits, st,
                           count_earlier ? 0 : kLookbackPolls));
+  HR_CUDA(ctx, cudaStreamSynchronize(st));
+  return HR_OK;
+}
+
+hr_status hr_table_export(hr_ctx* ctx, float* im32_out, uint16_t* im16_out, uint32_t* n_theta,
+                          uint32_t* n_beta) {
+  API_ENTER(ctx);
+  if (n_theta) *n_theta = kImNT;
+  if (n_beta) *n_beta = kImNB;
+  cudaStream_t st = ctx->stream;
+  const size_t n = (size_t)kImNT * kImNB;
+  if (im32_out)
+    HR_CUDA(ctx, cudaMemcpyAsync(im32_out, ctx->im32, n * sizeof(float),
+                                 is_device_ptr(im32_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  if (im16_out)
+    HR_CUDA(ctx, cudaMemcpyAsync(im16_out, ctx->im16, n * sizeof(__half),
+                                 is_device_ptr(im16_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  HR_CUDA(ctx, cudaStreamSynchronize(st));
+  return HR_OK;
+}
+
+hr_status hr_im_lookup(hr_ctx* ctx, const float* theta, const float* beta, uint32_t m,
+                       int precision, float* out) {
+  API_ENTER(ctx);
+  if (m == 0) return HR_OK;
+  if (!theta || !beta || !out) return set_error(ctx, HR_EINVAL, "null argument");
+  if (precision != HR_PREC_FP32 && precision != HR_PREC_FP16)
+    return set_error(ctx, HR_EINVAL, "hr_im_lookup: precision must be HR_PREC_FP32 or HR_PREC_FP16");
+  cudaStream_t st = ctx->stream;
+  float* buf = nullptr;
+  HR_TRY(scratch(ctx, 51, (size_t)m * 3 * sizeof(float), (void**)&buf));
+  HR_TRY(to_device(ctx, buf, theta, (size_t)m * 4, st));
+  HR_TRY(to_device(ctx, buf + m, beta, (size_t)m * 4, st));
+  HR_TRY(launch_im_lookup(ctx, precision, buf, buf + m, m, buf + 2 * (size_t)m, st));
+  HR_CUDA(ctx, cudaMemcpyAsync(out, buf + 2 * (size_t)m, (size_t)m * 4,
+                               is_device_ptr(out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   HR_CUDA(ctx, cudaStreamSynchronize(st));
   return HR_OK;
 }

@@ -7,13 +7,15 @@
 // its global primitive ids.
 //
 // LBVH (Karras 2012, "Maximizing parallelism in the construction of BVHs,
-// octrees, and k-d trees"): 30-bit Morton codes of the primitive box
-// centroids in the scene bounds, stable radix sort of (code, id), one thread
-// per internal node finds its key range and split from the longest common
-// prefix (ties between equal codes broken by index), then bounds are
-// propagated bottom-up with one arrival counter per internal node: in shared
-// memory for the nodes whose leaf range lies inside the thread block's leaves
-// (nearly all of them), in global memory for the few that span blocks.
+// octrees, and k-d trees"): 21-bit Morton codes (7 bits per axis) of the
+// primitive box centroids in the strand boxes' bounds, stable single-sweep
+// radix sort of (code, position in the active list), one thread per internal
+// node finds its key range and split from the longest common prefix (ties
+// between equal codes broken by index).  Bounds go bottom-up in two kernels:
+// k_gather_refit copies the leaf records into Morton order and finishes the
+// nodes whose leaf range lies inside its thread block's leaves (nearly all of
+// them) in barrier-separated rounds in shared memory; k_climb finishes the few
+// nodes that span blocks by float atomic min / max from each climb start.
 //
 // Node layout (4 x float4 = 64 bytes), children's boxes stored in the parent:
 //   n0 = (lo0.x, hi0.x, lo0.y, hi0.y)  n1 = (lo1.x, hi1.x, lo1.y, hi1.y)

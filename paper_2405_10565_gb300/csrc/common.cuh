@@ -23,14 +23,9 @@ constexpr int kImNT = 256;
 constexpr int kImNB = 64;
 constexpr float kImBetaLo = 0.04f;
 constexpr float kImBetaHi = 0.68f;
-// Gaussian lobe table g(z) = exp(-z^2 / 2), z in [0, kGzMax].
-constexpr int kGzN = 1024;
-constexpr float kGzMax = 8.0f;
-
 struct Tables {
   const float* im32;   // [kImNB][kImNT]
   const __half* im16;  // [kImNB][kImNT]
-  const __half* gz16;  // [kGzN + 1]
 };
 
 // One BVH over the active primitives of an asset.
@@ -191,7 +186,7 @@ hr_status refit_bvh(hr_ctx* ctx, hr_asset* a, const uint8_t* lod_dev, Bvh& bv, c
 void free_bvh(hr_ctx* ctx, Bvh& b);
 
 // --- tables.cu
-hr_status bake_tables(hr_ctx* ctx, float** im32, __half** im16, __half** gz16);
+hr_status bake_tables(hr_ctx* ctx, float** im32, __half** im16);
 
 // --- trace.cu
 struct LaunchCam {
@@ -248,6 +243,9 @@ hr_status launch_frame_shadow(hr_ctx* ctx, const FrameArgs& fa, int precision, b
                        float* rgb_dev, cudaStream_t st);
 hr_status launch_samples(hr_ctx* ctx, const FrameArgs& fa, int precision, const uint32_t* sids,
                          uint32_t m, float* rad_dev, int32_t* hit_dev, cudaStream_t st);
+// IM(theta, beta) lookups at m device points (test export of the shading code)
+hr_status launch_im_lookup(hr_ctx* ctx, int precision, const float* theta, const float* beta,
+                           uint32_t m, float* out, cudaStream_t st);
 
 // Batched serving launch: a list of tiles from several requests.
 struct ServeItem {

@@ -4,9 +4,13 @@
 // every device allocation under a fixed memory budget (a game engine's frame
 // loop, a host framework whose own allocator must see all memory), or a
 // real-time loop where cudaMalloc / cudaFree are off limits because they
-// synchronise the device.  For them this entry point runs the same clustering
-// kernels as hr_build_clusters, with all of its scratch in one file-scope
-// device array of fixed size, and writes only the caller's output buffers.
+// synchronise the device.  For them this entry point runs the root-bounds,
+// Morton-code and cluster kernels of hr_build_clusters with all of its scratch
+// in one file-scope device array of fixed size, and writes only the caller's
+// output buffers.  Its stable radix sort is the four-kernel-per-digit sort
+// (digit histogram per 2,048-key tile, scan, scatter), not the single-sweep
+// sort of hr_build_clusters, because its scratch has a fixed size; both sorts
+// are stable, so the order and cluster ids are the same.
 //
 // The array's name is meaningful to device code only; on the host it is a
 // stand-in, so host code takes its device address with cudaGetSymbolAddress

@@ -264,21 +264,13 @@ __device__ __forceinline__ void load_mat(const float* __restrict__ m, Mat& o) {
   o.bR = c.y; o.bT = c.z; o.gT = c.w;
 }
 
-// Gaussian G(beta, x) = exp(-x^2 / 2 beta^2) / (sqrt(2 pi) beta), Section 3.2.
-template <int PREC>
-__device__ __forceinline__ float gauss(const Tables& tb, float beta, float x) {
+// Gaussian G(beta, x) = exp(-x^2 / 2 beta^2) / (sqrt(2 pi) beta), Section 3.2,
+// evaluated with the hardware exponential in both table precisions (a table
+// gather costs more than the exponential it replaces).
+__device__ __forceinline__ float gauss(float beta, float x) {
   const float ib = 1.0f / beta;
-  if (PREC == HR_PREC_FP32) {
-    const float z = x * ib;
-    return __expf(-0.5f * z * z) * (kInvSqrt2Pi * ib);
-  } else {
-    const float z = fabsf(x) * ib * (kGzN / kGzMax);
-    if (!(z < (float)kGzN)) return 0.f;
-    const int i = (int)z;
-    const float fr = z - (float)i;
-    const float g0 = __half2float(tb.gz16[i]), g1 = __half2float(tb.gz16[i + 1]);
-    return fmaf(fr, g1 - g0, g0) * (kInvSqrt2Pi * ib);
-  }
+  const float z = x * ib;
+  return __expf(-0.5f * z * z) * (kInvSqrt2Pi * ib);
 }
 
 // Longitudinal albedo factor IM(theta, beta), bilinear in the baked table.
@@ -311,21 +303,24 @@ constexpr float kInvPi = 0.3183098861837907f;
 constexpr float kInv2Pi2 = 0.05066059182116889f;  // 1 / (2 pi^2)
 
 // Single-fibre BCSDF, Eq. (1).  sg2: the spread variance gathered on the
-// light's path (0 without shadow rays), added to every lobe's variance.
+// light's path (0 without shadow rays), added to every lobe's variance.  With
+// trt (HR_FLAG_TRT, Marschner's R / TT / TRT fibre) the third lobe is
+// A_TRT G(2 beta_R, theta_h) / 2 pi instead of the diffuse A_D / 2 pi^2.
 template <int PREC>
 __device__ __forceinline__ void f_single(const Tables& tb, const Mat& m, float th_i, float th_o,
-                                         float cphi, float sg2, float out[3]) {
+                                         float cphi, float sg2, bool trt, float out[3]) {
   const float th_h = 0.5f * (th_i + th_o);
   const float phi = acosf(clampf(cphi, -1.f, 1.f));
   const bool wide = sg2 > 0.f;
   const float bR = wide ? sqrtf(fmaf(m.bR, m.bR, sg2)) : m.bR;
   const float bT = wide ? sqrtf(fmaf(m.bT, m.bT, sg2)) : m.bT;
   const float gT = wide ? sqrtf(fmaf(m.gT, m.gT, sg2)) : m.gT;
-  const float mR = gauss<PREC>(tb, bR, th_h) * kInv2Pi;
-  const float mT = gauss<PREC>(tb, bT, th_h) * gauss<PREC>(tb, gT, phi - kPi);
+  const float mR = gauss(bR, th_h) * kInv2Pi;
+  const float mT = gauss(bT, th_h) * gauss(gT, phi - kPi);
+  const float m3 = trt ? gauss(sqrtf(fmaf(4.f * m.bR, m.bR, sg2)), th_h) * kInv2Pi : kInv2Pi2;
 #pragma unroll
   for (int c = 0; c < 3; ++c)
-    out[c] = fmaf(m.A[0][c], mR, fmaf(m.A[1][c], mT, m.A[2][c] * kInv2Pi2));
+    out[c] = fmaf(m.A[0][c], mR, fmaf(m.A[1][c], mT, m.A[2][c] * m3));
 }
 
 // Per-hit constants of the aggregated model.
@@ -345,32 +340,40 @@ __device__ __forceinline__ void f_ours(const Tables& tb, const Mat& m, const Eth
   const float th_h = 0.5f * (th_i + th_o);
   const float ta = 0.5f * fabsf(th_i - th_o);
   const float phi = acosf(clampf(cphi, -1.f, 1.f));
+  const bool trt = flags & HR_FLAG_TRT;
   const float imR = im_lookup<PREC>(tb, ta, m.bR);
   const float imT = im_lookup<PREC>(tb, ta, m.bT);
+  // third lobe: diffuse (a quarter of A_D per half) or TRT (half of
+  // A_TRT IM(2 beta_R) per half, its width weighted into the forward spread)
+  const float im3 = trt ? 0.5f * im_lookup<PREC>(tb, ta, 2.f * m.bR) : 0.25f;
   float aF[3], aB[3];
-  float wR = 0.f, wT = 0.f;
+  float wR = 0.f, wT = 0.f, w3 = 0.f;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const float r = m.A[0][c] * imR * 0.5f;
     const float tt = m.A[1][c] * imT;
-    aF[c] = r + tt * eh.nF + m.A[2][c] * 0.25f;
-    aB[c] = r + tt * eh.nB + m.A[2][c] * 0.25f;
+    const float third = m.A[2][c] * im3;
+    aF[c] = r + tt * eh.nF + third;
+    aB[c] = r + tt * eh.nB + third;
     wR += r;
     wT += tt * eh.nF;
+    w3 += third;
   }
   const float bR2 = m.bR * m.bR, bT2 = m.bT * m.bT;
-  const float s2 = (wR * bR2 + wT * bT2) / (wR + wT);
+  const float s2 = trt ? (wR * bR2 + wT * bT2 + w3 * 4.f * bR2) / (wR + wT + w3)
+                       : (wR * bR2 + wT * bT2) / (wR + wT);
   const bool back = cphi > 0.f;
   const float n = back ? 1.f : eh.n_view;
   const float nm1 = n - 1.f;
-  const float mR = gauss<PREC>(tb, sqrtf(fmaf(nm1, s2, bR2) + sg2), th_h) * kInv2Pi;
-  const float mT = gauss<PREC>(tb, sqrtf(fmaf(nm1, s2, bT2) + sg2), th_h) *
-                   gauss<PREC>(tb, sqrtf(fmaf(nm1, s2, m.gT * m.gT) + sg2), phi - kPi);
+  const float mR = gauss(sqrtf(fmaf(nm1, s2, bR2) + sg2), th_h) * kInv2Pi;
+  const float mT = gauss(sqrtf(fmaf(nm1, s2, bT2) + sg2), th_h) *
+                   gauss(sqrtf(fmaf(nm1, s2, m.gT * m.gT) + sg2), phi - kPi);
+  const float m3 = trt ? gauss(sqrtf(fmaf(nm1, s2, 4.f * bR2) + sg2), th_h) * kInv2Pi : kInv2Pi2;
   float lob[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const float att = nm1 > 0.f ? exp2f(nm1 * __log2f(aF[c])) : 1.f;
-    lob[c] = att * fmaf(m.A[0][c], mR, fmaf(m.A[1][c], mT, m.A[2][c] * kInv2Pi2));
+    lob[c] = att * fmaf(m.A[0][c], mR, fmaf(m.A[1][c], mT, m.A[2][c] * m3));
   }
   if (back) {
     float A1[3], A3[3], A1p[3];
@@ -389,7 +392,7 @@ __device__ __forceinline__ void f_ours(const Tables& tb, const Mat& m, const Eth
     }
     const float vB = (w1 * (bR2 + 2.f * s2) + w3 * (3.f * bR2 + 2.f * s2) +
                       w1p * (bR2 + (eh.n_view + 1.f) * s2)) / (w1 + w3 + w1p);
-    const float mB = gauss<PREC>(tb, sqrtf(vB + sg2), th_h) * kInvPi;
+    const float mB = gauss(sqrtf(vB + sg2), th_h) * kInvPi;
 #pragma unroll
     for (int c = 0; c < 3; ++c) lob[c] = fmaf(A1p[c] + A1[c] + A3[c], mB, lob[c]);
     if (!(flags & HR_FLAG_NO_S)) {
@@ -408,20 +411,25 @@ __device__ __forceinline__ void f_ours(const Tables& tb, const Mat& m, const Eth
 // at incidence |theta| (the a_F reading of the aggregated model).
 template <int PREC>
 __device__ __forceinline__ void forward_albedo(const Tables& tb, const Mat& m, float theta_abs,
-                                               float aF[3], float& s2) {
+                                               bool trt, float aF[3], float& s2) {
   const float imR = im_lookup<PREC>(tb, theta_abs, m.bR);
   const float imT = im_lookup<PREC>(tb, theta_abs, m.bT);
+  const float im3 = trt ? 0.5f * im_lookup<PREC>(tb, theta_abs, 2.f * m.bR) : 0.25f;
   const float nF = erff(kPi / (2.f * 1.41421356f * m.gT));
-  float wR = 0.f, wT = 0.f;
+  float wR = 0.f, wT = 0.f, w3 = 0.f;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const float r = m.A[0][c] * imR * 0.5f;
     const float tt = m.A[1][c] * imT * nF;
-    aF[c] = r + tt + m.A[2][c] * 0.25f;
+    const float third = m.A[2][c] * im3;
+    aF[c] = r + tt + third;
     wR += r;
     wT += tt;
+    w3 += third;
   }
-  s2 = (wR * m.bR * m.bR + wT * m.bT * m.bT) / (wR + wT);
+  const float bR2 = m.bR * m.bR;
+  s2 = trt ? (wR * bR2 + wT * m.bT * m.bT + w3 * 4.f * bR2) / (wR + wT + w3)
+           : (wR * bR2 + wT * m.bT * m.bT) / (wR + wT);
 }
 
 // The hair a shadow ray crosses in one leaf: the ray's interval inside the
@@ -524,7 +532,7 @@ __device__ __forceinline__ void shadow_path(const FrameArgs& fa, const float3 x,
         Mat m;
         load_mat(fa.mat + (size_t)__float_as_uint(aux.x) * HR_MAT_FLOATS, m);
         float aF[3], s2;
-        forward_albedo<PREC>(fa.tables, m, fabsf(asinf(si)), aF, s2);
+        forward_albedo<PREC>(fa.tables, m, fabsf(asinf(si)), (fa.flags & HR_FLAG_TRT) != 0, aF, s2);
         if (aux.y > 0.f) {  // thick hair: its hair number over the chord
           const float ntot = aux.y, r = aux.z, ab = aux.w;
           const float rho = fminf(1.f, ntot * r * r / ab);
@@ -615,7 +623,7 @@ __device__ __forceinline__ void shade_hit(const FrameArgs& fa, uint32_t leaf, fl
       f_ours<PREC>(fa.tables, m, eh, th_i, th_o, cphi, fa.flags, sg2, f);
       if (COUNT) ++cn.eshade;
     } else {
-      f_single<PREC>(fa.tables, m, th_i, th_o, cphi, sg2, f);
+      f_single<PREC>(fa.tables, m, th_i, th_o, cphi, sg2, (fa.flags & HR_FLAG_TRT) != 0, f);
       if (COUNT) ++cn.sshade;
     }
     const float g = E * sqrtf(fmaxf(0.f, 1.f - si * si));

@@ -40,6 +40,15 @@ hr_status launch_p(hr_ctx* ctx, const FrameArgs& fa, const uint32_t* sids, uint3
   return HR_OK;
 }
 
+// The bilinear IM(theta, beta) lookup of the shading code at listed points
+// (test export).
+template <int PREC>
+__global__ void k_im_lookup(const Tables tb, const float* __restrict__ theta,
+                            const float* __restrict__ beta, uint32_t m, float* __restrict__ out) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) out[i] = tr::im_lookup<PREC>(tb, theta[i], beta[i]);
+}
+
 template <bool SHADOW>
 hr_status launch_t(hr_ctx* ctx, const FrameArgs& fa, int precision, const uint32_t* sids,
                    uint32_t m, float* rad, int32_t* hit, cudaStream_t st) {
@@ -48,6 +57,18 @@ hr_status launch_t(hr_ctx* ctx, const FrameArgs& fa, int precision, const uint32
 }
 
 }  // namespace
+
+hr_status launch_im_lookup(hr_ctx* ctx, int precision, const float* theta, const float* beta,
+                           uint32_t m, float* out, cudaStream_t st) {
+  if (m == 0) return HR_OK;
+  const uint32_t g = (m + 127) / 128;
+  if (precision == HR_PREC_FP16)
+    k_im_lookup<HR_PREC_FP16><<<g, 128, 0, st>>>(ctx_tables(ctx), theta, beta, m, out);
+  else
+    k_im_lookup<HR_PREC_FP32><<<g, 128, 0, st>>>(ctx_tables(ctx), theta, beta, m, out);
+  HR_LAUNCHED(ctx);
+  return HR_OK;
+}
 
 hr_status launch_samples(hr_ctx* ctx, const FrameArgs& fa, int precision, const uint32_t* sids,
                          uint32_t m, float* rad_dev, int32_t* hit_dev, cudaStream_t st) {

@@ -81,3 +81,20 @@ def compare(rad_g, hit_g, rad_o, hit_o):
 def oracle_prepare(w, lod=None):
     return oracle.prepare(w.scene, w.n_clusters, w.lod_setting, w.camera.pack(), w.eps_w,
                           lod=lod)
+
+
+def hair_pixels(w, n, seed):
+    """Up to n distinct pixels that contain the projection of a seeded hair
+    vertex (perspective camera), so that their samples land on hair."""
+    v = w.scene.verts[..., :3].reshape(-1, 3).astype(np.float64)
+    c = w.camera
+    st = scenegen.Stream(seed, 98)
+    idx = (st.u64(8 * n) % np.uint64(v.shape[0])).astype(np.int64)
+    r = v[idx] - c.eye.astype(np.float64)
+    z = r @ c.fwd.astype(np.float64)
+    X = (r @ c.right.astype(np.float64)) / z * c.pix_scale + 0.5 * c.width
+    Y = 0.5 * c.height - (r @ c.up.astype(np.float64)) / z * c.pix_scale
+    ok = (z > 0) & (X >= 0) & (X < c.width) & (Y >= 0) & (Y < c.height)
+    pix = np.floor(Y[ok]).astype(np.int64) * c.width + np.floor(X[ok]).astype(np.int64)
+    _, first = np.unique(pix, return_index=True)
+    return pix[np.sort(first)][:n]

@@ -13,7 +13,7 @@ import oracle
 import paper_2405_10565_gb300 as hr
 import scenegen
 from gpu_util import (HIT_AGREE_MIN, KBUF_AGREE_MIN, RMSE_FP16, RMSE_FP32, compare, desc_of,
-                      gpu_lod, gpu_samples, oracle_prepare, upload)
+                      gpu_lod, gpu_samples, hair_pixels, oracle_prepare, upload)
 
 pytestmark = pytest.mark.gpu
 
@@ -300,16 +300,56 @@ def test_device_pointer_inputs_and_outputs(ctx):
         hr.hr_asset_destroy(ctx, a)
 
 
-def test_full_head_full_size_sampled(ctx):
-    """The bench workload (100k strands x 64 segments, 1920x1080, 8 spp, 8
-    lights, LoD selected over 4096 clusters) on sampled pixels: every sample
-    of 48 seeded pixels plus one 8x8 pixel tile, through the sample kernel, and
-    the frame kernel's values at those pixels."""
-    w = scenegen.full_head()
+def _full_size_sampled(ctx, w, pix, precision=None, min_hair=2000):
+    """Every sample of the listed pixels through the sample kernel against the
+    oracle (nearest-hit and k-buffer agreement, radiance bar of the table
+    precision), and the frame kernel's pixel values there against the
+    oracle's pixel means."""
     W, H, spp = w.camera.width, w.camera.height, w.spp
+    prec = w.precision if precision is None else precision
+    bar = RMSE_FP16 if prec == 1 else RMSE_FP32
+    sids = scenegen.pixel_samples(W, spp, pix)
+    a = upload(ctx, w.scene)
+    try:
+        lod_g = gpu_lod(ctx, a, w)
+        prep = _oracle_with_lod(w, None, lod_g)
+        L = int(lod_g.max()) if lod_g is not None else 0
+        print(f"{w.name}: LoD levels {np.bincount(lod_g, minlength=L + 1).tolist()}, "
+              f"active primitives {prep.rows.shape[0]}")
+        d = desc_of(w, precision=prec)
+        rg, hg = gpu_samples(ctx, a, d, sids)
+        ro, ho = oracle.render_samples(prep, w.camera.pack(), w.lights, sids, spp, w.k_depth,
+                                       w.sample_seed)
+        frac, full, r_agree, r_all = compare(rg, hg, ro, ho)
+        on_hair = int((ho[:, 0] >= 0).sum())
+        print(f"{w.name} {'fp16' if prec else 'fp32'} sampled: {len(sids)} samples, "
+              f"{on_hair} on hair, nearest {frac:.5f} k-buffer {full:.5f} rmse {r_agree:.2e} "
+              f"all {r_all:.2e}, eth hits {(ho[:, 0] >= w.scene.n_strands * w.scene.n_segments).mean():.3f}")
+        assert frac >= HIT_AGREE_MIN and full >= KBUF_AGREE_MIN and r_agree <= bar
+        assert on_hair >= min_hair, "sampled pixels must cover the hair"
+        img = np.zeros((H, W, 3), np.float32)
+        hr.hr_render(ctx, a, d, img)
+        got = img.reshape(-1, 3)[pix]
+        want = ro.reshape(-1, spp, 3).mean(1)
+        agree_px = (hg.reshape(-1, spp * w.k_depth) == ho.reshape(-1, spp * w.k_depth)).all(1)
+        num = np.linalg.norm((got - want)[agree_px])
+        assert num <= bar * np.linalg.norm(want[agree_px]) + 1e-12
+        return r_agree
+    finally:
+        hr.hr_asset_destroy(ctx, a)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_head_full_size_sampled(ctx, precision):
+    """The bench workload (100k strands x 64 segments, 1920x1080, 8 spp, 8
+    lights, LoD selected over 4096 clusters), with FP32 and with FP16 tables,
+    on sampled pixels: every sample of 16 seeded pixels anywhere, 48 inside
+    the hair's screen box, one 8x8 tile at the centre and 256 pixels that
+    contain a projected hair vertex (over 2,000 samples on hair), through the
+    sample kernel, and the frame kernel's values at those pixels."""
+    w = scenegen.full_head()
+    W, H = w.camera.width, w.camera.height
     st = scenegen.Stream(7, 99)
-    # 16 pixels anywhere, 48 inside the hair's screen box (the central
-    # 15% of the frame height) and one 8x8 tile at the centre
     pix = list((st.u64(16) % np.uint64(W * H)).astype(np.int64))
     half = int(0.09 * H)
     xs = (W // 2 - half + (st.u64(48) % np.uint64(2 * half))).astype(np.int64)
@@ -317,33 +357,15 @@ def test_full_head_full_size_sampled(ctx):
     pix += list(ys * W + xs)
     x0, y0 = W // 2 - 4, H // 2 - 4
     pix += [(y0 + j) * W + x0 + i for j in range(8) for i in range(8)]
-    pix = np.unique(np.asarray(pix, np.int64))
-    sids = scenegen.pixel_samples(W, spp, pix)
-    a = upload(ctx, w.scene)
-    try:
-        lod_g = gpu_lod(ctx, a, w)
-        prep = _oracle_with_lod(w, None, lod_g)
-        print(f"full head LoD levels {np.bincount(lod_g, minlength=3).tolist()}, "
-              f"active primitives {prep.rows.shape[0]}")
-        d = desc_of(w)
-        rg, hg = gpu_samples(ctx, a, d, sids)
-        ro, ho = oracle.render_samples(prep, w.camera.pack(), w.lights, sids, spp, w.k_depth,
-                                       w.sample_seed)
-        frac, full, r_agree, r_all = compare(rg, hg, ro, ho)
-        print(f"full head sampled: nearest {frac:.5f} k-buffer {full:.5f} rmse {r_agree:.2e} "
-              f"all {r_all:.2e}, hits {(ho[:, 0] >= 0).mean():.3f}, "
-              f"eth hits {(ho[:, 0] >= w.scene.n_strands * 64).mean():.3f}")
-        assert frac >= HIT_AGREE_MIN and full >= KBUF_AGREE_MIN and r_agree <= RMSE_FP32
-        assert (ho[:, 0] >= 0).mean() > 0.2, "sampled pixels must cover the hair"
-        img = np.zeros((H, W, 3), np.float32)
-        hr.hr_render(ctx, a, d, img)
-        got = img.reshape(-1, 3)[pix]
-        want = ro.reshape(-1, spp, 3).mean(1)
-        agree_px = (hg.reshape(-1, spp * w.k_depth) == ho.reshape(-1, spp * w.k_depth)).all(1)
-        num = np.linalg.norm((got - want)[agree_px])
-        assert num <= RMSE_FP32 * np.linalg.norm(want[agree_px]) + 1e-12
-    finally:
-        hr.hr_asset_destroy(ctx, a)
+    pix += list(hair_pixels(w, 256, 1 + precision))
+    _full_size_sampled(ctx, w, np.unique(np.asarray(pix, np.int64)), precision)
+
+
+def test_full_head_close_view_sampled(ctx):
+    """The full head in the close view (hair 90% of the frame height, every
+    cluster on strands: 6.4M active segments), 160 hair pixels x 8 spp."""
+    w = scenegen.full_head(fill=0.9)
+    _full_size_sampled(ctx, w, hair_pixels(w, 160, 4), min_hair=1000)
 
 
 def _sampled_pixels(W, H, n_any, n_center, half_frac, seed):
@@ -372,14 +394,17 @@ def test_clustered_full_size_sampled(ctx, setting):
 def test_stress_sampled(ctx):
     """The stress workload (500,000 long straight strands x 64 segments,
     16,384 clusters, eccentricity 0.9, 3840x2160, 16 spp, 4 lights, K = 8, FP16
-    tables, LoD selected) on every sample of 12 seeded pixels on the hair: the
-    oracle runs brute force over tens of millions of primitives per sample."""
+    tables, LoD selected) on every sample of 12 seeded pixels in the centre
+    and 128 pixels that contain a projected hair vertex (over 2,000 samples on
+    hair): the oracle runs brute force over 28.5M primitives per sample."""
     w = scenegen.stress()
     W, H = w.camera.width, w.camera.height
-    pix = _sampled_pixels(W, H, 0, 12, 0.2, 6)
+    pix = np.unique(np.concatenate([_sampled_pixels(W, H, 0, 12, 0.2, 6), hair_pixels(w, 128, 6)]))
     sids = scenegen.pixel_samples(W, w.spp, pix)
     rg, hg, ro, ho = _render_check(ctx, w, sids)
-    print(f"stress: hit fraction {(ho[:, 0] >= 0).mean():.3f}")
+    on_hair = int((ho[:, 0] >= 0).sum())
+    print(f"stress: {len(sids)} samples, {on_hair} on hair")
+    assert on_hair >= 2000
 
 
 def test_asset_update_matches_a_fresh_asset(ctx):
@@ -606,3 +631,98 @@ def test_radix_sort_is_stable_and_matches_numpy(ctx, n, bits, dups):
         vv = v.cpu().numpy().view(np.uint32)
         assert np.array_equal(vv, vals[order]), count_earlier
         assert np.array_equal(kk, keys[order]), count_earlier
+
+
+def test_thick_hair_image_converges_to_the_strand_image(ctx):
+    """Section 4 (Eq. 5 against Eq. 1): the GPU's image of the level-L thick
+    hairs approaches its strand image of the same clusters as L rises (the
+    relative RMSE falls strictly from level to level), and every level's
+    samples match the oracle.  A scene whose rays cross few semi-transparent
+    thick-hair layers, so a k-buffer of 8 holds them (1,200 strands x 12
+    segments in 8 clusters: 1, 4, 16 and 64 thick hairs per cluster)."""
+    w = scenegen.clustered(n=1200, S=12, res=48, spp=4, lod_setting="strands", n_clusters=8)
+    n = w.camera.width * w.camera.height * w.spp
+    sids = np.arange(n)
+    a = upload(ctx, w.scene)
+    try:
+        hr.hr_build_clusters(ctx, a, w.n_clusters)
+        C, L, E = hr.hr_hierarchy_info(ctx, a)
+        assert L == 4
+        imgs = []
+        for lv in list(range(L)) + [L]:
+            lod = np.full(C, lv, np.uint8)
+            hr.hr_build_bvh(ctx, a, lod)
+            d = desc_of(w, k=8)
+            rg, hg = gpu_samples(ctx, a, d, sids)
+            prep = oracle_prepare(w, lod=lod)
+            ro, ho = oracle.render_samples(prep, w.camera.pack(), w.lights, sids, w.spp, 8,
+                                           w.sample_seed)
+            frac, full, r_agree, _ = compare(rg, hg, ro, ho)
+            assert frac >= HIT_AGREE_MIN and full >= KBUF_AGREE_MIN and r_agree <= RMSE_FP32, \
+                (lv, frac, full, r_agree)
+            imgs.append(rg.astype(np.float64).reshape(-1, w.spp, 3).mean(1))
+        ref = imgs[-1]
+        err = [float(np.linalg.norm(im - ref) / np.linalg.norm(ref)) for im in imgs[:-1]]
+        print(f"GPU rel-RMSE against the strand image per level: {[round(e, 3) for e in err]}")
+        assert all(b < a_ for a_, b in zip(err, err[1:])), err
+    finally:
+        hr.hr_asset_destroy(ctx, a)
+
+
+def _with_trt_materials(w, seed=4):
+    N = w.scene.n_strands
+    st = scenegen.Stream(seed, 1)
+    mel = 0.1 + 0.8 * st.uniform(N)
+    rough = 0.1 + 0.2 * st.uniform(N)
+    w.scene = scenegen.Scene(w.scene.verts, scenegen.material_marschner(mel, rough),
+                             w.scene.shape, w.scene.name)
+    return w
+
+
+@pytest.mark.parametrize("wl,precision", [("tiny", 0), ("clusters_half", 0), ("clusters_half", 1),
+                                          ("clusters_eth", 0), ("full_head_small", 0)])
+def test_marschner_trt_lobe(ctx, wl, precision):
+    """HR_FLAG_TRT (Section 7: the Marschner R / TT / TRT fibre inside the
+    aggregate) on strands, on thick hairs and on a selected LoD, against the
+    oracle with the same flag."""
+    if wl == "tiny":
+        w = scenegen.tiny_strands()
+    elif wl == "clusters_half":
+        w = scenegen.clustered(n=3000, S=12, res=48, spp=2, lod_setting="half", n_clusters=64)
+    elif wl == "clusters_eth":
+        w = scenegen.clustered(n=3000, S=12, res=40, spp=1, lod_setting="eth", n_clusters=64)
+    else:
+        w = scenegen.full_head(n=8000, S=16, width=96, height=64, spp=2, n_lights=8,
+                               n_clusters=320, fill=0.25)
+    w = _with_trt_materials(w)
+    n = w.camera.width * w.camera.height * w.spp
+    rg, hg, ro, ho = _render_check(ctx, w, np.arange(n), precision=precision,
+                                   flags=hr.HR_FLAG_TRT)
+    assert np.linalg.norm(ro) > 0
+
+
+def test_marschner_trt_with_shadow_rays(ctx):
+    w = _with_trt_materials(scenegen.clustered(n=3000, S=12, res=40, spp=2, lod_setting="half",
+                                               n_clusters=64))
+    a = upload(ctx, w.scene)
+    try:
+        lod_g = gpu_lod(ctx, a, w)
+        prep = _oracle_with_lod(w, None, lod_g)
+        flags = hr.HR_FLAG_TRT | hr.HR_FLAG_SHADOWS
+        sids = np.random.default_rng(3).choice(w.camera.width * w.camera.height * w.spp, 1500,
+                                               replace=False)
+        rg, hg = gpu_samples(ctx, a, desc_of(w, flags=flags), sids)
+        ro, ho = oracle.render_samples(prep, w.camera.pack(), w.lights, sids, w.spp, w.k_depth,
+                                       w.sample_seed, flags=oracle.FLAG_SHADOWS | oracle.FLAG_TRT)
+        same = np.all(np.asarray(hg, np.int64) == ho, axis=1)
+        on = np.linalg.norm(ro, axis=1)
+        err = np.linalg.norm(rg.astype(np.float64) - ro, axis=1) / np.maximum(on, 1e-3 * on.mean())
+        ok = same & (err <= 1e-3)
+        rmse = np.linalg.norm(rg[ok].astype(np.float64) - ro[ok]) / np.linalg.norm(ro[ok])
+        print(f"TRT + shadows: k-buffer agreement {same.mean():.5f}, "
+              f"shadow agreement {ok.sum() / max(1, same.sum()):.5f}, rel-RMSE {rmse:.2e}")
+        assert same.mean() >= KBUF_AGREE_MIN
+        assert ok.sum() / max(1, same.sum()) >= SHADOW_AGREE_MIN
+        assert rmse <= RMSE_FP32
+    finally:
+        hr.hr_asset_destroy(ctx, a)

@@ -199,3 +199,55 @@ def test_budget_admission(ctx):
         hr.hr_asset_destroy(c2, a)
     finally:
         hr.hr_destroy(c2)
+
+
+def test_served_full_size_asset_vs_oracle(ctx):
+    """A served request on the serving stream's largest asset (100,000 strands
+    x 64 segments, 4,000 clusters) at 1280x720, 4 spp, 8 lights, K = 4, LoD
+    budget 1, FP16 tables, through hr_submit / hr_poll: the served image at 256
+    pixels on the hair and 32 anywhere against the oracle's pixel means."""
+    from gpu_util import hair_pixels
+    w = scenegen.full_head(n=100000, S=64, width=1280, height=720, spp=4, n_clusters=4000,
+                           seed=12, fill=0.3, precision=1)
+    budget = 1
+    a = hr.hr_asset_create(ctx, w.scene.verts, w.scene.mat, w.scene.shape)
+    try:
+        hr.hr_build_clusters(ctx, a, w.n_clusters)
+        d = hr.render_desc(w.camera.pack(), w.lights, w.spp, w.k_depth, w.sample_seed, 1)
+        hr.hr_serve_start(ctx, 2, 1 << 20)
+        try:
+            img = np.zeros((720, 1280, 3), np.float32)
+            t = hr.hr_submit(ctx, a, d, img, w.eps_w, budget)
+            st, res = hr.hr_poll(ctx, t, 120000)
+            assert st == hr.HR_OK and res.status == hr.HR_OK
+        finally:
+            hr.hr_serve_stop(ctx)
+        # the LoD the request rendered: the same selection and budget through the
+        # C ABI, equal to the oracle's outside the band where a width sits within
+        # 1e-4 of epsilon_w
+        C, L, E = hr.hr_hierarchy_info(ctx, a)
+        lod = np.zeros(C, np.uint8)
+        hr.hr_select_lod(ctx, a, w.camera.pack(), w.eps_w, 0, budget, lod)
+        prep = oracle.prepare(w.scene, w.n_clusters, "select", w.camera.pack(), w.eps_w,
+                              budget=budget)
+        if not np.array_equal(prep.lod, lod):
+            wo = oracle.cluster_level_widths(prep.hier, prep.eth, w.camera.pack())
+            near = np.any(np.abs(wo / np.float32(w.eps_w) - 1) < 1e-4, axis=1)
+            assert np.array_equal(prep.lod[~near], lod[~near])
+            prep = oracle.prepare(w.scene, w.n_clusters, lod=lod)
+        st_ = scenegen.Stream(9, 99)
+        pix = np.unique(np.concatenate([hair_pixels(w, 256, 9),
+                                        (st_.u64(32) % np.uint64(1280 * 720)).astype(np.int64)]))
+        sids = scenegen.pixel_samples(1280, w.spp, pix)
+        ro, ho = oracle.render_samples(prep, w.camera.pack(), w.lights, sids, w.spp, w.k_depth,
+                                       w.sample_seed)
+        want = ro.reshape(-1, w.spp, 3).mean(1)
+        got = img.reshape(-1, 3)[pix].astype(np.float64)
+        rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+        print(f"served 100k-strand 720p fp16: {len(pix)} pixels, "
+              f"{int((ho[:, 0] >= 0).sum())} of {len(sids)} samples on hair, levels "
+              f"{np.bincount(lod, minlength=L + 1).tolist()}, rel-RMSE {rel:.2e}")
+        assert (ho[:, 0] >= 0).sum() >= 800
+        assert rel <= RMSE_FP16
+    finally:
+        hr.hr_asset_destroy(ctx, a)
