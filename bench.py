@@ -276,7 +276,9 @@ def measure_config(hr, ctx, torch, dev, w, steps: int, warmup: int = 2, peak_tfl
            "strands": w.scene.n_strands, "segments": w.scene.n_segments,
            "lod": w.lod_setting, "precision": "fp16" if w.precision else "fp32", "k_depth": w.k_depth,
            "active_prims": int(st.n_active_prims), "eth_prims": int(st.n_eth_prims),
-           "traced_samples": int(st.traced_samples), "frame_ms": frame_ms}
+           "traced_samples": int(st.traced_samples), "frame_ms": frame_ms,
+           "prim_tests": int(st.prim_tests), "refined_tests": int(st.refined_tests),
+           "refined_rays": int(st.refined_rays)}
     out["traced_msamples_per_s_frame"] = st.traced_samples / (frame_ms * 1e-3) / 1e6
     if peak_tflops:
         tf = event_flops(st) / (frame_ms * 1e-3) / 1e12
@@ -612,22 +614,28 @@ def main():
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3}
 
     # animated frames: the strands alternate between two poses (a smooth
-    # displacement field of amplitude `amp`), uploaded from pinned memory each
-    # frame; full BVH rebuild against a refit when the LoD (Eq. 14 deferred
-    # selection) is unchanged.  Subtle motion keeps every cluster's level and
-    # the BVH is refit; larger motion moves some of the 4096 clusters across
-    # a level boundary every frame and the frame call rebuilds.
+    # displacement field of amplitude `amp` that grows from 0 at the root, so
+    # roots stay on the scalp), uploaded from pinned memory each frame; full
+    # BVH rebuild against a refit when the clusters and their levels are
+    # unchanged (Eq. 14 deferred selection, with or without the hysteresis
+    # band).  "skinned" is the paper's run time (Section 5.2): the guide-driven
+    # hierarchy is built once, each frame uploads only the guides' poses, and
+    # hr_asset_skin moves strands and thick hairs by their weights (no new
+    # clustering or fit) before the LoD, the BVH and the frame.
     animation = None
     if not args.no_e2e:
         p = w.scene.verts[..., :3].astype(np.float64)
+        grow = np.linspace(0.0, 1.0, w.scene.verts.shape[1])[None, :]
         animation = {"frames": args.e2e_steps * 4}
         for amp in (2e-5, 2e-3):
             moved = np.array(w.scene.verts, copy=True)
-            moved[..., 0] += (amp * np.sin(7.0 * p[..., 1] + 1.3)).astype(np.float32)
-            moved[..., 2] += (amp * np.cos(5.0 * p[..., 0] - 1.3)).astype(np.float32)
+            moved[..., 0] += (amp * grow * np.sin(7.0 * p[..., 1] + 1.3)).astype(np.float32)
+            moved[..., 2] += (amp * grow * np.cos(5.0 * p[..., 0] - 1.3)).astype(np.float32)
             poses = [torch.from_numpy(moved).pin_memory(), pv]
             res = {}
-            for key, flags in (("rebuild", 0), ("refit", hr.HR_FLAG_REFIT | hr.HR_FLAG_DEFERRED_LOD)):
+            for key, flags in (("rebuild", 0), ("refit", hr.HR_FLAG_REFIT | hr.HR_FLAG_DEFERRED_LOD),
+                               ("refit_hysteresis", hr.HR_FLAG_REFIT | hr.HR_FLAG_DEFERRED_LOD |
+                                hr.HR_FLAG_LOD_HYSTERESIS)):
                 da = hr.render_desc(w.camera.pack(), w.lights, w.spp, w.k_depth, w.sample_seed,
                                     w.precision, flags)
                 for i in range(2):  # warm-up
@@ -645,7 +653,43 @@ def main():
                 torch.cuda.synchronize(dev)
                 dt = (time.perf_counter() - t0) / animation["frames"]
                 res[key] = {"ms_per_frame": dt * 1e3, "bvh_ms": statistics.median(bvh),
-                            "bvh_refits": refits}
+                            "bvh_refits": refits, "h2d_bytes_per_frame": pv.numel() * 4}
+            # the guide-driven hierarchy, once, then skinned frames
+            G = 256
+            hr.hr_asset_update(ctx, asset, pv)
+            t0 = time.perf_counter()
+            hr.hr_build_guided_clusters(ctx, asset, G, 4)
+            torch.cuda.synchronize(dev)
+            build_s = time.perf_counter() - t0
+            gid = np.zeros(G, np.int32)
+            hr.hr_guides_export(ctx, asset, gid)
+            gposes = []
+            for vv in (moved, w.scene.verts):
+                gv = np.zeros((G, w.scene.verts.shape[1], 4), np.float32)
+                ok = gid >= 0
+                gv[ok] = vv[gid[ok]]
+                gposes.append(torch.from_numpy(gv).pin_memory())
+            ds = hr.render_desc(w.camera.pack(), w.lights, w.spp, w.k_depth, w.sample_seed,
+                                w.precision, hr.HR_FLAG_KEEP_HIERARCHY | hr.HR_FLAG_REFIT |
+                                hr.HR_FLAG_DEFERRED_LOD | hr.HR_FLAG_LOD_HYSTERESIS)
+            for i in range(2):
+                hr.hr_asset_skin(ctx, asset, gposes[i])
+                hr.hr_render_frame(ctx, asset, 0, w.eps_w, 0, ds, hout)
+            torch.cuda.synchronize(dev)
+            refits, bvh = 0, []
+            t0 = time.perf_counter()
+            for i in range(animation["frames"]):
+                hr.hr_asset_skin(ctx, asset, gposes[i % 2])
+                sa = hr.hr_render_frame(ctx, asset, 0, w.eps_w, 0, ds, hout, stats=True)
+                refits += sa.bvh_refit
+                bvh.append(sa.bvh_ms)
+            torch.cuda.synchronize(dev)
+            dt = (time.perf_counter() - t0) / animation["frames"]
+            C_g, L_g, E_g = hr.hr_hierarchy_info(ctx, asset)
+            res["skinned"] = {"ms_per_frame": dt * 1e3, "bvh_ms": statistics.median(bvh),
+                              "bvh_refits": refits, "h2d_bytes_per_frame": gposes[0].numel() * 4,
+                              "guides": G, "clusters": C_g, "levels": L_g,
+                              "guided_build_ms": build_s * 1e3}
             animation[f"displacement_{amp:g}"] = res
         hr.hr_asset_update(ctx, asset, pv)
 
@@ -696,7 +740,8 @@ def main():
                   "events": {"node_visits": cst.node_visits, "prim_tests": cst.prim_tests,
                              "strand_shades": cst.strand_shades, "eth_shades": cst.eth_shades,
                              "hits": cst.shaded_hits, "traced_samples": cst.traced_samples,
-                             "samples": samples}}
+                             "samples": samples, "refined_tests": cst.refined_tests,
+                             "refined_rays": cst.refined_rays}}
     # FP32 work of the cross-section fit: every strand is a member of one thick
     # hair per level, so the members sum to N * levels over S+1 sections
     C_, L_, E_ = n_levels_info

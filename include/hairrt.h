@@ -142,9 +142,22 @@ typedef struct hr_light {
  *    instead of rebuilding it.  The hits are the same; traversal may slow
  *    down after large motion.  Otherwise the BVH is rebuilt.
  *  - HR_FLAG_DEFERRED_LOD: choose the LoD with Eq. 14 from the previous
- *    frame's selection when there is one (else the initial rule). */
+ *    frame's selection when there is one (else the initial rule).
+ *  - HR_FLAG_LOD_HYSTERESIS (with HR_FLAG_DEFERRED_LOD): Eq. 14 with a band
+ *    around eps_w: refine when w_cur > 1.1 eps_w, coarsen when
+ *    w_cur- <= 0.9 eps_w (each threshold one FP32 product).  Eq. 14 as
+ *    printed changes a cluster's level whenever its width crosses eps_w; the
+ *    paper calls its deferred selection approximately correct, and the band
+ *    keeps the levels of clusters whose widths hover at eps_w under small
+ *    motion, so that animated frames can refit the BVH. */
 #define HR_FLAG_REFIT 512u
 #define HR_FLAG_DEFERRED_LOD 1024u
+#define HR_FLAG_LOD_HYSTERESIS 2048u
+/* hr_render_frame: keep the asset's hierarchy and thick hairs as they are
+ * (built by hr_build_clusters or hr_build_guided_clusters, moved by
+ * hr_asset_skin); n_clusters is ignored.  Section 5.2: at run time the hair
+ * moves by its guides' weights, without a new clustering or fit. */
+#define HR_FLAG_KEEP_HIERARCHY 4096u
 
 typedef struct hr_render_desc {
   hr_camera camera;
@@ -179,6 +192,10 @@ typedef struct hr_stats {
   double bvh_ms;            /* compaction and LBVH (K5, K6), or the refit */
   uint32_t bvh_refit;       /* 1 when hr_render_frame refit the BVH (HR_FLAG_REFIT) */
   uint32_t lod_deferred;    /* 1 when it chose the LoD with Eq. 14 (HR_FLAG_DEFERRED_LOD) */
+  /* filled only with HR_FLAG_COUNT: the precise decision path */
+  uint64_t refined_tests;   /* primitive tests decided precisely (near an outline,
+                               an end, the search cut or another hit) */
+  uint64_t refined_rays;    /* samples whose k-buffer switched to precise ordering */
 } hr_stats;
 
 /* ---------------------------------------------------------------- context */
@@ -238,6 +255,54 @@ hr_status hr_asset_update(hr_ctx* ctx, hr_asset* asset, const float* vertices);
  * order_out: optional, host or device, [N] uint32 strand ids in Morton order. */
 hr_status hr_build_clusters(hr_ctx* ctx, hr_asset* asset, uint32_t n_clusters,
                             uint32_t max_levels, uint32_t* cluster_of_out, uint32_t* order_out);
+/* The paper's own hierarchy (Section 5.1 steps 1, 2 and 4), in place of the
+ * Morton rule of hr_build_clusters:
+ *  1. guide hairs: k-means over the strands with D(i, j) = sum_k
+ *     |p^{i,k} - p^{j,k}|^2 over corresponding vertices (n_guides clusters,
+ *     `iterations` update rounds from the strands at Morton ranks
+ *     floor((2g + 1) N / 2 n_guides), then a final assignment; ties to the
+ *     lower index; an empty cluster keeps its centroid and has no guide);
+ *     each cluster's guide is its medoid (least sum of D to its members);
+ *  2. clusters of the coarsest level: strands sharing their three nearest
+ *     guides (under D), in ascending order of the guide triple, each listing
+ *     its strands by (Morton code of the root, id); level k splits a cluster
+ *     into 4^k rank buckets as hr_build_clusters does (a cluster of fewer
+ *     than 4^k strands leaves buckets empty: such a thick hair has no
+ *     primitives); thick hairs fitted as in hr_build_clusters;
+ *  4. skinning weights: every strand vertex and every thick-hair
+ *     cross-section centre and corner (c +- a e1, c +- b e2) in the
+ *     triangular prism of its cluster's three guides' corresponding points
+ *     (p = g0 + w1 (g1 - g0) + w2 (g2 - g0) + h n, n the triangle's unit
+ *     normal; a degenerate triangle, |e1 x e2| <= 1e-6 |e1| |e2|, keeps the
+ *     offset p - g0), for hr_asset_skin.
+ * D, the centroid sums and the medoid sums are FP32 in vertex order (and in
+ * ascending strand id over members), so the clustering is reproducible.
+ * n_guides: 3..min(1024, N); iterations: 0..1000; max_levels as for
+ * hr_build_clusters.  The number of clusters C depends on the hair
+ * (hr_hierarchy_info).  cluster_of_out, order_out: optional, host or device,
+ * [N] uint32.  HR_EINVAL when fewer than three guide clusters are non-empty. */
+hr_status hr_build_guided_clusters(hr_ctx* ctx, hr_asset* asset, uint32_t n_guides,
+                                   uint32_t iterations, uint32_t max_levels,
+                                   uint32_t* cluster_of_out, uint32_t* order_out);
+/* The guides of hr_build_guided_clusters: guides_out [n_guides] int32, the
+ * guide strand of every k-means cluster (-1 when empty); cluster_guides_out
+ * [n_clusters][3] uint32, the three guides (ascending k-means cluster
+ * indices) of every cluster.  Both optional, host or device. */
+hr_status hr_guides_export(hr_ctx* ctx, hr_asset* asset, int32_t* guides_out,
+                           uint32_t* cluster_guides_out);
+/* Move the hair with its guides (Section 5.2, "Runtime"): guide_vertices
+ * [n_guides][n_segments + 1][4] floats (host or device; xyz of the guide
+ * strand of every k-means cluster, w ignored, rows of empty clusters
+ * unused) carry every strand vertex and every thick-hair cross-section
+ * centre and corner by its weights (FP32; the radius is kept); a
+ * cross-section's a and e1 come from its skinned corners c +- a e1, b and e2
+ * from c +- b e2; the strand and thick-hair records are rebuilt, the
+ * clustering and the fits are not.  Render with HR_FLAG_KEEP_HIERARCHY.
+ * HR_ESTATE without a guide-driven hierarchy. */
+hr_status hr_asset_skin(hr_ctx* ctx, hr_asset* asset, const float* guide_vertices);
+/* The asset's current strand vertices (test export): verts_out [N][S + 1][4]
+ * floats, host or device. */
+hr_status hr_vertex_export(hr_ctx* ctx, hr_asset* asset, float* verts_out);
 /* Number of clusters and thick-hair levels of the built hierarchy. */
 hr_status hr_hierarchy_info(hr_ctx* ctx, hr_asset* asset, uint32_t* n_clusters,
                             uint32_t* n_levels, uint32_t* n_eths);
@@ -261,6 +326,7 @@ hr_status hr_lod_widths(hr_ctx* ctx, hr_asset* asset, const hr_camera* camera, f
  * mode 0: initial rule (Section 5.1 step 5): the coarsest level whose width is
  *         below eps_w_px, else the strands.
  * mode 1: deferred rule, Eq. (14), from the levels in lod_inout.
+ * mode 2: Eq. (14) with the hysteresis band of HR_FLAG_LOD_HYSTERESIS.
  * budget_bias >= 0 then coarsens every cluster: L <- max(0, L - budget_bias).
  * lod_inout: host or device, [n_clusters] uint8 (read in mode 1, written
  * always).  The selection is also kept in the asset for hr_build_bvh. */

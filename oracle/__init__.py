@@ -336,18 +336,32 @@ def build_hierarchy(roots: np.ndarray, n_clusters: int, max_levels: int = 0) -> 
     C = n_clusters
     code = morton30(quantize_roots(roots))
     order = np.lexsort((np.arange(N), code)).astype(np.int64)
+    first = np.array([-(-c * N // C) for c in range(C + 1)], np.int64)  # ceil(c N / C)
+    return hierarchy_from_clusters(N, C, order, code, first, max_levels)
+
+
+def hierarchy_from_clusters(N: int, C: int, order: np.ndarray, code: np.ndarray,
+                            first: np.ndarray, max_levels: int = 0) -> Hierarchy:
+    """The levels of a hierarchy whose cluster c holds the strands of ranks
+    first[c] .. first[c + 1] - 1 of `order`: at level k cluster c of m
+    members splits into 4^k thick hairs, rank-in-cluster i going to
+    floor(i 4^k / m) (a bucket with no member is an empty thick hair when
+    m < 4^k).  Levels: n_eth_levels_for(N, C).
+
+    Pinned through build_hierarchy's and build_guided_hierarchy's tests.
+    """
     rank = np.empty(N, np.int64)
     rank[order] = np.arange(N)
-    cluster = (rank * C) // N
-    first = np.array([-(-c * N // C) for c in range(C + 1)], np.int64)  # ceil(c N / C)
+    cl_of_rank = np.searchsorted(first, np.arange(N), side="right") - 1
+    cluster = cl_of_rank[rank]
     L = n_eth_levels_for(N, C, max_levels)
     eth_of = np.zeros((L, N), np.int64)
     offs = np.zeros(L + 1, np.int64)
     e_first, e_count, e_cluster, e_level = [], [], [], []
+    m = first[1:] - first[:-1]
     for k in range(L):
         offs[k + 1] = offs[k] + C * 4 ** k
         sub_n = 4 ** k
-        m = first[1:] - first[:-1]
         ric = rank - first[cluster]
         sub = (ric * sub_n) // m[cluster]
         eth_of[k] = offs[k] + cluster * sub_n + sub
@@ -483,8 +497,9 @@ def fit_eths(verts: np.ndarray, mat: np.ndarray, hier: Hierarchy, chunk: int = 5
     ntot = hier.eth_count.astype(np.float64)
     radius = np.zeros(E)
     emat = np.zeros((E, mat.shape[1]))
-    for e0 in range(0, E, chunk):
-        ee = np.arange(e0, min(E, e0 + chunk))
+    live = np.nonzero(hier.eth_count > 0)[0]  # an empty thick hair has no fit
+    for e0 in range(0, live.size, chunk):
+        ee = live[e0:e0 + chunk]
         M = int(hier.eth_count[ee].max())
         idx = hier.eth_first_rank[ee][:, None] + np.arange(M)[None, :]
         mask = np.arange(M)[None, :] < hier.eth_count[ee][:, None]
@@ -533,10 +548,12 @@ def fit_eths(verts: np.ndarray, mat: np.ndarray, hier: Hierarchy, chunk: int = 5
         sc = np.where(s > 1.0, s, 1.0)
         center[ee], tangent[ee], E1[ee], E2[ee] = c, t, e1, e2
         A[ee], B[ee] = a * sc, b * sc
-    ax = center[:, 1:] - center[:, :-1]
-    ax = ax / np.linalg.norm(ax, axis=-1, keepdims=True)
-    v = E1[:, :-1] - np.sum(E1[:, :-1] * ax, -1, keepdims=True) * ax
-    seg_e1 = v / np.linalg.norm(v, axis=-1, keepdims=True)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        ax = center[:, 1:] - center[:, :-1]
+        ax = ax / np.linalg.norm(ax, axis=-1, keepdims=True)
+        v = E1[:, :-1] - np.sum(E1[:, :-1] * ax, -1, keepdims=True) * ax
+        seg_e1 = v / np.linalg.norm(v, axis=-1, keepdims=True)
+    seg_e1[hier.eth_count == 0] = 0.0
     seg_a = np.maximum(A[:, :-1], A[:, 1:])
     seg_b = np.maximum(B[:, :-1], B[:, 1:])
     return ETHs(center=center, tangent=tangent, e1=E1, e2=E2, a=A, b=B, seg_e1=seg_e1,
@@ -625,6 +642,8 @@ def cluster_level_widths(hier: Hierarchy, eth: ETHs, cam: np.ndarray) -> np.ndar
     w = cross_section_widths(eth, cam).max(1)
     out = np.zeros((hier.n_clusters, max(1, hier.n_levels)), np.float32)
     for e in range(hier.n_eths):
+        if hier.eth_count[e] == 0:  # an empty thick hair has no width
+            continue
         c = hier.eth_cluster[e]
         L = hier.eth_level[e]
         out[c, L] = max(out[c, L], w[e])
@@ -648,23 +667,28 @@ def select_lod_init(wcl: np.ndarray, eps: float, n_levels: int) -> np.ndarray:
     return lod
 
 
-def select_lod_deferred(wcl: np.ndarray, prev: np.ndarray, eps: float, n_levels: int) -> np.ndarray:
+def select_lod_deferred(wcl: np.ndarray, prev: np.ndarray, eps: float, n_levels: int,
+                        hysteresis: bool = False) -> np.ndarray:
     """Eq. (14): L+1 if w_cur > eps; L if w_cur <= eps < w_cur-; L-1 if
     w_cur- <= eps; cases tested in that order.  READING: w_cur- is +inf at
     L = 0; at the strand level only the coarsening case applies; L stays in
-    [0, n_levels].
+    [0, n_levels].  READING (hysteresis=True, the paper's "approximately
+    correct" deferred selection with a band): refine when w_cur > 1.1 eps and
+    coarsen when w_cur- <= 0.9 eps, each threshold one float32 product.
 
-    Pinned by test_deferred_rule_hand_worked.
+    Pinned by test_deferred_rule_hand_worked and test_deferred_rule_with_hysteresis_hand_worked.
     """
     eps = np.float32(eps)
+    refine = np.float32(eps * np.float32(1.1)) if hysteresis else eps
+    coarsen = np.float32(eps * np.float32(0.9)) if hysteresis else eps
     out = np.array(prev, np.uint8).copy()
     for c in range(wcl.shape[0]):
         L = min(int(prev[c]), n_levels)
         wcur = wcl[c, L] if L < n_levels else -np.inf
         wminus = wcl[c, L - 1] if L > 0 else np.inf
-        if L < n_levels and wcur > eps:
+        if L < n_levels and wcur > refine:
             L += 1
-        elif wminus <= eps:
+        elif wminus <= coarsen:
             L -= 1
         out[c] = L
     return out
@@ -771,7 +795,8 @@ def active_set(n_strands: int, S: int, hier: Optional[Hierarchy], lod: Optional[
         return np.arange(n_strands, dtype=np.int64), np.zeros(0, np.int64)
     lod = np.minimum(np.asarray(lod, np.int64), hier.n_levels)
     st = np.nonzero(lod[hier.cluster_of] == hier.n_levels)[0].astype(np.int64)
-    eh = np.nonzero(lod[hier.eth_cluster] == hier.eth_level)[0].astype(np.int64)
+    eh = np.nonzero((lod[hier.eth_cluster] == hier.eth_level) & (hier.eth_count > 0))[0]
+    eh = eh.astype(np.int64)
     return st, eh
 
 
@@ -854,3 +879,7 @@ def render_samples(prep: Prepared, cam: np.ndarray, lights: np.ndarray, samples:
     if rc != 0:
         raise RuntimeError(f"oracle_render failed with {rc}")
     return rad, hit
+
+
+from .guides import (build_guided_hierarchy, guide_kmeans, nearest_guides,  # noqa: E402,F401
+                     prism_weights, skin_points, strand_distance)

@@ -39,6 +39,8 @@ HR_FLAG_TRT = 8
 HR_FLAG_COUNT = 256
 HR_FLAG_REFIT = 512
 HR_FLAG_DEFERRED_LOD = 1024
+HR_FLAG_LOD_HYSTERESIS = 2048
+HR_FLAG_KEEP_HIERARCHY = 4096
 
 
 class HairRTError(RuntimeError):
@@ -76,7 +78,8 @@ class hr_stats(ctypes.Structure):
                 ("eth_shades", c_u64), ("shaded_hits", c_u64), ("traced_samples", c_u64),
                 ("hierarchy_ms", ctypes.c_double), ("fit_ms", ctypes.c_double),
                 ("lod_ms", ctypes.c_double), ("bvh_ms", ctypes.c_double),
-                ("bvh_refit", c_u32), ("lod_deferred", c_u32)]
+                ("bvh_refit", c_u32), ("lod_deferred", c_u32),
+                ("refined_tests", c_u64), ("refined_rays", c_u64)]
 
 
 class hr_request(ctypes.Structure):
@@ -109,6 +112,10 @@ _SIGS = {
     "hr_bvh_export": (c_int, [P, P, P, ctypes.POINTER(c_u32)]),
     "hr_sort_pairs": (c_int, [P, P, P, c_u32, c_u32, c_int]),
     "hr_table_export": (c_int, [P, P, P, ctypes.POINTER(c_u32), ctypes.POINTER(c_u32)]),
+    "hr_build_guided_clusters": (c_int, [P, P, c_u32, c_u32, c_u32, P, P]),
+    "hr_guides_export": (c_int, [P, P, P, P]),
+    "hr_asset_skin": (c_int, [P, P, P]),
+    "hr_vertex_export": (c_int, [P, P, P]),
     "hr_im_lookup": (c_int, [P, P, P, c_u32, c_int, P]),
     "hr_render": (c_int, [P, P, ctypes.POINTER(hr_render_desc), P, ctypes.POINTER(hr_stats)]),
     "hr_render_samples": (c_int, [P, P, ctypes.POINTER(hr_render_desc), P, c_u32, P, P]),
@@ -311,6 +318,29 @@ def hr_im_lookup(ctx: int, theta, beta, out, precision: int = 0) -> None:
     m = int(theta.shape[0])
     _check(ctx, load().hr_im_lookup(ctx, ptr(theta), ptr(beta), m, precision, ptr(out)),
            "hr_im_lookup")
+
+
+def hr_build_guided_clusters(ctx: int, asset: int, n_guides: int, iterations: int = 8,
+                             max_levels: int = 0, cluster_of_out=None, order_out=None) -> None:
+    """Guide k-means, clusters of strands sharing their three nearest guides,
+    thick-hair fits and skinning weights (Section 5.1)."""
+    _check(ctx, load().hr_build_guided_clusters(ctx, asset, n_guides, iterations, max_levels,
+                                                ptr(cluster_of_out), ptr(order_out)),
+           "hr_build_guided_clusters")
+
+
+def hr_guides_export(ctx: int, asset: int, guides_out=None, cluster_guides_out=None) -> None:
+    _check(ctx, load().hr_guides_export(ctx, asset, ptr(guides_out), ptr(cluster_guides_out)),
+           "hr_guides_export")
+
+
+def hr_asset_skin(ctx: int, asset: int, guide_vertices) -> None:
+    """Move the hair with new guide vertices [n_guides, S+1, 4] (Section 5.2)."""
+    _check(ctx, load().hr_asset_skin(ctx, asset, ptr(guide_vertices)), "hr_asset_skin")
+
+
+def hr_vertex_export(ctx: int, asset: int, verts_out) -> None:
+    _check(ctx, load().hr_vertex_export(ctx, asset, ptr(verts_out)), "hr_vertex_export")
 
 
 def hr_bvh_export(ctx: int, asset: int, leaf_ids=None) -> int:

@@ -140,9 +140,13 @@ hr_status to_device(hr_ctx* ctx, void* dst, const void* src, size_t bytes, cudaS
 FrameArgs frame_args(hr_ctx* ctx, hr_asset* a, const Bvh& bv, const hr_render_desc& d) {
   FrameArgs fa{};
   fa.nodes = bv.nodes;
-  fa.leaf_xf = bv.leaf_xf;
-  fa.leaf_aux = bv.leaf_aux;
+  fa.prim_xf = a->prim_xf;
+  fa.prim_aux = a->prim_aux;
   fa.leaf_id = bv.leaf_id;
+  fa.verts = a->verts;
+  fa.xsec = a->xsec;
+  fa.N = a->N;
+  fa.S = a->S;
   fa.mat = a->mat;
   fa.n_prims = bv.n;
   fa.tables = ctx_tables(ctx);
@@ -343,6 +347,7 @@ hr_status hr_asset_destroy(hr_ctx* ctx, hr_asset* a) {
   if (a->cl_first) dfree(ctx, a->cl_first, (size_t)(a->C + 1) * 4);
   if (a->xsec) dfree(ctx, a->xsec, (size_t)a->E * S1 * 3 * sizeof(float4));
   if (a->lod) dfree(ctx, a->lod, a->C);
+  drop_guides(ctx, a);
   const uint64_t P = a->n_prims_total;
   if (a->prim_xf) dfree(ctx, a->prim_xf, P * 3 * sizeof(float4));
   if (a->prim_box) dfree(ctx, a->prim_box, P * 2 * sizeof(float4));
@@ -358,6 +363,8 @@ hr_status hr_build_clusters(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_l
   API_ENTER(ctx);
   if (!a) return set_error(ctx, HR_EINVAL, "null asset");
   if (C < 1 || C > a->N || C > (1u << 20)) return set_error(ctx, HR_EINVAL, "n_clusters out of range");
+  // served BVHs of this asset reference its primitive records, rewritten here
+  if (ctx->server) serve_forget_asset(ctx, ctx->server, a);
   HR_TRY(build_hierarchy(ctx, a, C, max_levels));
   cudaStream_t st = ctx->stream;
   if (cluster_of_out) {
@@ -370,6 +377,75 @@ hr_status hr_build_clusters(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_l
     HR_CUDA(ctx, cudaMemcpyAsync(order_out, a->order, (size_t)a->N * 4,
                                  dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   }
+  HR_CUDA(ctx, cudaStreamSynchronize(st));
+  return HR_OK;
+}
+
+hr_status hr_build_guided_clusters(hr_ctx* ctx, hr_asset* a, uint32_t n_guides, uint32_t iterations,
+                                   uint32_t max_levels, uint32_t* cluster_of_out,
+                                   uint32_t* order_out) {
+  API_ENTER(ctx);
+  if (!a) return set_error(ctx, HR_EINVAL, "null asset");
+  if (iterations > 1000) return set_error(ctx, HR_EINVAL, "iterations out of 0..1000");
+  if (ctx->server) serve_forget_asset(ctx, ctx->server, a);
+  HR_TRY(build_guided_hierarchy(ctx, a, n_guides, iterations, max_levels));
+  cudaStream_t st = ctx->stream;
+  if (cluster_of_out)
+    HR_CUDA(ctx, cudaMemcpyAsync(cluster_of_out, a->cluster_of, (size_t)a->N * 4,
+                                 is_device_ptr(cluster_of_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  if (order_out)
+    HR_CUDA(ctx, cudaMemcpyAsync(order_out, a->order, (size_t)a->N * 4,
+                                 is_device_ptr(order_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  HR_CUDA(ctx, cudaStreamSynchronize(st));
+  return HR_OK;
+}
+
+hr_status hr_guides_export(hr_ctx* ctx, hr_asset* a, int32_t* guides_out,
+                           uint32_t* cluster_guides_out) {
+  API_ENTER(ctx);
+  if (!a) return set_error(ctx, HR_EINVAL, "null asset");
+  if (a->G == 0) return set_error(ctx, HR_ESTATE, "no guides: call hr_build_guided_clusters");
+  cudaStream_t st = ctx->stream;
+  if (guides_out)
+    HR_CUDA(ctx, cudaMemcpyAsync(guides_out, a->guides, (size_t)a->G * 4,
+                                 is_device_ptr(guides_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  if (cluster_guides_out) {
+    std::vector<uint32_t> key(a->C), tri((size_t)a->C * 3);
+    HR_CUDA(ctx, cudaMemcpyAsync(key.data(), a->cl_tri, (size_t)a->C * 4, cudaMemcpyDeviceToHost, st));
+    HR_CUDA(ctx, cudaStreamSynchronize(st));
+    for (uint32_t c = 0; c < a->C; ++c) {
+      tri[3 * c] = key[c] >> 20;
+      tri[3 * c + 1] = (key[c] >> 10) & 1023u;
+      tri[3 * c + 2] = key[c] & 1023u;
+    }
+    HR_CUDA(ctx, cudaMemcpyAsync(cluster_guides_out, tri.data(), tri.size() * 4,
+                                 is_device_ptr(cluster_guides_out) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, st));
+  }
+  HR_CUDA(ctx, cudaStreamSynchronize(st));
+  return HR_OK;
+}
+
+hr_status hr_asset_skin(hr_ctx* ctx, hr_asset* a, const float* guide_vertices) {
+  API_ENTER(ctx);
+  if (!a || !guide_vertices) return set_error(ctx, HR_EINVAL, "hr_asset_skin: null argument");
+  if (a->G == 0 || !a->w_strand || a->guided_C != a->C || a->guided_E != a->E)
+    return set_error(ctx, HR_ESTATE, "no guide-driven hierarchy: call hr_build_guided_clusters");
+  if (ctx->server) serve_forget_asset(ctx, ctx->server, a);
+  cudaStream_t st = ctx->stream;
+  const size_t bytes = (size_t)a->G * (a->S + 1) * sizeof(float4);
+  float4* gv = nullptr;
+  HR_TRY(scratch(ctx, 62, bytes, (void**)&gv));
+  HR_TRY(to_device(ctx, gv, guide_vertices, bytes, st));
+  HR_TRY(skin_asset(ctx, a, gv));
+  return HR_OK;
+}
+
+hr_status hr_vertex_export(hr_ctx* ctx, hr_asset* a, float* verts_out) {
+  API_ENTER(ctx);
+  if (!a || !verts_out) return set_error(ctx, HR_EINVAL, "null argument");
+  cudaStream_t st = ctx->stream;
+  HR_CUDA(ctx, cudaMemcpyAsync(verts_out, a->verts, (size_t)a->N * (a->S + 1) * sizeof(float4),
+                               is_device_ptr(verts_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   HR_CUDA(ctx, cudaStreamSynchronize(st));
   return HR_OK;
 }
@@ -442,11 +518,11 @@ hr_status hr_select_lod(hr_ctx* ctx, hr_asset* a, const hr_camera* cam, float ep
   API_ENTER(ctx);
   if (!a || !cam) return set_error(ctx, HR_EINVAL, "null argument");
   if (a->n_levels == 0) return set_error(ctx, HR_ESTATE, "no thick-hair levels: call hr_build_clusters");
-  if ((mode != 0 && mode != 1) || bias < 0) return set_error(ctx, HR_EINVAL, "mode / bias");
-  if (mode == 1 && !lod_inout) return set_error(ctx, HR_EINVAL, "deferred mode needs lod_inout");
+  if (mode < 0 || mode > 2 || bias < 0) return set_error(ctx, HR_EINVAL, "mode / bias");
+  if (mode >= 1 && !lod_inout) return set_error(ctx, HR_EINVAL, "deferred mode needs lod_inout");
   cudaStream_t st = ctx->stream;
   uint8_t* prev = nullptr;
-  if (mode == 1) {
+  if (mode >= 1) {
     HR_TRY(scratch(ctx, 41, a->C, (void**)&prev));
     HR_TRY(to_device(ctx, prev, lod_inout, a->C, st));
   }
@@ -588,6 +664,8 @@ static hr_status render_impl(hr_ctx* ctx, hr_asset* a, const hr_render_desc* des
     stats->eth_shades = cnt[3];
     stats->shaded_hits = cnt[4];
     stats->traced_samples = cnt[5];
+    stats->refined_tests = cnt[6];
+    stats->refined_rays = cnt[7];
   } else if (!dev_out) {
     HR_CUDA(ctx, cudaStreamSynchronize(st));
   }
@@ -646,17 +724,22 @@ hr_status hr_render_frame(hr_ctx* ctx, hr_asset* a, uint32_t n_clusters, float e
   cudaEvent_t* ph = ctx->ph;
   if (stats) HR_CUDA(ctx, cudaEventRecord(ph[0], st));
   bool fit_ran = false;
-  if (n_clusters > 0) {
+  const bool keep = (desc->flags & HR_FLAG_KEEP_HIERARCHY) != 0;
+  if (keep) {
+    if (a->C == 0) return set_error(ctx, HR_ESTATE, "HR_FLAG_KEEP_HIERARCHY: no hierarchy built");
+  } else if (n_clusters > 0) {
     if (n_clusters > a->N) return set_error(ctx, HR_EINVAL, "n_clusters out of range");
     HR_TRY(build_hierarchy(ctx, a, n_clusters, 0, stats ? ph[1] : nullptr,
                            stats ? ph[2] : nullptr));
     fit_ran = a->E > 0;
   }
+  const bool clustered = keep || n_clusters > 0;
   if (stats) HR_CUDA(ctx, cudaEventRecord(ph[3], st));
   const bool deferred = (desc->flags & HR_FLAG_DEFERRED_LOD) && a->lod_valid;
-  if (n_clusters > 0 && a->n_levels > 0) {
+  if (clustered && a->n_levels > 0) {
     // Eq. 14 reads the previous selection and writes the new one in place
-    HR_TRY(lod_select(ctx, a, &desc->camera, eps_w_px, deferred ? 1 : 0, budget_bias,
+    const int mode = !deferred ? 0 : ((desc->flags & HR_FLAG_LOD_HYSTERESIS) ? 2 : 1);
+    HR_TRY(lod_select(ctx, a, &desc->camera, eps_w_px, mode, budget_bias,
                       deferred ? a->lod : nullptr, a->lod, st));
     a->lod_valid = 1;
     lod_dev = a->lod;
@@ -681,7 +764,7 @@ hr_status hr_render_frame(hr_ctx* ctx, hr_asset* a, uint32_t n_clusters, float e
     stats->lod_ms = l;
     stats->bvh_ms = b;
     stats->bvh_refit = refit ? 1u : 0u;
-    stats->lod_deferred = deferred && n_clusters > 0 && a->n_levels > 0 ? 1u : 0u;
+    stats->lod_deferred = deferred && clustered && a->n_levels > 0 ? 1u : 0u;
   }
   return HR_OK;
 }

@@ -36,8 +36,11 @@ __global__ void k_cluster_counts(const uint8_t* __restrict__ lod, const uint32_t
   const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
   const uint32_t l = min((uint32_t)lod[c], L);
-  counts[c] = (l == L) ? (cl_first[c + 1] - cl_first[c]) * S : (1u << (2 * l)) * S;
-  if (l < L) atomicAdd(counts + C + 1, (1u << (2 * l)) * S);
+  const uint32_t m = cl_first[c + 1] - cl_first[c];
+  // a cluster of m < 4^l strands has m non-empty level-l thick hairs
+  const uint32_t eths = min(1u << (2 * l), m);
+  counts[c] = (l == L) ? m * S : eths * S;
+  if (l < L) atomicAdd(counts + C + 1, eths * S);
 }
 
 __global__ void k_cluster_fill(const uint8_t* __restrict__ lod, const uint32_t* __restrict__ cl_first,
@@ -56,8 +59,17 @@ __global__ void k_cluster_fill(const uint8_t* __restrict__ lod, const uint32_t* 
   } else {
     const uint32_t sub = 1u << (2 * l);
     const uint32_t e0 = eth_off[l] + c * sub;
-    for (uint32_t j = threadIdx.x; j < sub * S; j += blockDim.x)
-      ids[base + j] = N * S + (e0 + j / S) * S + j % S;
+    const uint32_t m = cl_first[c + 1] - cl_first[c];
+    if (m >= sub) {
+      for (uint32_t j = threadIdx.x; j < sub * S; j += blockDim.x)
+        ids[base + j] = N * S + (e0 + j / S) * S + j % S;
+    } else {
+      // fewer strands than buckets: member i alone fills bucket floor(i 4^l / m)
+      for (uint32_t j = threadIdx.x; j < m * S; j += blockDim.x) {
+        const uint32_t b = (uint32_t)(((uint64_t)(j / S) * sub) / m);
+        ids[base + j] = N * S + (e0 + b) * S + j % S;
+      }
+    }
   }
 }
 
@@ -154,18 +166,10 @@ __global__ void k_karras(const uint32_t* __restrict__ keys, int n, int4* child,
   child[i] = make_int4(c0, c1, lo, hi);  // children and the node's leaf range
 }
 
-// Gather leaf records in Morton order.
-__global__ void k_gather(const uint32_t* __restrict__ sorted_ids, uint32_t n,
-                         const float4* __restrict__ xf, const float4* __restrict__ aux,
-                         float4* leaf_xf, float4* leaf_aux, uint32_t* leaf_id) {
+// The global primitive id of every leaf (Morton order).
+__global__ void k_gather(const uint32_t* __restrict__ sorted_ids, uint32_t n, uint32_t* leaf_id) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint32_t id = sorted_ids[i];
-  leaf_xf[3 * (size_t)i] = xf[3 * (size_t)id];
-  leaf_xf[3 * (size_t)i + 1] = xf[3 * (size_t)id + 1];
-  leaf_xf[3 * (size_t)i + 2] = xf[3 * (size_t)id + 2];
-  leaf_aux[i] = aux[id];
-  leaf_id[i] = id;
+  if (i < n) leaf_id[i] = sorted_ids[i];
 }
 
 __device__ __forceinline__ void node_union(const float4* nodes, int c, float* b) {
@@ -232,10 +236,11 @@ __device__ __forceinline__ void append_start(bool has, int v, unsigned* count, i
   if (has) list[base + __popc(m & ((1u << lane) - 1u))] = v;
 }
 
-// Leaf gather and bottom-up bounds in one kernel.  Thread j of block b owns
-// leaf b0 + j and internal node b0 + j (b0 = b * B).
-//  1. Gather: each thread copies its leaf's record into Morton order and
-//     keeps the leaf box in shared memory.
+// Leaf boxes and bottom-up bounds in one kernel.  Thread j of block b owns
+// leaf b0 + j and internal node b0 + j (b0 = b * B).  A node record names a
+// leaf child by ~(its global primitive id), so the frame kernel reads the
+// primitive's records where they are (no copy into leaf order).
+//  1. Gather: each thread reads its leaf's box (and id) into shared memory.
 //  2. Local subtrees: node i's leaf range starts or ends at leaf i, so a node
 //     whose range lies inside the block's leaves ("local") is owned by a
 //     thread of the block and so are its children.  These are finished in
@@ -250,10 +255,10 @@ template <int B>
 __global__ void __launch_bounds__(B) k_gather_refit(
     const int4* __restrict__ child, const int* __restrict__ parent_int,
     const int* __restrict__ parent_leaf, const float4* __restrict__ box,
-    const uint32_t* __restrict__ sorted_ids, const float4* __restrict__ xf,
-    const float4* __restrict__ aux, int n, float4* nodes, float4* lbox, float4* leaf_xf,
-    float4* leaf_aux, uint32_t* leaf_id, unsigned* n_starts, int* starts) {
+    const uint32_t* sorted_ids, int n, float4* nodes, float4* lbox, uint32_t* leaf_id,
+    unsigned* n_starts, int* starts) {
   __shared__ int4 s_child[B];
+  __shared__ uint32_t s_id[B];  // global primitive id of each of the block's leaves
   __shared__ float s_lbox[B][6];  // leaf boxes (lo.x, hi.x, lo.y, hi.y, lo.z, hi.z)
   __shared__ float s_nbox[B][6];  // unions of the block's local nodes
   __shared__ unsigned char s_done[B];
@@ -271,16 +276,11 @@ __global__ void __launch_bounds__(B) k_gather_refit(
   int lparent = -1;
   if (leaf < n) {
     const uint32_t id = sorted_ids[leaf];
-    const float4 r0 = xf[3 * (size_t)id], r1 = xf[3 * (size_t)id + 1], r2 = xf[3 * (size_t)id + 2];
-    const float4 ax = aux[id];
     bl = box[2 * (size_t)id];
     bh = box[2 * (size_t)id + 1];
     lparent = parent_leaf[leaf];
-    leaf_xf[3 * (size_t)leaf] = r0;
-    leaf_xf[3 * (size_t)leaf + 1] = r1;
-    leaf_xf[3 * (size_t)leaf + 2] = r2;
-    leaf_aux[leaf] = ax;
     leaf_id[leaf] = id;
+    s_id[j] = id;
     s_lbox[j][0] = bl.x; s_lbox[j][1] = bh.x; s_lbox[j][2] = bl.y;
     s_lbox[j][3] = bh.y; s_lbox[j][4] = bl.z; s_lbox[j][5] = bh.z;
   }
@@ -300,7 +300,10 @@ __global__ void __launch_bounds__(B) k_gather_refit(
         c0[q] = p0[q];
         c1[q] = p1[q];
       }
-      store_node(nodes, node, ch, c0, c1);
+      // a leaf child is named by its primitive id (the leaf lies in this block)
+      const int4 chp = make_int4(ch.x < 0 ? ~(int)s_id[~ch.x - b0] : ch.x,
+                                 ch.y < 0 ? ~(int)s_id[~ch.y - b0] : ch.y, ch.z, ch.w);
+      store_node(nodes, node, chp, c0, c1);
       s_nbox[j][0] = fminf(c0[0], c1[0]);
       s_nbox[j][1] = fmaxf(c0[1], c1[1]);
       s_nbox[j][2] = fminf(c0[2], c1[2]);
@@ -324,7 +327,9 @@ __global__ void __launch_bounds__(B) k_gather_refit(
     __stcg(o, e);
     __stcg(o + 1, e);
     __stcg(o + 2, e);
-    __stcg(o + 3, make_float4(__int_as_float(ch.x), __int_as_float(ch.y), 0.f, 0.f));
+    const int c0 = ch.x < 0 ? ~(int)sorted_ids[~ch.x] : ch.x;
+    const int c1 = ch.y < 0 ? ~(int)sorted_ids[~ch.y] : ch.y;
+    __stcg(o + 3, make_float4(__int_as_float(c0), __int_as_float(c1), 0.f, 0.f));
   }
   bool start_leaf = false, start_node = false;
   if (leaf < n && lparent >= 0) {
@@ -407,9 +412,8 @@ hr_status gather_refit(hr_ctx* ctx, hr_asset* a, Bvh& bv, const uint32_t* ids, c
   HR_TRY(scratch(ctx, 48, (size_t)n * 2 * 4, (void**)&starts));
   HR_CUDA(ctx, cudaMemsetAsync(n_starts, 0, 4, st));
   k_gather_refit<256><<<(n + 255) / 256, 256, 0, st>>>(bv.child, bv.par_int, bv.par_leaf,
-                                                       a->prim_box, ids, a->prim_xf, a->prim_aux,
-                                                       (int)n, bv.nodes, lbox, bv.leaf_xf,
-                                                       bv.leaf_aux, bv.leaf_id, n_starts, starts);
+                                                       a->prim_box, ids, (int)n, bv.nodes, lbox,
+                                                       bv.leaf_id, n_starts, starts);
   HR_LAUNCHED(ctx);
   static int climb_grid = 0;
   if (!climb_grid) {
@@ -433,8 +437,6 @@ hr_status gather_refit(hr_ctx* ctx, hr_asset* a, Bvh& bv, const uint32_t* ids, c
 void free_bvh(hr_ctx* ctx, Bvh& bv) {
   if (bv.cap) {
     dfree(ctx, bv.nodes, (size_t)std::max(bv.cap, 2u) * 4 * sizeof(float4));
-    dfree(ctx, bv.leaf_xf, (size_t)bv.cap * 3 * sizeof(float4));
-    dfree(ctx, bv.leaf_aux, (size_t)bv.cap * sizeof(float4));
     dfree(ctx, bv.leaf_id, (size_t)bv.cap * 4);
     dfree(ctx, bv.child, (size_t)bv.cap * sizeof(int4));
     dfree(ctx, bv.par_int, (size_t)bv.cap * 4);
@@ -483,8 +485,6 @@ hr_status build_bvh(hr_ctx* ctx, hr_asset* a, const uint8_t* lod_dev, Bvh& bv, c
       free_bvh(ctx, bv);
     }
     HR_TRY(dalloc(ctx, (void**)&bv.nodes, (size_t)std::max(n, 2u) * 4 * sizeof(float4), "BVH nodes"));
-    HR_TRY(dalloc(ctx, (void**)&bv.leaf_xf, (size_t)n * 3 * sizeof(float4), "BVH leaf records"));
-    HR_TRY(dalloc(ctx, (void**)&bv.leaf_aux, (size_t)n * sizeof(float4), "BVH leaf aux"));
     HR_TRY(dalloc(ctx, (void**)&bv.leaf_id, (size_t)n * 4, "BVH leaf ids"));
     HR_TRY(dalloc(ctx, (void**)&bv.child, (size_t)n * sizeof(int4), "BVH children"));
     HR_TRY(dalloc(ctx, (void**)&bv.par_int, (size_t)n * 4, "BVH parents"));
@@ -492,7 +492,8 @@ hr_status build_bvh(hr_ctx* ctx, hr_asset* a, const uint8_t* lod_dev, Bvh& bv, c
     bv.cap = n;
   }
   bv.n = n;
-  // what the topology is built for (checked by refit_bvh)
+  // what the topology is built for (checked by refit_bvh); the hierarchy as it is now
+  HR_CUDA(ctx, cudaMemsetAsync(a->d_bounds + kHierChanged, 0, 4, st));
   bv.topo = 0;
   bv.built_C = a->C;
   bv.built_E = a->E;
@@ -522,8 +523,7 @@ hr_status build_bvh(hr_ctx* ctx, hr_asset* a, const uint8_t* lod_dev, Bvh& bv, c
   HR_LAUNCHED(ctx);
   HR_TRY(radix_sort_pairs(ctx, keys, ids, k2, v2, n, kMortonBits, st));
   if (n == 1) {
-    k_gather<<<1, 32, 0, st>>>(ids, n, a->prim_xf, a->prim_aux, bv.leaf_xf, bv.leaf_aux,
-                               bv.leaf_id);
+    k_gather<<<1, 32, 0, st>>>(ids, n, bv.leaf_id);
     HR_LAUNCHED(ctx);
     bv.valid = 1;
     bv.topo = 1;
@@ -542,26 +542,27 @@ hr_status refit_bvh(hr_ctx* ctx, hr_asset* a, const uint8_t* lod_dev, Bvh& bv, c
   if (!bv.topo || bv.built_C != a->C || bv.built_E != a->E || bv.built_total != a->n_prims_total ||
       bv.built_with_lod != (lod_dev != nullptr))
     return set_error(ctx, HR_ESTATE, "refit: the BVH was built for another hierarchy");
-  if (lod_dev) {
+  {
+    // one read-back: the LoD selection against the build's, and whether a
+    // hierarchy build changed the strand order since
     uint32_t* diff = nullptr;
-    HR_TRY(scratch(ctx, 36, 4, (void**)&diff));
+    HR_TRY(scratch(ctx, 36, 8, (void**)&diff));
     HR_CUDA(ctx, cudaMemsetAsync(diff, 0, 4, st));
-    k_bytes_differ<<<(a->C + 255) / 256, 256, 0, st>>>(lod_dev, bv.lod_built, a->C, diff);
-    HR_LAUNCHED(ctx);
-    uint32_t h = 0;
-    HR_CUDA(ctx, cudaMemcpyAsync(&h, diff, 4, cudaMemcpyDeviceToHost, st));
+    if (lod_dev) {
+      k_bytes_differ<<<(a->C + 255) / 256, 256, 0, st>>>(lod_dev, bv.lod_built, a->C, diff);
+      HR_LAUNCHED(ctx);
+    }
+    HR_CUDA(ctx, cudaMemcpyAsync(diff + 1, a->d_bounds + kHierChanged, 4, cudaMemcpyDeviceToDevice, st));
+    uint32_t h[2] = {0, 0};
+    HR_CUDA(ctx, cudaMemcpyAsync(h, diff, 8, cudaMemcpyDeviceToHost, st));
     HR_CUDA(ctx, cudaStreamSynchronize(st));
-    if (h) return set_error(ctx, HR_ESTATE, "refit: the LoD selection changed since the build");
+    if (h[0]) return set_error(ctx, HR_ESTATE, "refit: the LoD selection changed since the build");
+    if (h[1]) return set_error(ctx, HR_ESTATE, "refit: the strand order changed since the build");
   }
   bv.valid = 0;
   const uint32_t n = bv.n;
-  if (n == 1) {
-    k_gather<<<1, 32, 0, st>>>(bv.leaf_id, n, a->prim_xf, a->prim_aux, bv.leaf_xf, bv.leaf_aux,
-                               bv.leaf_id);
-    HR_LAUNCHED(ctx);
-  } else if (n > 1) {
-    HR_TRY(gather_refit(ctx, a, bv, bv.leaf_id, st));
-  }
+  // a single leaf has no node; its records are the primitive's own
+  if (n > 1) HR_TRY(gather_refit(ctx, a, bv, bv.leaf_id, st));
   bv.valid = 1;
   return HR_OK;
 }

@@ -32,10 +32,8 @@ struct Tables {
 struct Bvh {
   uint32_t n = 0;           // active primitives (leaves)
   uint32_t cap = 0;         // allocated leaves
-  float4* nodes = nullptr;  // [(n-1) * 4]; see trace.cu for the layout
-  float4* leaf_xf = nullptr;   // [n * 3] world -> unit-cylinder rows, leaf order
-  float4* leaf_aux = nullptr;  // [n] (material index bits, n_tot, r, a*b)
-  uint32_t* leaf_id = nullptr; // [n] global primitive id
+  float4* nodes = nullptr;  // [(n-1) * 4]; a leaf child is ~(global primitive id)
+  uint32_t* leaf_id = nullptr; // [n] global primitive id of every leaf, Morton order
   uint32_t n_eth = 0;
   int valid = 0;               // bounds and leaf records match the primitives
   // topology kept for refits: children + leaf range, parents; the LoD and
@@ -78,12 +76,20 @@ struct hr_asset {
   float4* prim_xf = nullptr;   // [P_total * 3]
   float4* prim_box = nullptr;  // [P_total * 2]
   float4* prim_aux = nullptr;  // [P_total]
-  uint32_t* d_bounds = nullptr;  // [8] strand boxes' bounds, ordered float bits (lo xyz, hi xyz)
+  uint32_t* d_bounds = nullptr;  // [8] strand boxes' bounds, ordered float bits (lo xyz, hi xyz);
+                                 // word kHierChanged: the strand order changed since the last BVH build
   // LoD
   uint8_t* lod = nullptr;  // [C] current selection on the device
   int lod_valid = 0;
   hr::Bvh bvh;
   size_t bytes = 0;
+  // guide-driven hierarchy and skinning (hr_build_guided_clusters)
+  uint32_t G = 0;                 // k-means clusters; 0: no guides
+  int32_t* guides = nullptr;      // [G] guide strand of every k-means cluster, -1 when empty
+  uint32_t* cl_tri = nullptr;     // [C] the three guides of every cluster, 10 bits each
+  float4* w_strand = nullptr;     // [N * (S + 1)] prism weights of the strand vertices
+  float4* w_eth = nullptr;        // [E * (S + 1) * 5] of thick-hair centres and corners
+  uint32_t guided_C = 0, guided_E = 0;  // shape the weights were taken for
 };
 
 namespace hr {
@@ -158,6 +164,10 @@ hr_status update_strands(hr_ctx* ctx, hr_asset* a, const float4* src_dev);
 // page-locked host memory), or nullptr
 const void* device_view(const void* p);
 
+// Word of hr_asset::d_bounds set by a hierarchy build that changed the strand
+// order (or the hierarchy) and cleared by a BVH build: a refit is then invalid.
+constexpr int kHierChanged = 6;
+
 // Float <-> unsigned with the same order (atomic min / max of floats).
 __device__ __forceinline__ uint32_t ordered_bits(float f) {
   const uint32_t u = __float_as_uint(f);
@@ -168,6 +178,31 @@ __device__ __forceinline__ float from_ordered(uint32_t u) {
 }
 hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_levels,
                           cudaEvent_t fit_begin = nullptr, cudaEvent_t fit_end = nullptr);
+// The roots' Morton codes (sorted, into codes) and the strands in (code, id)
+// order (into order), both [N] device.
+hr_status root_morton_order(hr_ctx* ctx, hr_asset* a, uint32_t* codes, uint32_t* order,
+                            cudaStream_t st);
+// The levels, fits and records of a hierarchy given by its strand order and
+// cluster starts (device, [N] and [C + 1]).
+hr_status build_hierarchy_from(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_levels,
+                               const uint32_t* order_dev, const uint32_t* cl_first_dev);
+
+// The thick-hair materials and segment records from the current
+// cross-sections (after skinning moved them; no new fit).
+hr_status rebuild_eth_records(hr_ctx* ctx, hr_asset* a);
+
+// --- guides.cu
+// Free the guide-driven state of an asset (its hierarchy is being replaced).
+void drop_guides(hr_ctx* ctx, hr_asset* a);
+// Guides by k-means (G clusters, `iters` update rounds), clusters of strands
+// sharing their three nearest guides, the hierarchy's levels, fits and
+// records, and the skinning weights of strand vertices and thick-hair
+// centres and corners.
+hr_status build_guided_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t G, uint32_t iters,
+                                 uint32_t max_levels);
+// Move the strands and thick hairs with the guides' new vertices gv_dev
+// [G][S + 1] (device) by the skinning weights, and rebuild their records.
+hr_status skin_asset(hr_ctx* ctx, hr_asset* a, const float4* gv_dev);
 
 // --- lod.cu
 hr_status lod_widths(hr_ctx* ctx, hr_asset* a, const hr_camera* cam, float* wcl_dev,
@@ -200,10 +235,13 @@ struct LaunchLights {
   float4 rgb[HR_MAX_LIGHTS];
 };
 struct FrameArgs {
-  const float4* nodes;
-  const float4* leaf_xf;
-  const float4* leaf_aux;
-  const uint32_t* leaf_id;
+  const float4* nodes;     // BVH nodes; a leaf child is ~(global primitive id)
+  const float4* prim_xf;   // [P_total * 3] world -> unit-cylinder rows, by global id
+  const float4* prim_aux;  // [P_total] (material index bits, n_tot, r, a*b)
+  const uint32_t* leaf_id; // the single leaf's id when the BVH has one leaf
+  const float4* verts;     // strand vertices and thick-hair cross-sections: the
+  const float4* xsec;      // segments' start points for FP64 decisions
+  uint32_t N, S;           // strands, segments per strand
   const float* mat;
   uint32_t n_prims;
   Tables tables;
@@ -247,13 +285,42 @@ hr_status launch_samples(hr_ctx* ctx, const FrameArgs& fa, int precision, const 
 hr_status launch_im_lookup(hr_ctx* ctx, int precision, const float* theta, const float* beta,
                            uint32_t m, float* out, cudaStream_t st);
 
-// Batched serving launch: a list of tiles from several requests.
+// Warp tiles of a frame: a warp renders wtw x wth pixels (32 / grp pixels, a
+// pixel's samples on grp adjacent lanes); the tiles that overlap the projected
+// scene rectangle `rect` (pixel space, from the BVH root box) form an nx-wide
+// grid from pixel (x0, y0), n tiles in all.  The frame and serving kernels
+// enumerate only these; every other pixel is background.
+struct WarpGrid {
+  uint32_t wtw, wth, x0, y0, nx, n;
+};
+__host__ __device__ inline WarpGrid warp_grid(const float4 rect, uint32_t W, uint32_t H,
+                                              uint32_t grp) {
+  WarpGrid g{1, 1, 0, 0, 0, 0};
+  const uint32_t P = 32u / grp;  // pixels per warp tile
+  while (g.wtw * g.wtw < P) g.wtw <<= 1;
+  g.wth = P / g.wtw;
+  const float fx0 = fmaxf(0.f, floorf(rect.x)), fy0 = fmaxf(0.f, floorf(rect.y));
+  const float fx1 = fminf(rect.z, (float)W - 1.f), fy1 = fminf(rect.w, (float)H - 1.f);
+  if (fx0 <= fx1 && fy0 <= fy1) {
+    g.x0 = (uint32_t)fx0 / g.wtw * g.wtw;
+    g.y0 = (uint32_t)fy0 / g.wth * g.wth;
+    g.nx = ((uint32_t)fx1 - g.x0) / g.wtw + 1;
+    g.n = g.nx * (((uint32_t)fy1 - g.y0) / g.wth + 1);
+  }
+  return g;
+}
+
+// Batched serving launch: warp tiles from several requests.
 struct ServeItem {
   FrameArgs fa;
-  float* rgb;       // device output of the request
-  uint32_t tile0;   // first tile (of the request's frame) in this item
-  uint32_t ntiles;  // tiles in this item
+  float* rgb;       // device output of the request (cleared to background)
+  float4 rect;      // the request's projected scene rectangle
+  WarpGrid grid;    // its warp tiles
+  uint32_t wt0;     // first warp tile (of the request's grid) in this item
+  uint32_t nwt;     // warp tiles in this item
 };
+// Projected scene rectangle of a frame into rect_dev (one warp; device).
+hr_status launch_scene_rect(hr_ctx* ctx, const FrameArgs& fa, float4* rect_dev, cudaStream_t st);
 // items_dev[i] covers batch tiles [item_start_dev[i], item_start_dev[i+1]);
 // every item of one launch has the same k-buffer bound and precision.
 hr_status launch_serve_batch(hr_ctx* ctx, int kmax, int precision, const ServeItem* items_dev,

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "dword.cuh"
 
 namespace hr {
 namespace {
@@ -39,17 +40,6 @@ __device__ __forceinline__ d3 cross(d3 a, d3 b) {
   return mk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
 __device__ __forceinline__ d3 ld3(float4 v) { return mk(v.x, v.y, v.z); }
-
-// ------------------------------------------------ FP32 error-free transforms
-// Knuth's TwoSum: returns s = fl(a + b) and sets e with s + e == a + b
-// exactly (round to nearest, no overflow).  The _rn intrinsics keep the
-// compiler from contracting or reordering the steps.
-__device__ __forceinline__ float two_sum(float a, float b, float& e) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return s;
-}
 
 // Double-word FP32 sum hi + lo: hi is the running rounded sum, lo collects
 // every rounding error (Ogita, Rump and Oishi 2005, "Accurate sum and dot
@@ -75,44 +65,12 @@ __device__ __forceinline__ void ff_renorm(ffsum& s) {
   s.lo = e;
 }
 __device__ __forceinline__ double ff_value(const ffsum& s) { return (double)s.hi + (double)s.lo; }
-
-// Double-word FP32 numbers hi + lo, |lo| <= ulp(hi) / 2 (Dekker 1971; the
-// accurate addition of Li et al., "Design, implementation and testing of
-// extended and mixed precision BLAS", 2002): about 2^-44 relative error per
-// operation, at a few FP32 operations each instead of one FP64 operation
-// (1/64 of the FP32 rate on this GPU).
-struct df {
-  float hi, lo;
-};
-__device__ __forceinline__ df df_fast(float a, float b) {  // |a| >= |b|
-  const float s = __fadd_rn(a, b);
-  return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
 __device__ __forceinline__ df df_of(const ffsum& s) {
   float e;
   const float h = two_sum(s.hi, s.lo, e);
   return {h, e};
 }
-__device__ __forceinline__ df df_add(df a, df b) {
-  float e1, e2;
-  const float s = two_sum(a.hi, b.hi, e1);
-  const float t = two_sum(a.lo, b.lo, e2);
-  const df u = df_fast(s, __fadd_rn(e1, t));
-  return df_fast(u.hi, __fadd_rn(u.lo, e2));
-}
-__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, {-b.hi, -b.lo}); }
-__device__ __forceinline__ df df_mul(df a, df b) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  const float e = fmaf(a.hi, b.hi, -p);
-  return df_fast(p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e)));
-}
-__device__ __forceinline__ df df_mul(df a, float b) {
-  const float p = __fmul_rn(a.hi, b);
-  const float e = fmaf(a.hi, b, -p);
-  return df_fast(p, fmaf(a.lo, b, e));
-}
-__device__ __forceinline__ float df_float(df a) { return __fadd_rn(a.hi, a.lo); }
-__device__ __forceinline__ double df_double(df a) { return (double)a.hi + (double)a.lo; }
+
 // s += (xh + xl) (yh + yl), with the exact product xh yh (the FMA form of
 // Dekker's TwoProduct) and the cross terms; xl yl (2^-48 relative) dropped.
 __device__ __forceinline__ void ff_add_prod(ffsum& s, float xh, float xl, float yh, float yl) {
@@ -364,6 +322,22 @@ __global__ void k_cluster_first(uint32_t N, uint32_t C, uint32_t* first) {
   first[c] = (uint32_t)(((uint64_t)c * N + C - 1) / C);  // ceil(c N / C)
 }
 
+// *flag |= x != y over n words
+__global__ void k_words_differ(const uint32_t* __restrict__ x, const uint32_t* __restrict__ y,
+                               uint32_t n, uint32_t* flag) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && x[i] != y[i]) *flag = 1u;
+}
+
+// cluster_of of the strands of cluster c (ranks cl_first[c] .. cl_first[c+1]-1)
+__global__ void k_cluster_of_from_first(const uint32_t* __restrict__ order,
+                                        const uint32_t* __restrict__ cl_first,
+                                        uint32_t* cluster_of) {
+  const uint32_t c = blockIdx.x;
+  for (uint32_t r = cl_first[c] + threadIdx.x; r < cl_first[c + 1]; r += blockDim.x)
+    cluster_of[order[r]] = c;
+}
+
 struct LevelInfo {
   uint32_t n_levels;
   uint32_t off[16];  // first thick-hair index of each level; off[n_levels] = E
@@ -593,6 +567,11 @@ __global__ void __launch_bounds__(128, 8) k_fit_cross_sections(const float4* __r
   const uint32_t e = (uint32_t)(idx / (S + 1)), k = (uint32_t)(idx % (S + 1));
   uint32_t first, cnt, c, lv;
   eth_members(li, cl_first, e, &first, &cnt, &c, &lv);
+  if (cnt == 0) {  // an empty thick hair (a cluster of fewer than 4^k strands): a = b = 0
+    float4* o = xsec + idx * 3;
+    o[0] = o[1] = o[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
   const uint32_t k0 = k > 0 ? k - 1 : 0, k1 = k < S ? k + 1 : S;
   const float4 q0 = __ldg(verts + (size_t)__ldg(order + first) * (S + 1) + k);
   const float p0x = q0.x, p0y = q0.y, p0z = q0.z;
@@ -773,7 +752,7 @@ __global__ void k_eth_material(const float4* __restrict__ verts, uint32_t N, uin
     ff_add(acc, j < HR_MAT_FLOATS ? mat[(size_t)s * HR_MAT_FLOATS + j] : __ldg(&verts[(size_t)s * (S + 1)].w),
            0.f);
   }
-  const float mean = __fadd_rn(acc.hi, acc.lo) / (float)cnt;
+  const float mean = cnt ? __fadd_rn(acc.hi, acc.lo) / (float)cnt : 0.f;
   if (j < HR_MAT_FLOATS)
     mat[(size_t)(N + e) * HR_MAT_FLOATS + j] = mean;
   else
@@ -802,9 +781,15 @@ __global__ void k_eth_prims(const float4* __restrict__ xsec, uint32_t N, uint32_
   }
   const float a = fmaxf(q0.w, r0.w), b = fmaxf(q1.w, r1.w);
   const uint64_t p = (uint64_t)N * S + idx;
-  write_prim(xf + p * 3, box + p * 2, c0, c1, e1, a, b);
   uint32_t first, cnt, c, lv;
   eth_members(li, cl_first, e, &first, &cnt, &c, &lv);
+  if (cnt == 0) {  // empty thick hair: never active; records left inert
+    xf[p * 3] = xf[p * 3 + 1] = xf[p * 3 + 2] = make_float4(0.f, 0.f, 0.f, 0.f);
+    box[p * 2] = box[p * 2 + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    aux[p] = make_float4(__uint_as_float(N + e), 0.f, 0.f, 0.f);
+    return;
+  }
+  write_prim(xf + p * 3, box + p * 2, c0, c1, e1, a, b);
   aux[p] = make_float4(__uint_as_float(N + e), (float)cnt, eth_r[e], a * b);
 }
 
@@ -892,9 +877,12 @@ hr_status refresh_strand_prims(hr_ctx* ctx, hr_asset* a) {
   return scene_bounds(ctx, a, n);
 }
 
-hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_levels,
-                          cudaEvent_t fit_begin, cudaEvent_t fit_end) {
-  cudaStream_t st = ctx_stream(ctx);
+namespace {
+
+// Level offsets of a hierarchy of C clusters over N strands and its arrays
+// (reused when the shape is unchanged, as for a new frame of the same hair).
+hr_status hierarchy_setup(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_levels,
+                          LevelInfo& li, uint64_t& E_out, uint64_t& total_out) {
   const uint32_t N = a->N, S = a->S;
   // level count: 1 + max k with 4^k <= floor(N/C)/2, capped
   const uint32_t per = N / C;
@@ -906,7 +894,7 @@ hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_lev
     if (max_levels > 0 && L > max_levels) L = max_levels;
   }
   if (L > 8) L = 8;
-  LevelInfo li{};
+  li = LevelInfo{};
   li.n_levels = L;
   uint64_t E = 0;
   for (uint32_t k = 0; k < L; ++k) {
@@ -940,26 +928,17 @@ hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_lev
   a->n_levels = L;
   a->E = (uint32_t)E;
   for (uint32_t k = 0; k <= L && k < 16; ++k) a->eth_offset[k] = li.off[k];
+  E_out = E;
+  total_out = total;
+  return HR_OK;
+}
 
-  // K1: Morton order of the roots
-  uint32_t *bounds, *keys, *vals, *k2, *v2;
-  HR_TRY(scratch(ctx, 0, 64, (void**)&bounds));
-  HR_TRY(scratch(ctx, 1, (size_t)N * 4, (void**)&keys));
-  HR_TRY(scratch(ctx, 2, (size_t)N * 4, (void**)&k2));
-  HR_TRY(scratch(ctx, 3, (size_t)N * 4, (void**)&v2));
-  vals = a->order;
-  k_init_bounds<<<1, 32, 0, st>>>(bounds);
-  HR_LAUNCHED(ctx);
-  k_root_bounds<<<(N + 255) / 256, 256, 0, st>>>(a->verts, N, S, bounds);
-  HR_LAUNCHED(ctx);
-  k_root_morton<<<(N + 255) / 256, 256, 0, st>>>(a->verts, N, S, bounds, keys, vals);
-  HR_LAUNCHED(ctx);
-  HR_TRY(radix_sort_pairs(ctx, keys, vals, k2, v2, N, 30, st));
-  k_assign_clusters<<<(N + 255) / 256, 256, 0, st>>>(a->order, N, C, a->cluster_of);
-  HR_LAUNCHED(ctx);
-  k_cluster_first<<<(C + 1 + 255) / 256, 256, 0, st>>>(N, C, a->cl_first);
-  HR_LAUNCHED(ctx);
-
+// Thick-hair materials, fits and segment records of the hierarchy whose
+// order and cluster starts are set, growing the material and primitive arrays.
+hr_status hierarchy_finish(hr_ctx* ctx, hr_asset* a, const LevelInfo& li, uint64_t E,
+                           uint64_t total, cudaEvent_t fit_begin, cudaEvent_t fit_end) {
+  cudaStream_t st = ctx_stream(ctx);
+  const uint32_t N = a->N, S = a->S;
   // grow the material table to strands + thick hairs
   if (a->mat_cap < (size_t)N + E) {
     float* m2 = nullptr;
@@ -1020,6 +999,93 @@ hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_lev
                                                            a->prim_box, a->prim_aux);
   HR_LAUNCHED(ctx);
   return HR_OK;
+}
+
+}  // namespace
+
+hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_levels,
+                          cudaEvent_t fit_begin, cudaEvent_t fit_end) {
+  cudaStream_t st = ctx_stream(ctx);
+  const uint32_t N = a->N, S = a->S;
+  LevelInfo li{};
+  uint64_t E = 0, total = 0;
+  HR_TRY(hierarchy_setup(ctx, a, C, max_levels, li, E, total));
+  drop_guides(ctx, a);  // a Morton hierarchy replaces a guide-driven one
+  // K1: Morton order of the roots
+  uint32_t *bounds, *keys, *vals, *k2, *v2;
+  HR_TRY(scratch(ctx, 0, 64, (void**)&bounds));
+  HR_TRY(scratch(ctx, 1, (size_t)N * 4, (void**)&keys));
+  HR_TRY(scratch(ctx, 2, (size_t)N * 4, (void**)&k2));
+  HR_TRY(scratch(ctx, 3, (size_t)N * 4, (void**)&v2));
+  HR_TRY(scratch(ctx, 4, (size_t)N * 4, (void**)&vals));
+  k_init_bounds<<<1, 32, 0, st>>>(bounds);
+  HR_LAUNCHED(ctx);
+  k_root_bounds<<<(N + 255) / 256, 256, 0, st>>>(a->verts, N, S, bounds);
+  HR_LAUNCHED(ctx);
+  k_root_morton<<<(N + 255) / 256, 256, 0, st>>>(a->verts, N, S, bounds, keys, vals);
+  HR_LAUNCHED(ctx);
+  HR_TRY(radix_sort_pairs(ctx, keys, vals, k2, v2, N, 30, st));
+  // a new strand order (moved roots) changes the clusters: no refit of a BVH
+  // built before it
+  k_words_differ<<<(N + 255) / 256, 256, 0, st>>>(vals, a->order, N, a->d_bounds + kHierChanged);
+  HR_LAUNCHED(ctx);
+  HR_CUDA(ctx, cudaMemcpyAsync(a->order, vals, (size_t)N * 4, cudaMemcpyDeviceToDevice, st));
+  k_assign_clusters<<<(N + 255) / 256, 256, 0, st>>>(a->order, N, C, a->cluster_of);
+  HR_LAUNCHED(ctx);
+  k_cluster_first<<<(C + 1 + 255) / 256, 256, 0, st>>>(N, C, a->cl_first);
+  HR_LAUNCHED(ctx);
+
+  return hierarchy_finish(ctx, a, li, E, total, fit_begin, fit_end);
+}
+
+hr_status rebuild_eth_records(hr_ctx* ctx, hr_asset* a) {
+  cudaStream_t st = ctx_stream(ctx);
+  const uint32_t N = a->N, S = a->S, E = a->E;
+  if (E == 0) return HR_OK;
+  LevelInfo li{};
+  li.n_levels = a->n_levels;
+  for (uint32_t k = 0; k <= a->n_levels && k < 16; ++k) li.off[k] = a->eth_offset[k];
+  float* eth_r = nullptr;
+  HR_TRY(scratch(ctx, 5, (size_t)E * sizeof(float), (void**)&eth_r));
+  k_eth_material<<<(unsigned)(((uint64_t)E * (HR_MAT_FLOATS + 1) + 127) / 128), 128, 0, st>>>(
+      a->verts, N, S, a->order, a->cl_first, li, E, a->mat, eth_r);
+  HR_LAUNCHED(ctx);
+  k_eth_prims<<<(unsigned)(((uint64_t)E * S + 255) / 256), 256, 0, st>>>(
+      a->xsec, N, S, E, a->cl_first, li, eth_r, a->prim_xf, a->prim_box, a->prim_aux);
+  HR_LAUNCHED(ctx);
+  return HR_OK;
+}
+
+hr_status root_morton_order(hr_ctx* ctx, hr_asset* a, uint32_t* codes, uint32_t* order,
+                            cudaStream_t st) {
+  const uint32_t N = a->N, S = a->S;
+  uint32_t *bounds, *k2, *v2;
+  HR_TRY(scratch(ctx, 0, 64, (void**)&bounds));
+  HR_TRY(scratch(ctx, 2, (size_t)N * 4, (void**)&k2));
+  HR_TRY(scratch(ctx, 3, (size_t)N * 4, (void**)&v2));
+  k_init_bounds<<<1, 32, 0, st>>>(bounds);
+  HR_LAUNCHED(ctx);
+  k_root_bounds<<<(N + 255) / 256, 256, 0, st>>>(a->verts, N, S, bounds);
+  HR_LAUNCHED(ctx);
+  k_root_morton<<<(N + 255) / 256, 256, 0, st>>>(a->verts, N, S, bounds, codes, order);
+  HR_LAUNCHED(ctx);
+  return radix_sort_pairs(ctx, codes, order, k2, v2, N, 30, st);
+}
+
+hr_status build_hierarchy_from(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_levels,
+                               const uint32_t* order_dev, const uint32_t* cl_first_dev) {
+  cudaStream_t st = ctx_stream(ctx);
+  const uint32_t N = a->N;
+  LevelInfo li{};
+  uint64_t E = 0, total = 0;
+  HR_TRY(hierarchy_setup(ctx, a, C, max_levels, li, E, total));
+  HR_CUDA(ctx, cudaMemsetAsync(a->d_bounds + kHierChanged, 0xff, 4, st));  // a new hierarchy
+  HR_CUDA(ctx, cudaMemcpyAsync(a->order, order_dev, (size_t)N * 4, cudaMemcpyDeviceToDevice, st));
+  HR_CUDA(ctx, cudaMemcpyAsync(a->cl_first, cl_first_dev, (size_t)(C + 1) * 4,
+                               cudaMemcpyDeviceToDevice, st));
+  k_cluster_of_from_first<<<C, 256, 0, st>>>(a->order, a->cl_first, a->cluster_of);
+  HR_LAUNCHED(ctx);
+  return hierarchy_finish(ctx, a, li, E, total, nullptr, nullptr);
 }
 
 // Morton clustering of strand roots on caller-provided scratch (no

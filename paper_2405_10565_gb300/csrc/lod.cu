@@ -89,11 +89,20 @@ __global__ void k_widths(const float4* __restrict__ xsec, uint32_t E, uint32_t S
   }
   if (w != w) w = __int_as_float(0x7f800000);  // NaN (degenerate) counts as too wide
   // lanes of one (cluster, level) take their maximum first: one atomic each
-  const uint32_t slot = valid ? cluster * lv.n_levels + k : 0xffffffffu;
+  // an empty thick hair (a cluster of fewer than 4^k strands) has a = 0 and no width
+  const bool live = valid && a > 0.f;
+  const uint32_t slot = live ? cluster * lv.n_levels + k : 0xffffffffu;
   const uint32_t peers = __match_any_sync(0xffffffffu, slot);
-  const uint32_t wm = __reduce_max_sync(peers, valid ? __float_as_uint(w) : 0u);
-  if (valid && (threadIdx.x & 31) == (uint32_t)(__ffs(peers) - 1)) atomicMax(&wmax[slot], wm);
+  const uint32_t wm = __reduce_max_sync(peers, live ? __float_as_uint(w) : 0u);
+  if (live && (threadIdx.x & 31) == (uint32_t)(__ffs(peers) - 1)) atomicMax(&wmax[slot], wm);
 }
+
+// Deferred selection with a hysteresis band (mode 2): a cluster refines only
+// once its width exceeds eps by 10% and coarsens only once the coarser level
+// is 10% under eps, so that widths that hover at eps under small motion keep
+// their level and the BVH can be refit instead of rebuilt.
+constexpr float kLodRefine = 1.1f;
+constexpr float kLodCoarsen = 0.9f;
 
 __global__ void k_rule(const uint32_t* __restrict__ wmax, uint32_t C, uint32_t L, float eps,
                        int mode, int bias, const uint8_t* __restrict__ prev, uint8_t* out) {
@@ -111,13 +120,16 @@ __global__ void k_rule(const uint32_t* __restrict__ wmax, uint32_t C, uint32_t L
       }
   } else {
     // Eq. (14), cases in order; w_cur- = +inf at level 0; the strand level
-    // only coarsens
+    // only coarsens.  Mode 2 refines above eps (1 + h) and coarsens at or
+    // below eps (1 - h), h = 0.1 (both products rounded to FP32 once).
+    const float refine = mode == 2 ? __fmul_rn(eps, kLodRefine) : eps;
+    const float coarsen = mode == 2 ? __fmul_rn(eps, kLodCoarsen) : eps;
     lvl = min((int)prev[c], (int)L);
     const float wcur = lvl < (int)L ? __uint_as_float(w[lvl]) : -__int_as_float(0x7f800000);
     const float wminus = lvl > 0 ? __uint_as_float(w[lvl - 1]) : __int_as_float(0x7f800000);
-    if (lvl < (int)L && wcur > eps)
+    if (lvl < (int)L && wcur > refine)
       lvl += 1;
-    else if (wminus <= eps)
+    else if (wminus <= coarsen)
       lvl -= 1;
   }
   lvl = max(0, lvl - bias);

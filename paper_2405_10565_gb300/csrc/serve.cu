@@ -42,6 +42,7 @@ struct CachedBvh {
 struct Slot {
   uint8_t* lod = nullptr;
   uint32_t lod_cap = 0;
+  float4* rect = nullptr;  // the request's projected scene rectangle (device)
   float* out = nullptr;  // device staging when the caller's buffer is host memory
   size_t out_cap = 0;
   bool busy = false;
@@ -60,6 +61,8 @@ struct Request {
   CachedBvh* entry = nullptr;
   int kmax = 1;
   FrameArgs fa{};
+  float4 rect{};   // projected scene rectangle (pixels)
+  WarpGrid grid{};  // warp tiles over it (tiles_total of them)
   float* dev_out = nullptr;
   int64_t delay_ms = 0;
 };
@@ -110,10 +113,6 @@ double event_ms(Server* s, cudaEvent_t ev) {
     return ctx_now_ms(s->ctx);
   }
   return s->ref_ms + ms;
-}
-
-uint32_t request_tiles(const hr_render_desc& d) {
-  return tiles_for(d.camera.width, d.camera.height, d.spp);
 }
 
 // Upper bound of the device bytes admitting a request may add: a new resident
@@ -218,12 +217,27 @@ hr_status admit(Server* s, Request* r) {
     }
     r->dev_out = sl.out;
   }
+  // the warp tiles over the projected scene rectangle
+  r->fa = frame_args(ctx, a, e->bvh, r->req.desc);
+  r->kmax = kmax_for(r->req.desc.k_depth);
+  if (!sl.rect) HR_TRY(dalloc(ctx, (void**)&sl.rect, sizeof(float4), "serving rect"));
+  HR_TRY(launch_scene_rect(ctx, r->fa, sl.rect, bs));
+  HR_CUDA(ctx, cudaMemcpyAsync(&r->rect, sl.rect, sizeof(float4), cudaMemcpyDeviceToHost, bs));
   // the build must be complete before the batches (another stream) read it,
   // and the scratch it used is shared with API calls
   HR_CUDA(ctx, cudaStreamSynchronize(bs));
-  r->fa = frame_args(ctx, a, e->bvh, r->req.desc);
-  r->kmax = kmax_for(r->req.desc.k_depth);
-  r->tiles_total = request_tiles(r->req.desc);
+  r->grid = warp_grid(r->rect, r->req.desc.camera.width, r->req.desc.camera.height, r->fa.grp);
+  r->tiles_total = r->grid.n;
+  // every pixel outside the warp tiles is background: clear the output on the
+  // batch stream, ahead of the request's tiles
+  HR_CUDA(ctx, cudaMemsetAsync(r->dev_out, 0, out, s->stream));
+  if (r->tiles_total == 0) {  // nothing in view: complete with the background
+    r->finished_issue = true;
+    if (r->host_out)
+      HR_CUDA(ctx, cudaMemcpyAsync(r->req.rgb_out, r->dev_out, out, cudaMemcpyDeviceToHost,
+                                   s->stream));
+    HR_CUDA(ctx, cudaEventRecord(r->done_ev, s->stream));
+  }
   return HR_OK;
 }
 
@@ -345,15 +359,17 @@ void loop(Server* s) {
       const uint64_t share = std::max<uint64_t>(1, budget / grp.size());
       for (Request* r : grp) {
         if (n_items >= s->max_items) break;
-        const TileGeom tg = tile_geom(r->req.desc.spp);
-        const uint64_t spt = (uint64_t)tg.tile_w * tg.tile_h * r->req.desc.spp;
+        // samples per warp tile: 32 / grp pixels of spp samples each
+        const uint64_t spt = (uint64_t)(32u / r->fa.grp) * r->req.desc.spp;
         uint32_t take = (uint32_t)std::max<uint64_t>(1, share / spt);
         take = std::min(take, r->tiles_total - r->tiles_issued);
         ServeItem& it = s->h_items[b][n_items];
         it.fa = r->fa;
         it.rgb = r->dev_out;
-        it.tile0 = r->tiles_issued;
-        it.ntiles = take;
+        it.rect = r->rect;
+        it.grid = r->grid;
+        it.wt0 = r->tiles_issued;
+        it.nwt = take;
         s->h_starts[b][n_items] = total;
         total += take;
         ++n_items;
@@ -508,6 +524,7 @@ hr_status hr_serve_stop(hr_ctx* ctx) {
   for (Slot& sl : s->slots) {
     if (sl.lod) dfree(ctx, sl.lod, sl.lod_cap);
     if (sl.out) dfree(ctx, sl.out, sl.out_cap);
+    if (sl.rect) dfree(ctx, sl.rect, sizeof(float4));
   }
   for (int b = 0; b < 2; ++b) {
     if (s->h_items[b]) cudaFreeHost(s->h_items[b]);

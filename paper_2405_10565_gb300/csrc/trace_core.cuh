@@ -17,6 +17,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "dword.cuh"
 
 namespace hr {
 namespace tr {
@@ -38,84 +39,303 @@ __device__ __forceinline__ float3 operator*(float3 a, float s) { return f3(a.x *
 __device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 __device__ __forceinline__ float clampf(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
 
-// Camera ray of sample `sid` of pixel (x, y).
-__device__ __forceinline__ void camera_ray_xy(const LaunchCam& c, uint64_t seed, uint64_t sid,
-                                              uint32_t x, uint32_t y, float3& o, float3& d) {
-  const float jx = (float)(uint32_t)(splitmix_out(seed, 2 * sid) >> 40) * (1.0f / 16777216.0f);
-  const float jy = (float)(uint32_t)(splitmix_out(seed, 2 * sid + 1) >> 40) * (1.0f / 16777216.0f);
-  const float sx = ((float)x - 0.5f * (float)c.W + jx) / c.pix;
-  const float sy = (0.5f * (float)c.H - (float)y - jy) / c.pix;
-  if (c.kind == 1) {
-    o = c.eye;
-    float3 v = c.fwd + c.right * sx + c.up * sy;
-    d = v * rsqrtf(dot3(v, v));
-  } else {
-    o = c.eye + c.right * sx + c.up * sy;
-    d = c.fwd;
-  }
-}
-
-__device__ __forceinline__ void camera_ray(const LaunchCam& c, uint64_t seed, uint64_t sid,
-                                           uint32_t spp, float3& o, float3& d) {
-  const uint64_t pixel = sid / spp;
-  camera_ray_xy(c, seed, sid, (uint32_t)(pixel % (uint32_t)c.W), (uint32_t)(pixel / (uint32_t)c.W),
-                o, d);
-}
-
 // ------------------------------------------------------------------ geometry
 
-// Ray against the open elliptic cylinder of one record.  Returns the nearest
-// root in (0, tmax] whose axial coordinate lies in [0, 1], and the chord of the
-// ray inside the finite cylinder.
-__device__ __forceinline__ bool intersect(const float4* __restrict__ xf, const float3 o,
-                                          const float3 d, const float tmax, float& t_hit,
-                                          float& chord) {
+// ------------------------------------------------------------------ precision
+//
+// The hit decisions are taken in FP32 wherever FP32 rounding cannot change
+// them, and precisely otherwise.
+//  * Every camera ray is built in double-word FP32 (the oracle's FP64
+//    construction to about 2^-44) and re-based at its entry into the scene's
+//    bounding box: the FP32 ray (o', d) starts next to the hair, and depths
+//    are kept relative to the entry (t = t_off + t').  FP32 rounding then
+//    moves a hit by ~2^-24 of the scene's size instead of ~2^-24 of the
+//    camera distance.
+//  * intersect32 bounds the rounding of its affine rows and of the roots.  A
+//    test within that bound of the cylinder's outline or of an end of the
+//    segment, a hit whose depth bound could reorder it against another hit or
+//    the search cut, or whose bound is wide, is decided by refine: the
+//    double-word ray re-based near the hit relative to the segment's start
+//    point, and the quadratic solved about that point.  From then on the ray
+//    orders its k-buffer precisely.
+// Far cameras and thin fibres (4K views of 1e-3 strands ten units away)
+// otherwise turn up FP32 rounding errors of a few 1e-7 in position, enough
+// to swap two strands at nearly equal depth or drop a hit at the very edge of
+// a fibre.
+
+constexpr int kMiss = 0, kHit = 1, kBorder = 2;
+constexpr float kEps32 = 5.9604645e-8f;   // FP32 unit roundoff, 2^-24
+constexpr float kBoundK = 6.f;            // rounding steps per affine row, with margin
+// Relative depth (of the absolute depth) that widens the box cull, and above
+// which an FP32 depth bound sends the hit to refine.
+constexpr float kTieRel = 1.52587890625e-05f;  // 2^-16
+
+struct RayKey {  // what rebuilds the ray precisely: the sample id and the re-basing depth
+  uint64_t sid;
+  float t_off;
+};
+
+// Ray against the open elliptic cylinder of one record, in FP32, with a
+// bound on the rounding of each decision.  kMiss when the ray misses by more
+// than the bound; kBorder when the rounding could change the outcome; else
+// kHit with the nearest root t in (0, tmax] (axial coordinate in [0, 1]),
+// its error bound terr and the chord of the ray inside the finite cylinder.
+// M = |o.x| + |o.y| + |o.z| of the ray.
+__device__ __forceinline__ int intersect32(const float4* __restrict__ xf, const float3 o,
+                                           const float3 d, const float M, const float tmax,
+                                           float& t_hit, float& chord, float& terr) {
   const float4 r0 = __ldg(xf), r1 = __ldg(xf + 1), r2 = __ldg(xf + 2);
   const float u0 = fmaf(r0.x, o.x, fmaf(r0.y, o.y, fmaf(r0.z, o.z, r0.w)));
   const float v0 = fmaf(r1.x, o.x, fmaf(r1.y, o.y, fmaf(r1.z, o.z, r1.w)));
   const float du = fmaf(r0.x, d.x, fmaf(r0.y, d.y, r0.z * d.z));
   const float dv = fmaf(r1.x, d.x, fmaf(r1.y, d.y, r1.z * d.z));
   const float A = fmaf(du, du, dv * dv);
-  if (!(A > 0.f)) return false;
+  if (!(A > 0.f)) return kMiss;
   const float inv = 1.0f / A;
   const float tc = -fmaf(u0, du, v0 * dv) * inv;
   const float uc = fmaf(tc, du, u0), vc = fmaf(tc, dv, v0);
   const float h2 = fmaf(uc, uc, vc * vc);
-  if (h2 > 1.f) return false;
-  const float half = sqrtf((1.f - h2) * inv);
+  // rounding bound of (uc, vc): the rows' intermediate terms reach |r| (|o| + |tc|)
+  const float mag = M + fabsf(tc);
+  const float eu = kBoundK * kEps32 *
+                   fmaf(fabsf(r0.x) + fabsf(r0.y) + fabsf(r0.z), mag, fabsf(r0.w));
+  const float ev = kBoundK * kEps32 *
+                   fmaf(fabsf(r1.x) + fabsf(r1.y) + fabsf(r1.z), mag, fabsf(r1.w));
+  const float e = eu + ev;
+  const float dh = e * (2.f + e);
+  if (h2 > 1.f + dh) return kMiss;
+  bool border = h2 >= 1.f - dh;  // near the outline
+  const float g = fmaxf(1.f - h2, 0.f);
+  const float half = sqrtf(g * inv);
   const float tm = tc - half, tp = tc + half;
-  if (tp <= 0.f || tm > tmax) return false;
+  // depth bound: the (u, v) error over |(du, dv)|, the root's slope (near
+  // the outline at most sqrt(dh / A)), and the rounding of t itself
+  const float magt = mag + half;
+  const float eroot = border ? sqrtf(dh * inv) : dh * half * (0.5f / g);
+  terr = fmaf(e, sqrtf(inv), fmaf(4.f * kEps32, magt, eroot));
+  if (tp + terr <= 0.f || tm - terr > tmax) return kMiss;
   const float w0 = fmaf(r2.x, o.x, fmaf(r2.y, o.y, fmaf(r2.z, o.z, r2.w)));
   const float dw = fmaf(r2.x, d.x, fmaf(r2.y, d.y, r2.z * d.z));
-  float wlo, whi;
+  // axial coordinate of each root, and its error bound (the row's rounding
+  // and the root's depth error times the axial rate)
+  const float ew = fmaf(kBoundK * kEps32,
+                        fmaf(fabsf(r2.x) + fabsf(r2.y) + fabsf(r2.z), magt, fabsf(r2.w)),
+                        fabsf(dw) * terr);
+  const float wm = fmaf(tm, dw, w0), wp = fmaf(tp, dw, w0);
+  // each root: certainly in range, possibly in range, or certainly not
+  const bool m_in = tm > terr && wm >= ew && wm <= 1.f - ew;
+  const bool m_may = tm > -terr && wm >= -ew && wm <= 1.f + ew;
+  const bool p_in = tp > terr && wp >= ew && wp <= 1.f - ew;
+  const bool p_may = tp > -terr && wp >= -ew && wp <= 1.f + ew;
+  float t;
+  if (m_in) {
+    t = tm;
+  } else if (m_may) {
+    t = fmaxf(tm, 0.f);
+    border = true;
+  } else if (p_in) {
+    t = tp;
+  } else if (p_may) {
+    t = fmaxf(tp, 0.f);
+    border = true;
+  } else {
+    return kMiss;
+  }
+  if (t - terr > tmax) return kMiss;
+  t_hit = t;
+  // chord: the part of [tm, tp] where the axial coordinate lies in [0, 1]
+  float wlo = -kInf, whi = kInf;
   if (dw != 0.f) {
     const float idw = 1.0f / dw;
     const float ta = -w0 * idw, tb = (1.f - w0) * idw;
     wlo = fminf(ta, tb);
     whi = fmaxf(ta, tb);
-  } else {
-    if (w0 < 0.f || w0 > 1.f) return false;
-    wlo = -kInf;
-    whi = kInf;
   }
-  float t;
-  if (tm > 0.f && tm >= wlo && tm <= whi)
-    t = tm;
-  else if (tp > 0.f && tp >= wlo && tp <= whi)
-    t = tp;
+  chord = fmaxf(0.f, fminf(tp, whi) - fmaxf(tm, wlo));
+  return border ? kBorder : kHit;
+}
+
+// df / b with the exact remainder of the rounded quotient (FMA) folded into
+// a second quotient: about 2^-46 relative.
+__device__ __forceinline__ df df_div(df a, float b) {
+  const float q1 = __fdiv_rn(a.hi, b);
+  const float r = __fadd_rn(fmaf(-q1, b, a.hi), a.lo);
+  return df_fast(q1, __fdiv_rn(r, b));
+}
+
+// Camera ray of a sample in double-word FP32, the oracle's construction to
+// about 2^-44: sub-pixel offset from the top 24 bits of SplitMix64 outputs
+// 2 sid and 2 sid + 1, image-plane offset ((x + jx) - W / 2,
+// H / 2 - (y + jy)) / pix (exact pairs before the division); perspective
+// rays leave the eye along v = (fwd + sx right) + sy up, orthographic ones
+// leave (eye + sx right) + sy up along fwd.  v is left unnormalised: the
+// ray's point at parameter s is o + s v.
+struct PreciseRay {
+  df o[3], v[3];
+};
+static __device__ void camera_ray_dw(const LaunchCam& c, uint64_t seed, uint32_t spp, uint64_t sid,
+                                     PreciseRay& r) {
+  const float jx = (float)(uint32_t)(splitmix_out(seed, 2 * sid) >> 40) * (1.0f / 16777216.0f);
+  const float jy = (float)(uint32_t)(splitmix_out(seed, 2 * sid + 1) >> 40) * (1.0f / 16777216.0f);
+  uint32_t px, py;
+  if (sid < (1ull << 32)) {
+    const uint32_t pixel = (uint32_t)sid / spp;
+    px = pixel % (uint32_t)c.W;
+    py = pixel / (uint32_t)c.W;
+  } else {
+    const uint64_t pixel = sid / spp;
+    px = (uint32_t)(pixel % (uint64_t)c.W);
+    py = (uint32_t)(pixel / (uint64_t)c.W);
+  }
+  const float x = (float)px, y = (float)py;
+  float ex, ey;
+  const float ax = two_sum(__fsub_rn(x, 0.5f * (float)c.W), jx, ex);
+  const float ay = two_sum(__fsub_rn(0.5f * (float)c.H, y), -jy, ey);
+  const df sx = df_div(df{ax, ex}, c.pix), sy = df_div(df{ay, ey}, c.pix);
+  const float E[3] = {c.eye.x, c.eye.y, c.eye.z}, R[3] = {c.right.x, c.right.y, c.right.z};
+  const float U[3] = {c.up.x, c.up.y, c.up.z}, F[3] = {c.fwd.x, c.fwd.y, c.fwd.z};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const df w = df_add(df_add(df_mul(sx, R[i]), c.kind == 1 ? F[i] : E[i]), df_mul(sy, U[i]));
+    if (c.kind == 1) {
+      r.o[i] = df{E[i], 0.f};
+      r.v[i] = w;
+    } else {
+      r.o[i] = w;
+      r.v[i] = df{F[i], 0.f};
+    }
+  }
+}
+
+// |v|^2 of a double-word vector, its square root and a reciprocal, in
+// double-word (one Newton correction each from the exact FMA residual).
+__device__ __forceinline__ df df_norm2(const df v[3]) {
+  return df_add(df_add(df_mul(v[0], v[0]), df_mul(v[1], v[1])), df_mul(v[2], v[2]));
+}
+__device__ __forceinline__ df df_sqrt(df a) {
+  const float r = __fsqrt_rn(a.hi);
+  return df_fast(r, __fdiv_rn(__fadd_rn(fmaf(-r, r, a.hi), a.lo), 2.f * r));
+}
+__device__ __forceinline__ df df_recip(df a) {
+  const float q = __frcp_rn(a.hi);
+  const float e = __fsub_rn(fmaf(-q, a.hi, 1.f), __fmul_rn(q, a.lo));
+  return df_fast(q, __fmul_rn(q, e));
+}
+
+// The FP32 ray of a sample: the unit direction rounded from double-word, and
+// the origin moved to a little before the ray's entry into the scene's
+// bounding box (the root node's two boxes), o' = o + t_off d, formed in
+// double-word before rounding.  Hits are at depth t_off + t' along (o', d);
+// no primitive lies before the entry, so t' > 0 for every hit.
+__device__ __forceinline__ void primary_ray(const FrameArgs& fa, uint64_t sid, float3& o,
+                                            float3& d, RayKey& rk) {
+  PreciseRay ry;
+  camera_ray_dw(fa.cam, fa.seed, fa.spp, sid, ry);
+  const df il = df_recip(df_sqrt(df_norm2(ry.v)));
+  df du[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) du[i] = df_mul(ry.v[i], il);
+  d = f3(df_float(du[0]), df_float(du[1]), df_float(du[2]));
+  float t_off = 0.f;
+  if (fa.n_prims >= 2) {
+    const float4 n0 = __ldg(fa.nodes), n1 = __ldg(fa.nodes + 1), n2 = __ldg(fa.nodes + 2);
+    const float3 oo = f3(ry.o[0].hi, ry.o[1].hi, ry.o[2].hi);
+    const float3 inv = f3(1.0f / (fabsf(d.x) > 1e-12f ? d.x : copysignf(1e-12f, d.x)),
+                          1.0f / (fabsf(d.y) > 1e-12f ? d.y : copysignf(1e-12f, d.y)),
+                          1.0f / (fabsf(d.z) > 1e-12f ? d.z : copysignf(1e-12f, d.z)));
+    const float lx = (fminf(n0.x, n1.x) - oo.x) * inv.x, hx = (fmaxf(n0.y, n1.y) - oo.x) * inv.x;
+    const float ly = (fminf(n0.z, n1.z) - oo.y) * inv.y, hy = (fmaxf(n0.w, n1.w) - oo.y) * inv.y;
+    const float lz = (fminf(n2.x, n2.z) - oo.z) * inv.z, hz = (fmaxf(n2.y, n2.w) - oo.z) * inv.z;
+    const float t0 = fmaxf(fmaxf(fminf(lx, hx), fminf(ly, hy)), fminf(lz, hz));
+    const float t1 = fminf(fminf(fmaxf(lx, hx), fmaxf(ly, hy)), fmaxf(lz, hz));
+    // 2^-10 before the FP32 entry: far more than the slab test's rounding
+    if (t0 > 0.f && t0 <= t1) t_off = t0 * (1.f - 9.765625e-4f);
+  }
+  rk = RayKey{sid, t_off};
+  o = f3(df_float(df_add(ry.o[0], df_mul(du[0], t_off))),
+         df_float(df_add(ry.o[1], df_mul(du[1], t_off))),
+         df_float(df_add(ry.o[2], df_mul(du[2], t_off))));
+}
+
+// The precise decision of one test, for hits the FP32 test cannot order or
+// classify.  The ray is built in double-word FP32 and re-based at its point
+// s0 v (s0 from the FP32 depth estimate) relative to the segment's start
+// point c0 (a strand vertex or a thick-hair cross-section centre): that point
+// lies within about a segment length of c0, so rounding it to FP32 costs
+// ~2^-24 of a segment length instead of ~2^-24 of the camera distance.  The
+// cylinder (the record's FP32 linear rows, through c0) is then solved about
+// it in FP32: the nearest root of o + s v with s > 0 and axial coordinate in
+// [0, 1].  t_est and the result are depths past the ray's re-basing depth
+// rk.t_off; the result is a normalised pair t' = t_hi + t_lo, with the
+// chord.  About 300 FP32 operations, against ~200 FP64 operations (1/64 of
+// the FP32 rate on this GPU) for the same test in FP64.
+static __device__ __noinline__ bool refine(const FrameArgs& fa, const RayKey& rk, uint32_t id,
+                                           float t_est, float& t_hi, float& t_lo,
+                                           float& chord_out) {
+  PreciseRay ry;
+  camera_ray_dw(fa.cam, fa.seed, fa.spp, rk.sid, ry);
+  const float4* xf = fa.prim_xf + 3 * (size_t)id;
+  const float4 r0 = __ldg(xf), r1 = __ldg(xf + 1), r2 = __ldg(xf + 2);
+  const uint32_t S = fa.S, NS = fa.N * fa.S;
+  float4 c0;
+  if (id < NS)
+    c0 = __ldg(fa.verts + (size_t)(id / S) * (S + 1) + id % S);
+  else
+    c0 = __ldg(fa.xsec + ((size_t)((id - NS) / S) * (S + 1) + (id - NS) % S) * 3);
+  const float vx = ry.v[0].hi, vy = ry.v[1].hi, vz = ry.v[2].hi;
+  const df L = df_sqrt(df_norm2(ry.v));  // the absolute depth is s |v|
+  const float s0 = fmaxf((rk.t_off + t_est) / L.hi, 0.f);
+  const float C0[3] = {c0.x, c0.y, c0.z};
+  float p[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) p[i] = df_float(df_add(df_add(ry.o[i], -C0[i]), df_mul(ry.v[i], s0)));
+  const float u0 = fmaf(r0.x, p[0], fmaf(r0.y, p[1], __fmul_rn(r0.z, p[2])));
+  const float v0 = fmaf(r1.x, p[0], fmaf(r1.y, p[1], __fmul_rn(r1.z, p[2])));
+  const float w0 = fmaf(r2.x, p[0], fmaf(r2.y, p[1], __fmul_rn(r2.z, p[2])));
+  const float du = fmaf(r0.x, vx, fmaf(r0.y, vy, __fmul_rn(r0.z, vz)));
+  const float dv = fmaf(r1.x, vx, fmaf(r1.y, vy, __fmul_rn(r1.z, vz)));
+  const float dw = fmaf(r2.x, vx, fmaf(r2.y, vy, __fmul_rn(r2.z, vz)));
+  const float A = fmaf(du, du, __fmul_rn(dv, dv));
+  if (!(A > 0.f)) return false;
+  const float inv = 1.0f / A;
+  const float sc = __fmul_rn(-fmaf(u0, du, __fmul_rn(v0, dv)), inv);
+  const float uc = fmaf(sc, du, u0), vc = fmaf(sc, dv, v0);
+  const float h2 = fmaf(uc, uc, __fmul_rn(vc, vc));
+  if (h2 > 1.f) return false;
+  const float half = sqrtf(__fmul_rn(__fsub_rn(1.f, h2), inv));
+  const float sm = __fsub_rn(sc, half), sp = __fadd_rn(sc, half);
+  const float wm = fmaf(sm, dw, w0), wp = fmaf(sp, dw, w0);
+  float s;
+  if (__fadd_rn(s0, sm) > 0.f && wm >= 0.f && wm <= 1.f)
+    s = sm;
+  else if (__fadd_rn(s0, sp) > 0.f && wp >= 0.f && wp <= 1.f)
+    s = sp;
   else
     return false;
-  if (t > tmax) return false;
-  t_hit = t;
-  chord = fmaxf(0.f, fminf(tp, whi) - fmaxf(tm, wlo));
+  float e;
+  const float th = two_sum(s0, s, e);
+  const df t = df_add(df_mul(df_fast(th, e), L), -rk.t_off);
+  t_hi = t.hi;
+  t_lo = t.lo;
+  float wlo = -kInf, whi = kInf;
+  if (dw != 0.f) {
+    const float ta = -w0 / dw, tb = (1.f - w0) / dw;
+    wlo = fminf(ta, tb);
+    whi = fmaxf(ta, tb);
+  }
+  chord_out = fmaxf(0.f, fminf(sp, whi) - fmaxf(sm, wlo)) * L.hi;
   return true;
 }
 
+// The K nearest hits: distance, chord and global primitive id (which also
+// addresses the primitive's records).
+// t is the FP32 depth; tr the precise depth's low word when the hit was
+// refined (0 otherwise): entries order by (t, tr, id).
 template <int KMAX>
 struct KBuf {
   float t[KMAX];
+  float tr[KMAX];
   float ch[KMAX];
-  uint32_t leaf[KMAX];
   uint32_t id[KMAX];
 };
 
@@ -124,23 +344,28 @@ __device__ __forceinline__ void kbuf_init(KBuf<KMAX>& kb) {
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) {
     kb.t[j] = kInf;
+    kb.tr[j] = 0.f;
     kb.ch[j] = 0.f;
-    kb.leaf[j] = 0u;
     kb.id[j] = 0xffffffffu;
   }
 }
 
-// Insert keeping the k nearest by (t, id): the candidate bubbles through the
-// sorted slots and whatever falls off the end is dropped.
+__device__ __forceinline__ bool key_less(float t, float tr, uint32_t id, float t2, float tr2,
+                                         uint32_t id2) {
+  return t < t2 || (t == t2 && (tr < tr2 || (tr == tr2 && id < id2)));
+}
+
+// Insert keeping the k nearest by (t, tr, id): the candidate bubbles through
+// the sorted slots and whatever falls off the end is dropped.
 template <int KMAX>
-__device__ __forceinline__ void kbuf_insert(KBuf<KMAX>& kb, const uint32_t k, float t,
-                                            uint32_t id, uint32_t leaf, float ch) {
+__device__ __forceinline__ void kbuf_insert(KBuf<KMAX>& kb, const uint32_t k, float t, float tr,
+                                            uint32_t id, float ch) {
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) {
-    if (j < (int)k && (t < kb.t[j] || (t == kb.t[j] && id < kb.id[j]))) {
+    if (j < (int)k && key_less(t, tr, id, kb.t[j], kb.tr[j], kb.id[j])) {
       float a = kb.t[j]; kb.t[j] = t; t = a;
+      float r = kb.tr[j]; kb.tr[j] = tr; tr = r;
       uint32_t b = kb.id[j]; kb.id[j] = id; id = b;
-      uint32_t c = kb.leaf[j]; kb.leaf[j] = leaf; leaf = c;
       float e = kb.ch[j]; kb.ch[j] = ch; ch = e;
     }
   }
@@ -156,33 +381,109 @@ __device__ __forceinline__ float kbuf_last(const KBuf<KMAX>& kb, const uint32_t 
 }
 
 struct Counts {
-  uint32_t nodes, tests, sshade, eshade, hits, rays;
+  uint32_t nodes, tests, sshade, eshade, hits, rays, precise_tests, precise_rays;
 };
 
-template <int KMAX, bool COUNT>
-__device__ __forceinline__ void leaf_test(const FrameArgs& fa, uint32_t leaf, const float3 o,
-                                          const float3 d, KBuf<KMAX>& kb, float& tcut,
-                                          float& topq, Counts& cn) {
-  float th, ch;
-  if (COUNT) ++cn.tests;
-  if (intersect(fa.leaf_xf + 3 * (size_t)leaf, o, d, tcut, th, ch)) {
-    const uint32_t id = __ldg(fa.leaf_id + leaf);
-    kbuf_insert<KMAX>(kb, fa.k, th, id, leaf, ch);
-    if (__ldg(&fa.leaf_aux[leaf].y) == 0.f) topq = fminf(topq, th);  // strand: opaque
-    tcut = fminf(kbuf_last<KMAX>(kb, fa.k), topq);
+// The ray switches to precise ordering: every entry refined, the entries
+// re-sorted by (t, tr, id), the nearest opaque hit among them taken again.
+template <int KMAX>
+__device__ __forceinline__ void refine_all(const FrameArgs& fa, const RayKey& rk, KBuf<KMAX>& kb,
+                                           float& tq, float& tqr) {
+  tq = kInf;
+  tqr = 0.f;
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) {
+    if (j < (int)fa.k && kb.t[j] < kInf) {
+      float th, tl, c;
+      if (refine(fa, rk, kb.id[j], kb.t[j], th, tl, c)) {
+        kb.t[j] = th;
+        kb.tr[j] = tl;
+        kb.ch[j] = c;
+        if (__ldg(&fa.prim_aux[kb.id[j]].y) == 0.f && key_less(kb.t[j], kb.tr[j], 0u, tq, tqr, 1u)) {
+          tq = kb.t[j];
+          tqr = kb.tr[j];
+        }
+      } else {  // cannot happen for an FP32 hit outside its bounds; dropped if it does
+        kb.t[j] = kInf;
+        kb.tr[j] = 0.f;
+        kb.id[j] = 0xffffffffu;
+      }
+    }
   }
+#pragma unroll
+  for (int i = 0; i < KMAX; ++i)
+#pragma unroll
+    for (int j = 0; j + 1 < KMAX; ++j)
+      if (key_less(kb.t[j + 1], kb.tr[j + 1], kb.id[j + 1], kb.t[j], kb.tr[j], kb.id[j])) {
+        float a = kb.t[j]; kb.t[j] = kb.t[j + 1]; kb.t[j + 1] = a;
+        float r = kb.tr[j]; kb.tr[j] = kb.tr[j + 1]; kb.tr[j + 1] = r;
+        uint32_t b = kb.id[j]; kb.id[j] = kb.id[j + 1]; kb.id[j + 1] = b;
+        float e = kb.ch[j]; kb.ch[j] = kb.ch[j + 1]; kb.ch[j + 1] = e;
+      }
+}
+
+// Test primitive `id` (a leaf names its global primitive id) and keep it in
+// the k-buffer when it is among the K nearest before the nearest opaque
+// (strand) hit.  An FP32 hit is kept as it is when its depth bound is narrow
+// and no other hit or the cut lies within its bound plus the widest bound of
+// the FP32 hits kept so far (errmax); otherwise the ray switches to precise
+// ordering (`fine`) for the rest of its search.
+template <int KMAX, bool COUNT>
+__device__ __forceinline__ void leaf_test(const FrameArgs& fa, const RayKey& rk, uint32_t id,
+                                          const float3 o, const float3 d, KBuf<KMAX>& kb,
+                                          float& tcut, float& tq, float& tqr, float& errmax,
+                                          bool& fine, Counts& cn) {
+  float th, ch, terr;
+  if (COUNT) ++cn.tests;
+  const float M = fabsf(o.x) + fabsf(o.y) + fabsf(o.z);
+  const int r =
+      intersect32(fa.prim_xf + 3 * (size_t)id, o, d, M, tcut + errmax, th, ch, terr);
+  if (r == kMiss) return;
+  const float slack = terr + errmax;
+  bool need = fine || r == kBorder || terr > kTieRel * (rk.t_off + th) || th >= tcut - slack;
+  if (!need) {
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+      if (j < (int)fa.k && fabsf(th - kb.t[j]) <= slack) need = true;
+  }
+  float tr = 0.f;
+  if (need) {
+    if (!fine) {
+      fine = true;
+      refine_all<KMAX>(fa, rk, kb, tq, tqr);
+      errmax = 0.f;
+      if (COUNT) ++cn.precise_rays;
+    }
+    if (COUNT) ++cn.precise_tests;
+    float tl;
+    if (!refine(fa, rk, id, th, th, tl, ch)) return;
+    tr = tl;
+    if (key_less(tq, tqr, 0u, th, tr, 1u)) return;  // behind the nearest opaque hit
+  } else {
+    errmax = fmaxf(errmax, terr);
+  }
+  kbuf_insert<KMAX>(kb, fa.k, th, tr, id, ch);
+  if (__ldg(&fa.prim_aux[id].y) == 0.f && key_less(th, tr, 0u, tq, tqr, 1u)) {  // strand: opaque
+    tq = th;
+    tqr = tr;
+  }
+  tcut = fminf(kbuf_last<KMAX>(kb, fa.k), tq);
 }
 
 // K nearest hits of one ray.  Returns false when the traversal stack overflowed
 // (the far subtree was dropped; counted by the caller, never expected).
+// Boxes are culled against the cut widened by the FP32 hits' depth bound and
+// by 2 kTieRel of the absolute depth, so that no hit the precise ordering
+// would keep is lost to FP32 rounding of the slab tests.
 template <int KMAX, bool COUNT>
-__device__ __forceinline__ bool traverse(const FrameArgs& fa, const float3 o, const float3 d,
-                                         KBuf<KMAX>& kb, Counts& cn) {
+__device__ __forceinline__ bool traverse(const FrameArgs& fa, const RayKey& rk, const float3 o,
+                                         const float3 d, KBuf<KMAX>& kb, Counts& cn) {
   kbuf_init<KMAX>(kb);
   if (fa.n_prims == 0) return true;
-  float tcut = kInf, topq = kInf;
+  float tcut = kInf, tq = kInf, tqr = 0.f, errmax = 0.f;
+  bool fine = false;
   if (fa.n_prims == 1) {
-    leaf_test<KMAX, COUNT>(fa, 0, o, d, kb, tcut, topq, cn);
+    leaf_test<KMAX, COUNT>(fa, rk, __ldg(fa.leaf_id), o, d, kb, tcut, tq, tqr, errmax, fine, cn);
     return true;
   }
   // a zero direction component would turn the slab products into inf - inf;
@@ -200,18 +501,19 @@ __device__ __forceinline__ bool traverse(const FrameArgs& fa, const float3 o, co
       const float4* nd = fa.nodes + 4 * (size_t)node;
       const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
       if (COUNT) ++cn.nodes;
+      const float tb = fmaf(tcut + errmax, 1.f + 2.f * kTieRel, 2.f * kTieRel * rk.t_off);
       // child 0
       float lx = fmaf(n0.x, inv.x, -ooi.x), hx = fmaf(n0.y, inv.x, -ooi.x);
       float ly = fmaf(n0.z, inv.y, -ooi.y), hy = fmaf(n0.w, inv.y, -ooi.y);
       float lz = fmaf(n2.x, inv.z, -ooi.z), hz = fmaf(n2.y, inv.z, -ooi.z);
       const float a0 = fmaxf(fmaxf(fminf(lx, hx), fminf(ly, hy)), fmaxf(fminf(lz, hz), 0.f));
-      const float b0 = fminf(fminf(fmaxf(lx, hx), fmaxf(ly, hy)), fminf(fmaxf(lz, hz), tcut));
+      const float b0 = fminf(fminf(fmaxf(lx, hx), fmaxf(ly, hy)), fminf(fmaxf(lz, hz), tb));
       // child 1
       lx = fmaf(n1.x, inv.x, -ooi.x); hx = fmaf(n1.y, inv.x, -ooi.x);
       ly = fmaf(n1.z, inv.y, -ooi.y); hy = fmaf(n1.w, inv.y, -ooi.y);
       lz = fmaf(n2.z, inv.z, -ooi.z); hz = fmaf(n2.w, inv.z, -ooi.z);
       const float a1 = fmaxf(fmaxf(fminf(lx, hx), fminf(ly, hy)), fmaxf(fminf(lz, hz), 0.f));
-      const float b1 = fminf(fminf(fmaxf(lx, hx), fmaxf(ly, hy)), fminf(fmaxf(lz, hz), tcut));
+      const float b1 = fminf(fminf(fmaxf(lx, hx), fmaxf(ly, hy)), fminf(fmaxf(lz, hz), tb));
       const bool h0 = a0 <= b0, h1 = a1 <= b1;
       const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
       if (h0 && h1) {
@@ -229,7 +531,8 @@ __device__ __forceinline__ bool traverse(const FrameArgs& fa, const float3 o, co
         continue;
       }
     } else {
-      leaf_test<KMAX, COUNT>(fa, (uint32_t)(~node), o, d, kb, tcut, topq, cn);
+      leaf_test<KMAX, COUNT>(fa, rk, (uint32_t)(~node), o, d, kb, tcut, tq, tqr, errmax, fine,
+                             cn);
     }
     if (sp == 0) break;
     node = stack[--sp];
@@ -487,7 +790,7 @@ __device__ __forceinline__ void shadow_path(const FrameArgs& fa, const float3 x,
   ray_slabs(x, wi, inv, ooi);
   int stack[kStack];
   int sp = 0;
-  int node = fa.n_prims == 1 ? ~0 : 0;
+  int node = fa.n_prims == 1 ? ~(int)__ldg(fa.leaf_id) : 0;
   bool crossed = false;
   for (;;) {
     if (node >= 0) {
@@ -519,13 +822,13 @@ __device__ __forceinline__ void shadow_path(const FrameArgs& fa, const float3 x,
         continue;
       }
     } else {
-      const uint32_t leaf = (uint32_t)(~node);
-      const float4 aux = __ldg(fa.leaf_aux + leaf);
+      const uint32_t id = (uint32_t)(~node);
+      const float4 aux = __ldg(fa.prim_aux + id);
       float lo, hi;
       if (COUNT) ++cn.tests;
       if (__float_as_uint(aux.x) != self_mat &&
-          leaf_span(fa.leaf_xf + 3 * (size_t)leaf, x, wi, tmax, lo, hi)) {
-        const float4 r2 = __ldg(fa.leaf_xf + 3 * (size_t)leaf + 2);
+          leaf_span(fa.prim_xf + 3 * (size_t)id, x, wi, tmax, lo, hi)) {
+        const float4 r2 = __ldg(fa.prim_xf + 3 * (size_t)id + 2);
         const float si = clampf(dot3(wi, f3(r2.x, r2.y, r2.z)) *
                                     rsqrtf(r2.x * r2.x + r2.y * r2.y + r2.z * r2.z),
                                 -1.f, 1.f);
@@ -565,11 +868,11 @@ __device__ __forceinline__ void shadow_path(const FrameArgs& fa, const float3 x,
 // SHADOW is a template parameter so kernels without shadow rays carry none
 // of their registers.
 template <int PREC, bool COUNT, bool SHADOW = false>
-__device__ __forceinline__ void shade_hit(const FrameArgs& fa, uint32_t leaf, float t, float chord,
+__device__ __forceinline__ void shade_hit(const FrameArgs& fa, uint32_t id, float t, float chord,
                                           const float3 o, const float3 d, float rgb[3],
                                           float& alpha, Counts& cn) {
-  const float4 aux = __ldg(fa.leaf_aux + leaf);
-  const float4 r2 = __ldg(fa.leaf_xf + 3 * (size_t)leaf + 2);
+  const float4 aux = __ldg(fa.prim_aux + id);
+  const float4 r2 = __ldg(fa.prim_xf + 3 * (size_t)id + 2);
   const float3 T = f3(r2.x, r2.y, r2.z) * rsqrtf(r2.x * r2.x + r2.y * r2.y + r2.z * r2.z);
   Mat m;
   load_mat(fa.mat + (size_t)__float_as_uint(aux.x) * HR_MAT_FLOATS, m);
@@ -636,10 +939,11 @@ __device__ __forceinline__ void shade_hit(const FrameArgs& fa, uint32_t leaf, fl
 
 // One sample: ray, K nearest hits, shading and front-to-back compositing.
 template <int KMAX, int PREC, bool COUNT, bool SHADOW = false>
-__device__ __forceinline__ void render_ray(const FrameArgs& fa, const float3 o, const float3 d,
-                                           float out[3], int32_t* ids, bool& ok, Counts& cn) {
+__device__ __forceinline__ void render_ray(const FrameArgs& fa, const RayKey& rk, const float3 o,
+                                           const float3 d, float out[3], int32_t* ids, bool& ok,
+                                           Counts& cn) {
   KBuf<KMAX> kb;
-  ok = traverse<KMAX, COUNT>(fa, o, d, kb, cn);
+  ok = traverse<KMAX, COUNT>(fa, rk, o, d, kb, cn);
   float T = 1.f;
   out[0] = out[1] = out[2] = 0.f;
   if (ids) {  // the composited hits: none after the first opaque (strand) one
@@ -649,14 +953,14 @@ __device__ __forceinline__ void render_ray(const FrameArgs& fa, const float3 o, 
       if (j < (int)fa.k) {
         const bool live = kb.t[j] < kInf && !past;
         ids[j] = live ? (int32_t)kb.id[j] : -1;
-        if (live && __ldg(&fa.leaf_aux[kb.leaf[j]].y) == 0.f) past = true;
+        if (live && __ldg(&fa.prim_aux[kb.id[j]].y) == 0.f) past = true;
       }
   }
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) {
     if (j < (int)fa.k && kb.t[j] < kInf && T > 0.f) {
       float rgb[3], a;
-      shade_hit<PREC, COUNT, SHADOW>(fa, kb.leaf[j], kb.t[j], kb.ch[j], o, d, rgb, a, cn);
+      shade_hit<PREC, COUNT, SHADOW>(fa, kb.id[j], kb.t[j], kb.ch[j], o, d, rgb, a, cn);
       if (COUNT) ++cn.hits;
       const float ta = T * a;
       out[0] = fmaf(ta, rgb[0], out[0]);
@@ -670,15 +974,17 @@ __device__ __forceinline__ void render_ray(const FrameArgs& fa, const float3 o, 
 template <int KMAX, int PREC, bool COUNT, bool SHADOW = false>
 __device__ __forceinline__ void render_sample(const FrameArgs& fa, uint64_t sid, float out[3],
                                               int32_t* ids, bool& ok, Counts& cn) {
+  RayKey rk;
   float3 o, d;
-  camera_ray(fa.cam, fa.seed, sid, fa.spp, o, d);
-  render_ray<KMAX, PREC, COUNT, SHADOW>(fa, o, d, out, ids, ok, cn);
+  primary_ray(fa, sid, o, d, rk);
+  render_ray<KMAX, PREC, COUNT, SHADOW>(fa, rk, o, d, out, ids, ok, cn);
 }
 
 __device__ __forceinline__ void flush_counts(const FrameArgs& fa, const Counts& cn) {
-  unsigned long long v[6] = {cn.nodes, cn.tests, cn.sshade, cn.eshade, cn.hits, cn.rays};
+  unsigned long long v[8] = {cn.nodes, cn.tests, cn.sshade, cn.eshade, cn.hits, cn.rays,
+                             cn.precise_tests, cn.precise_rays};
 #pragma unroll
-  for (int i = 0; i < 6; ++i) {
+  for (int i = 0; i < 8; ++i) {
     unsigned long long x = v[i];
 #pragma unroll
     for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -732,58 +1038,6 @@ __device__ __forceinline__ void scene_rect_warp(const FrameArgs& fa, float4* rec
   }
 }
 
-// Block-wide version (the first warp computes, every thread reads `rect`).
-__device__ __forceinline__ void scene_rect(const FrameArgs& fa, float4* rect) {
-  if (threadIdx.x < 32) scene_rect_warp(fa, rect);
-  __syncthreads();
-}
-
-// Render one tile: each pixel's samples are spread over `grp` adjacent lanes
-// (sample s on lane s mod grp), every lane traces its samples and the pixel
-// mean is a fixed XOR-shuffle sum over the group divided by spp.  Pixels
-// outside `rect` are background.  All 32 lanes of every warp reach the
-// shuffles (no early return).
-template <int KMAX, int PREC, bool COUNT, bool SHADOW = false>
-__device__ __forceinline__ void render_tile_xy(const FrameArgs& fa, uint32_t tx, uint32_t ty,
-                                               const float4 rect, float* __restrict__ rgb,
-                                               Counts& cn, bool& overflow) {
-  const uint32_t G = fa.grp;
-  const uint32_t lane_g = threadIdx.x & (G - 1);
-  const uint32_t pib = threadIdx.x / G;  // pixel in block
-  const uint32_t x = tx * fa.tile_w + pib % fa.tile_w;
-  const uint32_t y = ty * fa.tile_h + pib / fa.tile_w;
-  const bool valid = x < (uint32_t)fa.cam.W && y < (uint32_t)fa.cam.H;
-  const bool inside = valid && (float)x + 1.f >= rect.x && (float)x <= rect.z &&
-                      (float)y + 1.f >= rect.y && (float)y <= rect.w;
-  const uint64_t pixel = (uint64_t)y * (uint32_t)fa.cam.W + x;
-  float acc[3] = {0.f, 0.f, 0.f};
-  if (inside) {
-    for (uint32_t s = lane_g; s < fa.spp; s += G) {
-      float v[3];
-      bool ok;
-      float3 o, d;
-      camera_ray_xy(fa.cam, fa.seed, pixel * fa.spp + s, x, y, o, d);
-      render_ray<KMAX, PREC, COUNT, SHADOW>(fa, o, d, v, nullptr, ok, cn);
-      if (COUNT) ++cn.rays;
-      overflow |= !ok;
-      acc[0] += v[0];
-      acc[1] += v[1];
-      acc[2] += v[2];
-    }
-  }
-  for (uint32_t o = 1; o < G; o <<= 1) {
-    acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
-    acc[1] += __shfl_xor_sync(0xffffffffu, acc[1], o);
-    acc[2] += __shfl_xor_sync(0xffffffffu, acc[2], o);
-  }
-  if (valid && lane_g == 0) {
-    const float inv = 1.0f / (float)fa.spp;
-    rgb[3 * pixel] = acc[0] * inv;
-    rgb[3 * pixel + 1] = acc[1] * inv;
-    rgb[3 * pixel + 2] = acc[2] * inv;
-  }
-}
-
 // Warp tile: the 32 / grp pixels one warp renders (wtw x wth); a pixel's
 // samples on `grp` adjacent lanes, summed with a fixed XOR-shuffle tree.
 // Called by whole warps.
@@ -806,9 +1060,10 @@ __device__ __forceinline__ void render_warp_tile(const FrameArgs& fa, uint32_t x
     for (uint32_t s = lane_g; s < fa.spp; s += G) {
       float v[3];
       bool ok;
+      RayKey rk;
       float3 o, d;
-      camera_ray_xy(fa.cam, fa.seed, pixel * fa.spp + s, x, y, o, d);
-      render_ray<KMAX, PREC, COUNT, SHADOW>(fa, o, d, v, nullptr, ok, cn);
+      primary_ray(fa, pixel * fa.spp + s, o, d, rk);
+      render_ray<KMAX, PREC, COUNT, SHADOW>(fa, rk, o, d, v, nullptr, ok, cn);
       if (COUNT) ++cn.rays;
       overflow |= !ok;
       acc[0] += v[0];
@@ -827,13 +1082,6 @@ __device__ __forceinline__ void render_warp_tile(const FrameArgs& fa, uint32_t x
     rgb[3 * pixel + 1] = acc[1] * inv;
     rgb[3 * pixel + 2] = acc[2] * inv;
   }
-}
-
-template <int KMAX, int PREC, bool COUNT, bool SHADOW = false>
-__device__ __forceinline__ void render_tile(const FrameArgs& fa, uint32_t tile, const float4 rect,
-                                            float* __restrict__ rgb, Counts& cn, bool& overflow) {
-  const uint32_t tiles_x = ((uint32_t)fa.cam.W + fa.tile_w - 1) / fa.tile_w;
-  render_tile_xy<KMAX, PREC, COUNT, SHADOW>(fa, tile % tiles_x, tile / tiles_x, rect, rgb, cn, overflow);
 }
 
 }  // namespace tr

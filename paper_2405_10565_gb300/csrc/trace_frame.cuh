@@ -29,30 +29,18 @@ __global__ void __launch_bounds__(kBlock, SHADOW ? 1 : 5)
     k_frame(const FrameArgs fa, const float4* __restrict__ rect_p, uint32_t* work,
             float* __restrict__ rgb) {
   const float4 rect = *rect_p;
-  const uint32_t P = 32u / fa.grp;  // pixels per warp tile
-  uint32_t wtw = 1;
-  while (wtw * wtw < P) wtw <<= 1;
-  const uint32_t wth = P / wtw;
-  const uint32_t W = (uint32_t)fa.cam.W, H = (uint32_t)fa.cam.H;
-  const float fx0 = fmaxf(0.f, floorf(rect.x)), fy0 = fmaxf(0.f, floorf(rect.y));
-  const float fx1 = fminf(rect.z, (float)W - 1.f), fy1 = fminf(rect.w, (float)H - 1.f);
-  uint32_t n = 0, nx = 0, x0 = 0, y0 = 0;
-  if (fx0 <= fx1 && fy0 <= fy1) {
-    x0 = (uint32_t)fx0 / wtw * wtw;
-    y0 = (uint32_t)fy0 / wth * wth;
-    nx = ((uint32_t)fx1 - x0) / wtw + 1;
-    n = nx * (((uint32_t)fy1 - y0) / wth + 1);
-  }
-  tr::Counts cn{0, 0, 0, 0, 0, 0};
+  const WarpGrid g = warp_grid(rect, (uint32_t)fa.cam.W, (uint32_t)fa.cam.H, fa.grp);
+  tr::Counts cn{0, 0, 0, 0, 0, 0, 0, 0};
   bool overflow = false;
   const uint32_t lane = threadIdx.x & 31;
   for (;;) {
     uint32_t t = 0;
     if (lane == 0) t = atomicAdd(work, 1u);
     t = __shfl_sync(0xffffffffu, t, 0);
-    if (t >= n) break;
-    tr::render_warp_tile<KMAX, PREC, COUNT, SHADOW>(fa, x0 + (t % nx) * wtw, y0 + (t / nx) * wth, wtw,
-                                            rect, rgb, cn, overflow);
+    if (t >= g.n) break;
+    tr::render_warp_tile<KMAX, PREC, COUNT, SHADOW>(fa, g.x0 + (t % g.nx) * g.wtw,
+                                                    g.y0 + (t / g.nx) * g.wth, g.wtw, rect, rgb,
+                                                    cn, overflow);
   }
   if (COUNT) tr::flush_counts(fa, cn);
   if (overflow) atomicAdd(fa.overflow, 1u);

@@ -12,7 +12,7 @@ __global__ void __launch_bounds__(128)
               float* __restrict__ rad, int32_t* __restrict__ hit) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
-  tr::Counts cn{0, 0, 0, 0, 0, 0};
+  tr::Counts cn{0, 0, 0, 0, 0, 0, 0, 0};
   float v[3];
   int32_t ids[KMAX];
   bool ok;

@@ -1,8 +1,10 @@
-// Batched persistent serving kernel: one launch renders tiles of several
-// requests.  Blocks take batch tiles from a work counter until the batch is
-// exhausted (no block ever waits on another), locate the owning item by
-// binary search over the items' first batch tiles, and render that tile with
-// the item's own scene, camera and output.
+// Batched persistent serving kernel: one launch renders warp tiles of several
+// requests.  Warps take batch tiles from a work counter until the batch is
+// exhausted (no warp ever waits on another), locate the owning item by binary
+// search over the items' first batch tiles, and render that warp tile with
+// the item's own scene, camera and output, as the frame kernel does: only the
+// tiles over a request's projected scene rectangle are enumerated, the rest
+// of its image having been cleared to background at admission.
 #include <algorithm>
 
 #include "serve.h"
@@ -11,18 +13,18 @@
 namespace hr {
 namespace {
 
+__global__ void k_serve_rect(const FrameArgs fa, float4* rect) { tr::scene_rect_warp(fa, rect); }
+
 template <int KMAX, int PREC>
 // 5 blocks per SM (at most 96 registers), as for the frame kernel.
 __global__ void __launch_bounds__(kBlock, 5)
     k_serve(const ServeItem* __restrict__ items, const uint32_t* __restrict__ item_start,
             uint32_t n_items, uint32_t total, uint32_t* work) {
-  __shared__ uint32_t s_tile;
-  __shared__ float4 s_rect;
+  const uint32_t lane = threadIdx.x & 31;
   for (;;) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(work, 1u);
-    __syncthreads();
-    const uint32_t bt = s_tile;
-    __syncthreads();
+    uint32_t bt = 0;
+    if (lane == 0) bt = atomicAdd(work, 1u);
+    bt = __shfl_sync(0xffffffffu, bt, 0);
     if (bt >= total) return;
     uint32_t lo = 0, hi = n_items;  // last item with start <= bt
     while (hi - lo > 1) {
@@ -30,11 +32,13 @@ __global__ void __launch_bounds__(kBlock, 5)
       if (item_start[mid] <= bt) lo = mid; else hi = mid;
     }
     const ServeItem& it = items[lo];
-    tr::scene_rect(it.fa, &s_rect);
-    tr::Counts cn{0, 0, 0, 0, 0, 0};
+    const WarpGrid g = it.grid;
+    const uint32_t t = it.wt0 + (bt - item_start[lo]);
+    tr::Counts cn{0, 0, 0, 0, 0, 0, 0, 0};
     bool overflow = false;
-    tr::render_tile<KMAX, PREC, false>(it.fa, it.tile0 + (bt - item_start[lo]), s_rect, it.rgb,
-                                       cn, overflow);
+    tr::render_warp_tile<KMAX, PREC, false>(it.fa, g.x0 + (t % g.nx) * g.wtw,
+                                            g.y0 + (t / g.nx) * g.wth, g.wtw, it.rect, it.rgb, cn,
+                                            overflow);
     if (overflow) atomicAdd(it.fa.overflow, 1u);
   }
 }
@@ -71,6 +75,12 @@ int serve_grid(int kmax, int precision) {
     blocks = 4;
   }
   return sms * std::max(1, blocks);
+}
+
+hr_status launch_scene_rect(hr_ctx* ctx, const FrameArgs& fa, float4* rect_dev, cudaStream_t st) {
+  k_serve_rect<<<1, 32, 0, st>>>(fa, rect_dev);
+  HR_LAUNCHED(ctx);
+  return HR_OK;
 }
 
 hr_status launch_serve_batch(hr_ctx* ctx, int kmax, int precision, const ServeItem* items_dev,

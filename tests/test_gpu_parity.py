@@ -165,6 +165,13 @@ def test_lod_widths_and_selection(ctx, fill):
         lb = np.zeros(C, np.uint8)
         hr.hr_select_lod(ctx, a, cam, w.eps_w, 0, 1, lb)
         assert np.array_equal(lb[~near], oracle.apply_budget(lo, 1)[~near])
+        # Eq. 14 with the hysteresis band (mode 2): thresholds 1.1 eps and 0.9 eps
+        near_h = near | np.any(np.abs(wo / np.float32(1.1 * w.eps_w) - 1) < 1e-4, axis=1) | \
+            np.any(np.abs(wo / np.float32(0.9 * w.eps_w) - 1) < 1e-4, axis=1)
+        lh = prev.copy()
+        hr.hr_select_lod(ctx, a, cam, w.eps_w, 2, 0, lh)
+        want_h = oracle.select_lod_deferred(wo, prev, w.eps_w, L, hysteresis=True)
+        assert np.array_equal(lh[~near_h], want_h[~near_h])
         print(f"fill {fill}: levels {np.bincount(lg, minlength=L + 1).tolist()}, near {near.sum()}, "
               f"widths bit-identical {exact.mean():.3f}")
     finally:
@@ -450,13 +457,16 @@ def test_asset_update_matches_a_fresh_asset(ctx):
         hr.hr_asset_destroy(ctx, b)
 
 
-def _moved(verts, amp, seed=3):
-    """The same strands displaced by a smooth field (radius column kept)."""
+def _moved(verts, amp, seed=3, anchored=False):
+    """The same strands displaced by a smooth field (radius column kept);
+    anchored: the displacement grows from 0 at the root (roots stay on the
+    scalp, as attached hair does)."""
     v = np.array(verts, np.float32, copy=True)
     p = v[..., :3].astype(np.float64)
     ph = 1.0 + 0.1 * seed
-    v[..., 0] += (amp * np.sin(7.0 * p[..., 1] + ph)).astype(np.float32)
-    v[..., 2] += (amp * np.cos(5.0 * p[..., 0] - ph)).astype(np.float32)
+    g = np.linspace(0.0, 1.0, v.shape[1])[None, :] if anchored else 1.0
+    v[..., 0] += (amp * g * np.sin(7.0 * p[..., 1] + ph)).astype(np.float32)
+    v[..., 2] += (amp * g * np.cos(5.0 * p[..., 0] - ph)).astype(np.float32)
     return v
 
 
@@ -466,7 +476,7 @@ def test_frame_refit_matches_rebuild(ctx):
     rebuilt one; with the LoD changed the frame call rebuilds."""
     w = scenegen.full_head(n=6000, S=16, width=96, height=64, spp=2, n_lights=2, n_clusters=256)
     d = desc_of(w)
-    moved = _moved(w.scene.verts, 2e-5)
+    moved = _moved(w.scene.verts, 2e-5, anchored=True)
     a = upload(ctx, w.scene)
     b = hr.hr_asset_create(ctx, moved, np.ascontiguousarray(w.scene.mat),
                            np.ascontiguousarray(w.scene.shape))
@@ -724,5 +734,40 @@ def test_marschner_trt_with_shadow_rays(ctx):
         assert same.mean() >= KBUF_AGREE_MIN
         assert ok.sum() / max(1, same.sum()) >= SHADOW_AGREE_MIN
         assert rmse <= RMSE_FP32
+    finally:
+        hr.hr_asset_destroy(ctx, a)
+
+
+def test_refit_engages_under_small_motion_with_hysteresis(ctx):
+    """Animated frames (hr_asset_update with a small displacement every frame,
+    roots kept on the scalp) under HR_FLAG_REFIT | HR_FLAG_DEFERRED_LOD |
+    HR_FLAG_LOD_HYSTERESIS keep every cluster's strands and level, so every
+    frame after the first refits its BVH, and a refit frame equals a rebuilt
+    BVH at the same LoD.  Motion that moves the roots reorders the clusters,
+    and the frame then rebuilds."""
+    w = scenegen.full_head(n=20000, S=32, width=192, height=128, spp=2, n_lights=4,
+                           n_clusters=800)
+    poses = [np.ascontiguousarray(w.scene.verts), _moved(w.scene.verts, 2e-5, anchored=True)]
+    flags = hr.HR_FLAG_REFIT | hr.HR_FLAG_DEFERRED_LOD | hr.HR_FLAG_LOD_HYSTERESIS
+    d = desc_of(w, flags=flags)
+    a = upload(ctx, w.scene)
+    try:
+        img = np.zeros((128, 192, 3), np.float32)
+        hr.hr_render_frame(ctx, a, w.n_clusters, w.eps_w, 0, d, img)
+        refits = 0
+        for i in range(6):
+            hr.hr_asset_update(ctx, a, poses[(i + 1) % 2])
+            st = hr.hr_render_frame(ctx, a, w.n_clusters, w.eps_w, 0, d, img, stats=True)
+            refits += st.bvh_refit
+        assert refits == 6, refits
+        ref = np.zeros_like(img)
+        hr.hr_build_bvh(ctx, a, None)  # the asset's current selection
+        hr.hr_render(ctx, a, desc_of(w), ref)
+        assert ref.max() > 0
+        assert np.allclose(img, ref, rtol=1e-6, atol=1e-7), np.abs(img - ref).max()
+        # roots moved: the Morton clusters change, so no refit
+        hr.hr_asset_update(ctx, a, _moved(w.scene.verts, 2e-3))
+        st = hr.hr_render_frame(ctx, a, w.n_clusters, w.eps_w, 0, d, img, stats=True)
+        assert st.bvh_refit == 0
     finally:
         hr.hr_asset_destroy(ctx, a)

@@ -101,3 +101,19 @@ def test_cluster_level_widths_hand_worked():
     h = oracle.Hierarchy(0, 2, 2, None, None, None, None, None, None, np.ones(E, np.int64), cl, lv)
     w = oracle.cluster_level_widths(h, eth, cam)
     assert np.allclose(w, [[6.0, 4.0], [2.0, 1.4]], rtol=1e-6)
+
+
+def test_deferred_rule_with_hysteresis_hand_worked():
+    # eps = 2 px: refine above 2.2 px, coarsen at or below 1.8 px
+    w = np.array([[5.0, 2.1, 1.0],    # L=1, w_cur 2.1: over eps but inside the band -> stay 1
+                  [5.0, 2.3, 1.0],    # L=1, w_cur 2.3 > 2.2 -> 2
+                  [5.0, 1.9, 1.0],    # L=2, w_cur- 1.9 > 1.8 -> stay 2
+                  [5.0, 1.8, 1.0],    # L=2, w_cur- 1.8 <= 1.8 -> 1
+                  [3.0, 1.5, 0.7],    # L=3 (strands), w_cur- 0.7 <= 1.8 -> 2
+                  [2.15, 1.0, 0.5]],  # L=0, w_cur 2.15 inside the band, w_cur- = inf -> stay 0
+                 np.float32)
+    prev = np.array([1, 1, 2, 2, 3, 0], np.uint8)
+    out = oracle.select_lod_deferred(w, prev, 2.0, 3, hysteresis=True)
+    assert out.tolist() == [1, 2, 2, 1, 2, 0]
+    # without the band the first and last rows refine, the third coarsens
+    assert oracle.select_lod_deferred(w, prev, 2.0, 3).tolist() == [2, 2, 1, 1, 2, 1]
