@@ -278,7 +278,7 @@ def measure_config(hr, ctx, torch, dev, w, steps: int, warmup: int = 2, peak_tfl
            "active_prims": int(st.n_active_prims), "eth_prims": int(st.n_eth_prims),
            "traced_samples": int(st.traced_samples), "frame_ms": frame_ms,
            "prim_tests": int(st.prim_tests), "refined_tests": int(st.refined_tests),
-           "refined_rays": int(st.refined_rays)}
+           "refined_entries": int(st.refined_entries)}
     out["traced_msamples_per_s_frame"] = st.traced_samples / (frame_ms * 1e-3) / 1e6
     if peak_tflops:
         tf = event_flops(st) / (frame_ms * 1e-3) / 1e12
@@ -741,7 +741,7 @@ def main():
                              "strand_shades": cst.strand_shades, "eth_shades": cst.eth_shades,
                              "hits": cst.shaded_hits, "traced_samples": cst.traced_samples,
                              "samples": samples, "refined_tests": cst.refined_tests,
-                             "refined_rays": cst.refined_rays}}
+                             "refined_entries": cst.refined_entries}}
     # FP32 work of the cross-section fit: every strand is a member of one thick
     # hair per level, so the members sum to N * levels over S+1 sections
     C_, L_, E_ = n_levels_info

@@ -193,9 +193,10 @@ typedef struct hr_stats {
   uint32_t bvh_refit;       /* 1 when hr_render_frame refit the BVH (HR_FLAG_REFIT) */
   uint32_t lod_deferred;    /* 1 when it chose the LoD with Eq. 14 (HR_FLAG_DEFERRED_LOD) */
   /* filled only with HR_FLAG_COUNT: the precise decision path */
-  uint64_t refined_tests;   /* primitive tests decided precisely (near an outline,
-                               an end, the search cut or another hit) */
-  uint64_t refined_rays;    /* samples whose k-buffer switched to precise ordering */
+  uint64_t refined_tests;   /* hits decided precisely (near an outline, an end, the
+                               search cut or another hit, or a wide FP32 bound) */
+  uint64_t refined_entries; /* kept FP32 hits decided precisely afterwards (their
+                               order against a precise hit was open) */
 } hr_stats;
 
 /* ---------------------------------------------------------------- context */
@@ -218,7 +219,9 @@ uint64_t hr_kernel_launches(hr_ctx* ctx);
 
 /* Copy a hair model to the device and precompute every strand segment's
  * elliptic-cylinder record (Section 4 "elliptical cross-section").
- * n_strands >= 1, 1 <= n_segments <= 4096, n_strands * n_segments < 2^31. */
+ * n_strands >= 1, 1 <= n_segments <= 4096, n_strands * n_segments < 2^30
+ * (primitive ids are 30 bits; strand and thick-hair segments together must
+ * stay below 2^30, else hr_build_clusters gives HR_EINVAL). */
 hr_status hr_asset_create(hr_ctx* ctx, const hr_hair_desc* desc, hr_asset** out);
 hr_status hr_asset_destroy(hr_ctx* ctx, hr_asset* asset);
 

@@ -79,7 +79,7 @@ class hr_stats(ctypes.Structure):
                 ("hierarchy_ms", ctypes.c_double), ("fit_ms", ctypes.c_double),
                 ("lod_ms", ctypes.c_double), ("bvh_ms", ctypes.c_double),
                 ("bvh_refit", c_u32), ("lod_deferred", c_u32),
-                ("refined_tests", c_u64), ("refined_rays", c_u64)]
+                ("refined_tests", c_u64), ("refined_entries", c_u64)]
 
 
 class hr_request(ctypes.Structure):

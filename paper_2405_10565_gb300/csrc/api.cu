@@ -290,7 +290,7 @@ hr_status hr_asset_create(hr_ctx* ctx, const hr_hair_desc* d, hr_asset** out) {
     return set_error(ctx, HR_EINVAL, "hr_asset_create: null argument");
   *out = nullptr;
   if (d->n_strands < 1 || d->n_segments < 1 || d->n_segments > 4096 ||
-      (uint64_t)d->n_strands * d->n_segments >= (1ull << 31))
+      (uint64_t)d->n_strands * d->n_segments >= (1ull << 30))
     return set_error(ctx, HR_EINVAL, "hr_asset_create: sizes out of range");
   cudaStream_t st = ctx->stream;
   hr_asset* a = new hr_asset();
@@ -665,7 +665,7 @@ static hr_status render_impl(hr_ctx* ctx, hr_asset* a, const hr_render_desc* des
     stats->shaded_hits = cnt[4];
     stats->traced_samples = cnt[5];
     stats->refined_tests = cnt[6];
-    stats->refined_rays = cnt[7];
+    stats->refined_entries = cnt[7];
   } else if (!dev_out) {
     HR_CUDA(ctx, cudaStreamSynchronize(st));
   }

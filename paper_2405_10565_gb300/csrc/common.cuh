@@ -227,6 +227,7 @@ hr_status bake_tables(hr_ctx* ctx, float** im32, __half** im16);
 struct LaunchCam {
   int kind, W, H;
   float pix;
+  float ipix_hi, ipix_lo;  // 1 / pix as a double-word pair (host-rounded from FP64)
   float3 eye, right, up, fwd;
 };
 struct LaunchLights {

@@ -903,8 +903,8 @@ hr_status hierarchy_setup(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_lev
   }
   li.off[L] = (uint32_t)E;
   const uint64_t total = (uint64_t)N * S + E * S;
-  if (total >= (1ull << 31) || E >= (1ull << 28))
-    return set_error(ctx, HR_EINVAL, "hierarchy too large for 31-bit primitive ids");
+  if (total >= (1ull << 30) || E >= (1ull << 28))
+    return set_error(ctx, HR_EINVAL, "hierarchy too large for 30-bit primitive ids");
 
   // A hierarchy of the same shape (a new frame of the same hair) reuses the
   // arrays, and keeps the LoD selection as the previous frame's (Eq. 14);

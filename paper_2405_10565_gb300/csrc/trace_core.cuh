@@ -48,7 +48,7 @@ __device__ __forceinline__ float clampf(float x, float lo, float hi) { return fm
 //  * Every camera ray is built in double-word FP32 (the oracle's FP64
 //    construction to about 2^-44) and re-based at its entry into the scene's
 //    bounding box: the FP32 ray (o', d) starts next to the hair, and depths
-//    are kept relative to the entry (t = t_off + t').  FP32 rounding then
+//    are kept relative to that origin.  FP32 rounding then
 //    moves a hit by ~2^-24 of the scene's size instead of ~2^-24 of the
 //    camera distance.
 //  * intersect32 bounds the rounding of its affine rows and of the roots.  A
@@ -56,8 +56,8 @@ __device__ __forceinline__ float clampf(float x, float lo, float hi) { return fm
 //    segment, a hit whose depth bound could reorder it against another hit or
 //    the search cut, or whose bound is wide, is decided by refine: the
 //    double-word ray re-based near the hit relative to the segment's start
-//    point, and the quadratic solved about that point.  From then on the ray
-//    orders its k-buffer precisely.
+//    point, and the quadratic solved about that point.  Kept FP32 hits whose
+//    order against a precise one their bounds leave open are refined too.
 // Far cameras and thin fibres (4K views of 1e-3 strands ten units away)
 // otherwise turn up FP32 rounding errors of a few 1e-7 in position, enough
 // to swap two strands at nearly equal depth or drop a hit at the very edge of
@@ -70,20 +70,20 @@ constexpr float kBoundK = 6.f;            // rounding steps per affine row, with
 // which an FP32 depth bound sends the hit to refine.
 constexpr float kTieRel = 1.52587890625e-05f;  // 2^-16
 
-struct RayKey {  // what rebuilds the ray precisely: the sample id and the re-basing depth
+struct RayKey {  // what rebuilds the ray precisely: the sample id and the re-basing offset
   uint64_t sid;
-  float t_off;
+  float s_off;  // o' = o + s_off v, v the unnormalised direction (|v| >= 1)
 };
 
 // Ray against the open elliptic cylinder of one record, in FP32, with a
 // bound on the rounding of each decision.  kMiss when the ray misses by more
 // than the bound; kBorder when the rounding could change the outcome; else
 // kHit with the nearest root t in (0, tmax] (axial coordinate in [0, 1]),
-// its error bound terr and the chord of the ray inside the finite cylinder.
+// and its error bound terr.
 // M = |o.x| + |o.y| + |o.z| of the ray.
 __device__ __forceinline__ int intersect32(const float4* __restrict__ xf, const float3 o,
                                            const float3 d, const float M, const float tmax,
-                                           float& t_hit, float& chord, float& terr) {
+                                           float& t_hit, float& terr) {
   const float4 r0 = __ldg(xf), r1 = __ldg(xf + 1), r2 = __ldg(xf + 2);
   const float u0 = fmaf(r0.x, o.x, fmaf(r0.y, o.y, fmaf(r0.z, o.z, r0.w)));
   const float v0 = fmaf(r1.x, o.x, fmaf(r1.y, o.y, fmaf(r1.z, o.z, r1.w)));
@@ -143,30 +143,14 @@ __device__ __forceinline__ int intersect32(const float4* __restrict__ xf, const 
   }
   if (t - terr > tmax) return kMiss;
   t_hit = t;
-  // chord: the part of [tm, tp] where the axial coordinate lies in [0, 1]
-  float wlo = -kInf, whi = kInf;
-  if (dw != 0.f) {
-    const float idw = 1.0f / dw;
-    const float ta = -w0 * idw, tb = (1.f - w0) * idw;
-    wlo = fminf(ta, tb);
-    whi = fmaxf(ta, tb);
-  }
-  chord = fmaxf(0.f, fminf(tp, whi) - fmaxf(tm, wlo));
   return border ? kBorder : kHit;
-}
-
-// df / b with the exact remainder of the rounded quotient (FMA) folded into
-// a second quotient: about 2^-46 relative.
-__device__ __forceinline__ df df_div(df a, float b) {
-  const float q1 = __fdiv_rn(a.hi, b);
-  const float r = __fadd_rn(fmaf(-q1, b, a.hi), a.lo);
-  return df_fast(q1, __fdiv_rn(r, b));
 }
 
 // Camera ray of a sample in double-word FP32, the oracle's construction to
 // about 2^-44: sub-pixel offset from the top 24 bits of SplitMix64 outputs
 // 2 sid and 2 sid + 1, image-plane offset ((x + jx) - W / 2,
-// H / 2 - (y + jy)) / pix (exact pairs before the division); perspective
+// H / 2 - (y + jy)) / pix (exact pairs times the double-word 1 / pix);
+// perspective
 // rays leave the eye along v = (fwd + sx right) + sy up, orthographic ones
 // leave (eye + sx right) + sy up along fwd.  v is left unnormalised: the
 // ray's point at parameter s is o + s v.
@@ -191,7 +175,8 @@ static __device__ void camera_ray_dw(const LaunchCam& c, uint64_t seed, uint32_t
   float ex, ey;
   const float ax = two_sum(__fsub_rn(x, 0.5f * (float)c.W), jx, ex);
   const float ay = two_sum(__fsub_rn(0.5f * (float)c.H, y), -jy, ey);
-  const df sx = df_div(df{ax, ex}, c.pix), sy = df_div(df{ay, ey}, c.pix);
+  const df ipix{c.ipix_hi, c.ipix_lo};
+  const df sx = df_mul(df{ax, ex}, ipix), sy = df_mul(df{ay, ey}, ipix);
   const float E[3] = {c.eye.x, c.eye.y, c.eye.z}, R[3] = {c.right.x, c.right.y, c.right.z};
   const float U[3] = {c.up.x, c.up.y, c.up.z}, F[3] = {c.fwd.x, c.fwd.y, c.fwd.z};
 #pragma unroll
@@ -207,8 +192,8 @@ static __device__ void camera_ray_dw(const LaunchCam& c, uint64_t seed, uint32_t
   }
 }
 
-// |v|^2 of a double-word vector, its square root and a reciprocal, in
-// double-word (one Newton correction each from the exact FMA residual).
+// |v|^2 of a double-word vector and its square root in double-word (one
+// Newton correction from the exact FMA residual).
 __device__ __forceinline__ df df_norm2(const df v[3]) {
   return df_add(df_add(df_mul(v[0], v[0]), df_mul(v[1], v[1])), df_mul(v[2], v[2]));
 }
@@ -216,27 +201,21 @@ __device__ __forceinline__ df df_sqrt(df a) {
   const float r = __fsqrt_rn(a.hi);
   return df_fast(r, __fdiv_rn(__fadd_rn(fmaf(-r, r, a.hi), a.lo), 2.f * r));
 }
-__device__ __forceinline__ df df_recip(df a) {
-  const float q = __frcp_rn(a.hi);
-  const float e = __fsub_rn(fmaf(-q, a.hi, 1.f), __fmul_rn(q, a.lo));
-  return df_fast(q, __fmul_rn(q, e));
-}
 
-// The FP32 ray of a sample: the unit direction rounded from double-word, and
-// the origin moved to a little before the ray's entry into the scene's
-// bounding box (the root node's two boxes), o' = o + t_off d, formed in
-// double-word before rounding.  Hits are at depth t_off + t' along (o', d);
-// no primitive lies before the entry, so t' > 0 for every hit.
+// The FP32 ray of a sample: the direction normalised in FP32 (correctly
+// rounded steps, so |d| = 1 within a few ulps), and the origin moved to a
+// little before the ray's entry into the scene's bounding box (the root
+// node's two boxes), o' = o + s_off v, formed in double-word before rounding.
+// Hits are at depth t' past o' along d; no primitive lies before the entry,
+// so t' > 0 for every hit.
 __device__ __forceinline__ void primary_ray(const FrameArgs& fa, uint64_t sid, float3& o,
                                             float3& d, RayKey& rk) {
   PreciseRay ry;
   camera_ray_dw(fa.cam, fa.seed, fa.spp, sid, ry);
-  const df il = df_recip(df_sqrt(df_norm2(ry.v)));
-  df du[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) du[i] = df_mul(ry.v[i], il);
-  d = f3(df_float(du[0]), df_float(du[1]), df_float(du[2]));
-  float t_off = 0.f;
+  const float vx = ry.v[0].hi, vy = ry.v[1].hi, vz = ry.v[2].hi;
+  const float il = __frcp_rn(__fsqrt_rn(fmaf(vx, vx, fmaf(vy, vy, __fmul_rn(vz, vz)))));
+  d = f3(__fmul_rn(vx, il), __fmul_rn(vy, il), __fmul_rn(vz, il));
+  float s_off = 0.f;
   if (fa.n_prims >= 2) {
     const float4 n0 = __ldg(fa.nodes), n1 = __ldg(fa.nodes + 1), n2 = __ldg(fa.nodes + 2);
     const float3 oo = f3(ry.o[0].hi, ry.o[1].hi, ry.o[2].hi);
@@ -249,12 +228,12 @@ __device__ __forceinline__ void primary_ray(const FrameArgs& fa, uint64_t sid, f
     const float t0 = fmaxf(fmaxf(fminf(lx, hx), fminf(ly, hy)), fminf(lz, hz));
     const float t1 = fminf(fminf(fmaxf(lx, hx), fmaxf(ly, hy)), fmaxf(lz, hz));
     // 2^-10 before the FP32 entry: far more than the slab test's rounding
-    if (t0 > 0.f && t0 <= t1) t_off = t0 * (1.f - 9.765625e-4f);
+    if (t0 > 0.f && t0 <= t1) s_off = t0 * (1.f - 9.765625e-4f) * il;
   }
-  rk = RayKey{sid, t_off};
-  o = f3(df_float(df_add(ry.o[0], df_mul(du[0], t_off))),
-         df_float(df_add(ry.o[1], df_mul(du[1], t_off))),
-         df_float(df_add(ry.o[2], df_mul(du[2], t_off))));
+  rk = RayKey{sid, s_off};
+  o = f3(df_float(df_add(ry.o[0], df_mul(ry.v[0], s_off))),
+         df_float(df_add(ry.o[1], df_mul(ry.v[1], s_off))),
+         df_float(df_add(ry.o[2], df_mul(ry.v[2], s_off))));
 }
 
 // The precise decision of one test, for hits the FP32 test cannot order or
@@ -265,13 +244,11 @@ __device__ __forceinline__ void primary_ray(const FrameArgs& fa, uint64_t sid, f
 // ~2^-24 of a segment length instead of ~2^-24 of the camera distance.  The
 // cylinder (the record's FP32 linear rows, through c0) is then solved about
 // it in FP32: the nearest root of o + s v with s > 0 and axial coordinate in
-// [0, 1].  t_est and the result are depths past the ray's re-basing depth
-// rk.t_off; the result is a normalised pair t' = t_hi + t_lo, with the
-// chord.  About 300 FP32 operations, against ~200 FP64 operations (1/64 of
+// [0, 1].  t_est and the result are depths past the re-based origin
+// o' = o + s_off v; the result is a normalised pair t' = t_hi + t_lo.  About 300 FP32 operations, against ~200 FP64 operations (1/64 of
 // the FP32 rate on this GPU) for the same test in FP64.
 static __device__ __noinline__ bool refine(const FrameArgs& fa, const RayKey& rk, uint32_t id,
-                                           float t_est, float& t_hi, float& t_lo,
-                                           float& chord_out) {
+                                           float t_est, float& t_hi, float& t_lo) {
   PreciseRay ry;
   camera_ray_dw(fa.cam, fa.seed, fa.spp, rk.sid, ry);
   const float4* xf = fa.prim_xf + 3 * (size_t)id;
@@ -283,12 +260,16 @@ static __device__ __noinline__ bool refine(const FrameArgs& fa, const RayKey& rk
   else
     c0 = __ldg(fa.xsec + ((size_t)((id - NS) / S) * (S + 1) + (id - NS) % S) * 3);
   const float vx = ry.v[0].hi, vy = ry.v[1].hi, vz = ry.v[2].hi;
-  const df L = df_sqrt(df_norm2(ry.v));  // the absolute depth is s |v|
-  const float s0 = fmaxf((rk.t_off + t_est) / L.hi, 0.f);
+  const df L = df_sqrt(df_norm2(ry.v));  // depth along the unit direction = s |v|
+  // re-base at o + (s_off + s0) v, s0 the FP32 depth estimate past o' in units of v
+  const float s0 = t_est / L.hi;
+  float sb;
+  const float sa = two_sum(rk.s_off, s0, sb);
+  const df sp0{sa, sb};
   const float C0[3] = {c0.x, c0.y, c0.z};
   float p[3];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) p[i] = df_float(df_add(df_add(ry.o[i], -C0[i]), df_mul(ry.v[i], s0)));
+  for (int i = 0; i < 3; ++i) p[i] = df_float(df_add(df_add(ry.o[i], -C0[i]), df_mul(ry.v[i], sp0)));
   const float u0 = fmaf(r0.x, p[0], fmaf(r0.y, p[1], __fmul_rn(r0.z, p[2])));
   const float v0 = fmaf(r1.x, p[0], fmaf(r1.y, p[1], __fmul_rn(r1.z, p[2])));
   const float w0 = fmaf(r2.x, p[0], fmaf(r2.y, p[1], __fmul_rn(r2.z, p[2])));
@@ -306,36 +287,34 @@ static __device__ __noinline__ bool refine(const FrameArgs& fa, const RayKey& rk
   const float sm = __fsub_rn(sc, half), sp = __fadd_rn(sc, half);
   const float wm = fmaf(sm, dw, w0), wp = fmaf(sp, dw, w0);
   float s;
-  if (__fadd_rn(s0, sm) > 0.f && wm >= 0.f && wm <= 1.f)
+  // in front of the eye: s_off + s0 + s > 0 (s_off is 0 unless the eye is
+  // outside the scene box, and then every root is far in front of it)
+  if (__fadd_rn(sa, sm) > 0.f && wm >= 0.f && wm <= 1.f)
     s = sm;
-  else if (__fadd_rn(s0, sp) > 0.f && wp >= 0.f && wp <= 1.f)
+  else if (__fadd_rn(sa, sp) > 0.f && wp >= 0.f && wp <= 1.f)
     s = sp;
   else
     return false;
   float e;
   const float th = two_sum(s0, s, e);
-  const df t = df_add(df_mul(df_fast(th, e), L), -rk.t_off);
+  const df t = df_mul(df_fast(th, e), L);
   t_hi = t.hi;
   t_lo = t.lo;
-  float wlo = -kInf, whi = kInf;
-  if (dw != 0.f) {
-    const float ta = -w0 / dw, tb = (1.f - w0) / dw;
-    wlo = fminf(ta, tb);
-    whi = fmaxf(ta, tb);
-  }
-  chord_out = fmaxf(0.f, fminf(sp, whi) - fmaxf(sm, wlo)) * L.hi;
   return true;
 }
 
-// The K nearest hits: distance, chord and global primitive id (which also
-// addresses the primitive's records).
-// t is the FP32 depth; tr the precise depth's low word when the hit was
-// refined (0 otherwise): entries order by (t, tr, id).
+// The K nearest hits: depth and entry word.  The entry word holds the
+// global primitive id (which also addresses the primitive's records; a thick
+// hair's chord is recomputed from them when it is shaded) and two flags:
+// kExact when the depth was decided precisely (t + tr is then a normalised
+// double-word depth) and kOpaque for a strand hit.  An FP32 entry has tr = 0.
+// Entries order by (t, tr, id).
+constexpr uint32_t kIdMask = 0x3fffffffu, kOpaque = 0x40000000u, kExact = 0x80000000u;
+constexpr uint32_t kNoEntry = kIdMask;  // an empty slot (t = inf)
 template <int KMAX>
 struct KBuf {
   float t[KMAX];
   float tr[KMAX];
-  float ch[KMAX];
   uint32_t id[KMAX];
 };
 
@@ -345,129 +324,114 @@ __device__ __forceinline__ void kbuf_init(KBuf<KMAX>& kb) {
   for (int j = 0; j < KMAX; ++j) {
     kb.t[j] = kInf;
     kb.tr[j] = 0.f;
-    kb.ch[j] = 0.f;
-    kb.id[j] = 0xffffffffu;
+    kb.id[j] = kNoEntry;
   }
 }
 
 __device__ __forceinline__ bool key_less(float t, float tr, uint32_t id, float t2, float tr2,
                                          uint32_t id2) {
-  return t < t2 || (t == t2 && (tr < tr2 || (tr == tr2 && id < id2)));
+  return t < t2 || (t == t2 && (tr < tr2 || (tr == tr2 && (id & kIdMask) < (id2 & kIdMask))));
 }
 
 // Insert keeping the k nearest by (t, tr, id): the candidate bubbles through
 // the sorted slots and whatever falls off the end is dropped.
 template <int KMAX>
 __device__ __forceinline__ void kbuf_insert(KBuf<KMAX>& kb, const uint32_t k, float t, float tr,
-                                            uint32_t id, float ch) {
+                                            uint32_t id) {
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) {
     if (j < (int)k && key_less(t, tr, id, kb.t[j], kb.tr[j], kb.id[j])) {
       float a = kb.t[j]; kb.t[j] = t; t = a;
       float r = kb.tr[j]; kb.tr[j] = tr; tr = r;
       uint32_t b = kb.id[j]; kb.id[j] = id; id = b;
-      float e = kb.ch[j]; kb.ch[j] = ch; ch = e;
     }
   }
 }
 
+// The search cut: the depth of the k-th entry, or of the first opaque entry
+// when it comes earlier (nothing behind an opaque hit is composited).
 template <int KMAX>
-__device__ __forceinline__ float kbuf_last(const KBuf<KMAX>& kb, const uint32_t k) {
+__device__ __forceinline__ float kbuf_cut(const KBuf<KMAX>& kb, const uint32_t k) {
   float r = kInf;
 #pragma unroll
-  for (int j = 0; j < KMAX; ++j)
-    if (j == (int)k - 1) r = kb.t[j];
+  for (int j = KMAX - 1; j >= 0; --j)
+    if (j < (int)k && (j == (int)k - 1 || (kb.id[j] & kOpaque))) r = kb.t[j];
   return r;
 }
 
 struct Counts {
-  uint32_t nodes, tests, sshade, eshade, hits, rays, precise_tests, precise_rays;
+  uint32_t nodes, tests, sshade, eshade, hits, rays, precise_tests, precise_entries;
 };
-
-// The ray switches to precise ordering: every entry refined, the entries
-// re-sorted by (t, tr, id), the nearest opaque hit among them taken again.
-template <int KMAX>
-__device__ __forceinline__ void refine_all(const FrameArgs& fa, const RayKey& rk, KBuf<KMAX>& kb,
-                                           float& tq, float& tqr) {
-  tq = kInf;
-  tqr = 0.f;
-#pragma unroll
-  for (int j = 0; j < KMAX; ++j) {
-    if (j < (int)fa.k && kb.t[j] < kInf) {
-      float th, tl, c;
-      if (refine(fa, rk, kb.id[j], kb.t[j], th, tl, c)) {
-        kb.t[j] = th;
-        kb.tr[j] = tl;
-        kb.ch[j] = c;
-        if (__ldg(&fa.prim_aux[kb.id[j]].y) == 0.f && key_less(kb.t[j], kb.tr[j], 0u, tq, tqr, 1u)) {
-          tq = kb.t[j];
-          tqr = kb.tr[j];
-        }
-      } else {  // cannot happen for an FP32 hit outside its bounds; dropped if it does
-        kb.t[j] = kInf;
-        kb.tr[j] = 0.f;
-        kb.id[j] = 0xffffffffu;
-      }
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < KMAX; ++i)
-#pragma unroll
-    for (int j = 0; j + 1 < KMAX; ++j)
-      if (key_less(kb.t[j + 1], kb.tr[j + 1], kb.id[j + 1], kb.t[j], kb.tr[j], kb.id[j])) {
-        float a = kb.t[j]; kb.t[j] = kb.t[j + 1]; kb.t[j + 1] = a;
-        float r = kb.tr[j]; kb.tr[j] = kb.tr[j + 1]; kb.tr[j + 1] = r;
-        uint32_t b = kb.id[j]; kb.id[j] = kb.id[j + 1]; kb.id[j + 1] = b;
-        float e = kb.ch[j]; kb.ch[j] = kb.ch[j + 1]; kb.ch[j + 1] = e;
-      }
-}
 
 // Test primitive `id` (a leaf names its global primitive id) and keep it in
 // the k-buffer when it is among the K nearest before the nearest opaque
-// (strand) hit.  An FP32 hit is kept as it is when its depth bound is narrow
-// and no other hit or the cut lies within its bound plus the widest bound of
-// the FP32 hits kept so far (errmax); otherwise the ray switches to precise
-// ordering (`fine`) for the rest of its search.
+// (strand) hit.  An FP32 hit is kept as it is when its depth bound terr is
+// narrow, it is not near the outline or an end, and neither the cut nor any
+// entry lies within terr + errmax of it, errmax being the widest bound of the
+// FP32 entries kept so far: the FP32 entries are then pairwise further apart
+// than the sum of their bounds, so their FP32 order is their true order.
+// Otherwise the hit is decided precisely, and so is every FP32 entry within
+// errmax of its precise depth (the only entries whose order against it the
+// FP32 depths leave open).
 template <int KMAX, bool COUNT>
 __device__ __forceinline__ void leaf_test(const FrameArgs& fa, const RayKey& rk, uint32_t id,
-                                          const float3 o, const float3 d, KBuf<KMAX>& kb,
-                                          float& tcut, float& tq, float& tqr, float& errmax,
-                                          bool& fine, Counts& cn) {
-  float th, ch, terr;
+                                          const float3 o, const float3 d, const float M,
+                                          KBuf<KMAX>& kb, float& tcut, float& errmax, Counts& cn) {
+  float th, terr;
   if (COUNT) ++cn.tests;
-  const float M = fabsf(o.x) + fabsf(o.y) + fabsf(o.z);
   const int r =
-      intersect32(fa.prim_xf + 3 * (size_t)id, o, d, M, tcut + errmax, th, ch, terr);
+      intersect32(fa.prim_xf + 3 * (size_t)id, o, d, M, tcut + errmax, th, terr);
   if (r == kMiss) return;
   const float slack = terr + errmax;
-  bool need = fine || r == kBorder || terr > kTieRel * (rk.t_off + th) || th >= tcut - slack;
+  bool need = r == kBorder || terr > kTieRel * (rk.s_off + th) || th >= tcut - slack;
   if (!need) {
 #pragma unroll
     for (int j = 0; j < KMAX; ++j)
       if (j < (int)fa.k && fabsf(th - kb.t[j]) <= slack) need = true;
   }
+  uint32_t word = id | (__ldg(&fa.prim_aux[id].y) == 0.f ? kOpaque : 0u);
   float tr = 0.f;
   if (need) {
-    if (!fine) {
-      fine = true;
-      refine_all<KMAX>(fa, rk, kb, tq, tqr);
-      errmax = 0.f;
-      if (COUNT) ++cn.precise_rays;
-    }
     if (COUNT) ++cn.precise_tests;
     float tl;
-    if (!refine(fa, rk, id, th, th, tl, ch)) return;
+    if (!refine(fa, rk, id, th, th, tl)) return;
     tr = tl;
-    if (key_less(tq, tqr, 0u, th, tr, 1u)) return;  // behind the nearest opaque hit
+    word |= kExact;
+    bool moved = false;
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) {
+      if (j < (int)fa.k && kb.t[j] < kInf && !(kb.id[j] & kExact) &&
+          fabsf(th - kb.t[j]) <= errmax) {
+        float h, l;
+        if (COUNT) ++cn.precise_entries;
+        if (refine(fa, rk, kb.id[j] & kIdMask, kb.t[j], h, l)) {
+          kb.t[j] = h;
+          kb.tr[j] = l;
+          kb.id[j] |= kExact;
+        } else {  // not expected for an FP32 hit inside its bounds; dropped if it happens
+          kb.t[j] = kInf;
+          kb.tr[j] = 0.f;
+          kb.id[j] = kNoEntry;
+        }
+        moved = true;
+      }
+    }
+    if (moved) {  // refined depths moved by at most errmax: restore the order
+#pragma unroll
+      for (int i = 0; i + 1 < KMAX; ++i)
+#pragma unroll
+        for (int j = 0; j + 1 < KMAX - i; ++j)
+          if (key_less(kb.t[j + 1], kb.tr[j + 1], kb.id[j + 1], kb.t[j], kb.tr[j], kb.id[j])) {
+            float a = kb.t[j]; kb.t[j] = kb.t[j + 1]; kb.t[j + 1] = a;
+            float q = kb.tr[j]; kb.tr[j] = kb.tr[j + 1]; kb.tr[j + 1] = q;
+            uint32_t b = kb.id[j]; kb.id[j] = kb.id[j + 1]; kb.id[j + 1] = b;
+          }
+    }
   } else {
     errmax = fmaxf(errmax, terr);
   }
-  kbuf_insert<KMAX>(kb, fa.k, th, tr, id, ch);
-  if (__ldg(&fa.prim_aux[id].y) == 0.f && key_less(th, tr, 0u, tq, tqr, 1u)) {  // strand: opaque
-    tq = th;
-    tqr = tr;
-  }
-  tcut = fminf(kbuf_last<KMAX>(kb, fa.k), tq);
+  kbuf_insert<KMAX>(kb, fa.k, th, tr, word);
+  tcut = kbuf_cut<KMAX>(kb, fa.k);
 }
 
 // K nearest hits of one ray.  Returns false when the traversal stack overflowed
@@ -480,10 +444,10 @@ __device__ __forceinline__ bool traverse(const FrameArgs& fa, const RayKey& rk, 
                                          const float3 d, KBuf<KMAX>& kb, Counts& cn) {
   kbuf_init<KMAX>(kb);
   if (fa.n_prims == 0) return true;
-  float tcut = kInf, tq = kInf, tqr = 0.f, errmax = 0.f;
-  bool fine = false;
+  float tcut = kInf, errmax = 0.f;
+  const float M = fabsf(o.x) + fabsf(o.y) + fabsf(o.z);
   if (fa.n_prims == 1) {
-    leaf_test<KMAX, COUNT>(fa, rk, __ldg(fa.leaf_id), o, d, kb, tcut, tq, tqr, errmax, fine, cn);
+    leaf_test<KMAX, COUNT>(fa, rk, __ldg(fa.leaf_id), o, d, M, kb, tcut, errmax, cn);
     return true;
   }
   // a zero direction component would turn the slab products into inf - inf;
@@ -501,7 +465,7 @@ __device__ __forceinline__ bool traverse(const FrameArgs& fa, const RayKey& rk, 
       const float4* nd = fa.nodes + 4 * (size_t)node;
       const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
       if (COUNT) ++cn.nodes;
-      const float tb = fmaf(tcut + errmax, 1.f + 2.f * kTieRel, 2.f * kTieRel * rk.t_off);
+      const float tb = fmaf(tcut + errmax, 1.f + 2.f * kTieRel, 2.f * kTieRel * rk.s_off);
       // child 0
       float lx = fmaf(n0.x, inv.x, -ooi.x), hx = fmaf(n0.y, inv.x, -ooi.x);
       float ly = fmaf(n0.z, inv.y, -ooi.y), hy = fmaf(n0.w, inv.y, -ooi.y);
@@ -531,8 +495,7 @@ __device__ __forceinline__ bool traverse(const FrameArgs& fa, const RayKey& rk, 
         continue;
       }
     } else {
-      leaf_test<KMAX, COUNT>(fa, rk, (uint32_t)(~node), o, d, kb, tcut, tq, tqr, errmax, fine,
-                             cn);
+      leaf_test<KMAX, COUNT>(fa, rk, (uint32_t)(~node), o, d, M, kb, tcut, errmax, cn);
     }
     if (sp == 0) break;
     node = stack[--sp];
@@ -735,10 +698,12 @@ __device__ __forceinline__ void forward_albedo(const Tables& tb, const Mat& m, f
            : (wR * bR2 + wT * m.bT * m.bT) / (wR + wT);
 }
 
-// The hair a shadow ray crosses in one leaf: the ray's interval inside the
-// leaf's finite cylinder, clipped to (0, tmax).  Returns false when empty.
+// The ray's interval inside one record's finite cylinder, clipped to
+// (tmin, tmax): the hair a shadow ray crosses, or the chord of a primary hit.
+// Returns false when empty.
 __device__ __forceinline__ bool leaf_span(const float4* __restrict__ xf, const float3 o,
-                                          const float3 d, const float tmax, float& lo, float& hi) {
+                                          const float3 d, const float tmin, const float tmax,
+                                          float& lo, float& hi) {
   const float4 r0 = __ldg(xf), r1 = __ldg(xf + 1), r2 = __ldg(xf + 2);
   const float u0 = fmaf(r0.x, o.x, fmaf(r0.y, o.y, fmaf(r0.z, o.z, r0.w)));
   const float v0 = fmaf(r1.x, o.x, fmaf(r1.y, o.y, fmaf(r1.z, o.z, r1.w)));
@@ -764,7 +729,7 @@ __device__ __forceinline__ bool leaf_span(const float4* __restrict__ xf, const f
   } else if (w0 < 0.f || w0 > 1.f) {
     return false;
   }
-  lo = fmaxf(lo, 0.f);
+  lo = fmaxf(lo, tmin);
   hi = fminf(hi, tmax);
   return hi > lo;
 }
@@ -827,7 +792,7 @@ __device__ __forceinline__ void shadow_path(const FrameArgs& fa, const float3 x,
       float lo, hi;
       if (COUNT) ++cn.tests;
       if (__float_as_uint(aux.x) != self_mat &&
-          leaf_span(fa.prim_xf + 3 * (size_t)id, x, wi, tmax, lo, hi)) {
+          leaf_span(fa.prim_xf + 3 * (size_t)id, x, wi, 0.f, tmax, lo, hi)) {
         const float4 r2 = __ldg(fa.prim_xf + 3 * (size_t)id + 2);
         const float si = clampf(dot3(wi, f3(r2.x, r2.y, r2.z)) *
                                     rsqrtf(r2.x * r2.x + r2.y * r2.y + r2.z * r2.z),
@@ -868,7 +833,7 @@ __device__ __forceinline__ void shadow_path(const FrameArgs& fa, const float3 x,
 // SHADOW is a template parameter so kernels without shadow rays carry none
 // of their registers.
 template <int PREC, bool COUNT, bool SHADOW = false>
-__device__ __forceinline__ void shade_hit(const FrameArgs& fa, uint32_t id, float t, float chord,
+__device__ __forceinline__ void shade_hit(const FrameArgs& fa, uint32_t id, float t,
                                           const float3 o, const float3 d, float rgb[3],
                                           float& alpha, Counts& cn) {
   const float4 aux = __ldg(fa.prim_aux + id);
@@ -886,6 +851,11 @@ __device__ __forceinline__ void shade_hit(const FrameArgs& fa, uint32_t id, floa
   EthHit eh{0.f, 1.f, 0.f, 0.f};
   alpha = 1.f;
   if (aux.y > 0.f) {
+    // the chord: the ray's length inside the finite cylinder (0 when FP32
+    // rounding puts a hit at the very outline outside it)
+    float lo, hi;
+    const float chord =
+        leaf_span(fa.prim_xf + 3 * (size_t)id, o, d, -kInf, kInf, lo, hi) ? hi - lo : 0.f;
     const float ntot = aux.y, r = aux.z, ab = aux.w;
     eh.rho = fminf(1.f, ntot * r * r / ab);
     const float n_raw = eh.rho * chord * sqrtf(ntot / (kPi * ab));
@@ -952,15 +922,15 @@ __device__ __forceinline__ void render_ray(const FrameArgs& fa, const RayKey& rk
     for (int j = 0; j < KMAX; ++j)
       if (j < (int)fa.k) {
         const bool live = kb.t[j] < kInf && !past;
-        ids[j] = live ? (int32_t)kb.id[j] : -1;
-        if (live && __ldg(&fa.prim_aux[kb.id[j]].y) == 0.f) past = true;
+        ids[j] = live ? (int32_t)(kb.id[j] & kIdMask) : -1;
+        if (live && (kb.id[j] & kOpaque)) past = true;
       }
   }
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) {
     if (j < (int)fa.k && kb.t[j] < kInf && T > 0.f) {
       float rgb[3], a;
-      shade_hit<PREC, COUNT, SHADOW>(fa, kb.id[j], kb.t[j], kb.ch[j], o, d, rgb, a, cn);
+      shade_hit<PREC, COUNT, SHADOW>(fa, kb.id[j] & kIdMask, kb.t[j], o, d, rgb, a, cn);
       if (COUNT) ++cn.hits;
       const float ta = T * a;
       out[0] = fmaf(ta, rgb[0], out[0]);
@@ -982,7 +952,7 @@ __device__ __forceinline__ void render_sample(const FrameArgs& fa, uint64_t sid,
 
 __device__ __forceinline__ void flush_counts(const FrameArgs& fa, const Counts& cn) {
   unsigned long long v[8] = {cn.nodes, cn.tests, cn.sshade, cn.eshade, cn.hits, cn.rays,
-                             cn.precise_tests, cn.precise_rays};
+                             cn.precise_tests, cn.precise_entries};
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     unsigned long long x = v[i];

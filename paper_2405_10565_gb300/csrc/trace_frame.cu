@@ -19,6 +19,9 @@ LaunchCam to_launch_cam(const hr_camera& c) {
   l.W = (int)c.width;
   l.H = (int)c.height;
   l.pix = c.pix_scale;
+  const double ip = 1.0 / (double)c.pix_scale;
+  l.ipix_hi = (float)ip;
+  l.ipix_lo = (float)(ip - (double)l.ipix_hi);
   l.eye = make_float3(c.eye[0], c.eye[1], c.eye[2]);
   l.right = make_float3(c.right[0], c.right[1], c.right[2]);
   l.up = make_float3(c.up[0], c.up[1], c.up[2]);

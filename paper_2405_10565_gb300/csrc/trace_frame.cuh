@@ -22,10 +22,12 @@ __global__ void k_scene_rect(const FrameArgs fa, float4* rect, uint32_t* work) {
 // are handed out one at a time through an atomic counter, so the few tiles
 // that see hair spread over every warp of the GPU and a warp that drew cheap
 // tiles takes more.  No warp ever waits for another.
-// The plain instantiations are held to 5 blocks per SM (96 registers, a few
-// spills): 1-2% faster than at 4 blocks; 6 blocks spill more and are slower.
+// The plain instantiations are held to 4 blocks per SM (128 registers, no
+// spills in the traversal): at 5 blocks (96 registers) the k-buffer's depth
+// pairs and the precise-decision state spill, and the full-head frame took
+// 1.01 instead of 0.64 ms; 3 blocks or no bound were no faster.
 template <int KMAX, int PREC, bool COUNT, bool SHADOW>
-__global__ void __launch_bounds__(kBlock, SHADOW ? 1 : 5)
+__global__ void __launch_bounds__(kBlock, SHADOW ? 1 : 4)
     k_frame(const FrameArgs fa, const float4* __restrict__ rect_p, uint32_t* work,
             float* __restrict__ rgb) {
   const float4 rect = *rect_p;

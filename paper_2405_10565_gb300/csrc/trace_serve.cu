@@ -16,8 +16,8 @@ namespace {
 __global__ void k_serve_rect(const FrameArgs fa, float4* rect) { tr::scene_rect_warp(fa, rect); }
 
 template <int KMAX, int PREC>
-// 5 blocks per SM (at most 96 registers), as for the frame kernel.
-__global__ void __launch_bounds__(kBlock, 5)
+// 4 blocks per SM (at most 128 registers), as for the frame kernel.
+__global__ void __launch_bounds__(kBlock, 4)
     k_serve(const ServeItem* __restrict__ items, const uint32_t* __restrict__ item_start,
             uint32_t n_items, uint32_t total, uint32_t* work) {
   const uint32_t lane = threadIdx.x & 31;
