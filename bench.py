@@ -90,8 +90,8 @@ def sources_hash(names):
     return h.hexdigest()[:16]
 
 
-TRACE_SOURCES = ["trace_core.cuh", "trace_frame.cuh", "trace_frame.cu", "common.cuh"]
-FIT_SOURCES = ["hierarchy.cu", "common.cuh"]
+TRACE_SOURCES = ["trace_core.cuh", "trace_frame.cuh", "trace_frame.cu", "common.cuh", "dword.cuh"]
+FIT_SOURCES = ["hierarchy.cu", "common.cuh", "dword.cuh"]
 
 
 def traffic_record(name, sources, workload_name):
@@ -286,6 +286,30 @@ def measure_config(hr, ctx, torch, dev, w, steps: int, warmup: int = 2, peak_tfl
         out["frame_fp32"] = {"achieved_tflops": tf, "frac": tf / peak_tflops,
                              "frac_source_count": ts / peak_tflops}
     return out
+
+
+def frame_tail(hr, ctx, asset, desc, img, capacity: int = 1 << 20):
+    """Per-warp-tile times of one counting frame (hr_render_profile): how long
+    the frame kernel's tiles take and how far the slowest ones set its length."""
+    st, rec, n = hr.hr_render_profile(ctx, asset, desc, img, capacity)
+    if rec.size == 0:
+        return {"tiles": n}
+    t0 = rec["t_start_ns"].astype(np.int64)
+    t1 = rec["t_end_ns"].astype(np.int64)
+    dur = (t1 - t0) / 1e3
+    span = (t1.max() - t0.min()) / 1e3
+    slow = int(np.argmax(dur))
+    warps = len(np.unique(rec["sm"])) * 16  # 4 blocks of 4 warps per SM
+    visits = int(rec["max_node_visits"][slow])
+    return {"tiles": n, "recorded": int(rec.size), "span_us": span,
+            "tile_us": {"median": float(np.median(dur)), "p99": float(np.percentile(dur, 99)),
+                        "max": float(dur.max())},
+            "balanced_span_us": float(dur.sum() / warps),
+            "slowest_tile": {"index": int(rec["tile"][slow]), "max_node_visits": visits,
+                             "max_prim_tests": int(rec["max_prim_tests"][slow]),
+                             "ns_per_node_visit": float(dur[slow] * 1e3 / max(visits, 1))},
+            "tiles_running_after_half_span": int(((t1 - t0.min()) / 1e3 > span / 2).sum()),
+            "note": "counting kernel (event counters on); tiles in hand-out order"}
 
 
 def max_over_ranks(x: float, dist, device) -> float:
@@ -553,6 +577,7 @@ def main():
     cdesc = hr.render_desc(w.camera.pack(), w.lights, spp, w.k_depth, w.sample_seed, w.precision,
                            hr.HR_FLAG_COUNT)
     cst = hr.hr_render(ctx, asset, cdesc, img, stats=True)
+    tail = frame_tail(hr, ctx, asset, cdesc, img)
     n_levels_info = hr.hr_hierarchy_info(ctx, asset)
     flops = event_flops(cst)
     uuid = None
@@ -772,7 +797,7 @@ def main():
                                                         elapsed),
             "traced_msamples_per_s_frame": cst.traced_samples / (render_avg * 1e-3) / 1e6,
             "frame_ms": render_avg, "frame_ms_fp32_warm": fp32_ms, "frame_ms_fp16_warm": fp16_ms,
-            "frame_ms_shadow_rays": shadow_ms,
+            "frame_ms_shadow_rays": shadow_ms, "frame_tail": tail,
             "active_prims": int(st.n_active_prims),
             "eth_prims": int(st.n_eth_prims), "stack_overflows": int(st.stack_overflows),
             "roofline": roof, "roofline_other": other,

@@ -389,8 +389,30 @@ hr_status hr_im_lookup(hr_ctx* ctx, const float* theta, const float* beta, uint3
  * opacity 1 - exp(-2 r l n_tot / (pi a b)) for view chord l), and the mean
  * over the pixel's samples.
  * rgb_out: host or device, [height][width][3] floats.  Requires hr_build_bvh. */
+/* One warp tile of a profiled frame (hr_render_profile): the 32 / spp-lane
+ * pixels (all their samples) that one warp traces, shades and composites. */
+typedef struct hr_tile_record {
+  uint64_t t_start_ns;       /* GPU global timer when the warp took the tile */
+  uint64_t t_end_ns;         /* and when it had written the tile's pixels */
+  uint32_t tile;             /* the tile's index in the frame's hand-out order */
+  uint32_t sm;               /* the SM that ran it */
+  uint32_t max_node_visits;  /* most BVH node visits of one lane (its rays) */
+  uint32_t max_prim_tests;   /* most primitive tests of one lane */
+} hr_tile_record;
+
 hr_status hr_render(hr_ctx* ctx, hr_asset* asset, const hr_render_desc* desc, float* rgb_out,
                     hr_stats* stats);
+/* hr_render with HR_FLAG_COUNT and, per warp tile of the frame kernel, its
+ * start and end times and its largest per-lane counts, for the study of the
+ * frame's tail (the kernel lasts as long as its slowest tiles).  No
+ * counterpart in the paper.  tiles_out: host or device, capacity records;
+ * the first min(capacity, tiles) of the frame's tiles in hand-out order are
+ * written.  n_tiles (optional): the frame's number of tiles.  The timing
+ * adds two timer reads and a warp reduction per tile to the counting
+ * kernel.  HR_EINVAL for a null tiles_out with capacity > 0. */
+hr_status hr_render_profile(hr_ctx* ctx, hr_asset* asset, const hr_render_desc* desc,
+                            float* rgb_out, hr_stats* stats, hr_tile_record* tiles_out,
+                            uint32_t capacity, uint32_t* n_tiles);
 
 /* Render only the listed samples (parity hook): radiance [m][3] and the
  * global ids of the composited hits, [m][k_depth]: the k nearest by (t, id),

@@ -82,6 +82,11 @@ class hr_stats(ctypes.Structure):
                 ("refined_tests", c_u64), ("refined_entries", c_u64)]
 
 
+class hr_tile_record(ctypes.Structure):
+    _fields_ = [("t_start_ns", c_u64), ("t_end_ns", c_u64), ("tile", c_u32), ("sm", c_u32),
+                ("max_node_visits", c_u32), ("max_prim_tests", c_u32)]
+
+
 class hr_request(ctypes.Structure):
     _fields_ = [("asset", c_void_p), ("desc", hr_render_desc), ("eps_w_px", c_float),
                 ("budget_bias", c_i32), ("rgb_out", c_void_p)]
@@ -119,6 +124,8 @@ _SIGS = {
     "hr_im_lookup": (c_int, [P, P, P, c_u32, c_int, P]),
     "hr_render": (c_int, [P, P, ctypes.POINTER(hr_render_desc), P, ctypes.POINTER(hr_stats)]),
     "hr_render_samples": (c_int, [P, P, ctypes.POINTER(hr_render_desc), P, c_u32, P, P]),
+    "hr_render_profile": (c_int, [P, P, ctypes.POINTER(hr_render_desc), P, ctypes.POINTER(hr_stats),
+                                  P, c_u32, ctypes.POINTER(c_u32)]),
     "hr_render_frame": (c_int, [P, P, c_u32, c_float, c_int, ctypes.POINTER(hr_render_desc), P,
                                 ctypes.POINTER(hr_stats)]),
     "hr_serve_start": (c_int, [P, c_u32, c_u64]),
@@ -354,6 +361,23 @@ def hr_render(ctx: int, asset: int, desc: hr_render_desc, rgb_out, stats: bool =
     _check(ctx, load().hr_render(ctx, asset, ctypes.byref(desc), ptr(rgb_out),
                                  ctypes.byref(st) if st is not None else None), "hr_render")
     return st
+
+
+def hr_render_profile(ctx: int, asset: int, desc: hr_render_desc, rgb_out, capacity: int):
+    """Counting render with per-warp-tile records: returns (hr_stats, records as
+    a numpy structured array [min(capacity, tiles)], number of tiles)."""
+    import numpy as np
+    st = hr_stats()
+    buf = (hr_tile_record * max(int(capacity), 1))()
+    nt = c_u32(0)
+    _check(ctx, load().hr_render_profile(ctx, asset, ctypes.byref(desc), ptr(rgb_out),
+                                         ctypes.byref(st), ctypes.cast(buf, c_void_p),
+                                         int(capacity), ctypes.byref(nt)), "hr_render_profile")
+    n = min(int(nt.value), int(capacity))
+    dt = np.dtype([("t_start_ns", np.uint64), ("t_end_ns", np.uint64), ("tile", np.uint32),
+                   ("sm", np.uint32), ("max_node_visits", np.uint32), ("max_prim_tests", np.uint32)])
+    rec = np.frombuffer(buf, dtype=dt, count=max(int(capacity), 1))[:n].copy()
+    return st, rec, int(nt.value)
 
 
 def hr_render_samples(ctx: int, asset: int, desc: hr_render_desc, sample_ids, radiance_out,

@@ -157,6 +157,9 @@ FrameArgs frame_args(hr_ctx* ctx, hr_asset* a, const Bvh& bv, const hr_render_de
   fa.flags = d.flags;
   fa.overflow = ctx->d_overflow;
   fa.counters = ctx->d_counters;
+  fa.tile_log = nullptr;
+  fa.tile_cap = 0;
+  fa.tile_count = nullptr;
   fa.k = d.k_depth;
   const TileGeom tg = tile_geom(d.spp);
   fa.grp = tg.grp;
@@ -624,7 +627,8 @@ hr_status hr_im_lookup(hr_ctx* ctx, const float* theta, const float* beta, uint3
 }
 
 static hr_status render_impl(hr_ctx* ctx, hr_asset* a, const hr_render_desc* desc, float* rgb_out,
-                             hr_stats* stats) {
+                             hr_stats* stats, hr_tile_record* tiles = nullptr,
+                             uint32_t tile_cap = 0, uint32_t* n_tiles = nullptr) {
   if (!a || !rgb_out) return set_error(ctx, HR_EINVAL, "null argument");
   HR_TRY(check_desc(ctx, desc));
   if (!a->bvh.valid) return set_error(ctx, HR_ESTATE, "no BVH: call hr_build_bvh");
@@ -634,7 +638,18 @@ static hr_status render_impl(hr_ctx* ctx, hr_asset* a, const hr_render_desc* des
   float* out = rgb_out;
   if (!dev_out) HR_TRY(scratch(ctx, 42, bytes, (void**)&out));
   FrameArgs fa = frame_args(ctx, a, a->bvh, *desc);
-  const bool count = (desc->flags & HR_FLAG_COUNT) != 0;
+  const bool profile = tiles != nullptr || n_tiles != nullptr;
+  const bool count = (desc->flags & HR_FLAG_COUNT) != 0 || profile;
+  hr_tile_record* tlog = nullptr;
+  if (profile) {
+    const bool dev_tiles = tiles && is_device_ptr(tiles);
+    tlog = dev_tiles ? tiles : nullptr;
+    if (!dev_tiles) HR_TRY(scratch(ctx, 37, (size_t)std::max(tile_cap, 1u) * sizeof(hr_tile_record), (void**)&tlog));
+    HR_TRY(scratch(ctx, 38, 4, (void**)&fa.tile_count));
+    HR_CUDA(ctx, cudaMemsetAsync(fa.tile_count, 0, 4, st));
+    fa.tile_log = tlog;
+    fa.tile_cap = tiles ? tile_cap : 0;
+  }
   if (stats || count) {
     HR_CUDA(ctx, cudaMemsetAsync(ctx->d_overflow, 0, 4, st));
     HR_CUDA(ctx, cudaMemsetAsync(ctx->d_counters, 0, 8 * sizeof(unsigned long long), st));
@@ -643,6 +658,17 @@ static hr_status render_impl(hr_ctx* ctx, hr_asset* a, const hr_render_desc* des
   HR_TRY(launch_frame(ctx, fa, desc->precision, count, out, st));
   if (stats) HR_CUDA(ctx, cudaEventRecord(ctx->ev1, st));
   if (!dev_out) HR_CUDA(ctx, cudaMemcpyAsync(rgb_out, out, bytes, cudaMemcpyDeviceToHost, st));
+  if (profile) {
+    uint32_t nt = 0;
+    HR_CUDA(ctx, cudaMemcpyAsync(&nt, fa.tile_count, 4, cudaMemcpyDeviceToHost, st));
+    HR_CUDA(ctx, cudaStreamSynchronize(st));
+    if (n_tiles) *n_tiles = nt;
+    const uint32_t nw = std::min(nt, fa.tile_cap);
+    if (tiles && tlog != tiles && nw)
+      HR_CUDA(ctx, cudaMemcpyAsync(tiles, tlog, (size_t)nw * sizeof(hr_tile_record),
+                                   cudaMemcpyDeviceToHost, st));
+    if (!stats) HR_CUDA(ctx, cudaStreamSynchronize(st));
+  }
   if (stats) {
     uint32_t ovf = 0;
     unsigned long long cnt[8] = {0};
@@ -676,6 +702,16 @@ hr_status hr_render(hr_ctx* ctx, hr_asset* a, const hr_render_desc* desc, float*
                     hr_stats* stats) {
   API_ENTER(ctx);
   return render_impl(ctx, a, desc, rgb_out, stats);
+}
+
+hr_status hr_render_profile(hr_ctx* ctx, hr_asset* a, const hr_render_desc* desc, float* rgb_out,
+                            hr_stats* stats, hr_tile_record* tiles_out, uint32_t capacity,
+                            uint32_t* n_tiles) {
+  API_ENTER(ctx);
+  if (!tiles_out && capacity) return set_error(ctx, HR_EINVAL, "hr_render_profile: null tiles_out");
+  hr_tile_record dummy;
+  return render_impl(ctx, a, desc, rgb_out, stats, tiles_out ? tiles_out : &dummy,
+                     tiles_out ? capacity : 0, n_tiles);
 }
 
 hr_status hr_render_samples(hr_ctx* ctx, hr_asset* a, const hr_render_desc* desc,

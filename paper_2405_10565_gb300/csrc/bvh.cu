@@ -450,14 +450,13 @@ hr_status build_bvh(hr_ctx* ctx, hr_asset* a, const uint8_t* lod_dev, Bvh& bv, c
   const uint32_t N = a->N, S = a->S;
   bv.valid = 0;
   // 1. active primitive ids
-  uint32_t n = 0;
+  uint32_t n = 0, n_eth = 0;
   uint32_t* ids = nullptr;
   if (a->C == 0 || a->n_levels == 0 || lod_dev == nullptr) {
     n = N * S;
     HR_TRY(scratch(ctx, 30, (size_t)n * 4, (void**)&ids));
     k_iota<<<(n + 255) / 256, 256, 0, st>>>(ids, n);
     HR_LAUNCHED(ctx);
-    bv.n_eth = 0;
   } else {
     const uint32_t C = a->C, L = a->n_levels;
     uint32_t* cnt = nullptr;
@@ -470,7 +469,7 @@ hr_status build_bvh(hr_ctx* ctx, hr_asset* a, const uint8_t* lod_dev, Bvh& bv, c
     HR_CUDA(ctx, cudaMemcpyAsync(tot, cnt + C, 8, cudaMemcpyDeviceToHost, st));
     HR_CUDA(ctx, cudaStreamSynchronize(st));
     n = tot[0];
-    bv.n_eth = tot[1];
+    n_eth = tot[1];
     uint32_t* eoff = nullptr;
     HR_TRY(scratch(ctx, 32, 16 * 4, (void**)&eoff));
     HR_CUDA(ctx, cudaMemcpyAsync(eoff, a->eth_offset, 16 * 4, cudaMemcpyHostToDevice, st));
@@ -491,7 +490,9 @@ hr_status build_bvh(hr_ctx* ctx, hr_asset* a, const uint8_t* lod_dev, Bvh& bv, c
     HR_TRY(dalloc(ctx, (void**)&bv.par_leaf, (size_t)n * 4, "BVH leaf parents"));
     bv.cap = n;
   }
+  // (after the grow: free_bvh resets every field)
   bv.n = n;
+  bv.n_eth = n_eth;
   // what the topology is built for (checked by refit_bvh); the hierarchy as it is now
   HR_CUDA(ctx, cudaMemsetAsync(a->d_bounds + kHierChanged, 0, 4, st));
   bv.topo = 0;

@@ -257,6 +257,9 @@ struct FrameArgs {
   uint32_t k;          // k-buffer depth (<= the kernel's KMAX)
   uint32_t grp;        // lanes per pixel (power of two <= 32; samples spread over them)
   uint32_t tile_w, tile_h;  // pixels per 128-thread block: tile_w x tile_h = 128 / grp
+  hr_tile_record* tile_log;  // counting kernel only: per warp tile times and counts, or null
+  uint32_t tile_cap;         // records tile_log holds
+  uint32_t* tile_count;      // the frame's number of warp tiles (written when tile_log is set)
 };
 
 // Tile geometry of the frame and serving kernels for a given spp: each pixel

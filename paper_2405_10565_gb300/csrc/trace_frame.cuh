@@ -35,14 +35,37 @@ __global__ void __launch_bounds__(kBlock, SHADOW ? 1 : 4)
   tr::Counts cn{0, 0, 0, 0, 0, 0, 0, 0};
   bool overflow = false;
   const uint32_t lane = threadIdx.x & 31;
+  if (COUNT && fa.tile_log && blockIdx.x == 0 && threadIdx.x == 0) *fa.tile_count = g.n;
   for (;;) {
     uint32_t t = 0;
     if (lane == 0) t = atomicAdd(work, 1u);
     t = __shfl_sync(0xffffffffu, t, 0);
     if (t >= g.n) break;
+    uint64_t t0 = 0;
+    uint32_t nodes0 = 0, tests0 = 0;
+    if (COUNT && fa.tile_log) {
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+      nodes0 = cn.nodes;
+      tests0 = cn.tests;
+    }
     tr::render_warp_tile<KMAX, PREC, COUNT, SHADOW>(fa, g.x0 + (t % g.nx) * g.wtw,
                                                     g.y0 + (t / g.nx) * g.wth, g.wtw, rect, rgb,
                                                     cn, overflow);
+    if (COUNT && fa.tile_log) {
+      uint32_t dn = cn.nodes - nodes0, dt = cn.tests - tests0;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        dn = max(dn, __shfl_xor_sync(0xffffffffu, dn, o));
+        dt = max(dt, __shfl_xor_sync(0xffffffffu, dt, o));
+      }
+      uint64_t t1;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+      if (lane == 0 && t < fa.tile_cap) {
+        uint32_t sm;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+        fa.tile_log[t] = hr_tile_record{t0, t1, t, sm, dn, dt};
+      }
+    }
   }
   if (COUNT) tr::flush_counts(fa, cn);
   if (overflow) atomicAdd(fa.overflow, 1u);

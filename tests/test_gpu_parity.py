@@ -196,6 +196,31 @@ def test_active_set_bit_exact(ctx, setting):
         hr.hr_asset_destroy(ctx, a)
 
 
+def test_active_counts_survive_a_growing_bvh(ctx):
+    """The statistics' active and thick-hair primitive counts after a build that
+    outgrows the previous BVH's storage (all thick hairs, then half the
+    clusters on strands) equal the exported leaves."""
+    w = scenegen.clustered(n=4000, S=8, res=32, spp=1, lod_setting="eth", n_clusters=100)
+    a = upload(ctx, w.scene)
+    try:
+        hr.hr_build_clusters(ctx, a, w.n_clusters)
+        C, L, _ = hr.hr_hierarchy_info(ctx, a)
+        img = np.zeros((32, 32, 3), np.float32)
+        d = desc_of(w)
+        NS = w.scene.n_strands * w.scene.n_segments
+        for setting in ("eth", "half"):
+            hr.hr_build_bvh(ctx, a, np.ascontiguousarray(scenegen.lod_preset(setting, C, L)))
+            n = hr.hr_bvh_export(ctx, a)
+            ids = np.zeros(n, np.uint32)
+            hr.hr_bvh_export(ctx, a, ids)
+            st = hr.hr_render(ctx, a, d, img, stats=True)
+            assert st.n_active_prims == n
+            assert st.n_eth_prims == int((ids >= NS).sum()) > 0
+            assert st.n_strand_prims == int((ids < NS).sum())
+    finally:
+        hr.hr_asset_destroy(ctx, a)
+
+
 # ---------------------------------------------------------------- rendering
 
 
@@ -529,6 +554,31 @@ def test_frame_deferred_lod_follows_eq14(ctx):
         hr.hr_bvh_export(ctx, a, ids)
         prep2 = oracle_prepare(w, lod=np.asarray(want, np.uint8))
         assert np.array_equal(np.sort(ids.astype(np.int64)), np.sort(prep2.ids))
+    finally:
+        hr.hr_asset_destroy(ctx, a)
+
+
+def test_render_profile_records_every_tile(ctx):
+    """hr_render_profile: the image of a plain render, one record per warp tile
+    (each tile index once), ordered times, and per-lane counts no larger than
+    the frame's totals."""
+    w = scenegen.full_head(n=3000, S=8, width=64, height=48, spp=4, n_lights=2, n_clusters=64)
+    a = upload(ctx, w.scene)
+    try:
+        gpu_lod(ctx, a, w)
+        ref = np.zeros((48, 64, 3), np.float32)
+        hr.hr_render(ctx, a, desc_of(w), ref)
+        img = np.zeros_like(ref)
+        st, rec, n = hr.hr_render_profile(ctx, a, desc_of(w, flags=hr.HR_FLAG_COUNT), img, 1 << 16)
+        assert n > 0 and rec.size == n
+        assert np.array_equal(np.sort(rec["tile"]), np.arange(n))
+        assert np.all(rec["t_end_ns"] >= rec["t_start_ns"])
+        assert np.allclose(img, ref, rtol=1e-5, atol=1e-7)
+        assert rec["max_prim_tests"].max() <= st.prim_tests
+        assert rec["max_node_visits"].max() <= st.node_visits and st.node_visits > 0
+        # a short buffer takes the first tiles only
+        st2, rec2, n2 = hr.hr_render_profile(ctx, a, desc_of(w), img, 3)
+        assert n2 == n and rec2.size == min(3, n)
     finally:
         hr.hr_asset_destroy(ctx, a)
 
