@@ -423,11 +423,29 @@ hr_status hr_render_samples(hr_ctx* ctx, hr_asset* asset, const hr_render_desc* 
                             const uint32_t* sample_ids, uint32_t m, float* radiance_out,
                             int32_t* hit_out);
 
-/* Whole hot path in one call: clusters (if n_clusters > 0 and not yet built),
- * LoD selection (mode 0, eps_w_px, budget_bias), BVH and frame. */
+/* Whole hot path in one call (Section 5.2, run time): clusters and the
+ * thick-hair fit (n_clusters > 0; none with HR_FLAG_KEEP_HIERARCHY), LoD
+ * selection (eps_w_px, budget_bias; Eq. 14 with HR_FLAG_DEFERRED_LOD), BVH
+ * (or its refit with HR_FLAG_REFIT) and frame.  With device output and no
+ * stats the call returns without waiting for the frame.  When the previous
+ * call on the context was also hr_render_frame (no other call in between,
+ * no serving loop) and the hierarchy keeps its shape, this frame's clusters
+ * and fit run on a second stream of the context as soon as the previous
+ * frame's BVH is built, overlapping that frame's rendering (they write a
+ * second cross-section buffer; the records that frame reads are rewritten
+ * after it).  Results are the same as without the overlap.  stats: optional;
+ * hierarchy_ms then runs from the start of the clusters, on whichever stream. */
 hr_status hr_render_frame(hr_ctx* ctx, hr_asset* asset, uint32_t n_clusters, float eps_w_px,
                           int budget_bias, const hr_render_desc* desc, float* rgb_out,
                           hr_stats* stats);
+/* Kernel times of the last n hr_render_frame calls on the context, oldest
+ * first, from events every call records (so a loop of frames needs no
+ * synchronisation per frame to be timed): frame_ms[i] the frame kernel
+ * (with the image clear and scene rectangle), fit_ms[i] the cross-section
+ * fit (0 when that call fitted nothing).  Waits for those frames.  At most
+ * the last 256 calls are kept; n_out (optional) receives the number written.
+ * frame_ms, fit_ms: optional host arrays of n floats. */
+hr_status hr_frame_times(hr_ctx* ctx, uint32_t n, float* frame_ms, float* fit_ms, uint32_t* n_out);
 
 /* Morton clustering without any device allocation.
  * The paper has no counterpart: this entry point exists for callers that may

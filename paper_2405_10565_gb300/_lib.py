@@ -124,6 +124,7 @@ _SIGS = {
     "hr_im_lookup": (c_int, [P, P, P, c_u32, c_int, P]),
     "hr_render": (c_int, [P, P, ctypes.POINTER(hr_render_desc), P, ctypes.POINTER(hr_stats)]),
     "hr_render_samples": (c_int, [P, P, ctypes.POINTER(hr_render_desc), P, c_u32, P, P]),
+    "hr_frame_times": (c_int, [P, c_u32, P, P, ctypes.POINTER(c_u32)]),
     "hr_render_profile": (c_int, [P, P, ctypes.POINTER(hr_render_desc), P, ctypes.POINTER(hr_stats),
                                   P, c_u32, ctypes.POINTER(c_u32)]),
     "hr_render_frame": (c_int, [P, P, c_u32, c_float, c_int, ctypes.POINTER(hr_render_desc), P,
@@ -361,6 +362,18 @@ def hr_render(ctx: int, asset: int, desc: hr_render_desc, rgb_out, stats: bool =
     _check(ctx, load().hr_render(ctx, asset, ctypes.byref(desc), ptr(rgb_out),
                                  ctypes.byref(st) if st is not None else None), "hr_render")
     return st
+
+
+def hr_frame_times(ctx: int, n: int):
+    """Frame-kernel and fit times (ms) of the last n hr_render_frame calls:
+    two numpy float32 arrays, oldest first."""
+    import numpy as np
+    f = np.zeros(max(int(n), 1), np.float32)
+    g = np.zeros(max(int(n), 1), np.float32)
+    m = c_u32(0)
+    _check(ctx, load().hr_frame_times(ctx, int(n), f.ctypes.data, g.ctypes.data, ctypes.byref(m)),
+           "hr_frame_times")
+    return f[:m.value].copy(), g[:m.value].copy()
 
 
 def hr_render_profile(ctx: int, asset: int, desc: hr_render_desc, rgb_out, capacity: int):

@@ -2,6 +2,7 @@
 // and the hierarchy / LoD / BVH / render entry points.  Every computation is
 // a kernel of this library; this file only validates, allocates, copies and
 // launches.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cstring>
@@ -31,6 +32,17 @@ struct hr_ctx {
   std::chrono::steady_clock::time_point t0;
   hr::Server* server = nullptr;
   std::atomic<uint64_t> launches{0};
+  // pipelined hr_render_frame: the side stream runs the next frame's clusters
+  // and fit once ev_built (the previous frame's BVH is done) has passed
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_built = nullptr, ev_fit = nullptr;
+  bool pipe_ready = false;  // the last API call was hr_render_frame
+  bool pipe_prev = false;   // ... as seen by the current call
+  // frame-time ring: per hr_render_frame, events around the fit and the frame
+  static constexpr int kRing = 256;
+  cudaEvent_t ring[kRing][4] = {};
+  uint64_t ring_n = 0;
+  std::vector<uint8_t> ring_fit;  // whether entry i's fit events were recorded
 };
 
 namespace hr {
@@ -44,6 +56,8 @@ hr_status set_error(hr_ctx* ctx, hr_status st, const std::string& msg) {
 }
 
 cudaStream_t ctx_stream(hr_ctx* ctx) { return ctx->stream; }
+cudaStream_t ctx_side_stream(hr_ctx* ctx) { return ctx->side; }
+cudaEvent_t ctx_fit_event(hr_ctx* ctx) { return ctx->ev_fit; }
 
 void note_launch(hr_ctx* ctx) { ctx->launches++; }
 
@@ -208,7 +222,9 @@ struct DeviceGuard {
 #define API_ENTER(ctx)                                                   \
   if (!(ctx)) return HR_EINVAL;                                          \
   std::lock_guard<std::recursive_mutex> api_lock_((ctx)->api_mu);        \
-  DeviceGuard dev_guard_((ctx)->device)
+  DeviceGuard dev_guard_((ctx)->device);                                 \
+  (ctx)->pipe_prev = (ctx)->pipe_ready;                                  \
+  (ctx)->pipe_ready = false
 
 }  // namespace
 
@@ -243,6 +259,14 @@ hr_status hr_create(hr_ctx** out, int device, uint64_t hbm_budget, void* cuda_st
     st = HR_ECUDA;
   for (int i = 0; i < 6 && st == HR_OK; ++i)
     if (cudaEventCreate(&ctx->ph[i]) != cudaSuccess) st = HR_ECUDA;
+  if (st == HR_OK && (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+                      cudaEventCreateWithFlags(&ctx->ev_built, cudaEventDisableTiming) != cudaSuccess ||
+                      cudaEventCreateWithFlags(&ctx->ev_fit, cudaEventDisableTiming) != cudaSuccess))
+    st = HR_ECUDA;
+  for (int i = 0; i < hr_ctx::kRing && st == HR_OK; ++i)
+    for (int j = 0; j < 4 && st == HR_OK; ++j)
+      if (cudaEventCreate(&ctx->ring[i][j]) != cudaSuccess) st = HR_ECUDA;
+  ctx->ring_fit.assign(hr_ctx::kRing, 0);
   if (st == HR_OK) st = dalloc(ctx, (void**)&ctx->d_overflow, 64, "flags");
   if (st == HR_OK) st = dalloc(ctx, (void**)&ctx->d_counters, 8 * sizeof(unsigned long long), "counters");
   if (st == HR_OK) st = bake_tables(ctx, &ctx->im32, &ctx->im16);
@@ -261,6 +285,7 @@ hr_status hr_destroy(hr_ctx* ctx) {
   {
     DeviceGuard g(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->side) cudaStreamSynchronize(ctx->side);
     for (auto& s : ctx->scratch)
       if (s.p) cudaFree(s.p);
     if (ctx->im32) cudaFree(ctx->im32);
@@ -271,6 +296,12 @@ hr_status hr_destroy(hr_ctx* ctx) {
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     for (int i = 0; i < 6; ++i)
       if (ctx->ph[i]) cudaEventDestroy(ctx->ph[i]);
+    for (int i = 0; i < hr_ctx::kRing; ++i)
+      for (int j = 0; j < 4; ++j)
+        if (ctx->ring[i][j]) cudaEventDestroy(ctx->ring[i][j]);
+    if (ctx->ev_built) cudaEventDestroy(ctx->ev_built);
+    if (ctx->ev_fit) cudaEventDestroy(ctx->ev_fit);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   }
   delete ctx;
@@ -341,6 +372,7 @@ hr_status hr_asset_destroy(hr_ctx* ctx, hr_asset* a) {
   if (!a) return HR_EINVAL;
   if (ctx->server) serve_forget_asset(ctx, ctx->server, a);
   cudaStreamSynchronize(ctx->stream);
+  cudaStreamSynchronize(ctx->side);
   const size_t S1 = a->S + 1;
   dfree(ctx, a->verts, (size_t)a->N * S1 * sizeof(float4));
   dfree(ctx, a->mat, a->mat_cap * HR_MAT_FLOATS * 4);
@@ -349,6 +381,7 @@ hr_status hr_asset_destroy(hr_ctx* ctx, hr_asset* a) {
   if (a->cluster_of) dfree(ctx, a->cluster_of, (size_t)a->N * 4);
   if (a->cl_first) dfree(ctx, a->cl_first, (size_t)(a->C + 1) * 4);
   if (a->xsec) dfree(ctx, a->xsec, (size_t)a->E * S1 * 3 * sizeof(float4));
+  if (a->xsec_other) dfree(ctx, a->xsec_other, (size_t)a->E * S1 * 3 * sizeof(float4));
   if (a->lod) dfree(ctx, a->lod, a->C);
   drop_guides(ctx, a);
   const uint64_t P = a->n_prims_total;
@@ -628,7 +661,8 @@ hr_status hr_im_lookup(hr_ctx* ctx, const float* theta, const float* beta, uint3
 
 static hr_status render_impl(hr_ctx* ctx, hr_asset* a, const hr_render_desc* desc, float* rgb_out,
                              hr_stats* stats, hr_tile_record* tiles = nullptr,
-                             uint32_t tile_cap = 0, uint32_t* n_tiles = nullptr) {
+                             uint32_t tile_cap = 0, uint32_t* n_tiles = nullptr,
+                             cudaEvent_t t_begin = nullptr, cudaEvent_t t_end = nullptr) {
   if (!a || !rgb_out) return set_error(ctx, HR_EINVAL, "null argument");
   HR_TRY(check_desc(ctx, desc));
   if (!a->bvh.valid) return set_error(ctx, HR_ESTATE, "no BVH: call hr_build_bvh");
@@ -655,7 +689,9 @@ static hr_status render_impl(hr_ctx* ctx, hr_asset* a, const hr_render_desc* des
     HR_CUDA(ctx, cudaMemsetAsync(ctx->d_counters, 0, 8 * sizeof(unsigned long long), st));
   }
   if (stats) HR_CUDA(ctx, cudaEventRecord(ctx->ev0, st));
+  if (t_begin) HR_CUDA(ctx, cudaEventRecord(t_begin, st));
   HR_TRY(launch_frame(ctx, fa, desc->precision, count, out, st));
+  if (t_end) HR_CUDA(ctx, cudaEventRecord(t_end, st));
   if (stats) HR_CUDA(ctx, cudaEventRecord(ctx->ev1, st));
   if (!dev_out) HR_CUDA(ctx, cudaMemcpyAsync(rgb_out, out, bytes, cudaMemcpyDeviceToHost, st));
   if (profile) {
@@ -756,17 +792,37 @@ hr_status hr_render_frame(hr_ctx* ctx, hr_asset* a, uint32_t n_clusters, float e
   HR_TRY(check_desc(ctx, desc));
   cudaStream_t st = ctx->stream;
   const uint8_t* lod_dev = nullptr;
-  // phase events: 0 start, 1 fit begin, 2 fit end, 3 hierarchy end, 4 LoD end, 5 BVH end
+  // phase events: 0 start, 3 hierarchy end, 4 LoD end, 5 BVH end; the fit's
+  // and the frame's begin / end go to this call's slot of the frame-time ring
   cudaEvent_t* ph = ctx->ph;
-  if (stats) HR_CUDA(ctx, cudaEventRecord(ph[0], st));
+  cudaEvent_t* rg = ctx->ring[ctx->ring_n % hr_ctx::kRing];
   bool fit_ran = false;
   const bool keep = (desc->flags & HR_FLAG_KEEP_HIERARCHY) != 0;
+  // Pipelining: when the previous API call was hr_render_frame, this frame's
+  // clusters and fit (which only the hierarchy build and the LoD read) run on
+  // the side stream as soon as the previous frame's BVH is built, overlapping
+  // that frame's rendering; they write the other cross-section buffer, so the
+  // frame in flight keeps reading its own.  The thick-hair records and
+  // materials, which that frame reads, follow on the main stream after it.
+  // Only for a hierarchy of the same shape (no reallocation) and without a
+  // serving loop.
+  const bool pipe = ctx->pipe_prev && !ctx->server && !keep && n_clusters > 0 &&
+                    n_clusters <= a->N && a->order && a->C == n_clusters && a->E > 0 &&
+                    a->xsec && !a->G;
+  cudaStream_t sh = pipe ? ctx->side : st;  // the stream of the clusters and the fit
+  if (pipe) {
+    if (!a->xsec_other)
+      HR_TRY(dalloc(ctx, (void**)&a->xsec_other, (size_t)a->E * (a->S + 1) * 3 * sizeof(float4),
+                    "cross-sections (second buffer)"));
+    std::swap(a->xsec, a->xsec_other);
+    HR_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_built, 0));
+  }
+  if (stats) HR_CUDA(ctx, cudaEventRecord(ph[0], sh));
   if (keep) {
     if (a->C == 0) return set_error(ctx, HR_ESTATE, "HR_FLAG_KEEP_HIERARCHY: no hierarchy built");
   } else if (n_clusters > 0) {
     if (n_clusters > a->N) return set_error(ctx, HR_EINVAL, "n_clusters out of range");
-    HR_TRY(build_hierarchy(ctx, a, n_clusters, 0, stats ? ph[1] : nullptr,
-                           stats ? ph[2] : nullptr));
+    HR_TRY(build_hierarchy(ctx, a, n_clusters, 0, rg[0], rg[1], pipe ? ctx->side : nullptr));
     fit_ran = a->E > 0;
   }
   const bool clustered = keep || n_clusters > 0;
@@ -788,11 +844,15 @@ hr_status hr_render_frame(hr_ctx* ctx, hr_asset* a, uint32_t n_clusters, float e
   }
   if (!refit) HR_TRY(build_bvh(ctx, a, lod_dev, a->bvh, st));
   if (stats) HR_CUDA(ctx, cudaEventRecord(ph[5], st));
-  HR_TRY(render_impl(ctx, a, desc, rgb_out, stats));
+  // the next frame's clusters and fit may start from here
+  HR_CUDA(ctx, cudaEventRecord(ctx->ev_built, st));
+  ctx->ring_fit[ctx->ring_n % hr_ctx::kRing] = fit_ran ? 1 : 0;
+  ++ctx->ring_n;
+  HR_TRY(render_impl(ctx, a, desc, rgb_out, stats, nullptr, 0, nullptr, rg[2], rg[3]));
   if (stats) {
     float h = 0.f, f = 0.f, l = 0.f, b = 0.f;
     HR_CUDA(ctx, cudaEventElapsedTime(&h, ph[0], ph[3]));
-    if (fit_ran) HR_CUDA(ctx, cudaEventElapsedTime(&f, ph[1], ph[2]));
+    if (fit_ran) HR_CUDA(ctx, cudaEventElapsedTime(&f, rg[0], rg[1]));
     HR_CUDA(ctx, cudaEventElapsedTime(&l, ph[3], ph[4]));
     HR_CUDA(ctx, cudaEventElapsedTime(&b, ph[4], ph[5]));
     stats->hierarchy_ms = h;
@@ -802,6 +862,25 @@ hr_status hr_render_frame(hr_ctx* ctx, hr_asset* a, uint32_t n_clusters, float e
     stats->bvh_refit = refit ? 1u : 0u;
     stats->lod_deferred = deferred && clustered && a->n_levels > 0 ? 1u : 0u;
   }
+  ctx->pipe_ready = true;
+  return HR_OK;
+}
+
+hr_status hr_frame_times(hr_ctx* ctx, uint32_t n, float* frame_ms, float* fit_ms, uint32_t* n_out) {
+  API_ENTER(ctx);
+  const uint64_t have = std::min<uint64_t>(ctx->ring_n, (uint64_t)hr_ctx::kRing);
+  const uint32_t m = (uint32_t)std::min<uint64_t>(n, have);
+  for (uint32_t i = 0; i < m; ++i) {
+    const uint64_t slot = (ctx->ring_n - m + i) % hr_ctx::kRing;
+    cudaEvent_t* rg = ctx->ring[slot];
+    HR_CUDA(ctx, cudaEventSynchronize(rg[3]));
+    float f = 0.f, g = 0.f;
+    HR_CUDA(ctx, cudaEventElapsedTime(&f, rg[2], rg[3]));
+    if (ctx->ring_fit[slot]) HR_CUDA(ctx, cudaEventElapsedTime(&g, rg[0], rg[1]));
+    if (frame_ms) frame_ms[i] = f;
+    if (fit_ms) fit_ms[i] = g;
+  }
+  if (n_out) *n_out = m;
   return HR_OK;
 }
 

@@ -71,6 +71,7 @@ struct hr_asset {
   uint32_t* cluster_of = nullptr;  // [N]
   uint32_t* cl_first = nullptr;    // [C + 1] first rank of each cluster
   float4* xsec = nullptr;          // [E * (S+1) * 3] (c,a) (e1,b) (e2,0)
+  float4* xsec_other = nullptr;    // the other buffer of a pipelined hr_render_frame (or null)
   // all potential primitives: strand segments then thick-hair segments
   uint32_t n_prims_total = 0;
   float4* prim_xf = nullptr;   // [P_total * 3]
@@ -99,6 +100,10 @@ namespace hr {
 uint64_t ctx_alloc_note(hr_ctx* ctx, int64_t delta);
 hr_status set_error(hr_ctx* ctx, hr_status st, const std::string& msg);
 cudaStream_t ctx_stream(hr_ctx* ctx);
+// Stream and event of a pipelined hr_render_frame: the next frame's clusters
+// and fit run on the side stream while the previous frame renders.
+cudaStream_t ctx_side_stream(hr_ctx* ctx);
+cudaEvent_t ctx_fit_event(hr_ctx* ctx);
 Tables ctx_tables(hr_ctx* ctx);
 // device allocation charged to the context budget
 hr_status dalloc(hr_ctx* ctx, void** p, size_t bytes, const char* what);
@@ -176,8 +181,12 @@ __device__ __forceinline__ uint32_t ordered_bits(float f) {
 __device__ __forceinline__ float from_ordered(uint32_t u) {
   return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
 }
+// st_fit: run the clusters and the fit on this stream (the side stream of a
+// pipelined hr_render_frame), the thick-hair records on the main stream after
+// them; null: everything on the main stream.
 hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_levels,
-                          cudaEvent_t fit_begin = nullptr, cudaEvent_t fit_end = nullptr);
+                          cudaEvent_t fit_begin = nullptr, cudaEvent_t fit_end = nullptr,
+                          cudaStream_t st_fit = nullptr);
 // The roots' Morton codes (sorted, into codes) and the strands in (code, id)
 // order (into order), both [N] device.
 hr_status root_morton_order(hr_ctx* ctx, hr_asset* a, uint32_t* codes, uint32_t* order,

@@ -917,6 +917,8 @@ hr_status hierarchy_setup(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_lev
     if (a->cluster_of) dfree(ctx, a->cluster_of, (size_t)N * 4), a->cluster_of = nullptr;
     if (a->cl_first) dfree(ctx, a->cl_first, (size_t)(a->C + 1) * 4), a->cl_first = nullptr;
     if (a->xsec) dfree(ctx, a->xsec, (size_t)a->E * (S + 1) * 3 * sizeof(float4)), a->xsec = nullptr;
+    if (a->xsec_other)
+      dfree(ctx, a->xsec_other, (size_t)a->E * (S + 1) * 3 * sizeof(float4)), a->xsec_other = nullptr;
     if (a->lod) dfree(ctx, a->lod, a->C), a->lod = nullptr;
     a->lod_valid = 0;
     HR_TRY(dalloc(ctx, (void**)&a->order, (size_t)N * 4, "order"));
@@ -935,9 +937,14 @@ hr_status hierarchy_setup(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_lev
 
 // Thick-hair materials, fits and segment records of the hierarchy whose
 // order and cluster starts are set, growing the material and primitive arrays.
+// The fit runs on st_fit (the side stream of a pipelined frame, or the main
+// stream); the thick-hair materials and records, which the frame in flight
+// reads, on the main stream after it.
 hr_status hierarchy_finish(hr_ctx* ctx, hr_asset* a, const LevelInfo& li, uint64_t E,
-                           uint64_t total, cudaEvent_t fit_begin, cudaEvent_t fit_end) {
+                           uint64_t total, cudaEvent_t fit_begin, cudaEvent_t fit_end,
+                           cudaStream_t st_fit = nullptr) {
   cudaStream_t st = ctx_stream(ctx);
+  cudaStream_t sf = st_fit ? st_fit : st;
   const uint32_t N = a->N, S = a->S;
   // grow the material table to strands + thick hairs
   if (a->mat_cap < (size_t)N + E) {
@@ -974,7 +981,13 @@ hr_status hierarchy_finish(hr_ctx* ctx, hr_asset* a, const LevelInfo& li, uint64
   // The scene bounds (for the BVH's Morton codes) are those of the strand
   // segments' boxes, taken when the asset was created: a thick-hair segment's
   // box centre is the mean of member vertices, so it lies inside them.
-  if (E == 0) return HR_OK;
+  if (E == 0) {
+    if (sf != st) {
+      HR_CUDA(ctx, cudaEventRecord(ctx_fit_event(ctx), sf));
+      HR_CUDA(ctx, cudaStreamWaitEvent(st, ctx_fit_event(ctx), 0));
+    }
+    return HR_OK;
+  }
 
   // K2: cross-section fits (FP64 covariance and eigenvectors), materials and
   // thick-hair segment records
@@ -983,12 +996,16 @@ hr_status hierarchy_finish(hr_ctx* ctx, hr_asset* a, const LevelInfo& li, uint64
   float* eth_r = nullptr;
   HR_TRY(scratch(ctx, 5, (size_t)E * sizeof(float), (void**)&eth_r));
   const uint64_t nx = E * (S + 1);
-  if (fit_begin) HR_CUDA(ctx, cudaEventRecord(fit_begin, st));
-  k_fit_cross_sections<<<(unsigned)((nx + 127) / 128), 128, 0, st>>>(a->verts, S, a->order,
+  if (fit_begin) HR_CUDA(ctx, cudaEventRecord(fit_begin, sf));
+  k_fit_cross_sections<<<(unsigned)((nx + 127) / 128), 128, 0, sf>>>(a->verts, S, a->order,
                                                                     a->cl_first, li, (uint32_t)E,
                                                                     a->xsec);
   HR_LAUNCHED(ctx);
-  if (fit_end) HR_CUDA(ctx, cudaEventRecord(fit_end, st));
+  if (fit_end) HR_CUDA(ctx, cudaEventRecord(fit_end, sf));
+  if (sf != st) {
+    HR_CUDA(ctx, cudaEventRecord(ctx_fit_event(ctx), sf));
+    HR_CUDA(ctx, cudaStreamWaitEvent(st, ctx_fit_event(ctx), 0));
+  }
   k_eth_material<<<(unsigned)((E * (HR_MAT_FLOATS + 1) + 127) / 128), 128, 0, st>>>(a->verts, N, S, a->order,
                                                              a->cl_first, li, (uint32_t)E,
                                                              a->mat, eth_r);
@@ -1004,8 +1021,9 @@ hr_status hierarchy_finish(hr_ctx* ctx, hr_asset* a, const LevelInfo& li, uint64
 }  // namespace
 
 hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_levels,
-                          cudaEvent_t fit_begin, cudaEvent_t fit_end) {
-  cudaStream_t st = ctx_stream(ctx);
+                          cudaEvent_t fit_begin, cudaEvent_t fit_end, cudaStream_t st_fit) {
+  // K1 and the fit on st_fit when the caller pipelines frames (see hierarchy_finish)
+  cudaStream_t st = st_fit ? st_fit : ctx_stream(ctx);
   const uint32_t N = a->N, S = a->S;
   LevelInfo li{};
   uint64_t E = 0, total = 0;
@@ -1035,7 +1053,7 @@ hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_lev
   k_cluster_first<<<(C + 1 + 255) / 256, 256, 0, st>>>(N, C, a->cl_first);
   HR_LAUNCHED(ctx);
 
-  return hierarchy_finish(ctx, a, li, E, total, fit_begin, fit_end);
+  return hierarchy_finish(ctx, a, li, E, total, fit_begin, fit_end, st_fit);
 }
 
 hr_status rebuild_eth_records(hr_ctx* ctx, hr_asset* a) {

@@ -583,6 +583,39 @@ def test_render_profile_records_every_tile(ctx):
         hr.hr_asset_destroy(ctx, a)
 
 
+def test_pipelined_frames_equal_single_frames(ctx):
+    """Back-to-back hr_render_frame calls (device output, no statistics) build
+    each frame's clusters and fit on the side stream while the previous frame
+    renders; alternating two views (so LoD and BVH change every frame), every
+    image equals a render of the same view without overlap."""
+    import torch
+    w = scenegen.full_head(n=6000, S=16, width=96, height=64, spp=2, n_lights=2, n_clusters=256)
+    cams = [w.camera.pack(),
+            scenegen.frame_camera(*w.scene.aabb(), 96, 64, perspective=True, fill=0.3).pack()]
+    descs = [hr.render_desc(c, w.lights, w.spp, w.k_depth, w.sample_seed, 0) for c in cams]
+    ref = []
+    for d in descs:  # a fresh asset per view: its first frame cannot overlap anything
+        b = upload(ctx, w.scene)
+        try:
+            img = np.zeros((64, 96, 3), np.float32)
+            hr.hr_render_frame(ctx, b, w.n_clusters, w.eps_w, 0, d, img, stats=True)
+            ref.append(img)
+        finally:
+            hr.hr_asset_destroy(ctx, b)
+    a = upload(ctx, w.scene)
+    try:
+        outs = [torch.zeros((64, 96, 3), dtype=torch.float32, device="cuda") for _ in range(6)]
+        for i, o in enumerate(outs):
+            hr.hr_render_frame(ctx, a, w.n_clusters, w.eps_w, 0, descs[i % 2], o)
+        torch.cuda.synchronize()
+        for i, o in enumerate(outs):
+            assert np.array_equal(o.cpu().numpy(), ref[i % 2]), i
+        frame_ms, fit_ms = hr.hr_frame_times(ctx, 6)
+        assert frame_ms.size == 6 and np.all(frame_ms > 0) and np.all(fit_ms > 0)
+    finally:
+        hr.hr_asset_destroy(ctx, a)
+
+
 # ---------------------------------------------------------------- shadow rays
 SHADOW_AGREE_MIN = 0.99  # samples whose radiance agrees to 1e-3 (shadow crossings decided alike)
 
