@@ -205,10 +205,13 @@ def oracle_baseline(w, seconds: float, seed: int = 11):
     oracle.render_samples(prep, w.camera.pack(), w.lights, sids, w.spp, w.k_depth, w.sample_seed,
                           threads=cores)
     dt = time.time() - t0
+    P = int(prep.rows.shape[0])
     return {"value": m / dt / 1e6, "unit": "Msamples/s", "cores": cores, "kind": "oracle",
             "sample": f"{m} seeded samples of the {total}-sample frame, brute force over "
-                      f"{prep.rows.shape[0]} active primitives (FP64); setup {t_prep:.1f}s untimed",
-            "seconds": dt}
+                      f"{P} active primitives (FP64); setup {t_prep:.1f}s untimed",
+            "seconds": dt,
+            "ns_per_sample_primitive": dt * cores / (m * max(P, 1)) * 1e9,
+            "full_frame_s_extrapolated": total * dt / m}
 
 
 def event_flops(st) -> int:
@@ -754,6 +757,8 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     sm_max = clocks.get("sm_max_mhz") or 2070.0
     peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    sm_load = clocks.get("sm_mhz") or sm_max
+    peak_load = props.multi_processor_count * 128 * 2 * sm_load * 1e6 / 1e12
     achieved = flops / (render_avg * 1e-3) / 1e12
     flops_src = event_flops_source(cst)
     roof_frame = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -768,6 +773,7 @@ def main():
                   "flops_per_launch": flops,
                   "peak_basis": f"FP32: {props.multi_processor_count} SMs x 128 lanes x 2 (FMA) x "
                                 f"{sm_max:.0f} MHz (derived from unit counts and clock)",
+                  "peak_at_load_clock": peak_load, "frac_at_load_clock": achieved / peak_load,
                   "events": {"node_visits": cst.node_visits, "prim_tests": cst.prim_tests,
                              "strand_shades": cst.strand_shades, "eth_shades": cst.eth_shades,
                              "hits": cst.shaded_hits, "traced_samples": cst.traced_samples,
