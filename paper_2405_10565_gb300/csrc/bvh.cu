@@ -522,7 +522,7 @@ hr_status build_bvh(hr_ctx* ctx, hr_asset* a, const uint8_t* lod_dev, Bvh& bv, c
   HR_TRY(scratch(ctx, 35, (size_t)n * 4, (void**)&v2));
   k_prim_morton<<<(n + 255) / 256, 256, 0, st>>>(a->prim_box, ids, n, a->d_bounds, keys);
   HR_LAUNCHED(ctx);
-  HR_TRY(radix_sort_pairs(ctx, keys, ids, k2, v2, n, kMortonBits, st));
+  HR_TRY(radix_sort_pairs(ctx, keys, ids, k2, v2, n, kMortonBits, st, kLookbackPolls, &keys, &ids));
   if (n == 1) {
     k_gather<<<1, 32, 0, st>>>(ids, n, bv.leaf_id);
     HR_LAUNCHED(ctx);

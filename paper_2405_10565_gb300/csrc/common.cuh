@@ -142,9 +142,14 @@ hr_status scan_u32(hr_ctx* ctx, uint32_t* data, uint32_t n, cudaStream_t st);
 // max_polls: reads of an unpublished earlier tile before counting instead
 // (0: count at once, for tests)
 constexpr int kLookbackPolls = 1 << 16;
+// The sorted pairs end in (keys, vals); with keys_out and vals_out given they
+// are left where the last pass wrote them (keys / vals or the temporaries)
+// and those pointers name them, which saves copying back after an odd number
+// of passes.
 hr_status radix_sort_pairs(hr_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp,
                            uint32_t* vals_tmp, uint32_t n, int bits, cudaStream_t st,
-                           int max_polls = kLookbackPolls);
+                           int max_polls = kLookbackPolls, uint32_t** keys_out = nullptr,
+                           uint32_t** vals_out = nullptr);
 
 // no-allocation variants on caller-provided scratch (sort.cu, hierarchy.cu)
 cudaError_t scan_u32_with(uint32_t* data, uint32_t n, uint32_t* sums, cudaStream_t st);

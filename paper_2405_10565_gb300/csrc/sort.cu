@@ -360,7 +360,9 @@ hr_status scan_u32(hr_ctx* ctx, uint32_t* data, uint32_t n, cudaStream_t st) {
 
 hr_status radix_sort_pairs(hr_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp,
                            uint32_t* vals_tmp, uint32_t n, int bits, cudaStream_t st,
-                           int max_polls) {
+                           int max_polls, uint32_t** keys_out, uint32_t** vals_out) {
+  if (keys_out) *keys_out = keys;
+  if (vals_out) *vals_out = vals;
   if (n <= 1) return HR_OK;
   if (n >= kFlagAgg || bits < 1 || bits > 32) return set_error(ctx, HR_EINVAL, "sort: size out of range");
   const int passes = (bits + 7) / 8;
@@ -388,7 +390,10 @@ hr_status radix_sort_pairs(hr_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t
     t = ki; ki = ko; ko = t;
     t = vi; vi = vo; vo = t;
   }
-  if (passes & 1) {
+  if (keys_out && vals_out) {  // the caller takes the result where the last pass left it
+    *keys_out = ki;
+    *vals_out = vi;
+  } else if (passes & 1) {
     HR_CUDA(ctx, cudaMemcpyAsync(keys, ki, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
     HR_CUDA(ctx, cudaMemcpyAsync(vals, vi, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
   }
