@@ -774,6 +774,11 @@ def main():
                   "peak_basis": f"FP32: {props.multi_processor_count} SMs x 128 lanes x 2 (FMA) x "
                                 f"{sm_max:.0f} MHz (derived from unit counts and clock)",
                   "peak_at_load_clock": peak_load, "frac_at_load_clock": achieved / peak_load,
+                  "frac_standalone": flops / (fp32_ms * 1e-3) / 1e12 / peak,
+                  "kernel_ms_standalone": fp32_ms,
+                  "kernel_ms_note": "kernel_ms: the timed steps' frames, each overlapping the next "
+                                    "step's clusters and fit; kernel_ms_standalone: the same frame "
+                                    "alone (median of 10)",
                   "events": {"node_visits": cst.node_visits, "prim_tests": cst.prim_tests,
                              "strand_shades": cst.strand_shades, "eth_shades": cst.eth_shades,
                              "hits": cst.shaded_hits, "traced_samples": cst.traced_samples,
