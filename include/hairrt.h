@@ -234,9 +234,14 @@ hr_status hr_asset_destroy(hr_ctx* ctx, hr_asset* asset);
  * directly by the rebuilding kernel (the transfer overlaps the rebuild);
  * either must stay unchanged until the context stream has passed it (the
  * next call that returns results, e.g. hr_render_frame).  Pageable host
- * memory is copied before the call returns.  The hierarchy, thick hairs and BVH of the old
- * positions are stale afterwards: hr_render_frame rebuilds them, or call
- * hr_build_clusters and hr_build_bvh.  The LoD kept for Eq. 14's deferred
+ * memory is copied before the call returns.  Right after hr_render_frame
+ * (no other call in between, no serving loop), with device or page-locked
+ * source vertices, the new positions and records go to a second set of the
+ * asset's buffers on a second stream while that frame renders from the set
+ * it was launched with (the first such call allocates the set: the asset's
+ * vertex and record memory once more); later calls see the new set.  The
+ * hierarchy, thick hairs and BVH of the old positions are stale afterwards:
+ * hr_render_frame rebuilds them, or call hr_build_clusters and hr_build_bvh.  The LoD kept for Eq. 14's deferred
  * rule is the previous frame's, as the paper intends.  With serving running,
  * the asset's queued requests end with HR_ESTATE, running ones are waited
  * for, and its cached BVHs are dropped. */

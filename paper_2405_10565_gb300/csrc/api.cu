@@ -13,6 +13,8 @@
 #include "common.cuh"
 #include "serve.h"
 
+constexpr int kFrameCall = 1, kUpdateCall = 2;
+
 struct hr_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -35,9 +37,10 @@ struct hr_ctx {
   // pipelined hr_render_frame: the side stream runs the next frame's clusters
   // and fit once ev_built (the previous frame's BVH is done) has passed
   cudaStream_t side = nullptr;
-  cudaEvent_t ev_built = nullptr, ev_fit = nullptr;
-  bool pipe_ready = false;  // the last API call was hr_render_frame
-  bool pipe_prev = false;   // ... as seen by the current call
+  cudaEvent_t ev_built = nullptr, ev_fit = nullptr, ev_update = nullptr;
+  // the kind of the last API call, as set by it (0 any other, kFrameCall,
+  // kUpdateCall a pipelined hr_asset_update) and as seen by the current call
+  int call_kind = 0, prev_kind = 0;
   // frame-time ring: per hr_render_frame, events around the fit and the frame
   static constexpr int kRing = 256;
   cudaEvent_t ring[kRing][4] = {};
@@ -223,8 +226,8 @@ struct DeviceGuard {
   if (!(ctx)) return HR_EINVAL;                                          \
   std::lock_guard<std::recursive_mutex> api_lock_((ctx)->api_mu);        \
   DeviceGuard dev_guard_((ctx)->device);                                 \
-  (ctx)->pipe_prev = (ctx)->pipe_ready;                                  \
-  (ctx)->pipe_ready = false
+  (ctx)->prev_kind = (ctx)->call_kind;                                   \
+  (ctx)->call_kind = 0
 
 }  // namespace
 
@@ -261,7 +264,8 @@ hr_status hr_create(hr_ctx** out, int device, uint64_t hbm_budget, void* cuda_st
     if (cudaEventCreate(&ctx->ph[i]) != cudaSuccess) st = HR_ECUDA;
   if (st == HR_OK && (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
                       cudaEventCreateWithFlags(&ctx->ev_built, cudaEventDisableTiming) != cudaSuccess ||
-                      cudaEventCreateWithFlags(&ctx->ev_fit, cudaEventDisableTiming) != cudaSuccess))
+                      cudaEventCreateWithFlags(&ctx->ev_fit, cudaEventDisableTiming) != cudaSuccess ||
+                      cudaEventCreateWithFlags(&ctx->ev_update, cudaEventDisableTiming) != cudaSuccess))
     st = HR_ECUDA;
   for (int i = 0; i < hr_ctx::kRing && st == HR_OK; ++i)
     for (int j = 0; j < 4 && st == HR_OK; ++j)
@@ -301,6 +305,7 @@ hr_status hr_destroy(hr_ctx* ctx) {
         if (ctx->ring[i][j]) cudaEventDestroy(ctx->ring[i][j]);
     if (ctx->ev_built) cudaEventDestroy(ctx->ev_built);
     if (ctx->ev_fit) cudaEventDestroy(ctx->ev_fit);
+    if (ctx->ev_update) cudaEventDestroy(ctx->ev_update);
     if (ctx->side) cudaStreamDestroy(ctx->side);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   }
@@ -357,6 +362,50 @@ hr_status hr_asset_update(hr_ctx* ctx, hr_asset* a, const float* vertices) {
   // once by the kernel that rebuilds the records, so the transfer overlaps
   // the build; anything else is copied first
   const float4* view = static_cast<const float4*>(device_view(vertices));
+  // Pipelining: right after hr_render_frame, the new positions go to the
+  // asset's other set of vertex and record buffers on the side stream, while
+  // the frame in flight keeps reading the set it was launched with; the next
+  // hr_render_frame's clusters and fit follow them there.  The other set was
+  // last read by the frame before, which ended before the last BVH was built.
+  const uint64_t ns = (uint64_t)a->N * a->S;
+  if (ctx->prev_kind == kFrameCall && !ctx->server && view && a->S + 1 <= kUpdateMaxVerts &&
+      a->n_prims_total >= ns) {
+    const uint64_t P = a->n_prims_total;
+    const size_t nv = (size_t)a->N * (a->S + 1);
+    if (a->other_total != P) {  // (re)size the other set to the current records
+      if (a->verts_other) dfree(ctx, a->verts_other, nv * sizeof(float4)), a->verts_other = nullptr;
+      if (a->xf_other) dfree(ctx, a->xf_other, (size_t)a->other_total * 3 * sizeof(float4)), a->xf_other = nullptr;
+      if (a->box_other) dfree(ctx, a->box_other, (size_t)a->other_total * 2 * sizeof(float4)), a->box_other = nullptr;
+      if (a->aux_other) dfree(ctx, a->aux_other, (size_t)a->other_total * sizeof(float4)), a->aux_other = nullptr;
+      a->other_total = 0;
+      HR_TRY(dalloc(ctx, (void**)&a->verts_other, nv * sizeof(float4), "vertices (second set)"));
+      HR_TRY(dalloc(ctx, (void**)&a->xf_other, P * 3 * sizeof(float4), "records (second set)"));
+      HR_TRY(dalloc(ctx, (void**)&a->box_other, P * 2 * sizeof(float4), "boxes (second set)"));
+      HR_TRY(dalloc(ctx, (void**)&a->aux_other, P * sizeof(float4), "aux (second set)"));
+      a->other_total = (uint32_t)P;
+    }
+    cudaStream_t sd = ctx->side;
+    HR_CUDA(ctx, cudaStreamWaitEvent(sd, ctx->ev_built, 0));
+    if (P > ns) {  // the thick-hair records too, so the new set is whole whatever comes next
+      HR_CUDA(ctx, cudaMemcpyAsync(a->xf_other + 3 * ns, a->prim_xf + 3 * ns, (P - ns) * 3 * sizeof(float4),
+                                   cudaMemcpyDeviceToDevice, sd));
+      HR_CUDA(ctx, cudaMemcpyAsync(a->box_other + 2 * ns, a->prim_box + 2 * ns, (P - ns) * 2 * sizeof(float4),
+                                   cudaMemcpyDeviceToDevice, sd));
+      HR_CUDA(ctx, cudaMemcpyAsync(a->aux_other + ns, a->prim_aux + ns, (P - ns) * sizeof(float4),
+                                   cudaMemcpyDeviceToDevice, sd));
+    }
+    std::swap(a->verts, a->verts_other);
+    std::swap(a->prim_xf, a->xf_other);
+    std::swap(a->prim_box, a->box_other);
+    std::swap(a->prim_aux, a->aux_other);
+    HR_TRY(update_strands(ctx, a, view, sd));
+    // everything enqueued on the main stream from here on sees the new set
+    HR_CUDA(ctx, cudaEventRecord(ctx->ev_update, sd));
+    HR_CUDA(ctx, cudaStreamWaitEvent(st, ctx->ev_update, 0));
+    a->bvh.valid = 0;
+    ctx->call_kind = kUpdateCall;
+    return HR_OK;
+  }
   if (view && a->S + 1 <= kUpdateMaxVerts) {
     HR_TRY(update_strands(ctx, a, view));
   } else {
@@ -382,6 +431,10 @@ hr_status hr_asset_destroy(hr_ctx* ctx, hr_asset* a) {
   if (a->cl_first) dfree(ctx, a->cl_first, (size_t)(a->C + 1) * 4);
   if (a->xsec) dfree(ctx, a->xsec, (size_t)a->E * S1 * 3 * sizeof(float4));
   if (a->xsec_other) dfree(ctx, a->xsec_other, (size_t)a->E * S1 * 3 * sizeof(float4));
+  if (a->verts_other) dfree(ctx, a->verts_other, (size_t)a->N * S1 * sizeof(float4));
+  if (a->xf_other) dfree(ctx, a->xf_other, (size_t)a->other_total * 3 * sizeof(float4));
+  if (a->box_other) dfree(ctx, a->box_other, (size_t)a->other_total * 2 * sizeof(float4));
+  if (a->aux_other) dfree(ctx, a->aux_other, (size_t)a->other_total * sizeof(float4));
   if (a->lod) dfree(ctx, a->lod, a->C);
   drop_guides(ctx, a);
   const uint64_t P = a->n_prims_total;
@@ -806,7 +859,7 @@ hr_status hr_render_frame(hr_ctx* ctx, hr_asset* a, uint32_t n_clusters, float e
   // materials, which that frame reads, follow on the main stream after it.
   // Only for a hierarchy of the same shape (no reallocation) and without a
   // serving loop.
-  const bool pipe = ctx->pipe_prev && !ctx->server && !keep && n_clusters > 0 &&
+  const bool pipe = ctx->prev_kind != 0 && !ctx->server && !keep && n_clusters > 0 &&
                     n_clusters <= a->N && a->order && a->C == n_clusters && a->E > 0 &&
                     a->xsec && !a->G;
   cudaStream_t sh = pipe ? ctx->side : st;  // the stream of the clusters and the fit
@@ -862,7 +915,7 @@ hr_status hr_render_frame(hr_ctx* ctx, hr_asset* a, uint32_t n_clusters, float e
     stats->bvh_refit = refit ? 1u : 0u;
     stats->lod_deferred = deferred && clustered && a->n_levels > 0 ? 1u : 0u;
   }
-  ctx->pipe_ready = true;
+  ctx->call_kind = kFrameCall;
   return HR_OK;
 }
 

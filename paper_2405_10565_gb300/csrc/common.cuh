@@ -72,6 +72,11 @@ struct hr_asset {
   uint32_t* cl_first = nullptr;    // [C + 1] first rank of each cluster
   float4* xsec = nullptr;          // [E * (S+1) * 3] (c,a) (e1,b) (e2,0)
   float4* xsec_other = nullptr;    // the other buffer of a pipelined hr_render_frame (or null)
+  // the other vertex and record buffers of a pipelined hr_asset_update (or
+  // null), sized for other_total records
+  float4* verts_other = nullptr;
+  float4 *xf_other = nullptr, *box_other = nullptr, *aux_other = nullptr;
+  uint32_t other_total = 0;
   // all potential primitives: strand segments then thick-hair segments
   uint32_t n_prims_total = 0;
   float4* prim_xf = nullptr;   // [P_total * 3]
@@ -169,7 +174,8 @@ hr_status refresh_strand_prims(hr_ctx* ctx, hr_asset* a);
 // device copy, strand records, Morton bounds; strands of at most
 // kUpdateMaxVerts vertices
 constexpr uint32_t kUpdateMaxVerts = 2048;
-hr_status update_strands(hr_ctx* ctx, hr_asset* a, const float4* src_dev);
+// on stream st (null: the context's stream)
+hr_status update_strands(hr_ctx* ctx, hr_asset* a, const float4* src_dev, cudaStream_t st = nullptr);
 // device address through which kernels can read p (device memory, or mapped
 // page-locked host memory), or nullptr
 const void* device_view(const void* p);

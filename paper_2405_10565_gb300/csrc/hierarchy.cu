@@ -826,8 +826,8 @@ __global__ void k_init_bounds(uint32_t* bounds) {
 
 // Bounds of the first n primitive boxes into a->d_bounds (ordered float
 // bits: lo xyz, hi xyz), on the stream; nothing is read back.
-hr_status scene_bounds(hr_ctx* ctx, hr_asset* a, uint64_t n) {
-  cudaStream_t st = ctx_stream(ctx);
+hr_status scene_bounds(hr_ctx* ctx, hr_asset* a, uint64_t n, cudaStream_t st = nullptr) {
+  if (!st) st = ctx_stream(ctx);
   k_init_bounds<<<1, 32, 0, st>>>(a->d_bounds);
   HR_LAUNCHED(ctx);
   const int blocks = (int)std::min<uint64_t>((n + 255) / 256, 152 * 8);
@@ -851,8 +851,8 @@ hr_status build_strand_prims(hr_ctx* ctx, hr_asset* a) {
 
 // Strand segment records and scene bounds from the current vertices, into
 // the asset's existing arrays (the first N * S records).
-hr_status update_strands(hr_ctx* ctx, hr_asset* a, const float4* src_dev) {
-  cudaStream_t st = ctx_stream(ctx);
+hr_status update_strands(hr_ctx* ctx, hr_asset* a, const float4* src_dev, cudaStream_t st) {
+  if (!st) st = ctx_stream(ctx);
   const uint32_t S1 = a->S + 1;
   const uint32_t per_block = std::min<uint32_t>(256u, kUpdateMaxVerts / S1);
   const size_t smem = ((size_t)per_block * S1 + per_block) * sizeof(float4);
@@ -860,7 +860,7 @@ hr_status update_strands(hr_ctx* ctx, hr_asset* a, const float4* src_dev) {
   k_strand_update<<<blocks, 256, smem, st>>>(src_dev, a->verts, a->shape, a->N, a->S, per_block,
                                              a->prim_xf, a->prim_box, a->prim_aux);
   HR_LAUNCHED(ctx);
-  return scene_bounds(ctx, a, (uint64_t)a->N * a->S);
+  return scene_bounds(ctx, a, (uint64_t)a->N * a->S, st);
 }
 
 hr_status refresh_strand_prims(hr_ctx* ctx, hr_asset* a) {

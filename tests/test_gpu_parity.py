@@ -616,6 +616,44 @@ def test_pipelined_frames_equal_single_frames(ctx):
         hr.hr_asset_destroy(ctx, a)
 
 
+def test_pipelined_updates_equal_single_frames(ctx):
+    """hr_asset_update right after hr_render_frame writes the asset's other
+    vertex and record set on the side stream while the frame renders; a loop
+    of (update, frame) over two poses, device output and no statistics, gives
+    every frame the image of a fresh asset in that pose."""
+    import torch
+    w = scenegen.full_head(n=6000, S=16, width=96, height=64, spp=2, n_lights=2, n_clusters=256)
+    poses = [np.ascontiguousarray(w.scene.verts), _moved(w.scene.verts, 2e-3, anchored=True)]
+    d = desc_of(w)
+    ref = []
+    for v in poses:  # a fresh asset per pose: nothing to overlap
+        b = hr.hr_asset_create(ctx, v, np.ascontiguousarray(w.scene.mat),
+                               np.ascontiguousarray(w.scene.shape))
+        try:
+            img = np.zeros((64, 96, 3), np.float32)
+            hr.hr_render_frame(ctx, b, w.n_clusters, w.eps_w, 0, d, img, stats=True)
+            ref.append(img)
+        finally:
+            hr.hr_asset_destroy(ctx, b)
+    a = upload(ctx, w.scene)
+    try:
+        pinned = [torch.from_numpy(v).pin_memory() for v in poses]
+        outs = [torch.zeros((64, 96, 3), dtype=torch.float32, device="cuda") for _ in range(7)]
+        hr.hr_render_frame(ctx, a, w.n_clusters, w.eps_w, 0, d, outs[0])
+        for i in range(1, 7):
+            hr.hr_asset_update(ctx, a, pinned[i % 2])
+            hr.hr_render_frame(ctx, a, w.n_clusters, w.eps_w, 0, d, outs[i])
+        torch.cuda.synchronize()
+        for i, o in enumerate(outs):
+            assert np.array_equal(o.cpu().numpy(), ref[i % 2]), i
+        # and a plain call afterwards sees the last pose
+        img = np.zeros((64, 96, 3), np.float32)
+        hr.hr_render_frame(ctx, a, w.n_clusters, w.eps_w, 0, d, img, stats=True)
+        assert np.array_equal(img, ref[0])
+    finally:
+        hr.hr_asset_destroy(ctx, a)
+
+
 # ---------------------------------------------------------------- shadow rays
 SHADOW_AGREE_MIN = 0.99  # samples whose radiance agrees to 1e-3 (shadow crossings decided alike)
 
