@@ -696,6 +696,24 @@ def main():
                 dt = (time.perf_counter() - t0) / animation["frames"]
                 res[key] = {"ms_per_frame": dt * 1e3, "bvh_ms": statistics.median(bvh),
                             "bvh_refits": refits, "h2d_bytes_per_frame": pv.numel() * 4}
+                # the same frames without statistics (device image, copied back
+                # asynchronously): each frame's upload, clusters and fit
+                # overlap the previous frame
+                for i in range(2):
+                    hr.hr_asset_update(ctx, asset, poses[i])
+                    hr.hr_render_frame(ctx, asset, w.n_clusters, w.eps_w, 0, da, img_e)
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                for i in range(animation["frames"]):
+                    hr.hr_asset_update(ctx, asset, poses[i % 2])
+                    hr.hr_render_frame(ctx, asset, w.n_clusters, w.eps_w, 0, da, img_e)
+                    with torch.cuda.stream(stream):
+                        hout.copy_(img_e, non_blocking=True)
+                torch.cuda.synchronize(dev)
+                dto = (time.perf_counter() - t0) / animation["frames"]
+                _, _, fl = hr.hr_frame_times(ctx, animation["frames"], with_flags=True)
+                res[key]["ms_per_frame_overlapped"] = dto * 1e3
+                res[key]["bvh_refits_overlapped"] = int(((fl >> 1) & 1).sum())
             # the guide-driven hierarchy, once, then skinned frames
             G = 256
             hr.hr_asset_update(ctx, asset, pv)

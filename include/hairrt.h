@@ -447,10 +447,12 @@ hr_status hr_render_frame(hr_ctx* ctx, hr_asset* asset, uint32_t n_clusters, flo
  * first, from events every call records (so a loop of frames needs no
  * synchronisation per frame to be timed): frame_ms[i] the frame kernel
  * (with the image clear and scene rectangle), fit_ms[i] the cross-section
- * fit (0 when that call fitted nothing).  Waits for those frames.  At most
- * the last 256 calls are kept; n_out (optional) receives the number written.
- * frame_ms, fit_ms: optional host arrays of n floats. */
-hr_status hr_frame_times(hr_ctx* ctx, uint32_t n, float* frame_ms, float* fit_ms, uint32_t* n_out);
+ * fit (0 when that call fitted nothing), flags[i] bit 0 the call fitted,
+ * bit 1 it refit the BVH instead of rebuilding it.  Waits for those frames.
+ * At most the last 256 calls are kept; n_out (optional) receives the number
+ * written.  frame_ms, fit_ms, flags: optional host arrays of n elements. */
+hr_status hr_frame_times(hr_ctx* ctx, uint32_t n, float* frame_ms, float* fit_ms, uint32_t* flags,
+                         uint32_t* n_out);
 
 /* Morton clustering without any device allocation.
  * The paper has no counterpart: this entry point exists for callers that may

@@ -124,7 +124,7 @@ _SIGS = {
     "hr_im_lookup": (c_int, [P, P, P, c_u32, c_int, P]),
     "hr_render": (c_int, [P, P, ctypes.POINTER(hr_render_desc), P, ctypes.POINTER(hr_stats)]),
     "hr_render_samples": (c_int, [P, P, ctypes.POINTER(hr_render_desc), P, c_u32, P, P]),
-    "hr_frame_times": (c_int, [P, c_u32, P, P, ctypes.POINTER(c_u32)]),
+    "hr_frame_times": (c_int, [P, c_u32, P, P, P, ctypes.POINTER(c_u32)]),
     "hr_render_profile": (c_int, [P, P, ctypes.POINTER(hr_render_desc), P, ctypes.POINTER(hr_stats),
                                   P, c_u32, ctypes.POINTER(c_u32)]),
     "hr_render_frame": (c_int, [P, P, c_u32, c_float, c_int, ctypes.POINTER(hr_render_desc), P,
@@ -364,16 +364,19 @@ def hr_render(ctx: int, asset: int, desc: hr_render_desc, rgb_out, stats: bool =
     return st
 
 
-def hr_frame_times(ctx: int, n: int):
-    """Frame-kernel and fit times (ms) of the last n hr_render_frame calls:
-    two numpy float32 arrays, oldest first."""
+def hr_frame_times(ctx: int, n: int, with_flags: bool = False):
+    """Frame-kernel and fit times (ms) of the last n hr_render_frame calls,
+    oldest first (numpy float32 arrays), and with with_flags their flags
+    (bit 0 fitted, bit 1 refit the BVH)."""
     import numpy as np
     f = np.zeros(max(int(n), 1), np.float32)
     g = np.zeros(max(int(n), 1), np.float32)
+    fl = np.zeros(max(int(n), 1), np.uint32)
     m = c_u32(0)
-    _check(ctx, load().hr_frame_times(ctx, int(n), f.ctypes.data, g.ctypes.data, ctypes.byref(m)),
-           "hr_frame_times")
-    return f[:m.value].copy(), g[:m.value].copy()
+    _check(ctx, load().hr_frame_times(ctx, int(n), f.ctypes.data, g.ctypes.data, fl.ctypes.data,
+                                      ctypes.byref(m)), "hr_frame_times")
+    out = (f[:m.value].copy(), g[:m.value].copy())
+    return out + (fl[:m.value].copy(),) if with_flags else out
 
 
 def hr_render_profile(ctx: int, asset: int, desc: hr_render_desc, rgb_out, capacity: int):

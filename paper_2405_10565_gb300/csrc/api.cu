@@ -45,7 +45,7 @@ struct hr_ctx {
   static constexpr int kRing = 256;
   cudaEvent_t ring[kRing][4] = {};
   uint64_t ring_n = 0;
-  std::vector<uint8_t> ring_fit;  // whether entry i's fit events were recorded
+  std::vector<uint8_t> ring_fit;  // entry i: bit 0 its fit events were recorded, bit 1 it refit the BVH
 };
 
 namespace hr {
@@ -899,7 +899,7 @@ hr_status hr_render_frame(hr_ctx* ctx, hr_asset* a, uint32_t n_clusters, float e
   if (stats) HR_CUDA(ctx, cudaEventRecord(ph[5], st));
   // the next frame's clusters and fit may start from here
   HR_CUDA(ctx, cudaEventRecord(ctx->ev_built, st));
-  ctx->ring_fit[ctx->ring_n % hr_ctx::kRing] = fit_ran ? 1 : 0;
+  ctx->ring_fit[ctx->ring_n % hr_ctx::kRing] = (fit_ran ? 1 : 0) | (refit ? 2 : 0);
   ++ctx->ring_n;
   HR_TRY(render_impl(ctx, a, desc, rgb_out, stats, nullptr, 0, nullptr, rg[2], rg[3]));
   if (stats) {
@@ -919,7 +919,8 @@ hr_status hr_render_frame(hr_ctx* ctx, hr_asset* a, uint32_t n_clusters, float e
   return HR_OK;
 }
 
-hr_status hr_frame_times(hr_ctx* ctx, uint32_t n, float* frame_ms, float* fit_ms, uint32_t* n_out) {
+hr_status hr_frame_times(hr_ctx* ctx, uint32_t n, float* frame_ms, float* fit_ms, uint32_t* flags,
+                         uint32_t* n_out) {
   API_ENTER(ctx);
   const uint64_t have = std::min<uint64_t>(ctx->ring_n, (uint64_t)hr_ctx::kRing);
   const uint32_t m = (uint32_t)std::min<uint64_t>(n, have);
@@ -929,9 +930,10 @@ hr_status hr_frame_times(hr_ctx* ctx, uint32_t n, float* frame_ms, float* fit_ms
     HR_CUDA(ctx, cudaEventSynchronize(rg[3]));
     float f = 0.f, g = 0.f;
     HR_CUDA(ctx, cudaEventElapsedTime(&f, rg[2], rg[3]));
-    if (ctx->ring_fit[slot]) HR_CUDA(ctx, cudaEventElapsedTime(&g, rg[0], rg[1]));
+    if (ctx->ring_fit[slot] & 1) HR_CUDA(ctx, cudaEventElapsedTime(&g, rg[0], rg[1]));
     if (frame_ms) frame_ms[i] = f;
     if (fit_ms) fit_ms[i] = g;
+    if (flags) flags[i] = ctx->ring_fit[slot];
   }
   if (n_out) *n_out = m;
   return HR_OK;
