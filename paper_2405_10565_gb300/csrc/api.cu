@@ -875,7 +875,8 @@ hr_status hr_render_frame(hr_ctx* ctx, hr_asset* a, uint32_t n_clusters, float e
     if (a->C == 0) return set_error(ctx, HR_ESTATE, "HR_FLAG_KEEP_HIERARCHY: no hierarchy built");
   } else if (n_clusters > 0) {
     if (n_clusters > a->N) return set_error(ctx, HR_EINVAL, "n_clusters out of range");
-    HR_TRY(build_hierarchy(ctx, a, n_clusters, 0, rg[0], rg[1], pipe ? ctx->side : nullptr));
+    HR_TRY(build_hierarchy(ctx, a, n_clusters, 0, rg[0], rg[1], pipe ? ctx->side : nullptr,
+                           pipe && ctx->prev_kind == kFrameCall));
     fit_ran = a->E > 0;
   }
   const bool clustered = keep || n_clusters > 0;

@@ -197,7 +197,7 @@ __device__ __forceinline__ float from_ordered(uint32_t u) {
 // them; null: everything on the main stream.
 hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_levels,
                           cudaEvent_t fit_begin = nullptr, cudaEvent_t fit_end = nullptr,
-                          cudaStream_t st_fit = nullptr);
+                          cudaStream_t st_fit = nullptr, bool hold_fit = false);
 // The roots' Morton codes (sorted, into codes) and the strands in (code, id)
 // order (into order), both [N] device.
 hr_status root_morton_order(hr_ctx* ctx, hr_asset* a, uint32_t* codes, uint32_t* order,
