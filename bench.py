@@ -630,16 +630,31 @@ def main():
     d2h = hout.numel() * 4
 
     img_e = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+    # two device images and two pinned host images, alternating; each step's
+    # image goes back on its own copy stream
+    img_pair = [img_e, torch.empty_like(img_e)]
+    hout_pair = [hout, torch.empty_like(hout).pin_memory()]
+    copy_stream = torch.cuda.Stream(device=dev)
+    frame_done = [torch.cuda.Event(), torch.cuda.Event()]
+    copy_done = [torch.cuda.Event(), torch.cuda.Event()]
+    e2e_i = [0]
 
     def e2e_step():
-        # upload, whole path, image back to pinned host memory; the copy back
-        # is ordered on the library's stream without blocking the host, so the
-        # next step's upload and clusters overlap this frame (hr_asset_update
-        # and hr_render_frame pipelining); the timed region ends after a sync
+        # upload, whole path, image back to pinned host memory.  The read-back
+        # runs on a copy stream without blocking the host, so the next step's
+        # upload, clusters and fit overlap this frame (hr_asset_update and
+        # hr_render_frame pipelining) and its main-stream work overlaps the
+        # read-back; a frame waits only for the copy that last read its image.
+        j = e2e_i[0] % 2
+        e2e_i[0] += 1
         hr.hr_asset_update(ctx, asset, pv)
-        hr.hr_render_frame(ctx, asset, w.n_clusters, w.eps_w, 0, desc, img_e)
-        with torch.cuda.stream(stream):
-            hout.copy_(img_e, non_blocking=True)
+        stream.wait_event(copy_done[j])
+        hr.hr_render_frame(ctx, asset, w.n_clusters, w.eps_w, 0, desc, img_pair[j])
+        frame_done[j].record(stream)
+        copy_stream.wait_event(frame_done[j])
+        with torch.cuda.stream(copy_stream):
+            hout_pair[j].copy_(img_pair[j], non_blocking=True)
+            copy_done[j].record(copy_stream)
 
     e2e = None
     if not args.no_e2e:
