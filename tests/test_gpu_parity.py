@@ -654,6 +654,38 @@ def test_pipelined_updates_equal_single_frames(ctx):
         hr.hr_asset_destroy(ctx, a)
 
 
+def test_frames_changing_the_hierarchy_shape(ctx):
+    """Back-to-back frames whose cluster count alternates (the hierarchy's
+    shape changes every frame, so no frame may build on the previous one's
+    buffers): every image equals a fresh render with that cluster count, and
+    the frame-time ring reports a fit for each call."""
+    import torch
+    w = scenegen.full_head(n=6000, S=16, width=96, height=64, spp=2, n_lights=2, n_clusters=256)
+    d = desc_of(w)
+    counts = [256, 128]
+    ref = []
+    for C in counts:
+        b = upload(ctx, w.scene)
+        try:
+            img = np.zeros((64, 96, 3), np.float32)
+            hr.hr_render_frame(ctx, b, C, w.eps_w, 0, d, img, stats=True)
+            ref.append(img)
+        finally:
+            hr.hr_asset_destroy(ctx, b)
+    a = upload(ctx, w.scene)
+    try:
+        outs = [torch.zeros((64, 96, 3), dtype=torch.float32, device="cuda") for _ in range(5)]
+        for i, o in enumerate(outs):
+            hr.hr_render_frame(ctx, a, counts[i % 2], w.eps_w, 0, d, o)
+        torch.cuda.synchronize()
+        for i, o in enumerate(outs):
+            assert np.array_equal(o.cpu().numpy(), ref[i % 2]), i
+        _, fit_ms, flags = hr.hr_frame_times(ctx, 5, with_flags=True)
+        assert np.all(flags & 1) and np.all(fit_ms > 0) and not np.any(flags & 2)
+    finally:
+        hr.hr_asset_destroy(ctx, a)
+
+
 # ---------------------------------------------------------------- shadow rays
 SHADOW_AGREE_MIN = 0.99  # samples whose radiance agrees to 1e-3 (shadow crossings decided alike)
 
@@ -890,5 +922,20 @@ def test_refit_engages_under_small_motion_with_hysteresis(ctx):
         hr.hr_asset_update(ctx, a, _moved(w.scene.verts, 2e-3))
         st = hr.hr_render_frame(ctx, a, w.n_clusters, w.eps_w, 0, d, img, stats=True)
         assert st.bvh_refit == 0
+        # the same loop with page-locked poses and device images: the uploads
+        # and clusters overlap the frames, and every frame after the first refits
+        import torch
+        pinned = [torch.from_numpy(p).pin_memory() for p in poses]
+        dimg = torch.zeros((128, 192, 3), dtype=torch.float32, device="cuda")
+        hr.hr_asset_update(ctx, a, pinned[0])
+        hr.hr_render_frame(ctx, a, w.n_clusters, w.eps_w, 0, d, dimg)
+        for i in range(6):
+            hr.hr_asset_update(ctx, a, pinned[(i + 1) % 2])
+            hr.hr_render_frame(ctx, a, w.n_clusters, w.eps_w, 0, d, dimg)
+        _, _, fl = hr.hr_frame_times(ctx, 6, with_flags=True)
+        assert np.all(fl & 2), fl
+        hr.hr_build_bvh(ctx, a, None)
+        hr.hr_render(ctx, a, desc_of(w), ref)
+        assert np.allclose(dimg.cpu().numpy(), ref, rtol=1e-6, atol=1e-7)
     finally:
         hr.hr_asset_destroy(ctx, a)
