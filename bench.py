@@ -667,8 +667,10 @@ def main():
             e2e_step()
         torch.cuda.synchronize(dev)
         e2e_s = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, dist, dev)
+        fr_ms, ft_ms = hr.hr_frame_times(ctx, args.e2e_steps)
         e2e = {"value": job_msamples_per_s(world, samples, 1, e2e_s), "unit": "Msamples/s",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3}
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3,
+               "frame_kernel_ms": float(np.mean(fr_ms)), "fit_kernel_ms": float(np.mean(ft_ms))}
 
     # animated frames: the strands alternate between two poses (a smooth
     # displacement field of amplitude `amp` that grows from 0 at the root, so

@@ -158,6 +158,19 @@ typedef struct hr_light {
  * hr_asset_skin); n_clusters is ignored.  Section 5.2: at run time the hair
  * moves by its guides' weights, without a new clustering or fit. */
 #define HR_FLAG_KEEP_HIERARCHY 4096u
+/* The frame kernel normally carries a schedule from one frame of an asset to
+ * the next (no counterpart in the paper): the warp tiles whose slowest lane
+ * took the most traversal steps in the previous frame (at most 16, at least
+ * half the steps of that frame's slowest) are traced first, four rays per
+ * warp, so that the frame is not held up by 32 long rays sharing one warp.
+ * Their pixels are composited with the same summation order, so the image
+ * does not depend on the schedule.  The schedule lives in the asset and is
+ * dropped when the image size or spp changes.  A frame right after an
+ * overlapped hr_asset_update (the call before it) uses the fixed order and
+ * leaves the schedule as it is, and so does HR_FLAG_FIXED_TILE_ORDER, which
+ * traces every tile whole, in raster order.  Counting renders (HR_FLAG_COUNT,
+ * hr_render_profile) always use the fixed order. */
+#define HR_FLAG_FIXED_TILE_ORDER 8192u
 
 typedef struct hr_render_desc {
   hr_camera camera;
@@ -197,6 +210,9 @@ typedef struct hr_stats {
                                search cut or another hit, or a wide FP32 bound) */
   uint64_t refined_entries; /* kept FP32 hits decided precisely afterwards (their
                                order against a precise hit was open) */
+  uint32_t heavy_tiles;     /* warp tiles traced a few rays per warp from the previous
+                               frame's schedule (see HR_FLAG_FIXED_TILE_ORDER) */
+  uint32_t reserved;
 } hr_stats;
 
 /* ---------------------------------------------------------------- context */

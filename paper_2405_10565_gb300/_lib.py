@@ -41,6 +41,7 @@ HR_FLAG_REFIT = 512
 HR_FLAG_DEFERRED_LOD = 1024
 HR_FLAG_LOD_HYSTERESIS = 2048
 HR_FLAG_KEEP_HIERARCHY = 4096
+HR_FLAG_FIXED_TILE_ORDER = 8192
 
 
 class HairRTError(RuntimeError):
@@ -79,7 +80,8 @@ class hr_stats(ctypes.Structure):
                 ("hierarchy_ms", ctypes.c_double), ("fit_ms", ctypes.c_double),
                 ("lod_ms", ctypes.c_double), ("bvh_ms", ctypes.c_double),
                 ("bvh_refit", c_u32), ("lod_deferred", c_u32),
-                ("refined_tests", c_u64), ("refined_entries", c_u64)]
+                ("refined_tests", c_u64), ("refined_entries", c_u64),
+                ("heavy_tiles", c_u32), ("reserved", c_u32)]
 
 
 class hr_tile_record(ctypes.Structure):

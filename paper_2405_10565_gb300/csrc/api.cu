@@ -436,6 +436,8 @@ hr_status hr_asset_destroy(hr_ctx* ctx, hr_asset* a) {
   if (a->box_other) dfree(ctx, a->box_other, (size_t)a->other_total * 2 * sizeof(float4));
   if (a->aux_other) dfree(ctx, a->aux_other, (size_t)a->other_total * sizeof(float4));
   if (a->lod) dfree(ctx, a->lod, a->C);
+  if (a->sched) dfree(ctx, a->sched, sizeof(TileSched));
+  if (a->tile_cost) dfree(ctx, a->tile_cost, (size_t)a->cost_cap * 4);
   drop_guides(ctx, a);
   const uint64_t P = a->n_prims_total;
   if (a->prim_xf) dfree(ctx, a->prim_xf, P * 3 * sizeof(float4));
@@ -712,6 +714,36 @@ hr_status hr_im_lookup(hr_ctx* ctx, const float* theta, const float* beta, uint3
   return HR_OK;
 }
 
+// The asset's warp-tile schedule (TileSched) and per-tile step counts, grown
+// to the warp tiles an image of this size can have; a grown step array holds
+// no previous frame.
+static hr_status tile_schedule(hr_ctx* ctx, hr_asset* a, FrameArgs& fa, cudaStream_t st) {
+  const uint32_t P = 32u / fa.grp;  // pixels per warp tile, as in warp_grid
+  uint32_t wtw = 1;
+  while (wtw * wtw < P) wtw <<= 1;
+  const uint32_t wth = P / wtw;
+  const size_t need = ((size_t)(fa.cam.W + wtw - 1) / wtw + 1) * ((size_t)(fa.cam.H + wth - 1) / wth + 1);
+  if (!a->sched) {
+    HR_TRY(dalloc(ctx, (void**)&a->sched, sizeof(TileSched), "tile schedule"));
+    HR_CUDA(ctx, cudaMemsetAsync(a->sched, 0, sizeof(TileSched), st));
+  }
+  if (need > a->cost_cap) {
+    if (a->tile_cost) {
+      HR_CUDA(ctx, cudaStreamSynchronize(st));
+      dfree(ctx, a->tile_cost, (size_t)a->cost_cap * 4);
+      a->tile_cost = nullptr;
+      a->cost_cap = 0;
+    }
+    HR_TRY(dalloc(ctx, (void**)&a->tile_cost, need * 4, "tile steps"));
+    a->cost_cap = (uint32_t)need;
+    HR_CUDA(ctx, cudaMemsetAsync(a->sched, 0, sizeof(TileSched), st));
+  }
+  fa.sched = a->sched;
+  fa.tile_cost = a->tile_cost;
+  fa.cost_cap = a->cost_cap;
+  return HR_OK;
+}
+
 static hr_status render_impl(hr_ctx* ctx, hr_asset* a, const hr_render_desc* desc, float* rgb_out,
                              hr_stats* stats, hr_tile_record* tiles = nullptr,
                              uint32_t tile_cap = 0, uint32_t* n_tiles = nullptr,
@@ -741,6 +773,13 @@ static hr_status render_impl(hr_ctx* ctx, hr_asset* a, const hr_render_desc* des
     HR_CUDA(ctx, cudaMemsetAsync(ctx->d_overflow, 0, 4, st));
     HR_CUDA(ctx, cudaMemsetAsync(ctx->d_counters, 0, 8 * sizeof(unsigned long long), st));
   }
+  // Right after an overlapped hr_asset_update the frame shares the GPU with
+  // the upload kernel on the side stream; there the ray-by-ray hand-outs ran
+  // far slower (animated frames through the C ABI: the frame kernel 1.3-2.0
+  // instead of 0.82 ms), so such a frame keeps the fixed order and leaves the
+  // schedule as it is.
+  if (!count && !(desc->flags & HR_FLAG_FIXED_TILE_ORDER) && ctx->prev_kind != kUpdateCall)
+    HR_TRY(tile_schedule(ctx, a, fa, st));
   if (stats) HR_CUDA(ctx, cudaEventRecord(ctx->ev0, st));
   if (t_begin) HR_CUDA(ctx, cudaEventRecord(t_begin, st));
   HR_TRY(launch_frame(ctx, fa, desc->precision, count, out, st));
@@ -759,9 +798,10 @@ static hr_status render_impl(hr_ctx* ctx, hr_asset* a, const hr_render_desc* des
     if (!stats) HR_CUDA(ctx, cudaStreamSynchronize(st));
   }
   if (stats) {
-    uint32_t ovf = 0;
+    uint32_t ovf = 0, heavy = 0;
     unsigned long long cnt[8] = {0};
     HR_CUDA(ctx, cudaMemcpyAsync(&ovf, ctx->d_overflow, 4, cudaMemcpyDeviceToHost, st));
+    if (fa.sched) HR_CUDA(ctx, cudaMemcpyAsync(&heavy, &fa.sched->n_heavy, 4, cudaMemcpyDeviceToHost, st));
     HR_CUDA(ctx, cudaMemcpyAsync(cnt, ctx->d_counters, sizeof(cnt), cudaMemcpyDeviceToHost, st));
     HR_CUDA(ctx, cudaStreamSynchronize(st));
     float ms = 0.f;
@@ -781,6 +821,7 @@ static hr_status render_impl(hr_ctx* ctx, hr_asset* a, const hr_render_desc* des
     stats->traced_samples = cnt[5];
     stats->refined_tests = cnt[6];
     stats->refined_entries = cnt[7];
+    stats->heavy_tiles = heavy;
   } else if (!dev_out) {
     HR_CUDA(ctx, cudaStreamSynchronize(st));
   }
@@ -875,8 +916,7 @@ hr_status hr_render_frame(hr_ctx* ctx, hr_asset* a, uint32_t n_clusters, float e
     if (a->C == 0) return set_error(ctx, HR_ESTATE, "HR_FLAG_KEEP_HIERARCHY: no hierarchy built");
   } else if (n_clusters > 0) {
     if (n_clusters > a->N) return set_error(ctx, HR_EINVAL, "n_clusters out of range");
-    HR_TRY(build_hierarchy(ctx, a, n_clusters, 0, rg[0], rg[1], pipe ? ctx->side : nullptr,
-                           pipe && ctx->prev_kind == kFrameCall));
+    HR_TRY(build_hierarchy(ctx, a, n_clusters, 0, rg[0], rg[1], pipe ? ctx->side : nullptr));
     fit_ran = a->E > 0;
   }
   const bool clustered = keep || n_clusters > 0;

@@ -29,6 +29,8 @@ struct Tables {
 };
 
 // One BVH over the active primitives of an asset.
+struct TileSched;
+
 struct Bvh {
   uint32_t n = 0;           // active primitives (leaves)
   uint32_t cap = 0;         // allocated leaves
@@ -96,6 +98,11 @@ struct hr_asset {
   float4* w_strand = nullptr;     // [N * (S + 1)] prism weights of the strand vertices
   float4* w_eth = nullptr;        // [E * (S + 1) * 5] of thick-hair centres and corners
   uint32_t guided_C = 0, guided_E = 0;  // shape the weights were taken for
+  // frame-kernel schedule carried between frames (TileSched) and the per-tile
+  // step counts of the last frame
+  hr::TileSched* sched = nullptr;
+  uint32_t* tile_cost = nullptr;
+  uint32_t cost_cap = 0;
 };
 
 namespace hr {
@@ -197,7 +204,7 @@ __device__ __forceinline__ float from_ordered(uint32_t u) {
 // them; null: everything on the main stream.
 hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_levels,
                           cudaEvent_t fit_begin = nullptr, cudaEvent_t fit_end = nullptr,
-                          cudaStream_t st_fit = nullptr, bool hold_fit = false);
+                          cudaStream_t st_fit = nullptr);
 // The roots' Morton codes (sorted, into codes) and the strands in (code, id)
 // order (into order), both [N] device.
 hr_status root_morton_order(hr_ctx* ctx, hr_asset* a, uint32_t* codes, uint32_t* order,
@@ -255,6 +262,38 @@ struct LaunchLights {
   float4 xyzw[HR_MAX_LIGHTS];
   float4 rgb[HR_MAX_LIGHTS];
 };
+// Warp-tile schedule carried from one frame of an asset to the next.  The
+// warp tiles whose slowest lane took the most traversal steps (node visits
+// plus primitive tests) in the previous frame are traced first, kHeavyRays
+// rays per warp: a ray that shares its warp with 31 other long rays advances
+// at a fraction of the pace it keeps with few (the slowest full-head ray:
+// ~550 us in its 32-ray tile, ~300 us alone), and these few tiles otherwise
+// set the frame's length.  Each traced lane of such a tile stores its partial
+// sums; the warp that finishes the tile's last hand-out composites its pixels
+// with the same shuffle tree as a whole-warp tile, so the image does not
+// depend on the schedule.  Measured on the full-head frame (FP32, 8 spp):
+// 16 tiles of 4-ray hand-outs took the frame from 0.58 to 0.48 ms alone;
+// 64 tiles, 1 or 2 rays per hand-out or a 60-70% threshold were no better,
+// and spent more warp time.
+constexpr uint32_t kHeavyMax = 16;         // heavy tiles per frame, at most
+constexpr uint32_t kHeavyRelPct = 50;      // steps of a heavy tile's slowest lane, at least, in
+                                           // percent of the frame's slowest tile
+constexpr uint32_t kHeavyMinSteps = 16;    // and more than this
+constexpr uint32_t kHeavyRays = 4;         // rays (lanes) of a heavy tile per hand-out
+constexpr uint32_t kHeavyItems = 32 / kHeavyRays;
+struct TileSched {
+  uint32_t n_heavy;    // heavy tiles of the frame being rendered
+  uint32_t grp;        // lanes per pixel the list was made for
+  uint32_t prev_n;     // warp tiles of the previous frame (0: no previous frame)
+  uint32_t prev_W, prev_H, prev_grp;
+  uint32_t pad[2];
+  float4 prev_rect;    // the previous frame's scene rectangle (its warp grid)
+  uint32_t heavy[kHeavyMax];            // tile origins x0 | y0 << 16, heaviest first
+  uint32_t done[kHeavyMax];             // rays finished per heavy tile
+  uint32_t ray_steps[kHeavyMax * 32];   // per ray of a heavy tile
+  float acc[kHeavyMax * 32 * 3];        // per-lane partial sums of a heavy tile
+};
+
 struct FrameArgs {
   const float4* nodes;     // BVH nodes; a leaf child is ~(global primitive id)
   const float4* prim_xf;   // [P_total * 3] world -> unit-cylinder rows, by global id
@@ -280,6 +319,9 @@ struct FrameArgs {
   hr_tile_record* tile_log;  // counting kernel only: per warp tile times and counts, or null
   uint32_t tile_cap;         // records tile_log holds
   uint32_t* tile_count;      // the frame's number of warp tiles (written when tile_log is set)
+  TileSched* sched;          // plain frame kernel: the heavy-tile schedule, or null
+  uint32_t* tile_cost;       // [cost_cap] per warp tile of the frame: its slowest lane's steps
+  uint32_t cost_cap;
 };
 
 // Tile geometry of the frame and serving kernels for a given spp: each pixel

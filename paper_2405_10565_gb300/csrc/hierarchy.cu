@@ -937,14 +937,13 @@ hr_status hierarchy_setup(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_lev
 
 // Thick-hair materials, fits and segment records of the hierarchy whose
 // order and cluster starts are set, growing the material and primitive arrays.
-constexpr size_t kFitOverlapSmem = 48 * 1024;
 
 // The fit runs on st_fit (the side stream of a pipelined frame, or the main
 // stream); the thick-hair materials and records, which the frame in flight
 // reads, on the main stream after it.
 hr_status hierarchy_finish(hr_ctx* ctx, hr_asset* a, const LevelInfo& li, uint64_t E,
                            uint64_t total, cudaEvent_t fit_begin, cudaEvent_t fit_end,
-                           cudaStream_t st_fit = nullptr, bool hold_fit = false) {
+                           cudaStream_t st_fit = nullptr) {
   cudaStream_t st = ctx_stream(ctx);
   cudaStream_t sf = st_fit ? st_fit : st;
   const uint32_t N = a->N, S = a->S;
@@ -999,18 +998,7 @@ hr_status hierarchy_finish(hr_ctx* ctx, hr_asset* a, const LevelInfo& li, uint64
   HR_TRY(scratch(ctx, 5, (size_t)E * sizeof(float), (void**)&eth_r));
   const uint64_t nx = E * (S + 1);
   if (fit_begin) HR_CUDA(ctx, cudaEventRecord(fit_begin, sf));
-  // Overlapping the previous frame (side stream, hold_fit: nothing else
-  // queued before it there), the fit is held to about 4 blocks per SM by a
-  // dynamic shared-memory reservation it does not use:
-  // its issue-bound warps would otherwise crowd the SMs that the frame's last,
-  // latency-bound warps run on.  At the full-head workload the step took
-  // 1.50 ms with the cap (the fit 0.41 ms, hidden) against 1.61 ms without
-  // (the fit 0.26 ms, the frame 0.87 instead of 0.76 ms); a cap of 3 or 2
-  // blocks made the fit too slow to hide (1.58, 1.75 ms).  After an upload on
-  // the side stream (animated frames) the fit runs unheld: the upload already
-  // fills the overlap.
-  const size_t fit_smem = sf != st && hold_fit ? kFitOverlapSmem : 0;
-  k_fit_cross_sections<<<(unsigned)((nx + 127) / 128), 128, fit_smem, sf>>>(a->verts, S, a->order,
+  k_fit_cross_sections<<<(unsigned)((nx + 127) / 128), 128, 0, sf>>>(a->verts, S, a->order,
                                                                     a->cl_first, li, (uint32_t)E,
                                                                     a->xsec);
   HR_LAUNCHED(ctx);
@@ -1034,8 +1022,7 @@ hr_status hierarchy_finish(hr_ctx* ctx, hr_asset* a, const LevelInfo& li, uint64
 }  // namespace
 
 hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_levels,
-                          cudaEvent_t fit_begin, cudaEvent_t fit_end, cudaStream_t st_fit,
-                          bool hold_fit) {
+                          cudaEvent_t fit_begin, cudaEvent_t fit_end, cudaStream_t st_fit) {
   // K1 and the fit on st_fit when the caller pipelines frames (see hierarchy_finish)
   cudaStream_t st = st_fit ? st_fit : ctx_stream(ctx);
   const uint32_t N = a->N, S = a->S;
@@ -1067,7 +1054,7 @@ hr_status build_hierarchy(hr_ctx* ctx, hr_asset* a, uint32_t C, uint32_t max_lev
   k_cluster_first<<<(C + 1 + 255) / 256, 256, 0, st>>>(N, C, a->cl_first);
   HR_LAUNCHED(ctx);
 
-  return hierarchy_finish(ctx, a, li, E, total, fit_begin, fit_end, st_fit, hold_fit);
+  return hierarchy_finish(ctx, a, li, E, total, fit_begin, fit_end, st_fit);
 }
 
 hr_status rebuild_eth_records(hr_ctx* ctx, hr_asset* a) {

@@ -361,6 +361,7 @@ __device__ __forceinline__ float kbuf_cut(const KBuf<KMAX>& kb, const uint32_t k
 
 struct Counts {
   uint32_t nodes, tests, sshade, eshade, hits, rays, precise_tests, precise_entries;
+  uint32_t steps;  // node visits plus primitive tests, counted in every kernel (tile schedule)
 };
 
 // Test primitive `id` (a leaf names its global primitive id) and keep it in
@@ -378,6 +379,7 @@ __device__ __forceinline__ void leaf_test(const FrameArgs& fa, const RayKey& rk,
                                           const float3 o, const float3 d, const float M,
                                           KBuf<KMAX>& kb, float& tcut, float& errmax, Counts& cn) {
   float th, terr;
+  ++cn.steps;
   if (COUNT) ++cn.tests;
   const int r =
       intersect32(fa.prim_xf + 3 * (size_t)id, o, d, M, tcut + errmax, th, terr);
@@ -464,6 +466,7 @@ __device__ __forceinline__ bool traverse(const FrameArgs& fa, const RayKey& rk, 
     if (node >= 0) {
       const float4* nd = fa.nodes + 4 * (size_t)node;
       const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+      ++cn.steps;
       if (COUNT) ++cn.nodes;
       const float tb = fmaf(tcut + errmax, 1.f + 2.f * kTieRel, 2.f * kTieRel * rk.s_off);
       // child 0
@@ -1009,13 +1012,14 @@ __device__ __forceinline__ void scene_rect_warp(const FrameArgs& fa, float4* rec
 }
 
 // Warp tile: the 32 / grp pixels one warp renders (wtw x wth); a pixel's
-// samples on `grp` adjacent lanes, summed with a fixed XOR-shuffle tree.
-// Called by whole warps.
+// samples on `grp` adjacent lanes.  tile_partials traces a lane's samples and
+// returns their sum in sample order, for the lanes in `lanes` (the others
+// return zeros).  tile_write sums a pixel's lanes with a fixed
+// XOR-shuffle tree and stores the mean.  Both are called by whole warps.
 template <int KMAX, int PREC, bool COUNT, bool SHADOW = false>
-__device__ __forceinline__ void render_warp_tile(const FrameArgs& fa, uint32_t x0, uint32_t y0,
-                                                 uint32_t wtw, const float4 rect,
-                                                 float* __restrict__ rgb, Counts& cn,
-                                                 bool& overflow) {
+__device__ __forceinline__ void tile_partials(const FrameArgs& fa, uint32_t x0, uint32_t y0,
+                                              uint32_t wtw, const float4 rect, uint32_t lanes,
+                                              float acc[3], Counts& cn, bool& overflow) {
   const uint32_t G = fa.grp;
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t lane_g = lane & (G - 1);
@@ -1023,9 +1027,9 @@ __device__ __forceinline__ void render_warp_tile(const FrameArgs& fa, uint32_t x
   const uint32_t x = x0 + p % wtw, y = y0 + p / wtw;
   const bool valid = x < (uint32_t)fa.cam.W && y < (uint32_t)fa.cam.H;
   const bool inside = valid && (float)x + 1.f >= rect.x && (float)x <= rect.z &&
-                      (float)y + 1.f >= rect.y && (float)y <= rect.w;
+                      (float)y + 1.f >= rect.y && (float)y <= rect.w && ((lanes >> lane) & 1u);
   const uint64_t pixel = (uint64_t)y * (uint32_t)fa.cam.W + x;
-  float acc[3] = {0.f, 0.f, 0.f};
+  acc[0] = acc[1] = acc[2] = 0.f;
   if (inside) {
     for (uint32_t s = lane_g; s < fa.spp; s += G) {
       float v[3];
@@ -1041,17 +1045,40 @@ __device__ __forceinline__ void render_warp_tile(const FrameArgs& fa, uint32_t x
       acc[2] += v[2];
     }
   }
+}
+
+__device__ __forceinline__ void tile_write(const FrameArgs& fa, uint32_t x0, uint32_t y0,
+                                           uint32_t wtw, const float4 rect, float acc[3],
+                                           float* __restrict__ rgb) {
+  const uint32_t G = fa.grp;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t p = lane / G;
+  const uint32_t x = x0 + p % wtw, y = y0 + p / wtw;
+  const bool valid = x < (uint32_t)fa.cam.W && y < (uint32_t)fa.cam.H;
+  const bool inside = valid && (float)x + 1.f >= rect.x && (float)x <= rect.z &&
+                      (float)y + 1.f >= rect.y && (float)y <= rect.w;
+  const uint64_t pixel = (uint64_t)y * (uint32_t)fa.cam.W + x;
   for (uint32_t o = 1; o < G; o <<= 1) {
     acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
     acc[1] += __shfl_xor_sync(0xffffffffu, acc[1], o);
     acc[2] += __shfl_xor_sync(0xffffffffu, acc[2], o);
   }
-  if (inside && lane_g == 0) {
+  if (inside && (lane & (G - 1)) == 0) {
     const float inv = 1.0f / (float)fa.spp;
     rgb[3 * pixel] = acc[0] * inv;
     rgb[3 * pixel + 1] = acc[1] * inv;
     rgb[3 * pixel + 2] = acc[2] * inv;
   }
+}
+
+template <int KMAX, int PREC, bool COUNT, bool SHADOW = false>
+__device__ __forceinline__ void render_warp_tile(const FrameArgs& fa, uint32_t x0, uint32_t y0,
+                                                 uint32_t wtw, const float4 rect,
+                                                 float* __restrict__ rgb, Counts& cn,
+                                                 bool& overflow) {
+  float acc[3];
+  tile_partials<KMAX, PREC, COUNT, SHADOW>(fa, x0, y0, wtw, rect, 0xffffffffu, acc, cn, overflow);
+  tile_write(fa, x0, y0, wtw, rect, acc, rgb);
 }
 
 }  // namespace tr

@@ -11,10 +11,94 @@ namespace hr {
 namespace {
 
 // Projected scene rectangle of the frame and a cleared work counter, once per
-// launch (one warp).
-__global__ void k_scene_rect(const FrameArgs fa, float4* rect, uint32_t* work) {
-  tr::scene_rect_warp(fa, rect);
+// launch (warp 0).  With a tile schedule (fa.sched), the block also picks
+// this frame's heavy tiles from the previous frame's per-tile steps: the
+// tiles whose slowest lane took at least kHeavyRelPct percent of the steps of
+// the frame's slowest and more than kHeavyMinSteps, at most kHeavyMax of them
+// (the heaviest), stored by their pixel origin heaviest first.  The previous
+// frame's warp grid is rebuilt from its scene rectangle, which the block then
+// replaces with this frame's.  A previous frame of another size or spp gives
+// no heavy tiles.
+constexpr int kRectThreads = 256;
+__global__ void __launch_bounds__(kRectThreads) k_scene_rect(const FrameArgs fa, float4* rect,
+                                                             uint32_t* work) {
+  if (threadIdx.x < 32) tr::scene_rect_warp(fa, rect);
   if (threadIdx.x == 0) *work = 0u;
+  TileSched* sc = fa.sched;
+  if (!sc) return;
+  __shared__ uint32_t s_max, s_hist[256], s_cut, s_n;
+  __shared__ uint32_t s_tile[kHeavyMax], s_steps[kHeavyMax];
+  const uint32_t tid = threadIdx.x;
+  const bool have = sc->prev_n > 0 && sc->prev_W == (uint32_t)fa.cam.W &&
+                    sc->prev_H == (uint32_t)fa.cam.H && sc->prev_grp == fa.grp &&
+                    sc->prev_n <= fa.cost_cap;
+  const uint32_t n = have ? sc->prev_n : 0u;
+  if (tid == 0) s_max = 0u;
+  for (uint32_t i = tid; i < 256; i += blockDim.x) s_hist[i] = 0u;
+  __syncthreads();
+  uint32_t m = 0;
+  for (uint32_t i = tid; i < n; i += blockDim.x) m = max(m, fa.tile_cost[i]);
+  atomicMax(&s_max, m);
+  __syncthreads();
+  const uint32_t M = s_max;
+  // steps in [lo, M] binned into 256 bins; the cut is the highest bin edge
+  // with at least kHeavyMax tiles at or above it (or the lowest bin), and
+  // the tiles past kHeavyMax in the cut's bin are left out
+  const uint32_t lo = max((uint32_t)((uint64_t)M * kHeavyRelPct / 100u), kHeavyMinSteps + 1);
+  const uint32_t span = M >= lo ? M - lo + 1 : 1u;
+  for (uint32_t i = tid; i < n; i += blockDim.x) {
+    const uint32_t c = fa.tile_cost[i];
+    if (c >= lo) atomicAdd(&s_hist[(uint32_t)((uint64_t)(c - lo) * 256u / span)], 1u);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t cum = 0, cut = 256;
+    for (int b = 255; b >= 0 && cum < kHeavyMax; --b) {
+      cum += s_hist[b];
+      cut = (uint32_t)b;
+    }
+    s_cut = cut;
+    s_n = 0;
+  }
+  __syncthreads();
+  const uint32_t cut = s_cut;
+  // the bins above the cut first (fewer than kHeavyMax tiles), then the cut's
+  for (int pass = 0; pass < 2; ++pass) {
+    for (uint32_t i = tid; i < n && M >= lo; i += blockDim.x) {
+      const uint32_t c = fa.tile_cost[i];
+      const uint32_t b = c >= lo ? (uint32_t)((uint64_t)(c - lo) * 256u / span) : 0u;
+      if (c >= lo && (pass == 0 ? b > cut : b == cut)) {
+        const uint32_t k = atomicAdd(&s_n, 1u);
+        if (k < kHeavyMax) {
+          s_tile[k] = i;
+          s_steps[k] = c;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const uint32_t nh = min(s_n, kHeavyMax);
+  if (tid < nh) {  // heaviest first (ties by tile index): rank by counting
+    uint32_t r = 0;
+    for (uint32_t k = 0; k < nh; ++k)
+      r += s_steps[k] > s_steps[tid] || (s_steps[k] == s_steps[tid] && s_tile[k] < s_tile[tid]);
+    const WarpGrid pg = warp_grid(sc->prev_rect, (uint32_t)fa.cam.W, (uint32_t)fa.cam.H, fa.grp);
+    const uint32_t t = s_tile[tid];
+    sc->heavy[r] = (pg.x0 + (t % pg.nx) * pg.wtw) | ((pg.y0 + (t / pg.nx) * pg.wth) << 16);
+  }
+  if (tid < kHeavyMax) sc->done[tid] = 0u;
+  __syncthreads();  // the previous grid is no longer read
+  if (tid == 0) {
+    sc->n_heavy = nh;
+    sc->grp = fa.grp;
+    const float4 r = *rect;  // written by warp 0 before the block's barriers
+    const WarpGrid g = warp_grid(r, (uint32_t)fa.cam.W, (uint32_t)fa.cam.H, fa.grp);
+    sc->prev_rect = r;
+    sc->prev_n = g.n <= fa.cost_cap ? g.n : 0u;
+    sc->prev_W = (uint32_t)fa.cam.W;
+    sc->prev_H = (uint32_t)fa.cam.H;
+    sc->prev_grp = fa.grp;
+  }
 }
 
 // Persistent frame kernel.  The image has been cleared to background; the
@@ -36,11 +120,67 @@ __global__ void __launch_bounds__(kBlock, SHADOW ? 1 : 4)
   bool overflow = false;
   const uint32_t lane = threadIdx.x & 31;
   if (COUNT && fa.tile_log && blockIdx.x == 0 && threadIdx.x == 0) *fa.tile_count = g.n;
+  // heavy tiles first, kHeavyRays rays per hand-out (kernels without a
+  // schedule: none)
+  TileSched* sc = fa.sched;
+  const uint32_t nh = sc && sc->grp == fa.grp ? min(sc->n_heavy, kHeavyMax) : 0u;
   for (;;) {
     uint32_t t = 0;
     if (lane == 0) t = atomicAdd(work, 1u);
     t = __shfl_sync(0xffffffffu, t, 0);
+    if (t < nh * kHeavyItems) {
+      const uint32_t ht = t / kHeavyItems, j0 = (t % kHeavyItems) * kHeavyRays;
+      const uint32_t mask = (0xffffffffu >> (32u - kHeavyRays)) << j0;
+      const uint32_t xy = sc->heavy[ht];
+      const uint32_t x0 = xy & 0xffffu, y0 = xy >> 16;
+      // a tile of the previous frame's grid that is not one of this grid's: skipped
+      const uint32_t gx = (x0 - g.x0) / g.wtw, gy = (y0 - g.y0) / g.wth;
+      if (x0 < g.x0 || y0 < g.y0 || (x0 - g.x0) % g.wtw || (y0 - g.y0) % g.wth || gx >= g.nx ||
+          gy * g.nx + gx >= g.n)
+        continue;
+      const uint32_t steps0 = cn.steps;
+      float acc[3];
+      tr::tile_partials<KMAX, PREC, COUNT, SHADOW>(fa, x0, y0, g.wtw, rect, mask, acc, cn,
+                                                   overflow);
+      if ((mask >> lane) & 1u) {
+        float* a = sc->acc + (size_t)(ht * 32u + lane) * 3;
+        a[0] = acc[0];
+        a[1] = acc[1];
+        a[2] = acc[2];
+        sc->ray_steps[ht * 32u + lane] = cn.steps - steps0;
+      }
+      __syncwarp();
+      uint32_t last = 0;
+      if (lane == j0) {
+        __threadfence();
+        last = atomicAdd(&sc->done[ht], 1u) == kHeavyItems - 1u;
+      }
+      last = __shfl_sync(0xffffffffu, last, j0);
+      if (last) {  // every ray of the tile is done: composite its pixels
+        __threadfence();
+        const float* a = sc->acc + (size_t)(ht * 32u + lane) * 3;
+        acc[0] = __ldcg(a);
+        acc[1] = __ldcg(a + 1);
+        acc[2] = __ldcg(a + 2);
+        uint32_t st = __ldcg(sc->ray_steps + ht * 32u + lane);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) st = max(st, __shfl_xor_sync(0xffffffffu, st, o));
+        tr::tile_write(fa, x0, y0, g.wtw, rect, acc, rgb);
+        const uint32_t tt = gy * g.nx + gx;
+        if (lane == 0 && fa.tile_cost && tt < fa.cost_cap) fa.tile_cost[tt] = st;
+      }
+      continue;
+    }
+    t -= nh * kHeavyItems;
     if (t >= g.n) break;
+    const uint32_t x0 = g.x0 + (t % g.nx) * g.wtw, y0 = g.y0 + (t / g.nx) * g.wth;
+    if (nh) {  // traced ray by ray above
+      const uint32_t xy = x0 | (y0 << 16);
+      const bool mine = (lane < nh && sc->heavy[lane] == xy) ||
+                        (lane + 32u < nh && sc->heavy[lane + 32u] == xy);
+      if (__any_sync(0xffffffffu, mine)) continue;
+    }
+    const uint32_t steps0 = cn.steps;
     uint64_t t0 = 0;
     uint32_t nodes0 = 0, tests0 = 0;
     if (COUNT && fa.tile_log) {
@@ -48,9 +188,13 @@ __global__ void __launch_bounds__(kBlock, SHADOW ? 1 : 4)
       nodes0 = cn.nodes;
       tests0 = cn.tests;
     }
-    tr::render_warp_tile<KMAX, PREC, COUNT, SHADOW>(fa, g.x0 + (t % g.nx) * g.wtw,
-                                                    g.y0 + (t / g.nx) * g.wth, g.wtw, rect, rgb,
-                                                    cn, overflow);
+    tr::render_warp_tile<KMAX, PREC, COUNT, SHADOW>(fa, x0, y0, g.wtw, rect, rgb, cn, overflow);
+    if (fa.tile_cost) {
+      uint32_t st = cn.steps - steps0;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) st = max(st, __shfl_xor_sync(0xffffffffu, st, o));
+      if (lane == 0 && t < fa.cost_cap) fa.tile_cost[t] = st;
+    }
     if (COUNT && fa.tile_log) {
       uint32_t dn = cn.nodes - nodes0, dt = cn.tests - tests0;
 #pragma unroll
@@ -95,11 +239,17 @@ hr_status launch_k(hr_ctx* ctx, const FrameArgs& fa, bool count, float* rgb, cud
   HR_TRY(scratch(ctx, 47, 2 * sizeof(float4), (void**)&rect));
   uint32_t* work = reinterpret_cast<uint32_t*>(rect + 1);
   HR_CUDA(ctx, cudaMemsetAsync(rgb, 0, (size_t)fa.cam.W * fa.cam.H * 3 * sizeof(float), st));
-  k_scene_rect<<<1, 32, 0, st>>>(fa, rect, work);
+  // the counting kernel keeps the plain hand-out order (its tile log is indexed by it)
+  FrameArgs f = fa;
+  if (count) {
+    f.sched = nullptr;
+    f.tile_cost = nullptr;
+  }
+  k_scene_rect<<<1, kRectThreads, 0, st>>>(f, rect, work);
   HR_LAUNCHED(ctx);
   if (count) {
     const int g = (int)std::min<uint32_t>(tiles, frame_grid<KMAX, PREC, true, SHADOW>());
-    k_frame<KMAX, PREC, true, SHADOW><<<g, kBlock, 0, st>>>(fa, rect, work, rgb);
+    k_frame<KMAX, PREC, true, SHADOW><<<g, kBlock, 0, st>>>(f, rect, work, rgb);
   } else {
     const int g = (int)std::min<uint32_t>(tiles, frame_grid<KMAX, PREC, false, SHADOW>());
     k_frame<KMAX, PREC, false, SHADOW><<<g, kBlock, 0, st>>>(fa, rect, work, rgb);

@@ -33,12 +33,12 @@ def test_struct_layout_matches_c(tmp_path, lib):
     src = tmp_path / "sz.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "hairrt.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
         "sizeof(hr_camera), sizeof(hr_light), sizeof(hr_render_desc), sizeof(hr_stats),"
         "sizeof(hr_hair_desc), sizeof(hr_request), sizeof(hr_result),"
         "offsetof(hr_render_desc, seed), offsetof(hr_render_desc, precision),"
         "offsetof(hr_request, rgb_out), sizeof(hr_tile_record),"
-        "offsetof(hr_stats, refined_entries));return 0;}\n")
+        "offsetof(hr_stats, refined_entries), offsetof(hr_stats, heavy_tiles));return 0;}\n")
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
@@ -47,7 +47,8 @@ def test_struct_layout_matches_c(tmp_path, lib):
             ctypes.sizeof(_lib.hr_hair_desc), ctypes.sizeof(_lib.hr_request),
             ctypes.sizeof(_lib.hr_result), _lib.hr_render_desc.seed.offset,
             _lib.hr_render_desc.precision.offset, _lib.hr_request.rgb_out.offset,
-            ctypes.sizeof(_lib.hr_tile_record), _lib.hr_stats.refined_entries.offset]
+            ctypes.sizeof(_lib.hr_tile_record), _lib.hr_stats.refined_entries.offset,
+            _lib.hr_stats.heavy_tiles.offset]
     assert got == want
 
 

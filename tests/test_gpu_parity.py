@@ -939,3 +939,52 @@ def test_refit_engages_under_small_motion_with_hysteresis(ctx):
         assert np.allclose(dimg.cpu().numpy(), ref, rtol=1e-6, atol=1e-7)
     finally:
         hr.hr_asset_destroy(ctx, a)
+
+
+def test_tile_schedule_keeps_the_image(ctx):
+    """The frame kernel traces the previous frame's heaviest warp tiles first,
+    a few rays per warp, and composites them from stored lane sums in the
+    fixed shuffle order: every frame equals the same frame rendered in the fixed
+    tile order (HR_FLAG_FIXED_TILE_ORDER), bit for bit, through a repeated
+    view (heavy tiles used), a change of view (tiles of the old grid), a
+    change of spp (another tile shape: schedule dropped) and of image size."""
+    w = scenegen.full_head(n=6000, S=16, width=128, height=96, spp=8, n_lights=2, n_clusters=256)
+    box = w.scene.aabb()
+    views = {"near": scenegen.frame_camera(*box, 128, 96, perspective=True, fill=0.6),
+             "far": scenegen.frame_camera(*box, 128, 96, perspective=True, fill=0.35),
+             "big": scenegen.frame_camera(*box, 160, 120, perspective=True, fill=0.6)}
+
+    def desc(view, spp, flags=0):
+        return hr.render_desc(views[view].pack(), w.lights, spp, w.k_depth, w.sample_seed, 0, flags)
+
+    def size(view):
+        return (views[view].height, views[view].width, 3)
+
+    seq = [("near", 8), ("near", 8), ("near", 8), ("far", 8), ("near", 8), ("near", 4),
+           ("near", 8), ("big", 8), ("big", 8)]
+    ref = {}
+    a = upload(ctx, w.scene)
+    try:
+        for view, spp in set(seq):
+            img = np.zeros(size(view), np.float32)
+            st = hr.hr_render_frame(ctx, a, w.n_clusters, w.eps_w, 0,
+                                    desc(view, spp, hr.HR_FLAG_FIXED_TILE_ORDER), img, stats=True)
+            assert st.heavy_tiles == 0
+            ref[(view, spp)] = img
+    finally:
+        hr.hr_asset_destroy(ctx, a)
+    a = upload(ctx, w.scene)
+    try:
+        heavy = []
+        for view, spp in seq:
+            img = np.zeros(size(view), np.float32)
+            st = hr.hr_render_frame(ctx, a, w.n_clusters, w.eps_w, 0, desc(view, spp), img,
+                                    stats=True)
+            heavy.append(st.heavy_tiles)
+            assert np.array_equal(img, ref[(view, spp)]), (view, spp, st.heavy_tiles)
+        # the first frame has no previous one; a repeated view has heavy tiles;
+        # a frame after an spp change or a resize has none
+        assert heavy[0] == 0 and heavy[1] > 0 and heavy[2] > 0, heavy
+        assert heavy[5] == 0 and heavy[6] == 0 and heavy[7] == 0 and heavy[8] > 0, heavy
+    finally:
+        hr.hr_asset_destroy(ctx, a)
