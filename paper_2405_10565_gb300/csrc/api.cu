@@ -437,7 +437,6 @@ hr_status hr_asset_destroy(hr_ctx* ctx, hr_asset* a) {
   if (a->aux_other) dfree(ctx, a->aux_other, (size_t)a->other_total * sizeof(float4));
   if (a->lod) dfree(ctx, a->lod, a->C);
   if (a->sched) dfree(ctx, a->sched, sizeof(TileSched));
-  if (a->tile_cost) dfree(ctx, a->tile_cost, (size_t)a->cost_cap * 4);
   drop_guides(ctx, a);
   const uint64_t P = a->n_prims_total;
   if (a->prim_xf) dfree(ctx, a->prim_xf, P * 3 * sizeof(float4));
@@ -714,33 +713,13 @@ hr_status hr_im_lookup(hr_ctx* ctx, const float* theta, const float* beta, uint3
   return HR_OK;
 }
 
-// The asset's warp-tile schedule (TileSched) and per-tile step counts, grown
-// to the warp tiles an image of this size can have; a grown step array holds
-// no previous frame.
+// The asset's warp-tile schedule (TileSched), allocated (cleared) on first use.
 static hr_status tile_schedule(hr_ctx* ctx, hr_asset* a, FrameArgs& fa, cudaStream_t st) {
-  const uint32_t P = 32u / fa.grp;  // pixels per warp tile, as in warp_grid
-  uint32_t wtw = 1;
-  while (wtw * wtw < P) wtw <<= 1;
-  const uint32_t wth = P / wtw;
-  const size_t need = ((size_t)(fa.cam.W + wtw - 1) / wtw + 1) * ((size_t)(fa.cam.H + wth - 1) / wth + 1);
   if (!a->sched) {
     HR_TRY(dalloc(ctx, (void**)&a->sched, sizeof(TileSched), "tile schedule"));
     HR_CUDA(ctx, cudaMemsetAsync(a->sched, 0, sizeof(TileSched), st));
   }
-  if (need > a->cost_cap) {
-    if (a->tile_cost) {
-      HR_CUDA(ctx, cudaStreamSynchronize(st));
-      dfree(ctx, a->tile_cost, (size_t)a->cost_cap * 4);
-      a->tile_cost = nullptr;
-      a->cost_cap = 0;
-    }
-    HR_TRY(dalloc(ctx, (void**)&a->tile_cost, need * 4, "tile steps"));
-    a->cost_cap = (uint32_t)need;
-    HR_CUDA(ctx, cudaMemsetAsync(a->sched, 0, sizeof(TileSched), st));
-  }
   fa.sched = a->sched;
-  fa.tile_cost = a->tile_cost;
-  fa.cost_cap = a->cost_cap;
   return HR_OK;
 }
 

@@ -98,11 +98,8 @@ struct hr_asset {
   float4* w_strand = nullptr;     // [N * (S + 1)] prism weights of the strand vertices
   float4* w_eth = nullptr;        // [E * (S + 1) * 5] of thick-hair centres and corners
   uint32_t guided_C = 0, guided_E = 0;  // shape the weights were taken for
-  // frame-kernel schedule carried between frames (TileSched) and the per-tile
-  // step counts of the last frame
+  // frame-kernel schedule carried between frames (TileSched)
   hr::TileSched* sched = nullptr;
-  uint32_t* tile_cost = nullptr;
-  uint32_t cost_cap = 0;
 };
 
 namespace hr {
@@ -281,13 +278,27 @@ constexpr uint32_t kHeavyRelPct = 50;      // steps of a heavy tile's slowest la
 constexpr uint32_t kHeavyMinSteps = 16;    // and more than this
 constexpr uint32_t kHeavyRays = 4;         // rays (lanes) of a heavy tile per hand-out
 constexpr uint32_t kHeavyItems = 32 / kHeavyRays;
+// Only frames of at most this many warp tiles per resident warp trace heavy
+// tiles: with many tiles per warp the hand-out balances the work by itself
+// (the close full-head view, ~160 tiles per warp, was 1.3% slower with them,
+// the middle one, ~24, 1.3% faster, the far one, ~2.4, 19% faster).
+constexpr uint32_t kHeavyTilesPerWarp = 64;
+// The frame kernel lists the tiles whose step count reaches a threshold (half
+// the previous frame's largest) as candidates, kCandMax at most, and keeps
+// the frame's largest; the next frame picks its heavy tiles among them.
+constexpr uint32_t kCandMax = 1024;
 struct TileSched {
   uint32_t n_heavy;    // heavy tiles of the frame being rendered
   uint32_t grp;        // lanes per pixel the list was made for
   uint32_t prev_n;     // warp tiles of the previous frame (0: no previous frame)
   uint32_t prev_W, prev_H, prev_grp;
-  uint32_t pad[2];
+  uint32_t thresh;     // steps that make a tile of this frame a candidate
+  uint32_t max_steps;  // this frame's largest tile step count (atomic max)
   float4 prev_rect;    // the previous frame's scene rectangle (its warp grid)
+  uint32_t cand_n;     // candidates listed by this frame (atomic; may exceed kCandMax)
+  uint32_t pad[3];
+  uint32_t cand_tile[kCandMax];   // grid index of each candidate tile
+  uint32_t cand_steps[kCandMax];  // and its slowest lane's steps
   uint32_t heavy[kHeavyMax];            // tile origins x0 | y0 << 16, heaviest first
   uint32_t done[kHeavyMax];             // rays finished per heavy tile
   uint32_t ray_steps[kHeavyMax * 32];   // per ray of a heavy tile
@@ -320,8 +331,7 @@ struct FrameArgs {
   uint32_t tile_cap;         // records tile_log holds
   uint32_t* tile_count;      // the frame's number of warp tiles (written when tile_log is set)
   TileSched* sched;          // plain frame kernel: the heavy-tile schedule, or null
-  uint32_t* tile_cost;       // [cost_cap] per warp tile of the frame: its slowest lane's steps
-  uint32_t cost_cap;
+  uint32_t frame_warps;      // with sched: resident warps of the frame kernel
 };
 
 // Tile geometry of the frame and serving kernels for a given spp: each pixel

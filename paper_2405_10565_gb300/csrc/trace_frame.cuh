@@ -12,67 +12,68 @@ namespace {
 
 // Projected scene rectangle of the frame and a cleared work counter, once per
 // launch (warp 0).  With a tile schedule (fa.sched), the block also picks
-// this frame's heavy tiles from the previous frame's per-tile steps: the
-// tiles whose slowest lane took at least kHeavyRelPct percent of the steps of
-// the frame's slowest and more than kHeavyMinSteps, at most kHeavyMax of them
-// (the heaviest), stored by their pixel origin heaviest first.  The previous
-// frame's warp grid is rebuilt from its scene rectangle, which the block then
-// replaces with this frame's.  A previous frame of another size or spp gives
-// no heavy tiles.
-constexpr int kRectThreads = 256;
+// this frame's heavy tiles among the previous frame's candidates (TileSched):
+// those whose slowest lane took at least kHeavyRelPct percent of the steps of
+// that frame's slowest tile and more than kHeavyMinSteps, at most kHeavyMax
+// of them (the heaviest), stored by their pixel origin heaviest first.  The
+// previous frame's warp grid is rebuilt from its scene rectangle, which the
+// block then replaces with this frame's, and the candidate threshold of this
+// frame is set from the previous frame's largest count.  A previous frame of
+// another size or spp, or a frame of more than kHeavyTilesPerWarp tiles per
+// resident warp, gives no heavy tiles.  One thread per candidate.
+constexpr int kRectThreads = (int)kCandMax;
 __global__ void __launch_bounds__(kRectThreads) k_scene_rect(const FrameArgs fa, float4* rect,
                                                              uint32_t* work) {
   if (threadIdx.x < 32) tr::scene_rect_warp(fa, rect);
   if (threadIdx.x == 0) *work = 0u;
   TileSched* sc = fa.sched;
   if (!sc) return;
-  __shared__ uint32_t s_max, s_hist[256], s_cut, s_n;
+  __shared__ uint32_t s_hist[256], s_cut, s_n;
   __shared__ uint32_t s_tile[kHeavyMax], s_steps[kHeavyMax];
   const uint32_t tid = threadIdx.x;
   const bool have = sc->prev_n > 0 && sc->prev_W == (uint32_t)fa.cam.W &&
-                    sc->prev_H == (uint32_t)fa.cam.H && sc->prev_grp == fa.grp &&
-                    sc->prev_n <= fa.cost_cap;
-  const uint32_t n = have ? sc->prev_n : 0u;
-  if (tid == 0) s_max = 0u;
-  for (uint32_t i = tid; i < 256; i += blockDim.x) s_hist[i] = 0u;
+                    sc->prev_H == (uint32_t)fa.cam.H && sc->prev_grp == fa.grp;
+  const uint32_t M = have ? sc->max_steps : 0u;
+  if (tid == 0) {
+    s_cut = 0u;
+    s_n = 0u;
+  }
+  if (tid < 256) s_hist[tid] = 0u;
   __syncthreads();
-  uint32_t m = 0;
-  for (uint32_t i = tid; i < n; i += blockDim.x) m = max(m, fa.tile_cost[i]);
-  atomicMax(&s_max, m);
-  __syncthreads();
-  const uint32_t M = s_max;
-  // steps in [lo, M] binned into 256 bins; the cut is the highest bin edge
-  // with at least kHeavyMax tiles at or above it (or the lowest bin), and
-  // the tiles past kHeavyMax in the cut's bin are left out
+  const float4 rc = *rect;  // written by warp 0 before the barrier
+  const WarpGrid g = warp_grid(rc, (uint32_t)fa.cam.W, (uint32_t)fa.cam.H, fa.grp);
+  const bool allow = (uint64_t)g.n <= (uint64_t)kHeavyTilesPerWarp * fa.frame_warps;
+  const uint32_t nc = have && allow ? min(sc->cand_n, kCandMax) : 0u;
+  const bool mine = tid < nc;
+  const uint32_t c = mine ? sc->cand_steps[tid] : 0u;
+  const uint32_t ct = mine ? sc->cand_tile[tid] : 0u;
+  // steps in [lo, M] binned into 256 bins; the cut is the highest bin with
+  // at least kHeavyMax candidates at or above it (else bin 0), and those
+  // past kHeavyMax in the cut's bin are left out
   const uint32_t lo = max((uint32_t)((uint64_t)M * kHeavyRelPct / 100u), kHeavyMinSteps + 1);
   const uint32_t span = M >= lo ? M - lo + 1 : 1u;
-  for (uint32_t i = tid; i < n; i += blockDim.x) {
-    const uint32_t c = fa.tile_cost[i];
-    if (c >= lo) atomicAdd(&s_hist[(uint32_t)((uint64_t)(c - lo) * 256u / span)], 1u);
-  }
+  const bool cand = mine && c >= lo && ct < sc->prev_n;
+  const uint32_t b = cand ? (uint32_t)((uint64_t)(min(c, M) - lo) * 256u / span) : 0u;
+  if (cand) atomicAdd(&s_hist[b], 1u);
   __syncthreads();
-  if (tid == 0) {
-    uint32_t cum = 0, cut = 256;
-    for (int b = 255; b >= 0 && cum < kHeavyMax; --b) {
-      cum += s_hist[b];
-      cut = (uint32_t)b;
-    }
-    s_cut = cut;
-    s_n = 0;
+  // suffix sums of the histogram (Hillis-Steele over 256 bins)
+  for (uint32_t o = 1; o < 256; o <<= 1) {
+    uint32_t v = 0;
+    if (tid < 256) v = s_hist[tid] + (tid + o < 256 ? s_hist[tid + o] : 0u);
+    __syncthreads();
+    if (tid < 256) s_hist[tid] = v;
+    __syncthreads();
   }
+  if (tid < 256 && s_hist[tid] >= kHeavyMax) atomicMax(&s_cut, tid);
   __syncthreads();
   const uint32_t cut = s_cut;
-  // the bins above the cut first (fewer than kHeavyMax tiles), then the cut's
+  // the bins above the cut first (fewer than kHeavyMax candidates), then the cut's
   for (int pass = 0; pass < 2; ++pass) {
-    for (uint32_t i = tid; i < n && M >= lo; i += blockDim.x) {
-      const uint32_t c = fa.tile_cost[i];
-      const uint32_t b = c >= lo ? (uint32_t)((uint64_t)(c - lo) * 256u / span) : 0u;
-      if (c >= lo && (pass == 0 ? b > cut : b == cut)) {
-        const uint32_t k = atomicAdd(&s_n, 1u);
-        if (k < kHeavyMax) {
-          s_tile[k] = i;
-          s_steps[k] = c;
-        }
+    if (cand && (pass == 0 ? b > cut : b == cut)) {
+      const uint32_t k = atomicAdd(&s_n, 1u);
+      if (k < kHeavyMax) {
+        s_tile[k] = ct;
+        s_steps[k] = c;
       }
     }
     __syncthreads();
@@ -87,14 +88,15 @@ __global__ void __launch_bounds__(kRectThreads) k_scene_rect(const FrameArgs fa,
     sc->heavy[r] = (pg.x0 + (t % pg.nx) * pg.wtw) | ((pg.y0 + (t / pg.nx) * pg.wth) << 16);
   }
   if (tid < kHeavyMax) sc->done[tid] = 0u;
-  __syncthreads();  // the previous grid is no longer read
+  __syncthreads();  // the previous frame's candidates and grid are no longer read
   if (tid == 0) {
     sc->n_heavy = nh;
     sc->grp = fa.grp;
-    const float4 r = *rect;  // written by warp 0 before the block's barriers
-    const WarpGrid g = warp_grid(r, (uint32_t)fa.cam.W, (uint32_t)fa.cam.H, fa.grp);
-    sc->prev_rect = r;
-    sc->prev_n = g.n <= fa.cost_cap ? g.n : 0u;
+    sc->thresh = lo;
+    sc->max_steps = 0u;
+    sc->cand_n = 0u;
+    sc->prev_rect = rc;
+    sc->prev_n = g.n;
     sc->prev_W = (uint32_t)fa.cam.W;
     sc->prev_H = (uint32_t)fa.cam.H;
     sc->prev_grp = fa.grp;
@@ -124,6 +126,20 @@ __global__ void __launch_bounds__(kBlock, SHADOW ? 1 : 4)
   // schedule: none)
   TileSched* sc = fa.sched;
   const uint32_t nh = sc && sc->grp == fa.grp ? min(sc->n_heavy, kHeavyMax) : 0u;
+  const uint32_t thresh = sc ? sc->thresh : 0u;
+  uint32_t wmax = 0;  // the warp's largest tile step count
+  // a tile's slowest-lane steps: the warp's maximum, and a candidate for the
+  // next frame's heavy tiles at or above the threshold (lane 0)
+  auto note = [&](uint32_t tile, uint32_t st) {
+    wmax = max(wmax, st);
+    if (lane == 0 && st >= thresh && __ldcg(&sc->cand_n) < kCandMax) {  // no atomics once full
+      const uint32_t k = atomicAdd(&sc->cand_n, 1u);
+      if (k < kCandMax) {
+        sc->cand_tile[k] = tile;
+        sc->cand_steps[k] = st;
+      }
+    }
+  };
   for (;;) {
     uint32_t t = 0;
     if (lane == 0) t = atomicAdd(work, 1u);
@@ -166,8 +182,7 @@ __global__ void __launch_bounds__(kBlock, SHADOW ? 1 : 4)
 #pragma unroll
         for (int o = 16; o; o >>= 1) st = max(st, __shfl_xor_sync(0xffffffffu, st, o));
         tr::tile_write(fa, x0, y0, g.wtw, rect, acc, rgb);
-        const uint32_t tt = gy * g.nx + gx;
-        if (lane == 0 && fa.tile_cost && tt < fa.cost_cap) fa.tile_cost[tt] = st;
+        note(gy * g.nx + gx, st);
       }
       continue;
     }
@@ -189,11 +204,11 @@ __global__ void __launch_bounds__(kBlock, SHADOW ? 1 : 4)
       tests0 = cn.tests;
     }
     tr::render_warp_tile<KMAX, PREC, COUNT, SHADOW>(fa, x0, y0, g.wtw, rect, rgb, cn, overflow);
-    if (fa.tile_cost) {
+    if (sc) {
       uint32_t st = cn.steps - steps0;
 #pragma unroll
       for (int o = 16; o; o >>= 1) st = max(st, __shfl_xor_sync(0xffffffffu, st, o));
-      if (lane == 0 && t < fa.cost_cap) fa.tile_cost[t] = st;
+      note(t, st);
     }
     if (COUNT && fa.tile_log) {
       uint32_t dn = cn.nodes - nodes0, dt = cn.tests - tests0;
@@ -211,6 +226,7 @@ __global__ void __launch_bounds__(kBlock, SHADOW ? 1 : 4)
       }
     }
   }
+  if (sc && lane == 0 && wmax) atomicMax(&sc->max_steps, wmax);
   if (COUNT) tr::flush_counts(fa, cn);
   if (overflow) atomicAdd(fa.overflow, 1u);
 }
@@ -241,10 +257,8 @@ hr_status launch_k(hr_ctx* ctx, const FrameArgs& fa, bool count, float* rgb, cud
   HR_CUDA(ctx, cudaMemsetAsync(rgb, 0, (size_t)fa.cam.W * fa.cam.H * 3 * sizeof(float), st));
   // the counting kernel keeps the plain hand-out order (its tile log is indexed by it)
   FrameArgs f = fa;
-  if (count) {
-    f.sched = nullptr;
-    f.tile_cost = nullptr;
-  }
+  if (count) f.sched = nullptr;
+  f.frame_warps = (uint32_t)frame_grid<KMAX, PREC, false, SHADOW>() * (kBlock / 32);
   k_scene_rect<<<1, kRectThreads, 0, st>>>(f, rect, work);
   HR_LAUNCHED(ctx);
   if (count) {
