@@ -107,7 +107,9 @@ __global__ void __launch_bounds__(kRectThreads) k_scene_rect(const FrameArgs fa,
 // warp tiles (32 / grp pixels each) that overlap the projected scene rectangle
 // are handed out one at a time through an atomic counter, so the few tiles
 // that see hair spread over every warp of the GPU and a warp that drew cheap
-// tiles takes more.  No warp ever waits for another.
+// tiles takes more.  With a schedule, the hand-outs start with the heavy
+// tiles (TileSched), kHeavyRays lanes each; the warp that finishes a heavy
+// tile's last hand-out composites it.  No warp ever waits for another.
 // The plain instantiations are held to 4 blocks per SM (128 registers, no
 // spills in the traversal): at 5 blocks (96 registers) the k-buffer's depth
 // pairs and the precise-decision state spill, and the full-head frame took
