@@ -69,3 +69,20 @@ def test_missing_library_fails_loudly(tmp_path):
             _lib.load(str(tmp_path / "nope.so"))
         finally:
             _lib._lib = None
+
+
+def test_header_constants_match_the_binding():
+    """Every #define HR_* value and hr_status code of hairrt.h equals the
+    binding's constant of the same name (a flag added on one side only would
+    otherwise pass unseen)."""
+    import re
+    text = open(os.path.join(ROOT, "include", "hairrt.h")).read()
+    defines = dict(re.findall(r"^#define (HR_[A-Z0-9_]+) (\d+)u?\b", text, re.M))
+    assert len(defines) >= 15
+    for name, value in defines.items():
+        assert hasattr(_lib, name), name
+        assert getattr(_lib, name) == int(value), name
+    codes = dict(re.findall(r"^\s+(HR_E?[A-Z]+) = (\d+),?", text, re.M))
+    assert codes.get("HR_OK") == "0" and len(codes) >= 8, codes
+    for name, value in codes.items():
+        assert getattr(_lib, name) == int(value), name
