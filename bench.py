@@ -570,8 +570,19 @@ def main():
     d16 = hr.render_desc(w.camera.pack(), w.lights, spp, w.k_depth, w.sample_seed, 1)
     fp16_ms = statistics.median(hr.hr_render(ctx, asset, d16, img, stats=True).render_ms
                                 for _ in range(10))
-    fp32_ms = statistics.median(hr.hr_render(ctx, asset, desc, img, stats=True).render_ms
-                                for _ in range(10))
+    fp32_st = [hr.hr_render(ctx, asset, desc, img, stats=True) for _ in range(10)]
+    fp32_ms = statistics.median(s.render_ms for s in fp32_st)
+    # the same frame in the fixed tile order (HR_FLAG_FIXED_TILE_ORDER: no
+    # heavy tiles first; the schedule is left as it is)
+    dfix = hr.render_desc(w.camera.pack(), w.lights, spp, w.k_depth, w.sample_seed, w.precision,
+                          hr.HR_FLAG_FIXED_TILE_ORDER)
+    fixed_ms = statistics.median(hr.hr_render(ctx, asset, dfix, img, stats=True).render_ms
+                                 for _ in range(10))
+    tile_schedule = {"heavy_tiles": int(fp32_st[-1].heavy_tiles), "frame_ms_warm": fp32_ms,
+                     "frame_ms_fixed_order_warm": fixed_ms,
+                     "note": "warm frames alone: the previous frame's heaviest warp tiles traced "
+                             "first, four rays per warp, against the fixed tile order; the images "
+                             "are identical"}
     # the same frame with dual-scattering light paths (a shadow ray per hit and
     # light, HR_FLAG_SHADOWS), outside the timed region
     dsh = hr.render_desc(w.camera.pack(), w.lights, spp, w.k_depth, w.sample_seed, w.precision,
@@ -857,7 +868,7 @@ def main():
                                                         elapsed),
             "traced_msamples_per_s_frame": cst.traced_samples / (render_avg * 1e-3) / 1e6,
             "frame_ms": render_avg, "frame_ms_fp32_warm": fp32_ms, "frame_ms_fp16_warm": fp16_ms,
-            "frame_ms_shadow_rays": shadow_ms, "frame_tail": tail,
+            "frame_ms_shadow_rays": shadow_ms, "frame_tail": tail, "tile_schedule": tile_schedule,
             "active_prims": int(st.n_active_prims),
             "eth_prims": int(st.n_eth_prims), "stack_overflows": int(st.stack_overflows),
             "roofline": roof, "roofline_other": other,
